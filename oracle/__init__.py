@@ -1,0 +1,204 @@
+"""FP64 CPU oracle for Wavelet Transparency (paper §2), reached through ctypes.
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library and its binding) never imports this package, and this package
+imports nothing from the product.
+
+The C source (``wt_oracle.c``) is compiled on first use with gcc into
+``liboracle.so`` beside it; ``build()`` does the same eagerly.
+"""
+from __future__ import annotations
+
+import ctypes
+import fcntl
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wt_oracle.c")
+_HDR = os.path.join(_HERE, "wt_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+# reading flags (the oracle's own definitions; numerically equal to the library's)
+SELF_EXCLUDE = 1
+INTERP_LINEAR = 2
+RESOLVE_NORMALIZED = 4
+DEFAULT_FLAGS = SELF_EXCLUDE | INTERP_LINEAR | RESOLVE_NORMALIZED
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (plain C11, -O2, no OpenMP: single-threaded)."""
+    lock = _LIB + ".lock"
+    with open(lock, "w") as lf:
+        fcntl.flock(lf, fcntl.LOCK_EX)
+        stale = not os.path.exists(_LIB) or any(
+            os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+        if force or stale:
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    i64, i32, u32 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
+    lib.wto_psi.argtypes = [i32, i32, ctypes.c_double]
+    lib.wto_psi.restype = ctypes.c_double
+    lib.wto_Psi.argtypes = [i32, i32, ctypes.c_double]
+    lib.wto_Psi.restype = ctypes.c_double
+    lib.wto_build.argtypes = [i64, P, P, P, i64, i32, P]
+    lib.wto_build_binned.argtypes = [i64, P, P, P, i64, i32, P]
+    lib.wto_bin_values.argtypes = [P, i32, P]
+    lib.wto_bin_values.restype = None
+    lib.wto_recon.argtypes = [P, i32, ctypes.c_double, i32]
+    lib.wto_recon.restype = ctypes.c_double
+    lib.wto_fragment_absorbance.argtypes = [i64, P, P, P, i64, i32, u32, P, P]
+    lib.wto_absorbance_at.argtypes = [i64, P, P, i64, i32, u32, P, P]
+    lib.wto_resolve.argtypes = [i64, P, P, P, P, P, P, i64, i32, u32, P, P, P, P, P]
+    lib.wto_abuffer.argtypes = [i64, P, P, P, P, P, P, i64, P, P, P]
+    lib.wto_grad.argtypes = [i64, P, P, P, P, P, P, i64, i32, u32, P, P, P, P, P]
+    for f in ("wto_build", "wto_build_binned", "wto_fragment_absorbance", "wto_absorbance_at",
+              "wto_resolve", "wto_abuffer", "wto_grad"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _u32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.uint32)
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float32)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+
+
+def _check(st, name):
+    if st != 0:
+        raise ValueError(f"oracle {name} failed with status {st}")
+
+
+def psi(n: int, k: int, x: float) -> float:
+    return _load().wto_psi(n, k, x)
+
+
+def Psi(n: int, k: int, x: float) -> float:
+    return _load().wto_Psi(n, k, x)
+
+
+def build_coeffs(pixel, z, alpha, P: int, J: int) -> np.ndarray:
+    """Closed-form coefficients (§2.3.1) -> float64 [P, 2^J]."""
+    pixel, z, alpha = _u32(pixel), _f32(z), _f32(alpha)
+    out = np.zeros((P, 1 << J), np.float64)
+    _check(_load().wto_build(len(z), _ptr(pixel), _ptr(z), _ptr(alpha), P, J, _ptr(out)), "build")
+    return out
+
+
+def build_coeffs_binned(pixel, z, alpha, P: int, J: int) -> np.ndarray:
+    """Independent construction: exact bin averages + Haar analysis."""
+    pixel, z, alpha = _u32(pixel), _f32(z), _f32(alpha)
+    out = np.zeros((P, 1 << J), np.float64)
+    _check(_load().wto_build_binned(len(z), _ptr(pixel), _ptr(z), _ptr(alpha), P, J, _ptr(out)),
+           "build_binned")
+    return out
+
+
+def bin_values(coeff_row, J: int) -> np.ndarray:
+    c = _f64(coeff_row)
+    out = np.zeros(1 << J, np.float64)
+    _load().wto_bin_values(_ptr(c), J, _ptr(out))
+    return out
+
+
+def recon(abar, J: int, x: float, linear: bool = True) -> float:
+    a = _f64(abar)
+    return _load().wto_recon(_ptr(a), J, float(x), int(linear))
+
+
+def fragment_absorbance(pixel, z, alpha, P, J, coeff, flags=DEFAULT_FLAGS) -> np.ndarray:
+    pixel, z, alpha, coeff = _u32(pixel), _f32(z), _f32(alpha), _f64(coeff)
+    out = np.zeros(len(z), np.float64)
+    _check(_load().wto_fragment_absorbance(len(z), _ptr(pixel), _ptr(z), _ptr(alpha), P, J,
+                                           flags, _ptr(coeff), _ptr(out)), "fragment_absorbance")
+    return out
+
+
+def absorbance_at(pixel, z, P, J, coeff, flags=DEFAULT_FLAGS) -> np.ndarray:
+    pixel, z, coeff = _u32(pixel), _f32(z), _f64(coeff)
+    out = np.zeros(len(z), np.float64)
+    _check(_load().wto_absorbance_at(len(z), _ptr(pixel), _ptr(z), P, J, flags, _ptr(coeff),
+                                     _ptr(out)), "absorbance_at")
+    return out
+
+
+def resolve(pixel, z, alpha, rgb, P, J, coeff, flags=DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5),
+            bg_img=None):
+    """Resolve + composite.  rgb is [n,3] or a tuple (r, g, b).
+
+    Returns (out [P,4], accum [P,6] = {R',G',B',W',S,Amin})."""
+    pixel, z, alpha, coeff = _u32(pixel), _f32(z), _f32(alpha), _f64(coeff)
+    r, g, b = _split_rgb(rgb)
+    out = np.zeros((P, 4), np.float64)
+    acc = np.zeros((P, 6), np.float64)
+    bgv = _f64(bg)
+    _check(_load().wto_resolve(len(z), _ptr(pixel), _ptr(z), _ptr(alpha), _ptr(r), _ptr(g),
+                               _ptr(b), P, J, flags, _ptr(coeff), _ptr(bgv), _ptr(_f64(bg_img)),
+                               _ptr(acc), _ptr(out)), "resolve")
+    return out, acc
+
+
+def composite(pixel, z, alpha, rgb, P, J, flags=DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5), bg_img=None):
+    """Build + resolve + composite in one call -> out [P,4]."""
+    coeff = build_coeffs(pixel, z, alpha, P, J)
+    return resolve(pixel, z, alpha, rgb, P, J, coeff, flags, bg, bg_img)[0]
+
+
+def abuffer(pixel, z, alpha, rgb, P, bg=(0.5, 0.5, 0.5), bg_img=None) -> np.ndarray:
+    """Exact sorted front-to-back composite -> out [P,4]."""
+    pixel, z, alpha = _u32(pixel), _f32(z), _f32(alpha)
+    r, g, b = _split_rgb(rgb)
+    out = np.zeros((P, 4), np.float64)
+    _check(_load().wto_abuffer(len(z), _ptr(pixel), _ptr(z), _ptr(alpha), _ptr(r), _ptr(g),
+                               _ptr(b), P, _ptr(_f64(bg)), _ptr(_f64(bg_img)), _ptr(out)),
+           "abuffer")
+    return out
+
+
+def grad(pixel, z, alpha, rgb, P, J, gout, flags=DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5), bg_img=None):
+    """Analytic gradient of sum(gout * out) -> (d alpha [n], d rgb [n,3])."""
+    pixel, z, alpha = _u32(pixel), _f32(z), _f32(alpha)
+    r, g, b = _split_rgb(rgb)
+    n = len(z)
+    ga = np.zeros(n, np.float64)
+    gc = np.zeros((n, 3), np.float64)
+    go = _f64(gout).reshape(P, 4)
+    _check(_load().wto_grad(n, _ptr(pixel), _ptr(z), _ptr(alpha), _ptr(r), _ptr(g), _ptr(b), P,
+                            J, flags, _ptr(_f64(bg)), _ptr(_f64(bg_img)), _ptr(go), _ptr(ga),
+                            _ptr(gc)), "grad")
+    return ga, gc
+
+
+def _split_rgb(rgb):
+    if isinstance(rgb, (tuple, list)) and len(rgb) == 3:
+        return tuple(_f32(c) for c in rgb)
+    a = np.asarray(rgb, dtype=np.float32)
+    return _f32(a[:, 0]), _f32(a[:, 1]), _f32(a[:, 2])

@@ -1,0 +1,385 @@
+"""Pins for the FP64 oracle: each test ties the oracle to something other than
+itself -- a value the paper prints, a closed form worked out by hand, a
+textbook routine (numerical quadrature, the sorted 'over' composite, finite
+differences) or an invariant that a dropped term, a wrong sign, a wrong index
+or a transposed operand would break."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_frags(rng, n, P, alpha=(0.05, 0.6)):
+    pix = rng.integers(0, P, n).astype(np.uint32)
+    z = rng.random(n).astype(np.float32)
+    al = rng.uniform(alpha[0], alpha[1], n).astype(np.float32)
+    rgb = rng.random((n, 3)).astype(np.float32)
+    return pix, z, al, rgb
+
+
+def _a(alpha):
+    return -np.log1p(-np.asarray(alpha, np.float64))
+
+
+# ---------------------------------------------------------------- paper values
+
+def test_paper_plane_example_visibility():
+    """§1.2: a 25%-opaque plane at 1 m: v = 1 in front, 0.75 behind."""
+    g = json.load(open(os.path.join(GOLD, "plane_25pct.json")))
+    z0 = (g["plane_depth_m"] - g["near_m"]) / (g["far_m"] - g["near_m"])
+    for J in range(1, 11):
+        C = 1 << J
+        coeff = o.build_coeffs([0], [z0], [g["alpha"]], 1, J)
+        abar = o.bin_values(coeff[0], J)
+        # depths whose interpolation uses only bins fully behind the plane
+        m0 = int(z0 * C)
+        behind = np.linspace((m0 + 0.5) / C, 1 - 1e-9, 7)
+        front = np.linspace(0, max(0.0, (m0 - 0.5) / C), 7)
+        for x in behind:
+            assert math.exp(-o.recon(abar, J, x)) == pytest.approx(g["v_behind"], abs=1e-14)
+        for x in front:
+            assert math.exp(-o.recon(abar, J, x)) == pytest.approx(g["v_in_front"], abs=1e-14)
+
+
+@pytest.mark.parametrize("normalized", [True, False])
+def test_paper_plane_example_composite(normalized):
+    """The same plane composited over bg: 0.25 c + 0.75 bg for every J."""
+    g = json.load(open(os.path.join(GOLD, "plane_25pct.json")))
+    c = np.array([[0.9, 0.2, 0.4]], np.float32)
+    flags = o.SELF_EXCLUDE | o.INTERP_LINEAR | (o.RESOLVE_NORMALIZED if normalized else 0)
+    for J in range(1, 9):
+        out = o.composite([0], [0.5], [g["alpha"]], c, 1, J, flags=flags, bg=(0.5, 0.5, 0.5))
+        exp_rgb = g["alpha"] * c[0].astype(np.float64) + g["v_behind"] * 0.5
+        np.testing.assert_allclose(out[0, :3], exp_rgb, atol=1e-7)
+        assert out[0, 3] == pytest.approx(1 - g["v_behind"], abs=1e-7)
+
+
+def test_rank_storage_counts():
+    """§2.1: rank N -> 2^(N+1) coefficients per channel (J = N + 1 levels)."""
+    g = json.load(open(os.path.join(GOLD, "rank_storage.json")))
+    for case in g["cases"]:
+        J = case["rank"] + 1
+        coeff = o.build_coeffs([0], [0.3], [0.5], 1, J)
+        assert coeff.shape[1] == case["coeffs_per_channel"]
+        assert case["channels"] * coeff.shape[1] == case["total_coeffs"]
+
+
+# ---------------------------------------------------------------- basis
+
+def test_Psi_is_antiderivative_of_psi():
+    """Psi_{n,k}(x) = integral_0^x psi_{n,k} (midpoint quadrature), and >= 0."""
+    for n in range(0, 5):
+        for k in range(0, 1 << n):
+            xs = np.linspace(0, 1, 4097)
+            h = 1.0 / (1 << 16)
+            mids = (np.arange(1 << 16) + 0.5) * h
+            vals = np.array([o.psi(n, k, x) for x in mids])
+            cum = np.concatenate([[0.0], np.cumsum(vals) * h])
+            for x in xs[::64]:
+                q = cum[int(round(x * (1 << 16)))]
+                assert o.Psi(n, k, x) == pytest.approx(q, abs=1e-12)
+                assert o.Psi(n, k, x) >= 0.0
+
+
+def test_haar_basis_orthonormal():
+    """<psi_{n,k}, psi_{n',k'}> = delta, <psi, phi_00> = 0 (midpoint quadrature)."""
+    J = 4
+    M = 1 << 10
+    mids = (np.arange(M) + 0.5) / M
+    basis = [np.ones(M)]
+    for n in range(J):
+        for k in range(1 << n):
+            basis.append(np.array([o.psi(n, k, x) for x in mids]))
+    B = np.stack(basis)
+    G = B @ B.T / M
+    np.testing.assert_allclose(G, np.eye(1 << J), atol=1e-12)
+
+
+# ---------------------------------------------------------------- coefficients
+
+def test_closed_form_matches_quadrature():
+    """chi_00 = int A, X_{n,k} = int A psi_{n,k}, by brute-force quadrature of
+    the step function A(x) = sum a_i theta(x - z_i) (§2.2)."""
+    rng = np.random.default_rng(1)
+    J, M = 4, 1 << 18
+    pix, z, al, _ = _rand_frags(rng, 9, 1)
+    coeff = o.build_coeffs(pix, z, al, 1, J)[0]
+    mids = (np.arange(M) + 0.5) / M
+    A = np.zeros(M)
+    for zi, ai in zip(z.astype(np.float64), _a(al)):
+        A += ai * (mids >= zi)
+    ref = [A.mean()]
+    for n in range(J):
+        for k in range(1 << n):
+            u = mids * (1 << n) - k
+            psi = np.where((u >= 0) & (u < 0.5), 1.0, np.where((u >= 0.5) & (u < 1), -1.0, 0.0))
+            ref.append((A * psi * 2 ** (n / 2)).mean())
+    np.testing.assert_allclose(coeff, ref, atol=9 * 1.0 / M)
+
+
+@pytest.mark.parametrize("J", [1, 3, 4, 5, 7])
+def test_closed_form_matches_binned_construction(J):
+    rng = np.random.default_rng(J)
+    pix, z, al, _ = _rand_frags(rng, 700, 13)
+    c1 = o.build_coeffs(pix, z, al, 13, J)
+    c2 = o.build_coeffs_binned(pix, z, al, 13, J)
+    np.testing.assert_allclose(c1, c2, rtol=1e-12, atol=1e-12 * np.abs(c1).max())
+
+
+def test_sign_property():
+    """§2.3.1: chi_00 >= 0 and every X_{n,k} <= 0."""
+    rng = np.random.default_rng(2)
+    pix, z, al, _ = _rand_frags(rng, 3000, 50, alpha=(0.0, 0.99))
+    c = o.build_coeffs(pix, z, al, 50, 5)
+    assert (c[:, 0] >= 0).all() and (c[:, 1:] <= 0).all()
+
+
+def test_log_many_coefficients_per_fragment():
+    """§2.3.1: one fragment touches J+1 coefficients (fewer on a dyadic edge)."""
+    J = 5
+    for zi in [0.013, 0.2, 0.377, 0.61, 0.99]:
+        c = o.build_coeffs([0], [zi], [0.4], 1, J)[0]
+        assert np.count_nonzero(c) == J + 1
+        for n in range(J):
+            nz = [k for k in range(1 << n) if c[(1 << n) + k] != 0]
+            assert nz == [int(np.float32(zi) * (1 << n))]
+    c = o.build_coeffs([0], [0.5], [0.4], 1, J)[0]
+    # Psi_{0,0}(1/2) = 1/2 and Psi_{n>=1,k}(1/2) = 0
+    assert np.count_nonzero(c) == 2
+    assert c[1] == pytest.approx(-0.5 * _a(0.4))
+
+
+def test_single_fragment_closed_form_values():
+    """Hand-evaluated: a at z = 0.3, J = 2: chi = a*0.7; X00 = -a*0.3;
+    X10 = -a*2^-1/2*(1-0.6); X11 = 0."""
+    a = float(_a(np.float32(0.5)))
+    zf = float(np.float32(0.3))
+    c = o.build_coeffs([0], [0.3], [0.5], 1, 2)[0]
+    np.testing.assert_allclose(
+        c, [a * (1 - zf), -a * zf, -a * 2 ** -0.5 * (1 - 2 * zf), 0.0], rtol=1e-14, atol=1e-15)
+
+
+def test_permutation_invariance_and_linearity():
+    rng = np.random.default_rng(3)
+    pix, z, al, _ = _rand_frags(rng, 500, 7)
+    c = o.build_coeffs(pix, z, al, 7, 4)
+    perm = rng.permutation(500)
+    cp = o.build_coeffs(pix[perm], z[perm], al[perm], 7, 4)
+    np.testing.assert_allclose(c, cp, rtol=1e-12, atol=1e-13)
+    ca = o.build_coeffs(pix[:200], z[:200], al[:200], 7, 4)
+    cb = o.build_coeffs(pix[200:], z[200:], al[200:], 7, 4)
+    np.testing.assert_allclose(c, ca + cb, rtol=1e-12, atol=1e-13)
+
+
+def test_parseval_and_monotone_bins():
+    """Orthonormal synthesis: sum coeff^2 = mean(Abar^2); Abar non-decreasing."""
+    rng = np.random.default_rng(4)
+    pix, z, al, _ = _rand_frags(rng, 400, 5)
+    for J in (2, 4, 6):
+        c = o.build_coeffs(pix, z, al, 5, J)
+        for p in range(5):
+            ab = o.bin_values(c[p], J)
+            assert (c[p] ** 2).sum() == pytest.approx((ab ** 2).mean(), rel=1e-12)
+            assert (np.diff(ab) >= -1e-12).all()
+            xs = np.linspace(0, 1 - 1e-9, 301)
+            rec = [o.recon(ab, J, x) for x in xs]
+            assert (np.diff(rec) >= -1e-12).all()
+
+
+def test_bin_values_are_exact_bin_averages():
+    """Synthesis at bin centres gives C * integral of A over each bin
+    (midpoint quadrature of the step function)."""
+    rng = np.random.default_rng(5)
+    J, M = 4, 1 << 16
+    pix, z, al, _ = _rand_frags(rng, 12, 1)
+    ab = o.bin_values(o.build_coeffs(pix, z, al, 1, J)[0], J)
+    mids = (np.arange(M) + 0.5) / M
+    A = np.zeros(M)
+    for zi, ai in zip(z.astype(np.float64), _a(al)):
+        A += ai * (mids >= zi)
+    ref = A.reshape(1 << J, -1).mean(axis=1)
+    np.testing.assert_allclose(ab, ref, atol=12 * (1 << J) / M)
+
+
+# ---------------------------------------------------------------- reconstruction
+
+def test_interpolation_between_bin_centres_single_step():
+    """One step a at z in bin m with fraction f, INCLUDE (own step kept):
+    hand-derived lerp between bin centres of the bin values {0, a(1-f), a}:
+      f < 1/2: a (1-f)(f+1/2);  f >= 1/2: a (1 - 1.5 f + f^2);
+      constant a(1-f) in the outer half-bins."""
+    J = 3
+    C = 1 << J
+    for zi in [0.01, 0.05, 0.2, 0.33, 0.4375, 0.6, 0.9, 0.97]:
+        zf = float(np.float32(zi))
+        m = int(zf * C)
+        f = zf * C - m
+        a = float(_a(np.float32(0.3)))
+        ab = o.bin_values(o.build_coeffs([0], [zi], [0.3], 1, J)[0], J)
+        got = o.recon(ab, J, zf)
+        if (m == 0 and f < 0.5) or (m == C - 1 and f >= 0.5):
+            exp = a * (1 - f)
+        elif f < 0.5:
+            exp = a * (1 - f) * (f + 0.5)
+        else:
+            exp = a * (1 - 1.5 * f + f * f)
+        assert got == pytest.approx(exp, rel=1e-12)
+        assert o.recon(ab, J, zf, linear=False) == pytest.approx(a * (1 - f), rel=1e-12)
+
+
+def test_self_exclusion_alone_in_pixel():
+    """A lone fragment sees nothing in front of itself under SELF_EXCLUDE."""
+    for zi in [0.0, 0.1, 0.5, 0.77, 0.9999]:
+        c = o.build_coeffs([0], [zi], [0.7], 1, 4)
+        A = o.fragment_absorbance([0], [zi], [0.7], 1, 4, c, flags=o.DEFAULT_FLAGS)
+        assert abs(A[0]) < 1e-15
+
+
+def test_behind_all_bins_is_total_absorbance():
+    """§1.2/§2.2: beyond the last occupied bin's neighbour v = prod (1 - alpha_i)."""
+    rng = np.random.default_rng(6)
+    z = (rng.random(20) * 0.7).astype(np.float32)
+    al = rng.uniform(0.05, 0.5, 20).astype(np.float32)
+    pix = np.zeros(20, np.uint32)
+    for J in (2, 4, 6):
+        ab = o.bin_values(o.build_coeffs(pix, z, al, 1, J)[0], J)
+        v = math.exp(-o.recon(ab, J, 1 - 1e-9))
+        assert v == pytest.approx(np.prod(1 - al.astype(np.float64)), rel=1e-12)
+
+
+# ---------------------------------------------------------------- resolve / composite
+
+def test_abuffer_textbook_over_operator():
+    """Two fragments front to back: a1 c1 + (1-a1) a2 c2 + (1-a1)(1-a2) bg,
+    independent of the input order."""
+    c1, c2 = np.array([1.0, 0.0, 0.2]), np.array([0.0, 1.0, 0.6])
+    a1, a2 = 0.3, 0.6
+    a1f, a2f = float(np.float32(a1)), float(np.float32(a2))
+    exp = a1f * c1 + (1 - a1f) * a2f * c2 + (1 - a1f) * (1 - a2f) * 0.5
+    for order in ([0, 1], [1, 0]):
+        z = np.array([0.2, 0.7], np.float32)[order]
+        al = np.array([a1, a2], np.float32)[order]
+        rgb = np.stack([c1, c2]).astype(np.float32)[order]
+        out = o.abuffer([0, 0], z, al, rgb, 1)
+        np.testing.assert_allclose(out[0, :3], exp, atol=1e-7)
+        assert out[0, 3] == pytest.approx(1 - (1 - a1f) * (1 - a2f), abs=1e-12)
+
+
+@pytest.mark.parametrize("flags", [7, 3])
+def test_converges_to_abuffer_when_depths_separated(flags):
+    """With depths more than two bins apart the lerp at each fragment sees
+    every other step in full, so the wavelet composite equals the A-buffer."""
+    rng = np.random.default_rng(7)
+    P, k, J = 6, 9, 8
+    pix = np.repeat(np.arange(P), k).astype(np.uint32)
+    z = np.concatenate([rng.permutation(rng.choice(np.arange(3, 250, 3), k, replace=False)) /
+                        256.0 + rng.random(k) / 256.0 for _ in range(P)]).astype(np.float32)
+    al = rng.uniform(0.05, 0.7, P * k).astype(np.float32)
+    rgb = rng.random((P * k, 3)).astype(np.float32)
+    ref = o.abuffer(pix, z, al, rgb, P)
+    out = o.composite(pix, z, al, rgb, P, J, flags=flags)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+
+
+def test_include_self_does_not_converge():
+    rng = np.random.default_rng(8)
+    P, k, J = 4, 8, 10
+    pix = np.repeat(np.arange(P), k).astype(np.uint32)
+    z = rng.random(P * k).astype(np.float32)
+    al = rng.uniform(0.2, 0.7, P * k).astype(np.float32)
+    rgb = rng.random((P * k, 3)).astype(np.float32)
+    ref = o.abuffer(pix, z, al, rgb, P)
+    inc = o.composite(pix, z, al, rgb, P, J, flags=o.INTERP_LINEAR | o.RESOLVE_NORMALIZED)
+    assert np.abs(inc - ref).max() > 1e-3
+
+
+def test_convergence_in_J_random_depths():
+    """Error to the A-buffer shrinks as J grows (random, unseparated depths)."""
+    rng = np.random.default_rng(9)
+    P = 30
+    pix, z, al, rgb = _rand_frags(rng, 150, P)
+    ref = o.abuffer(pix, z, al, rgb, P)
+    errs = [np.abs(o.composite(pix, z, al, rgb, P, J) - ref).mean() for J in (2, 4, 6, 8, 10)]
+    assert errs[-1] < 2e-3 and errs[-1] < errs[0] / 10
+
+
+def test_empty_and_transparent_pixels_give_background():
+    bg_img = np.array([[0.1, 0.2, 0.3], [0.4, 0.5, 0.6], [0.7, 0.8, 0.9]])
+    pix = np.array([1, 1], np.uint32)
+    out = o.composite(pix, [0.2, 0.6], [0.0, 0.0], np.ones((2, 3), np.float32), 3, 4,
+                      bg_img=bg_img)
+    np.testing.assert_allclose(out[:, :3], bg_img, atol=0)
+    np.testing.assert_allclose(out[:, 3], 0.0, atol=0)
+
+
+def test_staircase_mode_reads_bin_average():
+    rng = np.random.default_rng(10)
+    pix, z, al, _ = _rand_frags(rng, 60, 3)
+    J = 4
+    c = o.build_coeffs(pix, z, al, 3, J)
+    A = o.fragment_absorbance(pix, z, al, 3, J, c, flags=0)
+    for i in range(60):
+        ab = o.bin_values(c[pix[i]], J)
+        assert A[i] == pytest.approx(ab[min(int(z[i] * 16), 15)], rel=1e-13)
+
+
+def test_clamping():
+    """alpha >= 1 is clamped to 1 - 2^-20 (a = 20 ln 2); alpha <= 0 gives no
+    step; depths outside [0,1) land in the end bins."""
+    c = o.build_coeffs([0], [0.25], [1.0], 1, 3)[0]
+    assert c[0] == pytest.approx(20 * math.log(2) * 0.75, rel=1e-12)
+    c = o.build_coeffs([0], [0.25], [-0.5], 1, 3)[0]
+    assert not c.any()
+    c_lo = o.build_coeffs([0], [-3.0], [0.5], 1, 3)[0]
+    c_0 = o.build_coeffs([0], [0.0], [0.5], 1, 3)[0]
+    np.testing.assert_array_equal(c_lo, c_0)
+    c_hi = o.build_coeffs([0], [7.0], [0.5], 1, 3)[0]
+    assert c_hi[0] == pytest.approx(_a(0.5) * 2 ** -24, rel=1e-6)
+
+
+def test_underflow_safe_normalised_resolve():
+    """A pixel whose nearest fragment already sees A ~ 400 (all steps packed in
+    one bin): the normalised colour is still the weighted mean, not bg."""
+    k = 900
+    z = (0.5 + np.arange(k) / k / 64).astype(np.float32)
+    al = np.full(k, 0.6, np.float32)
+    rgb = np.tile(np.array([[0.9, 0.1, 0.3]], np.float32), (k, 1))
+    out = o.composite(np.zeros(k, np.uint32), z, al, rgb, 1, 4)
+    np.testing.assert_allclose(out[0, :3], [0.9, 0.1, 0.3], atol=1e-12)
+
+
+# ---------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("flags", [7, 3, 6])
+def test_gradient_matches_finite_differences(flags):
+    rng = np.random.default_rng(11)
+    P, J = 3, 4
+    pix, z, al, rgb = _rand_frags(rng, 24, P, alpha=(0.05, 0.5))
+    bg = (0.3, 0.5, 0.7)
+    gout = rng.standard_normal((P, 4))
+    ga, gc = o.grad(pix, z, al, rgb, P, J, gout, flags=flags, bg=bg)
+
+    def loss(alpha_vec, rgb_mat):
+        # the oracle's float32 inputs: perturb in float64 space via ctypes-free route
+        return (o.composite(pix, z, alpha_vec, rgb_mat, P, J, flags=flags, bg=bg) * gout).sum()
+
+    # central differences on float32 inputs need h >> float32 ulp: use h = 2^-12
+    h = 2.0 ** -12
+    for i in range(0, 24, 3):
+        ap, am = al.copy(), al.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (loss(ap, rgb) - loss(am, rgb)) / (float(ap[i]) - float(am[i]))
+        assert ga[i] == pytest.approx(fd, rel=2e-3, abs=2e-5)
+        for ch in range(3):
+            cp, cm = rgb.copy(), rgb.copy()
+            cp[i, ch] += h
+            cm[i, ch] -= h
+            fd = (loss(al, cp) - loss(al, cm)) / (float(cp[i, ch]) - float(cm[i, ch]))
+            assert gc[i, ch] == pytest.approx(fd, rel=1e-6, abs=1e-9)
