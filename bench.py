@@ -1,0 +1,413 @@
+"""Benchmark: Wavelet OIT build + resolve (+ composite) on one GB300 per rank.
+
+One step = one pass of the hot path over one synthetic frame resident in
+HBM: every fragment's absorbance step is projected onto its pixel's Haar
+coefficients (stored in the coefficient buffer), the visibility is
+reconstructed at every fragment, and the weighted resolve is composited over
+the background.  Default workload: the 4K heavy-smoke frame
+(3840x2160, lognormal fragments per pixel mean 24 cap 1024, ~199M fragments,
+J = 5), FP32 coefficient storage, fused kernel wt_build_resolve.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the reference arm of this build) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fragments/s build+resolve & % HBM roofline; served p50/p99 frame latency"
+UNIT = "fragments/s"
+WORKLOADS = {
+    "heavy4k": "4K heavy smoke: 3840x2160, lognormal fragments/pixel (mean 24, cap 1024), "
+               "5-slab depth mixture + 10% uniform, alpha U[.01,.4], J=5",
+    "smoke1080": "1080p smoke: 1920x1080, 30% smoke pixels lognormal (mean 32, cap 512), "
+                 "70% surface pixels U{0..4}, J=4",
+    "plain64": "64x64, Poisson(4) capped at 16, alpha U[.05,.6], J=4",
+}
+DTYPE_NAME = {0: "f32", 1: "bf16", 2: "f16"}
+DTYPE_BYTES = {0: 4, 1: 2, 2: 2}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2201_00094_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str, dtype: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rows = json.load(f)
+    except Exception:
+        return None
+    for r in rows:
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("dtype") == dtype:
+            if r.get("source_hash") == kernel_source_hash():
+                return r.get("dram_bytes_per_launch")
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(t)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+
+def sample_tiles(fr, ntiles_sample: int, seed: int):
+    """A seeded set of whole tiles and their fragments, renumbered to local
+    pixel ids (tiles are independent, so this is an exact sub-problem)."""
+    rng = np.random.default_rng(seed)
+    tiles = np.sort(rng.choice(fr.ntiles, size=min(ntiles_sample, fr.ntiles), replace=False))
+    off = fr.tile_offsets.cpu().numpy()
+    idx = np.concatenate([np.arange(off[t], off[t + 1]) for t in tiles]).astype(np.int64)
+    idx_t = torch.from_numpy(idx).to(fr.pixel.device)
+    pix = fr.pixel[idx_t].cpu().numpy().astype(np.int64)
+    uniq, local = np.unique(pix, return_inverse=True)
+    cols = {k: getattr(fr, k)[idx_t].cpu().numpy() for k in ("z", "alpha", "r", "g", "b")}
+    return tiles, uniq, local.astype(np.uint32), cols
+
+
+def run_oracle_sample(fr, ntiles_sample, seed):
+    import oracle
+    _, uniq, local, c = sample_tiles(fr, ntiles_sample, seed)
+    t0 = time.perf_counter()
+    coeff = oracle.build_coeffs(local, c["z"], c["alpha"], len(uniq), fr.J)
+    out, _ = oracle.resolve(local, c["z"], c["alpha"], (c["r"], c["g"], c["b"]), len(uniq), fr.J,
+                            coeff, bg=fr.bg)
+    dt = time.perf_counter() - t0
+    return dict(n=len(local), pixels=len(uniq), seconds=dt, out=out, pixel_ids=uniq)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_wt(args):
+    import paper_2201_00094_gb300 as wt
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+    # weak scaling: every rank renders its own independent frame
+    fr = synth.make(args.workload, seed=args.seed + rank, device=dev)
+    torch.cuda.synchronize()
+    n, P, J = fr.n, fr.P, fr.J
+    dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[args.dtype]
+    C = 1 << J
+    frags = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+    stream = torch.cuda.current_stream()
+
+    def buffers(dtype):
+        return (torch.empty(P, C, device=dev, dtype=wt.coeff_torch_dtype(dtype)),
+                torch.empty(P, 4, device=dev))
+
+    coeff, out = buffers(dt)
+    desc = wt.make_desc(fr.width, fr.height, J, dt)
+
+    def step_fused(d=desc, c=coeff, o=out):
+        wt.wt_build_resolve(d, frags, o, c, None, bg=fr.bg, stream=stream)
+
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        step_fused()
+    torch.cuda.synchronize()
+    assert wt.wt_get_error(stream) == 0
+    barrier(world)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        t_start.record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            step_fused()
+            ev[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    frags_all = sum_over_ranks(float(n), world)
+    value = frags_all * K / (total_ms / 1e3)
+
+    s = DTYPE_BYTES[dt]
+    alg_bytes = n * 24 + P * C * s + 16 * P  # fused: fragments once, coefficients + RGBA written
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    traffic = profiled_traffic("k_fused", args.workload, args.dtype)
+
+    # ---- variants (not part of `value`): two-pass path and 16-bit storage
+    variants = {}
+    if not args.no_variants:
+        for name, d2 in (("f32", wt.F32), ("bf16", wt.BF16), ("f16", wt.F16)):
+            dsc = wt.make_desc(fr.width, fr.height, J, d2)
+            c2, o2 = buffers(d2)
+            accum_bytes = n * 36 + 2 * P * C * DTYPE_BYTES[d2] + 16 * P
+
+            def two_pass(dsc=dsc, c2=c2, o2=o2):
+                wt.wt_build(dsc, frags, c2, None, stream=stream)
+                wt.wt_resolve_composite(dsc, frags, c2, None, o2, bg=fr.bg, stream=stream)
+
+            def fused(dsc=dsc, c2=c2, o2=o2):
+                wt.wt_build_resolve(dsc, frags, o2, c2, None, bg=fr.bg, stream=stream)
+
+            res = {}
+            for label, fn, byts in (("fused", fused, n * 24 + P * C * DTYPE_BYTES[d2] + 16 * P),
+                                    ("two_pass", two_pass, accum_bytes)):
+                for _ in range(3):
+                    fn()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(3, min(K, 20))
+                a.record(stream)
+                for _ in range(reps):
+                    fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / reps
+                res[label] = {"ms": round(ms, 4), "fragments_per_s": n / (ms / 1e3),
+                              "alg_bytes": byts, "alg_GBps": round(byts / (ms / 1e3) / 1e9, 1)}
+            variants[name] = res
+            del c2, o2
+
+    # ---- end to end through the C ABI from pinned host buffers
+    host = {k: getattr(fr, k).cpu().pin_memory() for k in ("pixel", "z", "alpha", "r", "g", "b",
+                                                             "tile_offsets")}
+    out_host = torch.empty(P, 4, pin_memory=True)
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = out_host.numel() * 4
+    dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    frags_e2e = wt.make_frags(dev_bufs["pixel"], dev_bufs["z"], dev_bufs["alpha"],
+                              dev_bufs["tile_offsets"], dev_bufs["r"], dev_bufs["g"], dev_bufs["b"])
+
+    def step_e2e():
+        for k, v in host.items():
+            dev_bufs[k].copy_(v, non_blocking=True)
+        wt.wt_build_resolve(desc, frags_e2e, out, coeff, None, bg=fr.bg, stream=stream)
+        out_host.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    Ke = max(3, min(K, 10))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    a.record(stream)
+    for _ in range(Ke):
+        step_e2e()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / Ke, world)
+    e2e_value = frags_all / (e2e_ms / 1e3)
+    del dev_bufs
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = run_oracle_sample(fr, args.cpu_tiles, seed=1234)
+        got = out.cpu().numpy()[res["pixel_ids"]]
+        cpu = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_tiles} seeded random 16x16 tiles of the same frame "
+                         f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
+                         f"composite, FP64, single thread, {res['seconds']:.1f} s",
+               "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                       "fragments_per_gpu": n, "pixels": P, "J": J,
+                       "coeff_storage": args.dtype, "path": "wt_build_resolve (fused kernel)",
+                       "l2": f"inputs larger than L2 ({n * 24 / 1e9:.1f} GB of fragments)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                         "traffic": traffic, "kernel": "k_fused",
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": round(launch_ms, 4),
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
+            "gpu_launches": K,
+            "clocks": clk.summary(),
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local) if torch.cuda.is_available() else torch.device("cpu")
+    fr = synth.make(args.workload, seed=args.seed, device=dev)
+    K, W = args.steps, args.warmup
+    # size each step's sample so the whole run stays near --ref-seconds
+    probe = run_oracle_sample(fr, 1, seed=99_999)
+    per_tile = max(probe["seconds"], 1e-3)
+    tiles = args.ref_tiles or max(1, int(args.ref_seconds / (K + W) / per_tile))
+    for w in range(W):
+        run_oracle_sample(fr, tiles, seed=10_000 + w)
+    tot_n, tot_s = 0, 0.0
+    for k in range(K):
+        r = run_oracle_sample(fr, tiles, seed=k)
+        tot_n += r["n"]
+        tot_s += r["seconds"]
+    value = tot_n / tot_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": tot_s / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                   "fragments_per_gpu": fr.n, "pixels": fr.P, "J": fr.J,
+                   "coeff_storage": "f64", "path": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step {tiles} seeded random 16x16 tiles of the frame, "
+                                   "build + resolve + composite, FP64, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="wt", choices=["wt", "reference"])
+    ap.add_argument("--workload", default="heavy4k", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-tiles", type=int, default=96)
+    ap.add_argument("--ref-tiles", type=int, default=0, help="tiles per step (0: sized by time)")
+    ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_wt(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * wt.h -- C ABI of the GB300 Wavelet OIT library (libwt.so).
+ *
+ * The library implements the hot path of "Wavelet Transparency"
+ * (Aizenshtein, Smal & McGuire, 2021) as hand-written CUDA for sm_103a:
+ *
+ *   build    (§2.1 step 2, §2.3.1)  project every fragment's absorbance step
+ *            a = -ln(1 - alpha) at normalised depth z onto a per-pixel Haar
+ *            basis of C = 2^J coefficients;
+ *   resolve  (§2.1 step 3, §2.2, §2.3.2)  reconstruct A(z) at each fragment,
+ *            v = exp(-A), and accumulate the order-independent weighted colour;
+ *   composite (§2.1 step 4)  composite the accumulation over the background.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller (for example
+ *   torch tensors).  The library never allocates, frees or retains them.
+ * - Every call is asynchronous on the given stream (NULL = legacy default
+ *   stream) and returns after the launch.  Argument errors are detected on the
+ *   host and returned synchronously; nothing is launched in that case.
+ * - Data errors (a fragment whose pixel id is >= width*height or lies outside
+ *   the tile it is filed under, NaN z or alpha, a decreasing tile_offsets
+ *   pair) are never fatal: the fragment (or tile range) is skipped and counted
+ *   in a per-device error word that wt_get_error() reads and clears.  No kernel
+ *   traps, asserts or spins.
+ * - Pixel id = y * width + x.  Coefficients are pixel-major,
+ *   coeff[p * C + j], in heap order: j = 0 holds chi_00, j = 2^n + k holds
+ *   X_{n,k} for level n = 0..J-1 and shift k = 0..2^n-1 (§2.3).
+ * - Depth is normalised to [0, 1) (the per-pixel bounds of §2.1 step 1 are
+ *   applied by the caller); z is clamped to [0, 1 - 2^-24] and alpha to
+ *   [0, 1 - 2^-20] before use.
+ * - Float pointers must be 16-byte aligned.
+ */
+#ifndef WT_H
+#define WT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so that the header needs no CUDA
+ * include. */
+typedef struct CUstream_st *wt_stream;
+
+typedef enum wt_status {
+    WT_OK = 0,
+    WT_ERR_ARG = 1,         /* bad argument: NULL, size out of range, misaligned */
+    WT_ERR_UNSUPPORTED = 2, /* valid but not supported (J > 5, flag combination) */
+    WT_ERR_INPUT = 3,       /* reported by wt_get_error when fragments were rejected */
+    WT_ERR_TIMEOUT = 4,     /* a bounded wait ran out (serving) */
+    WT_ERR_CUDA = 5,        /* a CUDA runtime call failed (launch error, bad device) */
+    WT_ERR_NOMEM = 6,       /* a request exceeds a memory cap (serving) */
+    WT_ERR_BUSY = 7         /* no free slot (serving) */
+} wt_status;
+
+/* Storage type of the coefficient buffer; accumulation is always FP32. */
+typedef enum wt_dtype { WT_F32 = 0, WT_BF16 = 1, WT_F16 = 2 } wt_dtype;
+
+/* Reading flags.  The default (WT_DEFAULT_FLAGS) is the reading under which
+ * the method converges to the exact sorted composite as J grows. */
+enum {
+    /* Visibility at a fragment excludes the fragment's own step: v is the
+     * transmittance in front of the interface (§1.2: v = 1 up to the plane,
+     * 0.75 beyond it). */
+    WT_SELF_EXCLUDE = 1u,
+    /* Reconstruct A(z) by linear interpolation between the bin centres
+     * (m + 1/2)/C, constant outside [c_0, c_{C-1}] (§2.3.2); off = staircase. */
+    WT_INTERP_LINEAR = 2u,
+    /* Normalised weighted resolve rgb = (R/W)(1 - T) + bg T; off = the literal
+     * compositing sum of §2.2, rgb = sum c_i alpha_i v(z_i) + bg T. */
+    WT_RESOLVE_NORMALIZED = 4u,
+    /* wt_build / wt_resolve add into coeff / accum instead of overwriting
+     * (several draw batches of one frame). */
+    WT_ACCUMULATE = 8u
+};
+#define WT_DEFAULT_FLAGS (WT_SELF_EXCLUDE | WT_INTERP_LINEAR | WT_RESOLVE_NORMALIZED)
+
+/* Frame descriptor. */
+typedef struct wt_desc {
+    int32_t width, height;  /* image size in pixels, each >= 1, width*height < 2^31 */
+    int32_t tile_w, tile_h; /* screen tile that groups the fragment stream;
+                               1 <= tile_w * tile_h <= 256; tiles are row-major,
+                               ntiles = ceil(width/tile_w) * ceil(height/tile_h) */
+    int32_t J;              /* Haar levels, 1..5; C = 2^J coefficients per pixel.
+                               The paper's rank N is J - 1 (Wavelet3: J = 4) */
+    int32_t coeff_dtype;    /* wt_dtype */
+    uint32_t flags;         /* WT_* reading flags */
+    int32_t reserved;       /* must be 0 */
+} wt_desc;
+
+/* Fragment stream, structure of arrays, device memory.  Fragments are grouped
+ * by tile: tile t owns [tile_offsets[t], tile_offsets[t+1]).  The order inside
+ * a tile is arbitrary (the method is order independent). */
+typedef struct wt_frags {
+    int64_t n;                   /* number of fragments, >= 0 */
+    const uint32_t *pixel;       /* [n] pixel id y*width + x */
+    const float *z;              /* [n] normalised depth */
+    const float *alpha;          /* [n] opacity */
+    const float *r, *g, *b;      /* [n] surface colour (not premultiplied);
+                                    may be NULL for wt_build */
+    const int64_t *tile_offsets; /* [ntiles + 1], non-decreasing, last = n */
+} wt_frags;
+
+/* Library version string (static storage). */
+const char *wt_version(void);
+
+/* Human-readable name of a status (static storage). */
+const char *wt_status_string(wt_status s);
+
+/* Bytes of the coefficient buffer: width*height * 2^J * sizeof(dtype);
+ * 0 if the descriptor is invalid. */
+size_t wt_coeff_bytes(const wt_desc *desc);
+
+/* Number of tiles of the descriptor (the length of tile_offsets minus one);
+ * 0 if the descriptor is invalid. */
+int64_t wt_num_tiles(const wt_desc *desc);
+
+/*
+ * wt_build -- §2.1 step 2 with §2.3.1 ("Coefficients").
+ * For every pixel p computes, in FP32, the closed-form Haar projection of
+ * A_p(z) = sum_i a_i theta(z - z_i) (§2.2):
+ *     chi_00 = sum a_i (1 - z_i),   X_{n,k} = -sum a_i Psi_{n,k}(z_i),
+ * with Psi_{n,k} the tent antiderivative of psi_{n,k}, and stores it once in
+ * coeff_dtype (round to nearest even).
+ *   coeff [P * C] of coeff_dtype, written (or added to under WT_ACCUMULATE);
+ *         pixels without fragments get zeros.
+ *   zmin  [P] float, nullable.  The nearest clamped depth of a fragment with
+ *         alpha > 0 (+inf if none), i.e. the near half of the tight per-pixel
+ *         depth bounds of §2.1 step 1; under WT_ACCUMULATE the minimum with
+ *         the stored value.  wt_resolve uses it to keep the normalised
+ *         resolve free of FP32 underflow in very deep pixels.
+ * frags->r, g, b are not read.
+ */
+wt_status wt_build(const wt_desc *desc, const wt_frags *frags, void *coeff, float *zmin,
+                   wt_stream stream);
+
+/*
+ * wt_resolve -- §2.1 step 3 with §2.2 and §2.3.2 ("Interpolation").
+ * For every fragment: A_i = reconstruction of the pixel's coefficients at z_i
+ * (minus the fragment's own step under WT_SELF_EXCLUDE), v_i = exp(-A_i),
+ * w_i = alpha_i v_i; per pixel accumulates R,G,B = sum c_i w_i, W = sum w_i
+ * and S = sum a_i.
+ *   coeff [P * C] as written by wt_build (same desc).
+ *   zmin  [P] from wt_build, nullable.  Under WT_RESOLVE_NORMALIZED and with
+ *         zmin given, R, G, B and W of a pixel are all multiplied by the same
+ *         positive factor exp(m_p) (m_p fixed by coeff and zmin), so only the
+ *         ratios R/W, G/W, B/W are meaningful; without zmin m_p = 0.  In the
+ *         literal mode m_p = 0 always.
+ *   accum [P * 5] float {R, G, B, W, S} per pixel, written (or added to under
+ *         WT_ACCUMULATE: batches of one frame share m_p).
+ */
+wt_status wt_resolve(const wt_desc *desc, const wt_frags *frags, const void *coeff,
+                     const float *zmin, float *accum, wt_stream stream);
+
+/*
+ * wt_composite -- §2.1 step 4 (composite over the opaque background).
+ * T = exp(-S).  WT_RESOLVE_NORMALIZED: rgb = (R/W)(1 - T) + bg T, or bg where
+ * W = 0.  Literal: rgb = R + bg T.  In both: out.a = 1 - T.
+ *   accum  [P * 5] from wt_resolve.
+ *   bg_img [P * 3] float background image, nullable (then bg is used).
+ *   bg     host pointer to 3 floats, used when bg_img is NULL.
+ *   out    [P * 4] float RGBA.
+ */
+wt_status wt_composite(const wt_desc *desc, const float *accum, const float *bg_img,
+                       const float bg[3], float *out, wt_stream stream);
+
+/* wt_resolve followed by wt_composite in one kernel (no accum buffer). */
+wt_status wt_resolve_composite(const wt_desc *desc, const wt_frags *frags, const void *coeff,
+                               const float *zmin, const float *bg_img, const float bg[3],
+                               float *out, wt_stream stream);
+
+/*
+ * wt_build_resolve -- steps 2, 3 and 4 of §2.1 fused per screen tile: the
+ * tile's coefficients are built in shared memory, rounded to coeff_dtype,
+ * reconstructed and used for the resolve without a round trip through device
+ * memory.  The result equals wt_build + wt_resolve_composite with the same
+ * desc up to FP32 summation order.
+ *   coeff [P * C] nullable: if given, the coefficients are also stored.
+ *   zmin  [P] nullable: if given, the depth bound is also stored.
+ *   out   [P * 4] float RGBA.
+ * WT_ACCUMULATE is not supported here (WT_ERR_UNSUPPORTED).
+ */
+wt_status wt_build_resolve(const wt_desc *desc, const wt_frags *frags, void *coeff, float *zmin,
+                           const float *bg_img, const float bg[3], float *out, wt_stream stream);
+
+/*
+ * wt_absorbance -- the evaluation half of §2.3 ("... a logarithmic number of
+ * coefficients ... Same applies during evaluation"): A(z) of pixel[q] at depth
+ * z[q] for q queries, reading J+1 coefficients per bin.  With alpha non-NULL
+ * and WT_SELF_EXCLUDE set, query q is treated as a fragment of that pixel and
+ * its own step alpha[q] is removed, exactly as in wt_resolve.
+ *   pixel [q], z [q], alpha [q] (nullable) device arrays; A_out [q] float.
+ *   Queries with a bad pixel id or NaN depth return NaN and are counted.
+ */
+wt_status wt_absorbance(const wt_desc *desc, const void *coeff, int64_t q, const uint32_t *pixel,
+                        const float *z, const float *alpha, float *A_out, wt_stream stream);
+
+/*
+ * wt_get_error -- synchronises `stream`, then returns in *bad_count the
+ * number of fragments (or queries, or tile ranges) rejected by any call on the
+ * current device since the previous wt_get_error, and clears the count.
+ * Returns WT_ERR_INPUT if the count was non-zero, WT_OK otherwise.
+ */
+wt_status wt_get_error(wt_stream stream, int64_t *bad_count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WT_H */

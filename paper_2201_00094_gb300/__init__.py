@@ -1,0 +1,230 @@
+"""Python binding of libwt.so: GB300 Wavelet OIT (Aizenshtein, Smal & McGuire,
+"Wavelet Transparency", 2021).
+
+Argument marshalling only.  Every step of the method runs in the CUDA kernels
+of libwt.so (built in-tree by ``build_lib.build()``); nothing here computes a
+result and there is no CPU fallback.  If the library is missing, the first
+call raises.
+
+Tensors are torch CUDA tensors (device memory and streams only).  Calls are
+asynchronous on ``stream`` (default: torch's current stream).  The names
+follow the C ABI in include/wt.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+__all__ = [
+    "F32", "BF16", "F16", "SELF_EXCLUDE", "INTERP_LINEAR", "RESOLVE_NORMALIZED", "ACCUMULATE",
+    "DEFAULT_FLAGS", "WtDesc", "WtFrags", "WtError", "lib", "library_path", "make_desc",
+    "make_frags", "coeff_torch_dtype", "wt_version", "wt_coeff_bytes", "wt_num_tiles", "wt_build",
+    "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
+    "wt_get_error",
+]
+
+F32, BF16, F16 = 0, 1, 2
+SELF_EXCLUDE, INTERP_LINEAR, RESOLVE_NORMALIZED, ACCUMULATE = 1, 2, 4, 8
+DEFAULT_FLAGS = SELF_EXCLUDE | INTERP_LINEAR | RESOLVE_NORMALIZED
+
+_DIR = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_DIR, "libwt.so")
+_STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "rejected input fragments",
+           4: "timeout", 5: "CUDA error", 6: "over memory cap", 7: "busy"}
+_TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+
+
+class WtError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn}: {_STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class WtDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("J", ctypes.c_int32), ("coeff_dtype", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+    @property
+    def P(self) -> int:
+        return self.width * self.height
+
+    @property
+    def C(self) -> int:
+        return 1 << self.J
+
+
+class WtFrags(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pixel", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p), ("r", ctypes.c_void_p), ("g", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("tile_offsets", ctypes.c_void_p)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libwt.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is not built; run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    D, Fr = ctypes.POINTER(WtDesc), ctypes.POINTER(WtFrags)
+    sig = {
+        "wt_version": ([], ctypes.c_char_p),
+        "wt_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "wt_coeff_bytes": ([D], ctypes.c_size_t),
+        "wt_num_tiles": ([D], i64),
+        "wt_build": ([D, Fr, vp, vp, vp], ctypes.c_int),
+        "wt_resolve": ([D, Fr, vp, vp, vp, vp], ctypes.c_int),
+        "wt_composite": ([D, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t: Optional[torch.Tensor], name: str, dtypes) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    return t.data_ptr()
+
+
+def _call(name: str, *args) -> None:
+    st = getattr(lib(), name)(*args)
+    if st != 0:
+        raise WtError(name, st)
+
+
+def coeff_torch_dtype(coeff_dtype: int) -> torch.dtype:
+    return _TORCH_DTYPE[coeff_dtype]
+
+
+def make_desc(width: int, height: int, J: int, coeff_dtype: int = F32,
+              flags: int = DEFAULT_FLAGS, tile_w: int = 16, tile_h: int = 16) -> WtDesc:
+    return WtDesc(width, height, tile_w, tile_h, J, coeff_dtype, flags, 0)
+
+
+def make_frags(pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tensor,
+               tile_offsets: torch.Tensor, r: Optional[torch.Tensor] = None,
+               g: Optional[torch.Tensor] = None, b: Optional[torch.Tensor] = None) -> WtFrags:
+    """Fragment stream descriptor.  The caller keeps the tensors alive."""
+    f32 = (torch.float32,)
+    return WtFrags(int(z.numel()), _dev(pixel, "pixel", (torch.int32, torch.uint32)),
+                   _dev(z, "z", f32), _dev(alpha, "alpha", f32), _dev(r, "r", f32),
+                   _dev(g, "g", f32), _dev(b, "b", f32),
+                   _dev(tile_offsets, "tile_offsets", (torch.int64,)))
+
+
+def _bg(bg: Sequence[float]):
+    return (ctypes.c_float * 3)(*[float(x) for x in bg])
+
+
+_COEFF_DT = (torch.float32, torch.bfloat16, torch.float16)
+
+
+# ---------------------------------------------------------------- entry points
+
+def wt_version() -> str:
+    return lib().wt_version().decode()
+
+
+def wt_coeff_bytes(desc: WtDesc) -> int:
+    return int(lib().wt_coeff_bytes(ctypes.byref(desc)))
+
+
+def wt_num_tiles(desc: WtDesc) -> int:
+    return int(lib().wt_num_tiles(ctypes.byref(desc)))
+
+
+def wt_build(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
+             zmin: Optional[torch.Tensor] = None, stream=None) -> None:
+    _call("wt_build", ctypes.byref(desc), ctypes.byref(frags), _dev(coeff, "coeff", _COEFF_DT),
+          _dev(zmin, "zmin", (torch.float32,)), _stream(stream))
+
+
+def wt_resolve(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor, zmin: Optional[torch.Tensor],
+               accum: torch.Tensor, stream=None) -> None:
+    _call("wt_resolve", ctypes.byref(desc), ctypes.byref(frags), _dev(coeff, "coeff", _COEFF_DT),
+          _dev(zmin, "zmin", (torch.float32,)), _dev(accum, "accum", (torch.float32,)),
+          _stream(stream))
+
+
+def wt_composite(desc: WtDesc, accum: torch.Tensor, out: torch.Tensor,
+                 bg: Sequence[float] = (0.5, 0.5, 0.5), bg_img: Optional[torch.Tensor] = None,
+                 stream=None) -> None:
+    _call("wt_composite", ctypes.byref(desc), _dev(accum, "accum", (torch.float32,)),
+          _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
+          _stream(stream))
+
+
+def wt_resolve_composite(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
+                         zmin: Optional[torch.Tensor], out: torch.Tensor,
+                         bg: Sequence[float] = (0.5, 0.5, 0.5),
+                         bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+    _call("wt_resolve_composite", ctypes.byref(desc), ctypes.byref(frags),
+          _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
+          _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
+          _stream(stream))
+
+
+def wt_build_resolve(desc: WtDesc, frags: WtFrags, out: torch.Tensor,
+                     coeff: Optional[torch.Tensor] = None, zmin: Optional[torch.Tensor] = None,
+                     bg: Sequence[float] = (0.5, 0.5, 0.5), bg_img: Optional[torch.Tensor] = None,
+                     stream=None) -> None:
+    _call("wt_build_resolve", ctypes.byref(desc), ctypes.byref(frags),
+          _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
+          _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
+          _stream(stream))
+
+
+def wt_absorbance(desc: WtDesc, coeff: torch.Tensor, pixel: torch.Tensor, z: torch.Tensor,
+                  A_out: torch.Tensor, alpha: Optional[torch.Tensor] = None, stream=None) -> None:
+    _call("wt_absorbance", ctypes.byref(desc), _dev(coeff, "coeff", _COEFF_DT), int(z.numel()),
+          _dev(pixel, "pixel", (torch.int32, torch.uint32)), _dev(z, "z", (torch.float32,)),
+          _dev(alpha, "alpha", (torch.float32,)), _dev(A_out, "A_out", (torch.float32,)),
+          _stream(stream))
+
+
+def wt_get_error(stream=None) -> int:
+    """Synchronises the stream; returns and clears the rejected-input count."""
+    cnt = ctypes.c_int64(0)
+    st = lib().wt_get_error(_stream(stream), ctypes.byref(cnt))
+    if st not in (0, 3):
+        raise WtError("wt_get_error", st)
+    return int(cnt.value)

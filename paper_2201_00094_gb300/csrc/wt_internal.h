@@ -1,0 +1,23 @@
+// Internal interface between the C-ABI layer (wt_api.cu) and the per-dtype
+// kernel translation units.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wt {
+
+struct Params;
+
+typedef cudaError_t (*TileLaunch)(const Params &, int ntiles, cudaStream_t);
+typedef cudaError_t (*QueryLaunch)(const Params &, int64_t q, const uint32_t *qpx, const float *qz,
+                                   const float *qal, float *outA, cudaStream_t);
+
+// [J-1] for J = 1..5; suffix = storage type (0 f32, 1 bf16, 2 f16)
+extern const TileLaunch kBuild0[5], kBuild1[5], kBuild2[5];
+extern const TileLaunch kResolve0[5], kResolve1[5], kResolve2[5];
+extern const TileLaunch kResolveComp0[5], kResolveComp1[5], kResolveComp2[5];
+extern const TileLaunch kFused0[5], kFused1[5], kFused2[5];
+extern const QueryLaunch kAbsorbance0[5], kAbsorbance1[5], kAbsorbance2[5];
+
+}  // namespace wt

@@ -1,0 +1,108 @@
+"""The C-ABI library loads, exports every entry point include/wt.h declares,
+and rejects bad arguments on the host (no GPU needed: argument checks run
+before any CUDA call)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2201_00094_gb300 as wt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(wt.library_path()):
+        from paper_2201_00094_gb300 import build_lib
+        build_lib.build()
+    return wt.lib()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(wt_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    declared = _declared()
+    assert {"wt_build", "wt_resolve", "wt_composite"} <= declared
+    out = subprocess.run(["nm", "-D", "--defined-only", wt.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (wt_[a-z_0-9]+)$", out, flags=re.M))
+    missing = declared - exported
+    assert not missing, missing
+    for name in declared:
+        getattr(L, name)
+
+
+def test_struct_layout_matches_header():
+    assert ctypes.sizeof(wt.WtDesc) == 32
+    assert ctypes.sizeof(wt.WtFrags) == 64
+
+
+def test_host_queries(L):
+    d = wt.make_desc(1920, 1080, 4)
+    assert wt.wt_coeff_bytes(d) == 1920 * 1080 * 16 * 4
+    assert wt.wt_num_tiles(d) == 120 * 68
+    d = wt.make_desc(3840, 2160, 5, wt.BF16)
+    assert wt.wt_coeff_bytes(d) == 3840 * 2160 * 32 * 2
+    d = wt.make_desc(53, 37, 3, tile_w=7, tile_h=3)
+    assert wt.wt_num_tiles(d) == 8 * 13
+    assert wt.wt_version().startswith("wt-gb300")
+
+
+@pytest.mark.parametrize("bad", [
+    dict(width=0), dict(height=-1), dict(J=0), dict(tile_w=0), dict(tile_w=32, tile_h=16),
+    dict(coeff_dtype=7), dict(flags=1 << 9), dict(width=65536, height=65536)])
+def test_bad_descriptor_rejected_on_host(L, bad):
+    kw = dict(width=64, height=64, J=4, coeff_dtype=wt.F32, flags=wt.DEFAULT_FLAGS, tile_w=16,
+              tile_h=16)
+    kw.update(bad)
+    d = wt.make_desc(**kw)
+    assert L.wt_coeff_bytes(ctypes.byref(d)) == 0
+    fr = wt.WtFrags()
+    st = L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None)
+    assert st == 1
+
+
+def test_unsupported_J_and_flags(L):
+    d = wt.make_desc(64, 64, 6)
+    fr = wt.WtFrags()
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 2
+    d = wt.make_desc(64, 64, 4, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
+    bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
+    st = L.wt_build_resolve(ctypes.byref(d), ctypes.byref(fr), None, None, None, bg,
+                            ctypes.c_void_p(16), None)
+    assert st == 2
+
+
+def test_bad_fragment_pointers_rejected_on_host(L):
+    d = wt.make_desc(64, 64, 4)
+    fr = wt.WtFrags(n=10, pixel=None, z=16, alpha=16, tile_offsets=16)
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 1
+    fr = wt.WtFrags(n=10, pixel=20, z=16, alpha=16, tile_offsets=16)  # misaligned
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 1
+    fr = wt.WtFrags(n=10, pixel=16, z=16, alpha=16, tile_offsets=16)  # resolve needs rgb
+    assert L.wt_resolve(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None,
+                        ctypes.c_void_p(16), None) == 1
+    assert L.wt_get_error(None, None) == 1
+
+
+def test_status_strings(L):
+    for s in range(8):
+        assert L.wt_status_string(s)
+
+
+def test_binding_requires_cuda_tensors():
+    import torch
+    with pytest.raises(ValueError):
+        wt.make_frags(torch.zeros(4, dtype=torch.int32), torch.zeros(4), torch.zeros(4),
+                      torch.zeros(2, dtype=torch.int64))

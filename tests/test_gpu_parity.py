@@ -1,0 +1,256 @@
+"""CUDA path vs FP64 oracle, element by element, on seeded synthetic frames
+sized so the oracle finishes in seconds but spanning many tiles and ragged
+edges.  All calls go through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2201_00094_gb300 as wt
+import synth
+from wtcheck import (absorbance_tol, coeff_tol, gpu_run, oracle_run, pixel_counts,
+                     pixel_step_sums, desc_of, frags_of)
+
+pytestmark = pytest.mark.gpu
+
+ALL_FLAGS = [7, 6, 5, 4, 3, 2, 1, 0]
+
+
+def test_plain64_fp32_build_and_composite():
+    fr = synth.plain64(seed=0)
+    g = gpu_run(fr)
+    r = oracle_run(fr)
+    assert g["bad"] == 0
+    assert (np.abs(g["coeff"] - r["coeff"]) <= coeff_tol(fr)).all()
+    np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
+
+
+@pytest.mark.parametrize("mode", ["fused", "two_step"])
+def test_plain64_other_paths(mode):
+    fr = synth.plain64(seed=1)
+    g = gpu_run(fr, fused=(mode == "fused"), two_step=(mode == "two_step"))
+    r = oracle_run(fr)
+    np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
+    if mode == "two_step":
+        # only ratios R/W are defined; S is exact
+        acc, ref = g["accum"], r["accum"]
+        has = ref[:, 3] > 0
+        np.testing.assert_allclose(acc[has, :3] / acc[has, 3:4], ref[has, :3] / ref[has, 3:4],
+                                   atol=1e-5)
+        np.testing.assert_allclose(acc[:, 4], ref[:, 4], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("J", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 4), (7, 3), (1, 1), (16, 1)])
+def test_ragged_tiles_every_J(J, tile):
+    fr = synth.uniform_frame(53, 37, 5.0, 40, J=J, seed=J * 7 + tile[0], tile_w=tile[0],
+                             tile_h=tile[1])
+    g = gpu_run(fr)
+    r = oracle_run(fr)
+    assert g["bad"] == 0
+    assert (np.abs(g["coeff"] - r["coeff"]) <= coeff_tol(fr)).all()
+    np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
+    gf = gpu_run(fr, fused=True)
+    np.testing.assert_allclose(gf["out"], r["out"], atol=1e-4, rtol=0)
+
+
+@pytest.mark.parametrize("flags", ALL_FLAGS)
+def test_every_reading_flag(flags):
+    fr = synth.uniform_frame(40, 24, 8.0, 64, J=4, seed=100 + flags)
+    r = oracle_run(fr, flags=flags)
+    for kw in (dict(), dict(fused=True), dict(two_step=True)):
+        g = gpu_run(fr, flags=flags, **kw)
+        np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0, err_msg=str(kw))
+
+
+def test_zmin_is_nearest_opaque_depth():
+    fr = synth.uniform_frame(33, 17, 4.0, 16, J=3, seed=5)
+    h = fr.numpy()
+    h["alpha"][::5] = 0.0  # transparent fragments do not count
+    fr.alpha = torch.from_numpy(h["alpha"])
+    g = gpu_run(fr)
+    ref = np.full(fr.P, np.inf, np.float32)
+    keep = h["alpha"] > 0
+    np.minimum.at(ref, h["pixel"][keep].astype(np.int64), np.clip(h["z"][keep], 0, 1 - 2 ** -24))
+    np.testing.assert_array_equal(g["zmin"], ref)
+
+
+@pytest.mark.parametrize("J", [3, 4, 5])
+def test_absorbance_queries_match_oracle(J):
+    fr = synth.uniform_frame(48, 32, 12.0, 64, J=J, seed=J)
+    dev = torch.device("cuda")
+    gfr = fr.to(dev)
+    d = desc_of(fr)
+    coeff = torch.empty(fr.P, 1 << J, device=dev)
+    wt.wt_build(d, frags_of(gfr), coeff)
+    # fragments themselves (self excluded) and free depth queries
+    A = torch.empty(fr.n, device=dev)
+    wt.wt_absorbance(d, coeff, gfr.pixel, gfr.z, A, alpha=gfr.alpha)
+    rng = np.random.default_rng(J)
+    qp = rng.integers(0, fr.P, 5000).astype(np.int32)
+    qz = rng.random(5000).astype(np.float32)
+    qz[:64] = np.arange(64) / 64.0  # bin edges and centres
+    Aq = torch.empty(5000, device=dev)
+    wt.wt_absorbance(d, coeff, torch.from_numpy(qp).to(dev), torch.from_numpy(qz).to(dev), Aq)
+    assert wt.wt_get_error() == 0
+    h = fr.numpy()
+    c = oracle.build_coeffs(h["pixel"], h["z"], h["alpha"], fr.P, J)
+    S = pixel_step_sums(fr)
+    ref = oracle.fragment_absorbance(h["pixel"], h["z"], h["alpha"], fr.P, J, c)
+    err = np.abs(A.cpu().numpy() - ref)
+    assert (err <= absorbance_tol(ref, S[h["pixel"].astype(np.int64)], J)).all(), err.max()
+    refq = oracle.absorbance_at(qp, qz, fr.P, J, c)
+    errq = np.abs(Aq.cpu().numpy() - refq)
+    assert (errq <= absorbance_tol(refq, S[qp], J)).all(), errq.max()
+    # where the pixel holds <= 16 of absorbance, v is within 1e-5 relative
+    small = S[h["pixel"].astype(np.int64)] <= 16
+    v_rel = np.abs(np.expm1(-(A.cpu().numpy() - ref)))[small]
+    assert v_rel.max() <= 1e-5
+
+
+def test_empty_frame_and_empty_tiles():
+    fr = synth.uniform_frame(40, 40, 0.0, 0, J=4, seed=0)
+    assert fr.n == 0
+    g = gpu_run(fr, bg=(0.1, 0.2, 0.3))
+    assert not g["coeff"].any()
+    np.testing.assert_array_equal(g["out"], np.tile([0.1, 0.2, 0.3, 0.0], (fr.P, 1)).astype(np.float32))
+    assert np.isinf(g["zmin"]).all()
+    gf = gpu_run(fr, fused=True, bg=(0.1, 0.2, 0.3))
+    np.testing.assert_array_equal(gf["out"], g["out"])
+
+
+def test_single_fragment_paper_plane():
+    """§1.2: one 25%-opaque plane -> 0.25 c + 0.75 bg for every J."""
+    for J in range(1, 6):
+        counts = torch.zeros(16 * 16, dtype=torch.int32)
+        counts[37] = 1
+        fr = synth.uniform_frame(16, 16, 0.0, None, J=J, seed=0, counts=counts)
+        fr.z[:] = 0.5
+        fr.alpha[:] = 0.25
+        g = gpu_run(fr, bg=(0.5, 0.5, 0.5))
+        c = np.array([fr.r[0], fr.g[0], fr.b[0]], np.float64)
+        np.testing.assert_allclose(g["out"][37, :3], 0.25 * c + 0.75 * 0.5, atol=1e-6)
+        assert g["out"][37, 3] == pytest.approx(0.25, abs=1e-6)
+
+
+def test_background_image():
+    fr = synth.uniform_frame(37, 29, 3.0, 10, J=4, seed=9)
+    bg_img = np.random.default_rng(0).random((fr.P, 3)).astype(np.float32)
+    r = oracle_run(fr, bg_img=bg_img)
+    for kw in (dict(), dict(fused=True), dict(two_step=True)):
+        g = gpu_run(fr, bg_img=bg_img, **kw)
+        np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
+
+
+def test_bad_fragments_are_skipped_and_counted():
+    fr = synth.uniform_frame(32, 32, 4.0, 16, J=4, seed=3)
+    h = fr.numpy()
+    bad_idx = np.array([0, 5, 17, 300])
+    pix = h["pixel"].copy()
+    pix[bad_idx[0]] = fr.P + 5                  # outside the image
+    pix[bad_idx[1]] = (pix[bad_idx[1]] + 16) % fr.P  # wrong tile (next tile over)
+    z = h["z"].copy()
+    z[bad_idx[2]] = np.nan
+    al = h["alpha"].copy()
+    al[bad_idx[3]] = np.nan
+    bad_fr = synth.Frame(**{**fr.__dict__, "pixel": torch.from_numpy(pix),
+                            "z": torch.from_numpy(z), "alpha": torch.from_numpy(al)})
+    g = gpu_run(bad_fr)
+    assert g["bad"] == 4
+    keep = np.setdiff1d(np.arange(fr.n), bad_idx)
+    rgb = (h["r"][keep], h["g"][keep], h["b"][keep])
+    c = oracle.build_coeffs(h["pixel"][keep], h["z"][keep], h["alpha"][keep], fr.P, fr.J)
+    ref = oracle.resolve(h["pixel"][keep], h["z"][keep], h["alpha"][keep], rgb, fr.P, fr.J, c)[0]
+    np.testing.assert_allclose(g["out"], ref, atol=1e-4)
+    gf = gpu_run(bad_fr, fused=True)
+    assert gf["bad"] == 4
+    np.testing.assert_allclose(gf["out"], ref, atol=1e-4)
+
+
+def test_corrupt_tile_range_is_skipped_and_counted():
+    fr = synth.uniform_frame(32, 32, 4.0, 16, J=4, seed=4)
+    off = fr.tile_offsets.clone()
+    off[2] = off[3] + 1  # tile 1 gets a decreasing range, tile 2 a range past its start
+    g = gpu_run(synth.Frame(**{**fr.__dict__, "tile_offsets": off}))
+    assert g["bad"] >= 1
+    assert np.isfinite(g["out"]).all()
+
+
+def test_accumulate_batches_equals_single_build():
+    fr = synth.uniform_frame(48, 48, 6.0, 32, J=4, seed=11)
+    dev = torch.device("cuda")
+    g = fr.to(dev)
+    d1 = desc_of(fr)
+    dA = desc_of(fr, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
+    # split every tile's range in two halves -> two batches with their own offsets
+    off = fr.tile_offsets
+    mid = (off[:-1] + off[1:]) // 2
+    idx1 = torch.cat([torch.arange(int(off[t]), int(mid[t])) for t in range(fr.ntiles)])
+    idx2 = torch.cat([torch.arange(int(mid[t]), int(off[t + 1])) for t in range(fr.ntiles)])
+    off1 = torch.cat([torch.zeros(1, dtype=torch.int64), torch.cumsum(mid - off[:-1], 0)])
+    off2 = torch.cat([torch.zeros(1, dtype=torch.int64), torch.cumsum(off[1:] - mid, 0)])
+    parts = []
+    for idx, o in ((idx1, off1), (idx2, off2)):
+        sub = {k: getattr(fr, k)[idx].contiguous().to(dev) for k in ("pixel", "z", "alpha", "r", "g", "b")}
+        parts.append((sub, o.to(dev)))
+    coeff = torch.empty(fr.P, 16, device=dev)
+    zmin = torch.empty(fr.P, device=dev)
+    accum = torch.empty(fr.P, 5, device=dev)
+    ref_coeff = torch.empty_like(coeff)
+    ref_zmin = torch.empty_like(zmin)
+    wt.wt_build(d1, frags_of(g), ref_coeff, ref_zmin)
+    for i, (sub, o) in enumerate(parts):
+        f = wt.make_frags(sub["pixel"], sub["z"], sub["alpha"], o, sub["r"], sub["g"], sub["b"])
+        wt.wt_build(d1 if i == 0 else dA, f, coeff, zmin)
+    torch.testing.assert_close(coeff, ref_coeff, atol=2e-6, rtol=1e-5)
+    torch.testing.assert_close(zmin, ref_zmin, atol=0, rtol=0)
+    for i, (sub, o) in enumerate(parts):
+        f = wt.make_frags(sub["pixel"], sub["z"], sub["alpha"], o, sub["r"], sub["g"], sub["b"])
+        wt.wt_resolve(d1 if i == 0 else dA, f, coeff, zmin, accum)
+    out = torch.empty(fr.P, 4, device=dev)
+    wt.wt_composite(d1, accum, out)
+    r = oracle_run(fr)
+    np.testing.assert_allclose(out.cpu().numpy(), r["out"], atol=1e-4)
+
+
+def test_permutation_invariance_on_gpu():
+    fr = synth.uniform_frame(32, 32, 10.0, 64, J=5, seed=12)
+    g1 = gpu_run(fr)
+    perm = torch.cat([int(fr.tile_offsets[t]) + torch.randperm(
+        int(fr.tile_offsets[t + 1] - fr.tile_offsets[t]), generator=torch.Generator().manual_seed(t))
+        for t in range(fr.ntiles)])
+    pf = synth.Frame(**{**fr.__dict__, **{k: getattr(fr, k)[perm].contiguous()
+                                           for k in ("pixel", "z", "alpha", "r", "g", "b")}})
+    g2 = gpu_run(pf)
+    assert (np.abs(g1["coeff"] - g2["coeff"]) <= coeff_tol(fr)).all()
+    np.testing.assert_allclose(g1["out"], g2["out"], atol=2e-5)
+
+
+def test_deep_pixel_underflow_safe():
+    """900 fragments in one depth bin: the nearest sees A ~ 400, every FP32
+    exp(-A) underflows; the offset m_p keeps the normalised colour right."""
+    k = 900
+    counts = torch.zeros(256, dtype=torch.int32)
+    counts[0] = k
+    counts[1] = 3
+    fr = synth.uniform_frame(16, 16, 0.0, None, J=4, seed=0, counts=counts)
+    sel = fr.pixel == 0
+    fr.z[sel] = (0.5 + torch.arange(k, dtype=torch.float32) / k / 64)[torch.randperm(k)]
+    fr.alpha[sel] = 0.6
+    r = oracle_run(fr)
+    for kw in (dict(), dict(fused=True), dict(two_step=True)):
+        g = gpu_run(fr, **kw)
+        np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, err_msg=str(kw))
+
+
+def test_alpha_and_depth_clamps():
+    fr = synth.uniform_frame(16, 16, 6.0, 20, J=4, seed=13)
+    n = fr.n
+    fr.alpha[: n // 4] = 1.0
+    fr.alpha[n // 4: n // 3] = -0.2
+    fr.z[n // 2: n // 2 + 20] = -1.0
+    fr.z[n // 2 + 20: n // 2 + 40] = 2.0
+    r = oracle_run(fr)
+    g = gpu_run(fr)
+    np.testing.assert_allclose(g["out"], r["out"], atol=1e-4)
+    assert (np.abs(g["coeff"] - r["coeff"]) <= coeff_tol(fr) * 4).all()

@@ -1,0 +1,95 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path on a synthetic
+frame and the FP64 oracle on the same inputs, and the tolerances.
+
+Tolerances (derived from the arithmetic; see the design notes):
+  * composite RGBA, FP32 storage: 1e-4 absolute.
+  * absorbance A in front of a fragment, FP32: the relative error of
+    v = exp(-A) equals the absolute error of A, held to
+        |dA| <= 1e-5 * max(1, A) + 4 (J + 2) u S_p,   u = 2^-24,
+    where S_p = sum of the pixel's steps: storing chi_00 ~ S_p in FP32 alone
+    moves A by u S_p, and J+1 stored terms of size <= S_p enter each bin value.
+    For S_p <= 16 this is within 1e-5 relative on v.
+  * coefficients, FP32: |dc| <= 8 u (k + 1) S_p (k = fragments of the pixel,
+    positive summands only).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+import paper_2201_00094_gb300 as wt
+import synth
+
+U32 = 2.0 ** -24
+
+
+def frags_of(g: synth.Frame):
+    return wt.make_frags(g.pixel, g.z, g.alpha, g.tile_offsets, g.r, g.g, g.b)
+
+
+def desc_of(fr: synth.Frame, J=None, dtype=wt.F32, flags=wt.DEFAULT_FLAGS):
+    return wt.make_desc(fr.width, fr.height, fr.J if J is None else J, dtype, flags, fr.tile_w,
+                        fr.tile_h)
+
+
+def gpu_run(fr: synth.Frame, J=None, dtype=wt.F32, flags=wt.DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5),
+            bg_img=None, fused=False, two_step=False):
+    """Returns dict with coeff (float64 numpy), zmin, out [P,4] (and accum)."""
+    dev = torch.device("cuda")
+    g = fr.to(dev)
+    d = desc_of(fr, J, dtype, flags)
+    f = frags_of(g)
+    C = 1 << d.J
+    coeff = torch.full((fr.P, C), float("nan"), device=dev, dtype=wt.coeff_torch_dtype(dtype))
+    zmin = torch.full((fr.P,), float("nan"), device=dev)
+    out = torch.full((fr.P, 4), float("nan"), device=dev)
+    bgt = None if bg_img is None else torch.as_tensor(bg_img, dtype=torch.float32, device=dev)
+    res = {}
+    if fused:
+        wt.wt_build_resolve(d, f, out, coeff, zmin, bg=bg, bg_img=bgt)
+    else:
+        wt.wt_build(d, f, coeff, zmin)
+        if two_step:
+            accum = torch.full((fr.P, 5), float("nan"), device=dev)
+            wt.wt_resolve(d, f, coeff, zmin, accum)
+            wt.wt_composite(d, accum, out, bg=bg, bg_img=bgt)
+            res["accum"] = accum.cpu().numpy().astype(np.float64)
+        else:
+            wt.wt_resolve_composite(d, f, coeff, zmin, out, bg=bg, bg_img=bgt)
+    res["bad"] = wt.wt_get_error()
+    torch.cuda.synchronize()
+    res["coeff"] = coeff.float().cpu().numpy().astype(np.float64)
+    res["zmin"] = zmin.cpu().numpy()
+    res["out"] = out.cpu().numpy().astype(np.float64)
+    return res
+
+
+def oracle_run(fr: synth.Frame, J=None, flags=wt.DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5), bg_img=None):
+    h = fr.numpy()
+    J = fr.J if J is None else J
+    rgb = (h["r"], h["g"], h["b"])
+    c = oracle.build_coeffs(h["pixel"], h["z"], h["alpha"], fr.P, J)
+    out, acc = oracle.resolve(h["pixel"], h["z"], h["alpha"], rgb, fr.P, J, c, flags=flags, bg=bg,
+                              bg_img=bg_img)
+    return dict(coeff=c, out=out, accum=acc)
+
+
+def pixel_step_sums(fr: synth.Frame) -> np.ndarray:
+    h = fr.numpy()
+    a = -np.log1p(-np.clip(h["alpha"].astype(np.float64), 0, 1 - 2 ** -20))
+    return np.bincount(h["pixel"].astype(np.int64), weights=a, minlength=fr.P)
+
+
+def pixel_counts(fr: synth.Frame) -> np.ndarray:
+    return np.bincount(fr.numpy()["pixel"].astype(np.int64), minlength=fr.P)
+
+
+def coeff_tol(fr: synth.Frame) -> np.ndarray:
+    S = pixel_step_sums(fr)
+    k = pixel_counts(fr)
+    return (8 * U32 * (k + 1) * S + 1e-30)[:, None]
+
+
+def absorbance_tol(A_ref: np.ndarray, S: np.ndarray, J: int) -> np.ndarray:
+    return 1e-5 * np.maximum(1.0, A_ref) + 4 * (J + 2) * U32 * S
