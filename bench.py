@@ -201,7 +201,7 @@ def run_wt(args):
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
     # weak scaling: every rank renders its own independent frame
-    fr = synth.make(args.workload, seed=args.seed + rank, device=dev)
+    fr = synth.make(args.workload, seed=args.seed + rank, device=dev, **size_kw(args))
     torch.cuda.synchronize()
     n, P, J = fr.n, fr.P, fr.J
     dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[args.dtype]
@@ -334,6 +334,7 @@ def run_wt(args):
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
                        "fragments_per_gpu": n, "pixels": P, "J": J,
                        "coeff_storage": args.dtype, "path": "wt_build_resolve (fused kernel)",
+                       "size_override": args.size or None,
                        "l2": f"inputs larger than L2 ({n * 24 / 1e9:.1f} GB of fragments)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -359,7 +360,7 @@ def run_reference(args):
     if rank != 0:
         return
     dev = torch.device("cuda", local) if torch.cuda.is_available() else torch.device("cpu")
-    fr = synth.make(args.workload, seed=args.seed, device=dev)
+    fr = synth.make(args.workload, seed=args.seed, device=dev, **size_kw(args))
     K, W = args.steps, args.warmup
     # size each step's sample so the whole run stays near --ref-seconds
     probe = run_oracle_sample(fr, 1, seed=99_999)
@@ -388,6 +389,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def size_kw(args):
+    if not args.size:
+        return {}
+    w, h = (int(x) for x in args.size.lower().split("x"))
+    return {"width": w, "height": h}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,6 +405,7 @@ def main():
     ap.add_argument("--workload", default="heavy4k", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--size", default="", help="override the workload's WxH (profiling runs)")
     ap.add_argument("--cpu-tiles", type=int, default=96)
     ap.add_argument("--ref-tiles", type=int, default=0, help="tiles per step (0: sized by time)")
     ap.add_argument("--ref-seconds", type=float, default=120.0)

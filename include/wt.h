@@ -205,6 +205,8 @@ wt_status wt_absorbance(const wt_desc *desc, const void *coeff, int64_t q, const
  * Returns WT_ERR_INPUT if the count was non-zero, WT_OK otherwise.
  */
 wt_status wt_get_error(wt_stream stream, int64_t *bad_count);
+/* (Every call counts the fragments it rejects, so a bad fragment seen by
+ * wt_build and then by wt_resolve is counted twice.) */
 
 #ifdef __cplusplus
 }
