@@ -217,7 +217,11 @@ def run_wt(args):
     desc = wt.make_desc(fr.width, fr.height, J, dt)
 
     def step_fused(d=desc, c=coeff, o=out):
-        wt.wt_build_resolve(d, frags, o, c, None, bg=fr.bg, stream=stream)
+        if args.path == "fused":
+            wt.wt_build_resolve(d, frags, o, c, None, bg=fr.bg, stream=stream)
+        else:
+            wt.wt_build(d, frags, c, None, stream=stream)
+            wt.wt_resolve_composite(d, frags, c, None, o, bg=fr.bg, stream=stream)
 
     K, W = args.steps, args.warmup
     for _ in range(W):
@@ -246,7 +250,10 @@ def run_wt(args):
     value = frags_all * K / (total_ms / 1e3)
 
     s = DTYPE_BYTES[dt]
-    alg_bytes = n * 24 + P * C * s + 16 * P  # fused: fragments once, coefficients + RGBA written
+    if args.path == "fused":
+        alg_bytes = n * 24 + P * C * s + 16 * P  # fragments once, coefficients + RGBA written
+    else:
+        alg_bytes = n * 36 + 2 * P * C * s + 16 * P  # two passes over the fragments
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = profiled_traffic("k_fused", args.workload, args.dtype)
@@ -285,6 +292,53 @@ def run_wt(args):
             del c2, o2
 
     # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all)
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = run_oracle_sample(fr, args.cpu_tiles, seed=1234)
+        got = out.cpu().numpy()[res["pixel_ids"]]
+        cpu = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_tiles} seeded random 16x16 tiles of the same frame "
+                         f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
+                         f"composite, FP64, single thread, {res['seconds']:.1f} s",
+               "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
+    kernel_name = "k_fused" if args.path == "fused" else "k_build + k_resolve"
+    path_name = ("wt_build_resolve (fused kernel)" if args.path == "fused"
+                 else "wt_build + wt_resolve_composite (two kernels)")
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                       "fragments_per_gpu": n, "pixels": P, "J": J,
+                       "coeff_storage": args.dtype, "path": path_name,
+                       "size_override": args.size or None,
+                       "l2": f"inputs larger than L2 ({n * 24 / 1e9:.1f} GB of fragments)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                         "traffic": traffic, "kernel": kernel_name,
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": round(launch_ms, 4),
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": K * (1 if args.path == "fused" else 2),
+            "clocks": clk.summary(),
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all):
+    """Same metric through the C ABI with the fragment stream copied from
+    pinned host memory and the composite copied back, every step."""
+    dev = out.device
+    P = fr.P
     host = {k: getattr(fr, k).cpu().pin_memory() for k in ("pixel", "z", "alpha", "r", "g", "b",
                                                              "tile_offsets")}
     out_host = torch.empty(P, 4, pin_memory=True)
@@ -312,45 +366,8 @@ def run_wt(args):
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(a.elapsed_time(b) / Ke, world)
-    e2e_value = frags_all / (e2e_ms / 1e3)
-    del dev_bufs
-
-    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = run_oracle_sample(fr, args.cpu_tiles, seed=1234)
-        got = out.cpu().numpy()[res["pixel_ids"]]
-        cpu = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_tiles} seeded random 16x16 tiles of the same frame "
-                         f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
-                         f"composite, FP64, single thread, {res['seconds']:.1f} s",
-               "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
-                       "fragments_per_gpu": n, "pixels": P, "J": J,
-                       "coeff_storage": args.dtype, "path": "wt_build_resolve (fused kernel)",
-                       "size_override": args.size or None,
-                       "l2": f"inputs larger than L2 ({n * 24 / 1e9:.1f} GB of fragments)"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                         "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                         "traffic": traffic, "kernel": "k_fused",
-                         "alg_bytes_per_launch": alg_bytes, "launch_ms": round(launch_ms, 4),
-                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
-            "gpu_launches": K,
-            "clocks": clk.summary(),
-            "variants": variants,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return {"value": frags_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -410,6 +427,9 @@ def main():
     ap.add_argument("--ref-tiles", type=int, default=0, help="tiles per step (0: sized by time)")
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--path", default="fused", choices=["fused", "two_pass"],
+                    help="fused kernel (default) or wt_build + wt_resolve_composite")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -1,23 +1,31 @@
 // Device-side building blocks of the Wavelet OIT kernels (sm_103a).
 //
-// One CTA owns one screen tile (<= 256 pixels).  Its fragments are a
-// contiguous range of the tile-grouped stream and are read with 16-byte
-// vector loads.  Per-pixel state lives in shared memory; fragments of the same
-// pixel meet in shared-memory atomics instead of global atomics (the
-// coefficient update of §2.3.3).
+// One CTA owns one screen tile (<= 256 pixels, one thread per pixel in the
+// per-pixel phases).  The tile's fragments are a contiguous range of the
+// tile-grouped stream, read with 16-byte vector loads.  Fragments of the same
+// pixel meet in shared memory (the coefficient update of §2.3.3), never in
+// global atomics.
 //
-// The build does not touch J+1 coefficients per fragment.  It accumulates two
-// per-bin sums per pixel at the finest level (bin m = floor(C z), fraction
-// f = C z - m):
+// Build.  Instead of touching J+1 coefficients per fragment, every fragment
+// adds (a f, a (1-f)) to one bin of its pixel at the finest level
+// (bin m = floor(C z), fraction f = C z - m):
 //     F_m = sum a_i f_i,      G_m = sum a_i (1 - f_i),
-// and turns them into the Haar coefficients of §2.3.1 with an O(C) tree: for
-// a dyadic interval I with children L, R and u the position normalised to I,
-//     F_I = sum_I a u = (F_L + F_R + S_R)/2,   G_I = sum_I a (1-u) = (S_L + G_L + G_R)/2,
-//     sum_I a Psi_{n,k} = 2^{-n/2} (F_L + G_R)/2   (Psi is u, then 1-u, scaled),
-// with S = F + G, so X_{n,k} = -2^{-n/2} (F_L + G_R)/2 and chi_00 = G_root.
-// Every term is a sum of non-negative numbers, so the FP32 tree adds no
-// cancellation.  This is exact algebra on the closed form, not an
-// approximation of it.
+// and an O(C) tree per pixel turns the bins into the coefficients of §2.3.1.
+// For a dyadic interval I with children L, R and u the position normalised to
+// I, F_I = sum_I a u and G_I = sum_I a (1-u) satisfy
+//     t = F_L + G_R,   F_I = t/2 + F_R,   G_I = t/2 + G_L,
+//     sum_I a Psi_{n,k} = 2^{-n/2} t / 2      (Psi is u then 1-u, scaled),
+// so X_{n,k} = -2^{-n/2} t / 2, chi_00 = G_root and sum a = F_root + G_root.
+// Every quantity is a sum of non-negative terms (no cancellation in FP32).
+//
+// Resolve.  The coefficients are synthesised once per pixel into the C bin
+// values at the bin centres (§2.3.2), kept in shared memory pre-multiplied by
+// log2(e), so a fragment's transmittance is one ex2 instruction.
+//
+// Shared-memory accumulation uses FP32 atomic adds on structure-of-arrays
+// planes (F and G bins; R, G, B, W accumulators) so that the lanes of a warp
+// spread over all 32 banks; the per-pixel accumulators are further spread
+// over kCopies lane-indexed copies so that lanes rarely contend for a word.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -27,13 +35,16 @@
 
 namespace wt {
 
-constexpr int kThreads = 256;    // threads per CTA
-constexpr int kMaxTilePx = 256;  // pixels per tile
+constexpr int kThreads = 256;    // threads per CTA (= max pixels per tile)
+constexpr int kMaxTilePx = 256;
+constexpr int kCopies = 4;       // lane-spread copies of the per-pixel accumulators
+constexpr int kCasLimit = 1 << 20;  // bound on CAS retries (never reached in practice)
 // alpha is clamped to [0, 1 - 2^-20] and z to [0, 1 - 2^-24] (exact in FP32)
 constexpr float kAlphaMax = 0.99999904632568359375f;
 constexpr float kZMax = 0.999999940395355224609375f;
-// the largest absorbance step after the clamp: -ln(2^-20) = 20 ln 2
-constexpr float kStepCap = 13.8629436111989061f;
+constexpr float kLog2e = 1.44269504088896340736f;
+// the largest step after the clamp is -ln(2^-20) = 20 ln 2, i.e. 20 in log2 units
+constexpr float kStepCapLog2 = 20.0f;
 
 struct Geom {
     int width, height, tile_w, tile_h, ntx;
@@ -43,6 +54,7 @@ struct Geom {
 struct Params {
     Geom g;
     uint32_t flags;
+    uint64_t wmagic;  // floor((2^64-1) / width) + 1 for the division by width (0 when width == 1)
     int64_t n;
     const uint32_t *__restrict__ pixel;
     const float *__restrict__ z;
@@ -62,6 +74,11 @@ struct Params {
 
 enum : uint32_t { kSelfExclude = 1u, kLinear = 2u, kNormalized = 4u, kAccumulate = 8u };
 
+template <int J> struct Shape {
+    static constexpr int C = 1 << J;
+    static constexpr int LD = C + 4;  // floats per pixel row of bins / bin values (16-byte rows)
+};
+
 // ---------------------------------------------------------------- storage
 
 template <typename T> struct Cvt;
@@ -77,14 +94,48 @@ template <> struct Cvt<__half> {
     static __device__ __forceinline__ __half to(float x) { return __float2half_rn(x); }
     static __device__ __forceinline__ float from(__half x) { return __half2float(x); }
 };
-template <typename T> __device__ __forceinline__ float round_to(float x) {
-    return Cvt<T>::from(Cvt<T>::to(x));
+
+// One pixel's C coefficients to / from global memory, 16-byte vectors when
+// the row is a multiple of 16 bytes (it is 16-byte aligned then).
+template <typename CT, int C>
+__device__ __forceinline__ void store_row(CT *dst, const float (&v)[C]) {
+    constexpr int PER = 16 / sizeof(CT);
+    if constexpr (C % PER == 0) {
+#pragma unroll
+        for (int q = 0; q < C / PER; ++q) {
+            union { uint4 u; CT e[PER]; } pk;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) pk.e[i] = Cvt<CT>::to(v[q * PER + i]);
+            reinterpret_cast<uint4 *>(dst)[q] = pk.u;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) dst[i] = Cvt<CT>::to(v[i]);
+    }
+}
+
+template <typename CT, int C>
+__device__ __forceinline__ void load_row(const CT *src, float (&v)[C]) {
+    constexpr int PER = 16 / sizeof(CT);
+    if constexpr (C % PER == 0) {
+#pragma unroll
+        for (int q = 0; q < C / PER; ++q) {
+            union { uint4 u; CT e[PER]; } pk;
+            pk.u = reinterpret_cast<const uint4 *>(src)[q];
+#pragma unroll
+            for (int i = 0; i < PER; ++i) v[q * PER + i] = Cvt<CT>::from(pk.e[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(src[i]);
+    }
 }
 
 // ---------------------------------------------------------------- tiles
 
 struct Tile {
     int tx0, ty0, tw, th;  // origin and clipped extent
+    uint32_t base, lim;    // pixel id of the tile origin; th * width
     int64_t s, e;          // fragment range
 };
 
@@ -95,6 +146,8 @@ __device__ __forceinline__ Tile tile_of(const Params &p, int t, bool count_bad) 
     T.ty0 = ty * p.g.tile_h;
     T.tw = min(p.g.tile_w, p.g.width - T.tx0);
     T.th = min(p.g.tile_h, p.g.height - T.ty0);
+    T.base = (uint32_t)T.ty0 * (uint32_t)p.g.width + (uint32_t)T.tx0;
+    T.lim = (uint32_t)T.th * (uint32_t)p.g.width;
     int64_t s = p.off[t], e = p.off[t + 1];
     if (s < 0 || e < s || e > p.n) {  // corrupt range: skip the tile, count once
         if (count_bad && threadIdx.x == 0) atomicAdd(p.err, 1ull);
@@ -105,22 +158,66 @@ __device__ __forceinline__ Tile tile_of(const Params &p, int t, bool count_bad) 
     return T;
 }
 
-// local pixel index inside the tile, or -1 when the pixel is not in it
+// Local pixel index inside the tile, or -1 when the pixel is not in it.
+// d = pixel - tile origin; its row is d / width, taken as the high word of
+// d * ceil(2^64 / width) (exact for 32-bit d; Granlund & Montgomery 1994).
 __device__ __forceinline__ int local_pixel(uint32_t px, const Params &p, const Tile &T) {
-    const uint32_t y = px / (uint32_t)p.g.width;
-    const uint32_t x = px - y * (uint32_t)p.g.width;
-    const int lx = (int)x - T.tx0;
-    const int ly = (int)min(y, 0x7fffffffu) - T.ty0;
-    if ((unsigned)lx >= (unsigned)T.tw || (unsigned)ly >= (unsigned)T.th) return -1;
-    return ly * p.g.tile_w + lx;
+    const uint32_t d = px - T.base;
+    if (d >= T.lim) return -1;
+    const uint32_t ly = p.wmagic ? (uint32_t)__umul64hi((uint64_t)d, p.wmagic) : d;
+    const uint32_t lx = d - ly * (uint32_t)p.g.width;
+    if (lx >= (uint32_t)T.tw) return -1;
+    return (int)(ly * (uint32_t)p.g.tile_w + lx);
+}
+
+// global pixel id of local pixel lp, or -1 if it lies outside the image
+__device__ __forceinline__ int64_t global_pixel(const Params &p, const Tile &T, int lp) {
+    const int lx = lp % p.g.tile_w, ly = lp / p.g.tile_w;
+    if (lx >= T.tw || ly >= T.th) return -1;
+    return (int64_t)(T.ty0 + ly) * p.g.width + T.tx0 + lx;
 }
 
 // ---------------------------------------------------------------- conditioning
 
 __device__ __forceinline__ float clamp_alpha(float al) { return fminf(fmaxf(al, 0.f), kAlphaMax); }
 __device__ __forceinline__ float clamp_depth(float z) { return fminf(fmaxf(z, 0.f), kZMax); }
-// absorbance step of one interface: v drops by (1 - alpha) across it
-__device__ __forceinline__ float step_of(float alpha_c) { return -log1pf(-alpha_c); }
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Absorbance step of one interface, a = -ln(1 - x) for x = clamped alpha
+// (v drops by the factor 1 - alpha across it).
+//  x <= 1/2: -ln(1 - x) = 2 atanh(s) with s = x / (2 - x) <= 1/3, summed as
+//            the odd power series 2 s (1 + s^2/3 + ... + s^12/13); the first
+//            omitted term is below 2e-8 relative.
+//  x >  1/2: 1 - x is exact in FP32 (Sterbenz), its log2 is >= 1 in magnitude,
+//            so the hardware log2 (relative error ~2^-22) suffices.
+// Checked against log1p in FP64 to a few ulp over the whole clamped range.
+__device__ __forceinline__ float step_of(float x) {
+    const float s = x * rcp(2.f - x);
+    const float s2 = s * s;
+    float q = fmaf(s2, 1.f / 13, 1.f / 11);
+    q = fmaf(s2, q, 1.f / 9);
+    q = fmaf(s2, q, 1.f / 7);
+    q = fmaf(s2, q, 1.f / 5);
+    q = fmaf(s2, q, 1.f / 3);
+    q = fmaf(s2, q, 1.f);
+    const float series = 2.f * s * q;
+    const float direct = -0.693147180559945309f * lg2(1.f - x);
+    return x <= 0.5f ? series : direct;
+}
 
 // ---------------------------------------------------------------- streaming
 
@@ -172,6 +269,13 @@ __device__ __forceinline__ void for_each_frag6(int64_t s, int64_t e, const Param
         body(p.pixel[i], p.z[i], p.alpha[i], p.r[i], p.gc[i], p.b[i]);
 }
 
+// ---------------------------------------------------------------- shared-memory updates
+
+__device__ __forceinline__ void fill_zero(void *smem, int bytes) {
+    float4 *p = static_cast<float4 *>(smem);
+    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------- error count
 
 __device__ __forceinline__ void flush_bad(unsigned bad, unsigned long long *err) {
@@ -179,18 +283,130 @@ __device__ __forceinline__ void flush_bad(unsigned bad, unsigned long long *err)
     if ((threadIdx.x & 31) == 0 && bad) atomicAdd(err, (unsigned long long)bad);
 }
 
-// ---------------------------------------------------------------- phases
+// ---------------------------------------------------------------- per-pixel transforms
 
-template <int J> struct Shape {
-    static constexpr int C = 1 << J;
-    static constexpr int LD = C + 1;  // padded row: thread-per-pixel access is conflict free
-};
+// 2^{n/2} and 2^{-n/2}/2 as compile-time constants
+__device__ __forceinline__ constexpr float sqrt2_pow(int n) {
+    return (n & 1 ? 1.41421356237309505f : 1.f) * (float)(1u << (n >> 1));
+}
+__device__ __forceinline__ constexpr float half_inv_sqrt2_pow(int n) { return 0.5f / sqrt2_pow(n); }
 
-__device__ __forceinline__ void fill_smem(float *a, int count, float v) {
-    for (int i = threadIdx.x; i < count; i += blockDim.x) a[i] = v;
+// One level of the bins -> coefficients tree (children at level n+1 in
+// F, G[0 .. 2^{n+1}), parents written to F, G[0 .. 2^n)).
+template <int J, int n>
+__device__ __forceinline__ void tree_level(float (&F)[1 << J], float (&G)[1 << J], float (&c)[1 << J]) {
+#pragma unroll
+    for (int k = 0; k < (1 << n); ++k) {
+        const float t = F[2 * k] + G[2 * k + 1];
+        c[(1 << n) + k] = -half_inv_sqrt2_pow(n) * t;
+        const float Fp = fmaf(0.5f, t, F[2 * k + 1]);
+        const float Gp = fmaf(0.5f, t, G[2 * k]);
+        F[k] = Fp;
+        G[k] = Gp;
+    }
+    if constexpr (n > 0) tree_level<J, n - 1>(F, G, c);
 }
 
-// Step 2 accumulation: per fragment, 2 shared-memory adds into its bin.
+// Bins (F, G) of one pixel -> Haar coefficients in heap order, and S = sum a.
+template <int J> __device__ __forceinline__ void get_row(const float *row, float (&v)[1 << J]) {
+    constexpr int C = 1 << J;
+    if constexpr (C % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+            const float4 x = reinterpret_cast<const float4 *>(row)[q];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] = row[i];
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void bins_to_coeffs(const float *Frow, const float *Grow, float (&c)[1 << J],
+                                               float &S) {
+    constexpr int C = 1 << J;
+    float F[C], G[C];
+    get_row<J>(Frow, F);
+    get_row<J>(Grow, G);
+    tree_level<J, J - 1>(F, G, c);
+    c[0] = G[0];
+    S = F[0] + G[0];
+}
+
+// One level of the synthesis: values on the 2^n intervals of level n in
+// v[0 .. 2^n) become values on the 2^{n+1} intervals of level n+1.
+template <int J, int n>
+__device__ __forceinline__ void synth_level(float (&v)[1 << J], const float (&c)[1 << J]) {
+#pragma unroll
+    for (int k = (1 << n) - 1; k >= 0; --k) {
+        const float d = sqrt2_pow(n) * c[(1 << n) + k];
+        const float base = v[k];
+        v[2 * k + 1] = base - d;
+        v[2 * k] = base + d;
+    }
+    if constexpr (n + 1 < J) synth_level<J, n + 1>(v, c);
+}
+
+// Haar synthesis at the bin centres, in place: values of the Haar series on
+// each finest bin, A_m = chi_00 + sum_n (+-) 2^{n/2} X_{n, m >> (J-n)}.
+template <int J> __device__ __forceinline__ void coeffs_to_bins(float (&v)[1 << J]) {
+    float c[1 << J];
+#pragma unroll
+    for (int i = 0; i < (1 << J); ++i) c[i] = v[i];
+    synth_level<J, 0>(v, c);
+}
+
+// Reconstruction (§2.3.2) from one pixel's bin values at s = C z, and the
+// fragment's own step there (a2 = its step in the same units as the row).
+// Linear: between bin centres, position pos = s - 1/2 in centre units,
+// clamped so that the outer half-bins are constant.  The own step has bin
+// values 0 before its bin m, 1-f in it and 1 after it.
+template <int J>
+__device__ __forceinline__ void recon(const float *A, float s, uint32_t flags, float a2, float &full,
+                                      float &self) {
+    constexpr int C = 1 << J;
+    const int m = (int)s;
+    const float f = s - (float)m;
+    if (flags & kLinear) {
+        const float pos = s - 0.5f;
+        const int lo = min(max((int)floorf(pos), 0), C - 2);
+        const float t = fminf(fmaxf(pos - (float)lo, 0.f), 1.f);
+        const float A0 = A[lo], A1 = A[lo + 1];
+        full = fmaf(t, A1 - A0, A0);
+        const float B0 = lo < m ? 0.f : (lo == m ? 1.f - f : 1.f);
+        const float B1 = lo + 1 < m ? 0.f : (lo + 1 == m ? 1.f - f : 1.f);
+        self = a2 * fmaf(t, B1 - B0, B0);
+    } else {
+        full = A[m];
+        self = a2 * (1.f - f);
+    }
+}
+
+// Absorbance in front of a fragment, in the units of A.
+template <int J>
+__device__ __forceinline__ float frag_absorbance(const float *A, float zc, float a2, uint32_t flags) {
+    float full, self;
+    recon<J>(A, zc * (float)(1 << J), flags, a2, full, self);
+    return (flags & kSelfExclude) ? fmaxf(full - self, 0.f) : full;
+}
+
+// Per-pixel weight offset m_p (log2 units): every fragment's absorbance is
+// >= m_p and the nearest one's is <= m_p + 20, so 2^(m_p - A_i) never
+// overflows and the largest weight never underflows.
+template <int J>
+__device__ __forceinline__ float weight_offset(const float *A2, float zmin, uint32_t flags) {
+    if (!(zmin < 1.f)) return 0.f;  // +inf: no fragment with alpha > 0
+    const float full = frag_absorbance<J>(A2, clamp_depth(zmin), 0.f, flags & kLinear);
+    return fmaxf(full - kStepCapLog2, 0.f);
+}
+
+// ---------------------------------------------------------------- fragment phases
+
+// Step 2 accumulation: two shared-memory adds into the fragment's bin.
 template <int J>
 __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, float *sF, float *sG,
                                            unsigned *sZ, unsigned &bad) {
@@ -217,128 +433,17 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, float
     });
 }
 
-// 2^{n/2} and 2^{-n/2}/2 as compile-time constants
-__device__ __forceinline__ constexpr float sqrt2_pow(int n) {
-    return (n & 1 ? 1.41421356237309505f : 1.f) * (float)(1u << (n >> 1));
-}
-__device__ __forceinline__ constexpr float half_inv_sqrt2_pow(int n) {
-    return 0.5f / sqrt2_pow(n);
-}
-
-// Bins (F, G) -> Haar coefficients in heap order, in place in sF.
-// C lanes per pixel (C <= 32), one shuffle tree per pixel.
-template <int J>
-__device__ __forceinline__ void phase_bins_to_coeffs(float *sF, const float *sG, int npx) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, PPW = 32 / C;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int seg = lane / C, m = lane % C;
-    for (int p0 = warp * PPW; p0 < npx; p0 += nwarps * PPW) {
-        const int px = p0 + seg;
-        const bool live = px < npx;
-        float F = live ? sF[px * LD + m] : 0.f;
-        float G = live ? sG[px * LD + m] : 0.f;
-        __syncwarp();
-#pragma unroll
-        for (int n = J - 1; n >= 0; --n) {
-            const int d = 1 << (J - 1 - n);  // lane distance between the two children
-            const float FR = __shfl_down_sync(0xffffffffu, F, d, C);
-            const float GR = __shfl_down_sync(0xffffffffu, G, d, C);
-            const float coef = -half_inv_sqrt2_pow(n) * (F + GR);
-            const float Fp = 0.5f * ((F + FR) + (FR + GR));
-            const float Gp = 0.5f * ((F + G) + (G + GR));
-            if (live && (m & (2 * d - 1)) == 0) sF[px * LD + (1 << n) + m / (2 * d)] = coef;
-            F = Fp;
-            G = Gp;
-        }
-        if (live && m == 0) sF[px * LD] = G;
-        __syncwarp();
-    }
-}
-
-// Haar synthesis at the bin centres, in place:
-// A_m = chi_00 + sum_n +-2^{n/2} X_{n, m>>(J-n)} (+ in the first half of psi's support).
-template <int J>
-__device__ __forceinline__ void phase_coeffs_to_bins(float *sC, int npx) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, PPW = 32 / C;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int seg = lane / C, m = lane % C;
-    for (int p0 = warp * PPW; p0 < npx; p0 += nwarps * PPW) {
-        const int px = p0 + seg;
-        float A = 0.f;
-        if (px < npx) {
-            const float *c = sC + px * LD;
-            A = c[0];
-#pragma unroll
-            for (int n = 0; n < J; ++n) {
-                const float d = sqrt2_pow(n) * c[(1 << n) + (m >> (J - n))];
-                A += ((m >> (J - 1 - n)) & 1) ? -d : d;
-            }
-        }
-        __syncwarp();
-        if (px < npx) sC[px * LD + m] = A;
-        __syncwarp();
-    }
-}
-
-// Reconstruction at (m, f) from bin values, and the fragment's own step there.
-// Linear: interpolate between bin centres; constant in the two outer half-bins.
-template <int J>
-__device__ __forceinline__ float recon(const float *A, int m, float f, uint32_t flags,
-                                       float a, float &self) {
-    constexpr int C = Shape<J>::C;
-    if (!(flags & kLinear)) {
-        self = a * (1.f - f);
-        return A[m];
-    }
-    if (f < 0.5f) {
-        if (m == 0) {
-            self = a * (1.f - f);
-            return A[0];
-        }
-        const float t = f + 0.5f;
-        self = a * (1.f - f) * t;
-        return fmaf(t, A[m] - A[m - 1], A[m - 1]);
-    }
-    if (m == C - 1) {
-        self = a * (1.f - f);
-        return A[C - 1];
-    }
-    const float t = f - 0.5f;
-    self = a * fmaf(1.f - f, 1.f - t, t);
-    return fmaf(t, A[m + 1] - A[m], A[m]);
-}
-
-// Absorbance in front of a fragment (§2.3.2 with the self term removed).
-template <int J>
-__device__ __forceinline__ float frag_absorbance(const float *A, float zc, float a, uint32_t flags) {
-    constexpr int C = Shape<J>::C;
-    const float s = zc * (float)C;
-    const int m = (int)s;
-    const float f = s - (float)m;
-    float self;
-    const float full = recon<J>(A, m, f, flags, a, self);
-    return (flags & kSelfExclude) ? fmaxf(full - self, 0.f) : full;
-}
-
-// Per-pixel weight offset m_p: every fragment's absorbance is >= m_p and the
-// nearest one's is <= m_p + kStepCap, so exp(m_p - A_i) never overflows and
-// the largest weight never underflows.
-template <int J>
-__device__ __forceinline__ float weight_offset(const float *A, float zmin, uint32_t flags) {
-    if (!(zmin < 1.f)) return 0.f;  // +inf: no fragment with alpha > 0
-    const float full = frag_absorbance<J>(A, clamp_depth(zmin), 0.f, flags & kLinear);
-    return fmaxf(full - kStepCap, 0.f);
-}
-
-// Step 3 (§2.1): per fragment v_i = exp(-A_i), w_i = alpha_i v_i; per pixel
-// R,G,B += c_i w_i, W += w_i, S += a_i (five shared-memory adds).  Weights
-// carry the pixel's offset m_p: w_i' = alpha_i exp(m_p - A_i).
+// Step 3 (§2.1): v_i = 2^(m_p - A_i) (log2 units), w_i = alpha_i v_i;
+// per pixel R, G, B += c w and W += w in a lane-spread copy of the
+// accumulator planes acc[5][kCopies][npx], and, when withS, S += a.
 template <int J, bool COUNT>
-__device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *sA,
-                                              const float *sMp, float *sAcc, int npx,
+__device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
+                                              const float *sMp, float *acc, bool withS, int npx,
                                               unsigned &bad) {
     constexpr int LD = Shape<J>::LD;
     const uint32_t flags = p.flags;
+    const int plane = kCopies * npx;
+    float *my = acc + ((threadIdx.x & 31) & (kCopies - 1)) * npx;
     for_each_frag6(T.s, T.e, p, [&](uint32_t px, float z, float al, float r, float g, float b) {
         if (!(z == z) || !(al == al)) {
             if (COUNT) ++bad;
@@ -351,22 +456,18 @@ __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, co
         }
         const float ac = clamp_alpha(al);
         const float a = step_of(ac);
-        const float Ah = frag_absorbance<J>(sA + lp * LD, clamp_depth(z), a, flags);
-        const float w = ac * expf(sMp[lp] - Ah);
-        atomicAdd(&sAcc[lp], r * w);
-        atomicAdd(&sAcc[npx + lp], g * w);
-        atomicAdd(&sAcc[2 * npx + lp], b * w);
-        atomicAdd(&sAcc[3 * npx + lp], w);
-        atomicAdd(&sAcc[4 * npx + lp], a);
+        const float Ah = frag_absorbance<J>(A2 + lp * LD, clamp_depth(z), a * kLog2e, flags);
+        const float w = ac * ex2(sMp[lp] - Ah);
+        float *q = my + lp;
+        atomicAdd(q, r * w);
+        atomicAdd(q + plane, g * w);
+        atomicAdd(q + 2 * plane, b * w);
+        atomicAdd(q + 3 * plane, w);
+        if (withS) atomicAdd(q + 4 * plane, a);
     });
 }
 
-// global pixel id of local pixel lp, or -1 if it lies outside the image
-__device__ __forceinline__ int64_t global_pixel(const Params &p, const Tile &T, int lp) {
-    const int lx = lp % p.g.tile_w, ly = lp / p.g.tile_w;
-    if (lx >= T.tw || ly >= T.th) return -1;
-    return (int64_t)(T.ty0 + ly) * p.g.width + T.tx0 + lx;
-}
+// ---------------------------------------------------------------- composite
 
 // Step 4 (§2.1): composite one pixel over the background.
 __device__ __forceinline__ void composite_pixel(const Params &p, int64_t gp, float R, float G,
@@ -400,88 +501,34 @@ __device__ __forceinline__ void composite_pixel(const Params &p, int64_t gp, flo
     reinterpret_cast<float4 *>(p.out)[gp] = o;
 }
 
-// Epilogue of the resolve: composite into out, or write/add accum.
-template <bool COMPOSITE>
-__device__ __forceinline__ void resolve_epilogue(const Params &p, const Tile &T, const float *sAcc,
-                                                 int npx) {
-    for (int lp = threadIdx.x; lp < npx; lp += blockDim.x) {
-        const int64_t gp = global_pixel(p, T, lp);
-        if (gp < 0) continue;
-        const float R = sAcc[lp], G = sAcc[npx + lp], B = sAcc[2 * npx + lp];
-        const float W = sAcc[3 * npx + lp], S = sAcc[4 * npx + lp];
-        if (COMPOSITE) {
-            composite_pixel(p, gp, R, G, B, W, S);
-        } else {
-            float *acc = p.accum + 5 * gp;
-            if (p.flags & kAccumulate) {
-                acc[0] += R;
-                acc[1] += G;
-                acc[2] += B;
-                acc[3] += W;
-                acc[4] += S;
-            } else {
-                acc[0] = R;
-                acc[1] = G;
-                acc[2] = B;
-                acc[3] = W;
-                acc[4] = S;
-            }
-        }
-    }
+// Sum of the kCopies copies of accumulator plane k of pixel lp.
+__device__ __forceinline__ float sum_copies(const float *acc, int npx, int k, int lp) {
+    const float *q = acc + k * kCopies * npx + lp;
+    float v = q[0];
+#pragma unroll
+    for (int c = 1; c < kCopies; ++c) v += q[c * npx];
+    return v;
 }
 
-// Coalesced tile <-> coefficient buffer copies.  Row ly of a tile is a
-// contiguous run of tw*C coefficients in the pixel-major buffer.
-template <int J, typename CT>
-__device__ __forceinline__ void load_coeffs(const Params &p, const Tile &T, float *sC) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
-    const CT *src = static_cast<const CT *>(p.coeff);
-    const int rowlen = T.tw * C;
-    for (int ly = 0; ly < T.th; ++ly) {
-        const int64_t base = ((int64_t)(T.ty0 + ly) * p.g.width + T.tx0) * C;
-        for (int e = threadIdx.x; e < rowlen; e += blockDim.x)
-            sC[(ly * p.g.tile_w + (e >> J)) * LD + (e & (C - 1))] = Cvt<CT>::from(src[base + e]);
-    }
-}
+// ---------------------------------------------------------------- shared-memory layouts (bytes)
 
-// Rounds the tile's coefficients to the storage type in place and, when
-// `store`, writes them (adding the stored values first when `accumulate`).
-template <int J, typename CT>
-__device__ __forceinline__ void round_store_coeffs(const Params &p, const Tile &T, float *sC,
-                                                   bool store, bool accumulate) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
-    CT *dst = static_cast<CT *>(p.coeff);
-    const int rowlen = T.tw * C;
-    for (int ly = 0; ly < T.th; ++ly) {
-        const int64_t base = ((int64_t)(T.ty0 + ly) * p.g.width + T.tx0) * C;
-        for (int e = threadIdx.x; e < rowlen; e += blockDim.x) {
-            float *slot = &sC[(ly * p.g.tile_w + (e >> J)) * LD + (e & (C - 1))];
-            float v = *slot;
-            if (accumulate) v += Cvt<CT>::from(dst[base + e]);
-            const CT q = Cvt<CT>::to(v);
-            *slot = Cvt<CT>::from(q);
-            if (store) dst[base + e] = q;
-        }
-    }
-}
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__device__ __forceinline__ void store_zmin(const Params &p, const Tile &T, const unsigned *sZ,
-                                           int npx, bool accumulate) {
-    for (int lp = threadIdx.x; lp < npx; lp += blockDim.x) {
-        const int64_t gp = global_pixel(p, T, lp);
-        if (gp < 0) continue;
-        float v = __uint_as_float(sZ[lp]);
-        if (accumulate) v = fminf(v, p.zmin[gp]);
-        p.zmin[gp] = v;
+// Every region starts on a 16-byte boundary (float4 row reads and writes).
+template <int J> struct Layout {
+    static constexpr size_t plane(int npx) { return align16((size_t)npx * Shape<J>::LD * 4); }
+    static constexpr size_t words(int npx) { return align16((size_t)npx * 4); }
+    // accumulator planes R, G, B, W (and S), kCopies copies each
+    static constexpr size_t acc(int npx, int planes) { return (size_t)planes * kCopies * words(npx); }
+    static constexpr size_t region(int npx) {
+        return 2 * plane(npx) > plane(npx) + acc(npx, 4) ? 2 * plane(npx) : plane(npx) + acc(npx, 4);
     }
-}
-
-// Shared-memory footprints (floats), shared by kernels and launchers.
-template <int J> struct Smem {
-    // build / fused: F and G rows + nearest-depth word per pixel
-    static constexpr size_t bins(int npx) { return (size_t)(2 * npx * Shape<J>::LD + npx); }
-    // resolve: coefficient/bin rows + m_p + 5 accumulators per pixel
-    static constexpr size_t resolve(int npx) { return (size_t)(npx * Shape<J>::LD + 6 * npx); }
+    // build: F and G bins + nearest-depth words
+    static constexpr size_t build(int npx) { return 2 * plane(npx) + words(npx); }
+    // fused: F, G bins, later bin values + accumulators; then S, m_p, depth words
+    static constexpr size_t fused(int npx) { return region(npx) + 3 * words(npx); }
+    // resolve: bin values + R, G, B, W, S accumulators + m_p
+    static constexpr size_t resolve(int npx) { return plane(npx) + acc(npx, 5) + words(npx); }
 };
 
 }  // namespace wt
