@@ -199,6 +199,24 @@ wt_status wt_absorbance(const wt_desc *desc, const void *coeff, int64_t q, const
                         const float *z, const float *alpha, float *A_out, wt_stream stream);
 
 /*
+ * wt_backward -- adjoint of wt_build_resolve (the paper has no gradient; this
+ * follows from the linearity of the coefficients in the steps, §2.3.1).
+ * Given dL/d(out) it returns dL/d(alpha) and dL/d(r, g, b) for every
+ * fragment, treating depth as fixed.  Coefficients are rebuilt inside the
+ * call from the fragments (nothing from the forward pass is stored), with the
+ * same desc (J, storage rounding, flags) and background as the forward call.
+ *   grad_out   [P * 4] float, dL/d(out RGBA).
+ *   grad_alpha [n] float, written; 0 where alpha is clamped (<= 0 or
+ *              >= 1 - 2^-20) and for rejected fragments.
+ *   grad_rgb   [3 * n] float, planar: dL/dr at [0, n), dL/dg at [n, 2n),
+ *              dL/db at [2n, 3n).
+ * The pixel-level sums use FP32; WT_ACCUMULATE is not supported.
+ */
+wt_status wt_backward(const wt_desc *desc, const wt_frags *frags, const float *bg_img,
+                      const float bg[3], const float *grad_out, float *grad_alpha,
+                      float *grad_rgb, wt_stream stream);
+
+/*
  * wt_get_error -- synchronises `stream`, then returns in *bad_count the
  * number of fragments (or queries, or tile ranges) rejected by any call on the
  * current device since the previous wt_get_error, and clears the count.

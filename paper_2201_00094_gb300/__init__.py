@@ -23,7 +23,7 @@ __all__ = [
     "DEFAULT_FLAGS", "WtDesc", "WtFrags", "WtError", "lib", "library_path", "make_desc",
     "make_frags", "coeff_torch_dtype", "wt_version", "wt_coeff_bytes", "wt_num_tiles", "wt_build",
     "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
-    "wt_get_error",
+    "wt_get_error", "wt_backward", "WaveletOIT",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -219,6 +220,44 @@ def wt_absorbance(desc: WtDesc, coeff: torch.Tensor, pixel: torch.Tensor, z: tor
           _dev(pixel, "pixel", (torch.int32, torch.uint32)), _dev(z, "z", (torch.float32,)),
           _dev(alpha, "alpha", (torch.float32,)), _dev(A_out, "A_out", (torch.float32,)),
           _stream(stream))
+
+
+def wt_backward(desc: WtDesc, frags: WtFrags, grad_out: torch.Tensor, grad_alpha: torch.Tensor,
+                grad_rgb: torch.Tensor, bg: Sequence[float] = (0.5, 0.5, 0.5),
+                bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+    """grad_rgb is planar [3, n]."""
+    _call("wt_backward", ctypes.byref(desc), ctypes.byref(frags),
+          _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg),
+          _dev(grad_out, "grad_out", (torch.float32,)),
+          _dev(grad_alpha, "grad_alpha", (torch.float32,)),
+          _dev(grad_rgb, "grad_rgb", (torch.float32,)), _stream(stream))
+
+
+class WaveletOIT(torch.autograd.Function):
+    """Differentiable composite: out [P, 4] = wt_build_resolve(fragments), with
+    gradients for alpha and the colour planes from wt_backward (depth, pixel
+    ids and tile offsets are not differentiated).  Arguments:
+    (pixel, z, alpha, r, g, b, tile_offsets, desc, bg)."""
+
+    @staticmethod
+    def forward(ctx, pixel, z, alpha, r, g, b, tile_offsets, desc, bg=(0.5, 0.5, 0.5)):
+        frags = make_frags(pixel, z, alpha, tile_offsets, r, g, b)
+        out = torch.empty(desc.P, 4, device=z.device, dtype=torch.float32)
+        wt_build_resolve(desc, frags, out, None, None, bg=bg)
+        ctx.save_for_backward(pixel, z, alpha, r, g, b, tile_offsets)
+        ctx.desc = desc
+        ctx.bg = tuple(bg)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        pixel, z, alpha, r, g, b, tile_offsets = ctx.saved_tensors
+        frags = make_frags(pixel, z, alpha, tile_offsets, r, g, b)
+        n = z.numel()
+        ga = torch.empty(n, device=z.device, dtype=torch.float32)
+        gc = torch.empty(3, n, device=z.device, dtype=torch.float32)
+        wt_backward(ctx.desc, frags, grad_out.contiguous().float(), ga, gc, bg=ctx.bg)
+        return None, None, ga, gc[0], gc[1], gc[2], None, None, None
 
 
 def wt_get_error(stream=None) -> int:

@@ -240,6 +240,25 @@ wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, flo
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
+wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, const float bg[3],
+                      const float *grad_out, float *grad_alpha, float *grad_rgb, wt_stream stream) {
+    wt_status st = check_desc(d);
+    if (st != WT_OK) return st;
+    if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
+    if ((st = check_frags(f, true)) != WT_OK) return st;
+    if (!grad_out || !aligned(grad_out, 16)) return WT_ERR_ARG;
+    if (f->n > 0 && (!grad_alpha || !grad_rgb)) return WT_ERR_ARG;
+    if (!aligned(grad_alpha, 4) || !aligned(grad_rgb, 4)) return WT_ERR_ARG;
+    Params p = make_params(d, f);
+    if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
+    p.gout = grad_out;
+    p.galpha = grad_alpha;
+    p.grgb = grad_rgb;
+    if (!(p.err = err_word())) return WT_ERR_CUDA;
+    const TileLaunch *t = table(kBackward0, kBackward1, kBackward2, d->coeff_dtype);
+    return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
+}
+
 wt_status wt_absorbance(const wt_desc *d, const void *coeff, int64_t q, const uint32_t *pixel,
                         const float *z, const float *alpha, float *A_out, wt_stream stream) {
     wt_status st = check_desc(d);

@@ -18,6 +18,7 @@ extern const TileLaunch kBuild0[5], kBuild1[5], kBuild2[5];
 extern const TileLaunch kResolve0[5], kResolve1[5], kResolve2[5];
 extern const TileLaunch kResolveComp0[5], kResolveComp1[5], kResolveComp2[5];
 extern const TileLaunch kFused0[5], kFused1[5], kFused2[5];
+extern const TileLaunch kBackward0[5], kBackward1[5], kBackward2[5];
 extern const QueryLaunch kAbsorbance0[5], kAbsorbance1[5], kAbsorbance2[5];
 
 }  // namespace wt

@@ -50,20 +50,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
     }
 }
 
-// Writes one pixel's bin values (log2 units) into its shared row.
-template <int J> __device__ __forceinline__ void put_vals(float *row, const float (&v)[1 << J]) {
-    constexpr int C = 1 << J;
-    if constexpr (C % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < C / 4; ++q)
-            reinterpret_cast<float4 *>(row)[q] =
-                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < C; ++i) row[i] = v[i];
-    }
-}
-
 // §2.1 step 3 (+ step 4 when COMPOSITE): resolve against stored coefficients.
 template <int J, typename CT, bool COMPOSITE>
 __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Params p) {
@@ -71,8 +57,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
     float *vals = reinterpret_cast<float *>(smem);
-    float *acc = reinterpret_cast<float *>(smem + Layout<J>::plane(npx));
-    float *sMp = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::acc(npx, 5));
+    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
+    float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
     const Tile T = tile_of(p, blockIdx.x, true);
     const int lp = threadIdx.x;
     int64_t gp = -1;
@@ -83,36 +69,33 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
         coeffs_to_bins<J>(v);
 #pragma unroll
         for (int i = 0; i < C; ++i) v[i] *= kLog2e;
-        put_vals<J>(vals + lp * LD, v);
-        const bool use_offset = (p.flags & kNormalized) && p.zmin;
-        sMp[lp] = use_offset ? weight_offset<J>(vals + lp * LD, p.zmin[gp], p.flags) : 0.f;
+        put_bins<J>(vals + lp * LD, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000), p.flags);
     }
-    fill_zero(acc, (int)Layout<J>::acc(npx, 5));
+    fill_zero(accw, (int)(Layout<J>::accw(npx) + Layout<J>::words(npx)));
     __syncthreads();
     unsigned bad = 0;
-    phase_resolve<J, true>(p, T, vals, sMp, acc, true, npx, bad);
+    phase_resolve<J, true>(p, T, vals, accw, sS, bad);
     flush_bad(bad, p.err);
     __syncthreads();
     if (gp < 0) return;
-    const float R = sum_copies(acc, npx, 0, lp), G = sum_copies(acc, npx, 1, lp);
-    const float B = sum_copies(acc, npx, 2, lp), W = sum_copies(acc, npx, 3, lp);
-    const float S = sum_copies(acc, npx, 4, lp);
+    const float4 a = sum_warps(accw, npx, lp);
+    const float S = sS[lp];
     if (COMPOSITE) {
-        composite_pixel(p, gp, R, G, B, W, S);
+        composite_pixel(p, gp, a.x, a.y, a.z, a.w, S);
     } else {
-        float *a = p.accum + 5 * gp;
+        float *o = p.accum + 5 * gp;
         if (p.flags & kAccumulate) {
-            a[0] += R;
-            a[1] += G;
-            a[2] += B;
-            a[3] += W;
-            a[4] += S;
+            o[0] += a.x;
+            o[1] += a.y;
+            o[2] += a.z;
+            o[3] += a.w;
+            o[4] += S;
         } else {
-            a[0] = R;
-            a[1] = G;
-            a[2] = B;
-            a[3] = W;
-            a[4] = S;
+            o[0] = a.x;
+            o[1] = a.y;
+            o[2] = a.z;
+            o[3] = a.w;
+            o[4] = S;
         }
     }
 }
@@ -125,12 +108,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params 
     const int npx = p.g.tile_w * p.g.tile_h;
     float *sF = reinterpret_cast<float *>(smem);
     float *sG = reinterpret_cast<float *>(smem + Layout<J>::plane(npx));
-    float *vals = sF;  // the bin values replace the F bins after the barrier
-    float *acc = sG;   // the accumulators replace the G bins
-    float *sS = reinterpret_cast<float *>(smem + Layout<J>::region(npx));
-    float *sMp = reinterpret_cast<float *>(smem + Layout<J>::region(npx) + Layout<J>::words(npx));
-    unsigned *sZ =
-        reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx) + 2 * Layout<J>::words(npx));
+    // after the build: bin values over the F bins, then the warps'
+    // accumulators and the S words over the G bins
+    float *vals = sF;
+    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
+    float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
+    unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
     const Tile T = tile_of(p, blockIdx.x, true);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
@@ -155,19 +138,224 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params 
     }
     __syncthreads();  // every bin row has been read
     if (gp >= 0) {
-        put_vals<J>(vals + lp * LD, v);
+        put_bins<J>(vals + lp * LD, v, __uint_as_float(sZ[lp]), p.flags);
         sS[lp] = S;
-        sMp[lp] = (p.flags & kNormalized)
-                      ? weight_offset<J>(vals + lp * LD, __uint_as_float(sZ[lp]), p.flags)
-                      : 0.f;
     }
-    fill_zero(acc, (int)Layout<J>::acc(npx, 4));
+    fill_zero(accw, (int)Layout<J>::accw(npx));
     __syncthreads();
-    phase_resolve<J, false>(p, T, vals, sMp, acc, false, npx, bad);
+    phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);
     __syncthreads();
     if (gp < 0) return;
-    composite_pixel(p, gp, sum_copies(acc, npx, 0, lp), sum_copies(acc, npx, 1, lp),
-                    sum_copies(acc, npx, 2, lp), sum_copies(acc, npx, 3, lp), sS[lp]);
+    const float4 a = sum_warps(accw, npx, lp);
+    composite_pixel(p, gp, a.x, a.y, a.z, a.w, sS[lp]);
+}
+
+// ---------------------------------------------------------------- adjoint
+
+// Shared-memory layout of the adjoint: F, G bins; later the bin values, the
+// warps' accumulators and then the scattered adjoint bins Gamma; then nine
+// per-pixel words (depth, S, u[3], ybar[3], const).
+template <int J> struct BackLayout {
+    static constexpr size_t P(int npx) { return Layout<J>::plane(npx); }
+    static constexpr size_t W(int npx) { return Layout<J>::words(npx); }
+    static constexpr size_t second(int npx) {
+        return Layout<J>::accw(npx) > P(npx) ? Layout<J>::accw(npx) : P(npx);
+    }
+    static constexpr size_t region(int npx) {
+        return 2 * P(npx) > P(npx) + second(npx) ? 2 * P(npx) : P(npx) + second(npx);
+    }
+    static constexpr size_t total(int npx) { return region(npx) + 9 * W(npx); }
+};
+
+// Re-derives everything the adjoint needs about one fragment from its inputs
+// and the pixel's bin values (log2 units, shifted by m_p): local pixel (or -1),
+// clamped alpha, step a, position q, and weight w = alpha 2^-A'.
+template <int J> struct FragState {
+    int lp;
+    float ac, a, w;
+    Pos q;
+};
+template <int J>
+__device__ __forceinline__ FragState<J> frag_state(const Params &p, const Tile &T, const float *vals,
+                                                   uint32_t px, float z, float al) {
+    FragState<J> st;
+    st.lp = -1;
+    if (!(z == z) || !(al == al)) return st;
+    st.lp = local_pixel(px, p, T);
+    if (st.lp < 0) return st;
+    st.ac = clamp_alpha(al);
+    st.a = step_of(st.ac);
+    st.q = locate<J>(clamp_depth(z) * (float)(1 << J), p.flags);
+    const float full = recon_at<J>(vals + st.lp * Shape<J>::LD, st.q, p.flags);
+    const float Ah = (p.flags & kSelfExclude) ? fmaxf(full - st.a * kLog2e * st.q.g, 0.f) : full;
+    st.w = st.ac * ex2(-Ah);
+    return st;
+}
+
+// Adjoint of build + resolve + composite (no counterpart in the paper; it
+// follows from the linearity of the closed-form coefficients of §2.3.1).
+// With g = dL/d(out) per pixel: u = g_rgb (1-T)/W and ybar = R/W (normalised;
+// u = g_rgb, ybar = 0 literal), tau = g_rgb.(bg - ybar) - g_a.  Per fragment
+// beta = u.(c - ybar), gamma = dL/dA = -beta w, dL/dc = u w.  Since
+// A_i = sum_j a_j K(z_i, z_j) with K the reconstruction at z_i of a unit step
+// at z_j, dL/da_j = sum_i gamma_i K(z_i, z_j) - T tau, and the sum is
+// sum_m Gamma_m B^(j)_m with Gamma the gammas scattered into the bins with the
+// interpolation weights and B^(j) the unit step's bin values (0, 1-f, 1):
+// with the inclusive suffix Q_m = sum_{m'>=m} Gamma_m', it is
+// (1 - f_j) Q_{m_j} + f_j Q_{m_j+1}; self-exclusion removes gamma_j g_j.
+// dL/dalpha = beta 2^-A' + (dL/da) / (1 - alpha) inside the clamp, else 0.
+// Coefficients are rebuilt here (never stored between the passes).
+template <int J, typename CT>
+__global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
+    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int npx = p.g.tile_w * p.g.tile_h;
+    const size_t PL = Layout<J>::plane(npx), WD = Layout<J>::words(npx);
+    float *sF = reinterpret_cast<float *>(smem);
+    float *sG = reinterpret_cast<float *>(smem + PL);
+    float *vals = sF;
+    float4 *accw = reinterpret_cast<float4 *>(smem + PL);
+    float *gam = reinterpret_cast<float *>(smem + PL);  // replaces the accumulators
+    unsigned char *wbase = smem + BackLayout<J>::region(npx);
+    unsigned *sZ = reinterpret_cast<unsigned *>(wbase);
+    float *sS = reinterpret_cast<float *>(wbase + WD);
+    float *sU = reinterpret_cast<float *>(wbase + 2 * WD);  // 3 planes
+    float *sY = reinterpret_cast<float *>(wbase + 5 * WD);  // 3 planes
+    float *sK = reinterpret_cast<float *>(wbase + 8 * WD);
+    const int wpl = (int)(WD / 4);  // floats per word plane
+    const Tile T = tile_of(p, blockIdx.x, true);
+    fill_zero(smem, (int)(2 * PL));
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
+    __syncthreads();
+    unsigned bad = 0;
+    phase_bins<J>(p, T, sF, sG, sZ, bad);
+    flush_bad(bad, p.err);
+    __syncthreads();
+    const int lp = threadIdx.x;
+    int64_t gp = -1;
+    if (lp < npx) gp = global_pixel(p, T, lp);
+    float v[C], S = 0.f;
+    if (gp >= 0) {
+        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S);
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(Cvt<CT>::to(v[i]));
+        coeffs_to_bins<J>(v);
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] *= kLog2e;
+    }
+    __syncthreads();
+    if (gp >= 0) {
+        put_bins<J>(vals + lp * LD, v, __uint_as_float(sZ[lp]), p.flags);
+        sS[lp] = S;
+    }
+    fill_zero(accw, (int)Layout<J>::accw(npx));
+    __syncthreads();
+    phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);  // forward sums, recomputed
+    __syncthreads();
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gp >= 0) acc = sum_warps(accw, npx, lp);
+    __syncthreads();  // accumulators consumed; their space becomes Gamma
+    if (gp >= 0) {
+        const float Tt = expf(-S), cover = -expm1f(-S);
+        const float *go = p.gout + 4 * gp;
+        float bgc[3] = {p.bg0, p.bg1, p.bg2};
+        if (p.bg_img) {
+            bgc[0] = p.bg_img[3 * gp];
+            bgc[1] = p.bg_img[3 * gp + 1];
+            bgc[2] = p.bg_img[3 * gp + 2];
+        }
+        const float Rc[3] = {acc.x, acc.y, acc.z};
+        float tau = -go[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            float u = 0.f, y = 0.f;
+            if (p.flags & kNormalized) {
+                if (acc.w > 0.f) {
+                    u = go[ch] * cover / acc.w;
+                    y = Rc[ch] / acc.w;
+                    tau += go[ch] * (bgc[ch] - y);
+                }
+            } else {
+                u = go[ch];
+                tau += go[ch] * bgc[ch];
+            }
+            sU[ch * wpl + lp] = u;
+            sY[ch * wpl + lp] = y;
+        }
+        sK[lp] = -Tt * tau;
+    }
+    fill_zero(gam, (int)PL);
+    __syncthreads();
+    const uint32_t flags = p.flags;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // pass 3: colour gradients and the scatter of gamma into the bins
+    for (int64_t i = T.s + tid; i < T.e; i += nt) {
+        const FragState<J> st = frag_state<J>(p, T, vals, p.pixel[i], p.z[i], p.alpha[i]);
+        if (st.lp < 0) {
+            p.grgb[i] = 0.f;
+            p.grgb[p.n + i] = 0.f;
+            p.grgb[2 * p.n + i] = 0.f;
+            continue;
+        }
+        const float c[3] = {p.r[i], p.gc[i], p.b[i]};
+        float beta = 0.f;
+        for (int ch = 0; ch < 3; ++ch) {
+            const float u = sU[ch * wpl + st.lp];
+            beta = fmaf(u, c[ch] - sY[ch * wpl + st.lp], beta);
+            p.grgb[ch * p.n + i] = u * st.w;
+        }
+        const float gamma = -beta * st.w;
+        float *row = gam + st.lp * LD;
+        if (flags & kLinear) {
+            atomicAdd(&row[st.q.lo], gamma * (1.f - st.q.t));
+            atomicAdd(&row[st.q.lo + 1], gamma * st.q.t);
+        } else {
+            atomicAdd(&row[st.q.m], gamma);
+        }
+    }
+    __syncthreads();
+    if (gp >= 0) {  // inclusive suffix sums Q_m, with Q_C = 0
+        float *row = gam + lp * LD;
+        float acc_s = 0.f;
+        row[C] = 0.f;
+        for (int m = C - 1; m >= 0; --m) {
+            acc_s += row[m];
+            row[m] = acc_s;
+        }
+    }
+    __syncthreads();
+    // pass 4: opacity gradients
+    for (int64_t i = T.s + tid; i < T.e; i += nt) {
+        const float al = p.alpha[i];
+        const FragState<J> st = frag_state<J>(p, T, vals, p.pixel[i], p.z[i], al);
+        if (st.lp < 0) {
+            p.galpha[i] = 0.f;
+            continue;
+        }
+        const float c[3] = {p.r[i], p.gc[i], p.b[i]};
+        float beta = 0.f;
+        for (int ch = 0; ch < 3; ++ch)
+            beta = fmaf(sU[ch * wpl + st.lp], c[ch] - sY[ch * wpl + st.lp], beta);
+        const float gamma = -beta * st.w;
+        const float *Q = gam + st.lp * LD;
+        float da = fmaf(st.q.f, Q[st.q.m + 1], (1.f - st.q.f) * Q[st.q.m]);
+        if (flags & kSelfExclude) da -= gamma * st.q.g;
+        da += sK[st.lp];
+        float g = 0.f;
+        if (al > 0.f && al < kAlphaMax) {
+            const float direct = st.ac > 0.f ? beta * (st.w / st.ac) : 0.f;
+            g = direct + da / (1.f - al);
+        }
+        p.galpha[i] = g;
+    }
+}
+
+template <int J, typename CT> cudaError_t launch_backward_t(const Params &p, int ntiles, cudaStream_t s) {
+    const int npx = p.g.tile_w * p.g.tile_h;
+    const size_t bytes = BackLayout<J>::total(npx);
+    cudaError_t e = cudaFuncSetAttribute(k_backward<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_backward<J, CT><<<ntiles, kThreads, bytes, s>>>(p);
+    return cudaGetLastError();
 }
 
 // Evaluation at arbitrary (pixel, depth) queries: J+1 coefficient reads per
@@ -275,6 +463,9 @@ cudaError_t launch_absorbance_t(const Params &p, int64_t q, const uint32_t *qpx,
     const TileLaunch kFused##IDX[5] = {launch_fused_t<1, CT>, launch_fused_t<2, CT>,               \
                                        launch_fused_t<3, CT>, launch_fused_t<4, CT>,               \
                                        launch_fused_t<5, CT>};                                     \
+    const TileLaunch kBackward##IDX[5] = {launch_backward_t<1, CT>, launch_backward_t<2, CT>,     \
+                                          launch_backward_t<3, CT>, launch_backward_t<4, CT>,     \
+                                          launch_backward_t<5, CT>};                              \
     const QueryLaunch kAbsorbance##IDX[5] = {                                                      \
         launch_absorbance_t<1, CT>, launch_absorbance_t<2, CT>, launch_absorbance_t<3, CT>,       \
         launch_absorbance_t<4, CT>, launch_absorbance_t<5, CT>};                                   \

@@ -22,10 +22,13 @@
 // values at the bin centres (§2.3.2), kept in shared memory pre-multiplied by
 // log2(e), so a fragment's transmittance is one ex2 instruction.
 //
-// Shared-memory accumulation uses FP32 atomic adds on structure-of-arrays
-// planes (F and G bins; R, G, B, W accumulators) so that the lanes of a warp
-// spread over all 32 banks; the per-pixel accumulators are further spread
-// over kCopies lane-indexed copies so that lanes rarely contend for a word.
+// The build's bins take FP32 shared-memory atomic adds (separate F and G
+// planes, so a warp's lanes spread over the banks).  The resolve's per-pixel
+// sums use a warp-segmented reduction instead of atomics: the lanes of a warp
+// that hold the same pixel are grouped (match.any), the group's leader adds
+// its peers' values through shuffles and applies one plain read-modify-write
+// to the warp's private copy of the accumulators; the copies are summed per
+// pixel at the end of the tile.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,7 +40,7 @@ namespace wt {
 
 constexpr int kThreads = 256;    // threads per CTA (= max pixels per tile)
 constexpr int kMaxTilePx = 256;
-constexpr int kCopies = 4;       // lane-spread copies of the per-pixel accumulators
+constexpr int kWarps = kThreads / 32;  // warp-private copies of the per-pixel accumulators
 constexpr int kCasLimit = 1 << 20;  // bound on CAS retries (never reached in practice)
 // alpha is clamped to [0, 1 - 2^-20] and z to [0, 1 - 2^-24] (exact in FP32)
 constexpr float kAlphaMax = 0.99999904632568359375f;
@@ -70,6 +73,10 @@ struct Params {
     const float *__restrict__ bg_img;
     float bg0, bg1, bg2;
     unsigned long long *err;
+    // adjoint: dL/d(out) [P*4] in, dL/dalpha [n] and dL/d(r,g,b) [3*n] out
+    const float *__restrict__ gout;
+    float *galpha;
+    float *grgb;
 };
 
 enum : uint32_t { kSelfExclude = 1u, kLinear = 2u, kNormalized = 4u, kAccumulate = 8u };
@@ -221,7 +228,8 @@ __device__ __forceinline__ float step_of(float x) {
 
 // ---------------------------------------------------------------- streaming
 
-// Calls body(pixel, z, alpha) for every fragment of [s, e), 4 per 16-byte load.
+// Calls body(pixel, z, alpha) for every fragment of [s, e), 4 per 16-byte load;
+// the loads of the next chunk are issued before the current one is processed.
 template <class Body>
 __device__ __forceinline__ void for_each_frag3(int64_t s, int64_t e, const Params &p, Body &&body) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -231,42 +239,89 @@ __device__ __forceinline__ void for_each_frag3(int64_t s, int64_t e, const Param
     const uint4 *px4 = reinterpret_cast<const uint4 *>(p.pixel);
     const float4 *z4 = reinterpret_cast<const float4 *>(p.z);
     const float4 *a4 = reinterpret_cast<const float4 *>(p.alpha);
-    for (int64_t q = (s4 >> 2) + tid; q < (e4 >> 2); q += nt) {
-        const uint4 pv = px4[q];
-        const float4 zv = z4[q];
-        const float4 av = a4[q];
-        body(pv.x, zv.x, av.x);
-        body(pv.y, zv.y, av.y);
-        body(pv.z, zv.z, av.z);
-        body(pv.w, zv.w, av.w);
+    {
+        const int64_t qe = e4 >> 2;
+        int64_t q = (s4 >> 2) + tid;
+        uint4 pv = make_uint4(0, 0, 0, 0);
+        float4 zv = make_float4(0.f, 0.f, 0.f, 0.f), av = zv;
+        if (q < qe) {
+            pv = px4[q];
+            zv = z4[q];
+            av = a4[q];
+        }
+        while (q < qe) {
+            const uint4 cp = pv;
+            const float4 cz = zv, ca = av;
+            const int64_t qn = q + nt;
+            if (qn < qe) {  // next chunk in flight while this one is processed
+                pv = px4[qn];
+                zv = z4[qn];
+                av = a4[qn];
+            }
+            body(cp.x, cz.x, ca.x);
+            body(cp.y, cz.y, ca.y);
+            body(cp.z, cz.z, ca.z);
+            body(cp.w, cz.w, ca.w);
+            q = qn;
+        }
     }
     for (int64_t i = e4 + tid; i < e; i += nt) body(p.pixel[i], p.z[i], p.alpha[i]);
 }
 
-// Same with colour: body(pixel, z, alpha, r, g, b).
+// With colour: body(valid, pixel, z, alpha, r, g, b).  Trip counts are the
+// same for every lane of the block (lanes past the range get valid = false),
+// so the body may use warp-wide collectives.
 template <class Body>
 __device__ __forceinline__ void for_each_frag6(int64_t s, int64_t e, const Params &p, Body &&body) {
     const int tid = threadIdx.x, nt = blockDim.x;
     int64_t s4 = (s + 3) & ~int64_t(3), e4 = e & ~int64_t(3);
     if (s4 > e4) s4 = e4 = e;
-    for (int64_t i = s + tid; i < s4; i += nt)
-        body(p.pixel[i], p.z[i], p.alpha[i], p.r[i], p.gc[i], p.b[i]);
+    for (int64_t b0 = s; b0 < s4; b0 += nt) {
+        const int64_t i = b0 + tid;
+        const bool v = i < s4;
+        body(v, v ? p.pixel[i] : 0u, v ? p.z[i] : 0.f, v ? p.alpha[i] : 0.f, v ? p.r[i] : 0.f,
+             v ? p.gc[i] : 0.f, v ? p.b[i] : 0.f);
+    }
     const uint4 *px4 = reinterpret_cast<const uint4 *>(p.pixel);
     const float4 *z4 = reinterpret_cast<const float4 *>(p.z);
     const float4 *a4 = reinterpret_cast<const float4 *>(p.alpha);
     const float4 *r4 = reinterpret_cast<const float4 *>(p.r);
     const float4 *g4 = reinterpret_cast<const float4 *>(p.gc);
     const float4 *b4 = reinterpret_cast<const float4 *>(p.b);
-    for (int64_t q = (s4 >> 2) + tid; q < (e4 >> 2); q += nt) {
-        const uint4 pv = px4[q];
-        const float4 zv = z4[q], av = a4[q], rv = r4[q], gv = g4[q], bv = b4[q];
-        body(pv.x, zv.x, av.x, rv.x, gv.x, bv.x);
-        body(pv.y, zv.y, av.y, rv.y, gv.y, bv.y);
-        body(pv.z, zv.z, av.z, rv.z, gv.z, bv.z);
-        body(pv.w, zv.w, av.w, rv.w, gv.w, bv.w);
+    const int64_t qe = e4 >> 2;
+    {
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t q = (s4 >> 2) + tid;
+        bool v = q < qe;
+        uint4 pv = v ? px4[q] : make_uint4(0, 0, 0, 0);
+        float4 zv = v ? z4[q] : zero, av = v ? a4[q] : zero, rv = v ? r4[q] : zero;
+        float4 gv = v ? g4[q] : zero, bv = v ? b4[q] : zero;
+        for (int64_t q0 = s4 >> 2; q0 < qe; q0 += nt) {
+            const uint4 cp = pv;
+            const float4 cz = zv, ca = av, cr = rv, cg = gv, cb = bv;
+            const bool cv = v;
+            q += nt;
+            v = q < qe;
+            if (v) {  // next chunk in flight while this one is processed
+                pv = px4[q];
+                zv = z4[q];
+                av = a4[q];
+                rv = r4[q];
+                gv = g4[q];
+                bv = b4[q];
+            }
+            body(cv, cp.x, cz.x, ca.x, cr.x, cg.x, cb.x);
+            body(cv, cp.y, cz.y, ca.y, cr.y, cg.y, cb.y);
+            body(cv, cp.z, cz.z, ca.z, cr.z, cg.z, cb.z);
+            body(cv, cp.w, cz.w, ca.w, cr.w, cg.w, cb.w);
+        }
     }
-    for (int64_t i = e4 + tid; i < e; i += nt)
-        body(p.pixel[i], p.z[i], p.alpha[i], p.r[i], p.gc[i], p.b[i]);
+    for (int64_t b0 = e4; b0 < e; b0 += nt) {
+        const int64_t i = b0 + tid;
+        const bool v = i < e;
+        body(v, v ? p.pixel[i] : 0u, v ? p.z[i] : 0.f, v ? p.alpha[i] : 0.f, v ? p.r[i] : 0.f,
+             v ? p.gc[i] : 0.f, v ? p.b[i] : 0.f);
+    }
 }
 
 // ---------------------------------------------------------------- shared-memory updates
@@ -274,6 +329,42 @@ __device__ __forceinline__ void for_each_frag6(int64_t s, int64_t e, const Param
 __device__ __forceinline__ void fill_zero(void *smem, int bytes) {
     float4 *p = static_cast<float4 *>(smem);
     for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Warp-segmented reduction by pixel: adds v into mine[lp] for every lane with
+// lp >= 0.  Called by all 32 lanes together.  Lanes holding the same pixel
+// are grouped; the lowest lane of each group gathers its peers' values one
+// shuffle round at a time (as many rounds as the largest group has extra
+// members, usually 0 or 1) and then updates the warp's own copy, so no two
+// lanes touch one word and no atomic is needed.
+__device__ __forceinline__ void warp_accumulate(float4 *mine, int lp, float4 v) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, lp);
+    const bool leader = lane == (unsigned)(__ffs(peers) - 1);
+    unsigned todo = (leader && lp >= 0) ? (peers & ~(1u << lane)) : 0u;
+    while (__any_sync(0xffffffffu, todo != 0u)) {
+        const int src = todo ? __ffs(todo) - 1 : (int)lane;
+        const float x = __shfl_sync(0xffffffffu, v.x, src);
+        const float y = __shfl_sync(0xffffffffu, v.y, src);
+        const float z = __shfl_sync(0xffffffffu, v.z, src);
+        const float w = __shfl_sync(0xffffffffu, v.w, src);
+        if (todo) {
+            v.x += x;
+            v.y += y;
+            v.z += z;
+            v.w += w;
+            todo &= todo - 1;
+        }
+    }
+    if (leader && lp >= 0) {
+        float4 o = mine[lp];
+        o.x += v.x;
+        o.y += v.y;
+        o.z += v.z;
+        o.w += v.w;
+        mine[lp] = o;
+    }
+    __syncwarp();  // the next call's readers see this write
 }
 
 // ---------------------------------------------------------------- error count
@@ -360,38 +451,51 @@ template <int J> __device__ __forceinline__ void coeffs_to_bins(float (&v)[1 << 
     synth_level<J, 0>(v, c);
 }
 
-// Reconstruction (§2.3.2) from one pixel's bin values at s = C z, and the
-// fragment's own step there (a2 = its step in the same units as the row).
-// Linear: between bin centres, position pos = s - 1/2 in centre units,
-// clamped so that the outer half-bins are constant.  The own step has bin
-// values 0 before its bin m, 1-f in it and 1 after it.
-template <int J>
-__device__ __forceinline__ void recon(const float *A, float s, uint32_t flags, float a2, float &full,
-                                      float &self) {
+// Where a depth falls for the reconstruction of §2.3.2, from s = C z:
+// bin m and fraction f; the interpolation segment lo (between the centres of
+// bins lo and lo+1) and weight t; and g, the fragment's own unit step
+// reconstructed at its own depth (its bin values are 0 before bin m, 1-f in
+// it and 1 after it).  Linear: position pos = s - 1/2 in centre units,
+// clamped so that the outer half-bins are constant.  Staircase: the bin value.
+struct Pos {
+    int m, lo;
+    float f, t, g;
+};
+template <int J> __device__ __forceinline__ Pos locate(float s, uint32_t flags) {
     constexpr int C = 1 << J;
-    const int m = (int)s;
-    const float f = s - (float)m;
+    Pos q;
+    q.m = (int)s;
+    q.f = s - (float)q.m;
     if (flags & kLinear) {
         const float pos = s - 0.5f;
-        const int lo = min(max((int)floorf(pos), 0), C - 2);
-        const float t = fminf(fmaxf(pos - (float)lo, 0.f), 1.f);
-        const float A0 = A[lo], A1 = A[lo + 1];
-        full = fmaf(t, A1 - A0, A0);
-        const float B0 = lo < m ? 0.f : (lo == m ? 1.f - f : 1.f);
-        const float B1 = lo + 1 < m ? 0.f : (lo + 1 == m ? 1.f - f : 1.f);
-        self = a2 * fmaf(t, B1 - B0, B0);
+        q.lo = min(max((int)floorf(pos), 0), C - 2);
+        q.t = fminf(fmaxf(pos - (float)q.lo, 0.f), 1.f);
+        const float B0 = q.lo < q.m ? 0.f : (q.lo == q.m ? 1.f - q.f : 1.f);
+        const float B1 = q.lo + 1 < q.m ? 0.f : (q.lo + 1 == q.m ? 1.f - q.f : 1.f);
+        q.g = fmaf(q.t, B1 - B0, B0);
     } else {
-        full = A[m];
-        self = a2 * (1.f - f);
+        q.lo = q.m;
+        q.t = 0.f;
+        q.g = 1.f - q.f;
     }
+    return q;
 }
 
-// Absorbance in front of a fragment, in the units of A.
+// Reconstruction at a located depth from one pixel's bin values.
+template <int J>
+__device__ __forceinline__ float recon_at(const float *A, const Pos &q, uint32_t flags) {
+    if (!(flags & kLinear)) return A[q.m];
+    const float A0 = A[q.lo], A1 = A[q.lo + 1];
+    return fmaf(q.t, A1 - A0, A0);
+}
+
+// Absorbance in front of a fragment, in the units of A (a2 = its step in
+// those units); the own step is removed under self-exclusion.
 template <int J>
 __device__ __forceinline__ float frag_absorbance(const float *A, float zc, float a2, uint32_t flags) {
-    float full, self;
-    recon<J>(A, zc * (float)(1 << J), flags, a2, full, self);
-    return (flags & kSelfExclude) ? fmaxf(full - self, 0.f) : full;
+    const Pos q = locate<J>(zc * (float)(1 << J), flags);
+    const float full = recon_at<J>(A, q, flags);
+    return (flags & kSelfExclude) ? fmaxf(full - a2 * q.g, 0.f) : full;
 }
 
 // Per-pixel weight offset m_p (log2 units): every fragment's absorbance is
@@ -402,6 +506,34 @@ __device__ __forceinline__ float weight_offset(const float *A2, float zmin, uint
     if (!(zmin < 1.f)) return 0.f;  // +inf: no fragment with alpha > 0
     const float full = frag_absorbance<J>(A2, clamp_depth(zmin), 0.f, flags & kLinear);
     return fmaxf(full - kStepCapLog2, 0.f);
+}
+
+// Stores one pixel's bin values (log2 units) into its shared row and, in the
+// normalised resolve, folds in the weight offset: the row becomes A' = A - m_p
+// with m_p from the pixel's nearest depth (every fragment then has A' >= 0 up
+// to rounding, which the self-excluded clamp at 0 absorbs).
+template <int J>
+__device__ __forceinline__ void put_bins(float *row, float (&v)[1 << J], float zmin, uint32_t flags) {
+    constexpr int C = 1 << J;
+    auto put = [&]() {
+        if constexpr (C % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < C / 4; ++q)
+                reinterpret_cast<float4 *>(row)[q] =
+                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < C; ++i) row[i] = v[i];
+        }
+    };
+    put();
+    if (!(flags & kNormalized)) return;
+    const float mp = weight_offset<J>(row, zmin, flags);
+    if (mp > 0.f) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] -= mp;
+        put();
+    }
 }
 
 // ---------------------------------------------------------------- fragment phases
@@ -428,43 +560,54 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, float
         const float f = s - (float)m;
         atomicAdd(&sF[lp * LD + m], a * f);
         atomicAdd(&sG[lp * LD + m], a * (1.f - f));
-        const unsigned zb = __float_as_uint(zc);
-        if (a > 0.f && zb < sZ[lp]) atomicMin(&sZ[lp], zb);
+        if (a > 0.f) atomicMin(&sZ[lp], __float_as_uint(zc));
     });
 }
 
-// Step 3 (§2.1): v_i = 2^(m_p - A_i) (log2 units), w_i = alpha_i v_i;
-// per pixel R, G, B += c w and W += w in a lane-spread copy of the
-// accumulator planes acc[5][kCopies][npx], and, when withS, S += a.
+// Step 3 (§2.1).  A2 holds each pixel's bin values in log2 units minus the
+// pixel's weight offset m_p, so v_i = 2^(m_p - A_i) = 2^-A'_i and
+// w_i = alpha_i v_i; per pixel (R, G, B, W) += (c w, w) through the
+// warp-segmented reduction into this warp's copy, and, when sS is given,
+// S += a with a shared-memory atomic.
 template <int J, bool COUNT>
 __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
-                                              const float *sMp, float *acc, bool withS, int npx,
-                                              unsigned &bad) {
+                                              float4 *accw, float *sS, unsigned &bad) {
     constexpr int LD = Shape<J>::LD;
     const uint32_t flags = p.flags;
-    const int plane = kCopies * npx;
-    float *my = acc + ((threadIdx.x & 31) & (kCopies - 1)) * npx;
-    for_each_frag6(T.s, T.e, p, [&](uint32_t px, float z, float al, float r, float g, float b) {
-        if (!(z == z) || !(al == al)) {
-            if (COUNT) ++bad;
-            return;
+    float4 *mine = accw + (threadIdx.x >> 5) * (p.g.tile_w * p.g.tile_h);
+    for_each_frag6(T.s, T.e, p,
+                   [&](bool valid, uint32_t px, float z, float al, float r, float g, float b) {
+        int lp = -1;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            if (z == z && al == al) lp = local_pixel(px, p, T);
+            if (lp >= 0) {
+                const float ac = clamp_alpha(al);
+                const float a = step_of(ac);
+                const float Ah = frag_absorbance<J>(A2 + lp * LD, clamp_depth(z), a * kLog2e, flags);
+                const float w = ac * ex2(-Ah);
+                c = make_float4(r * w, g * w, b * w, w);
+                if (sS) atomicAdd(&sS[lp], a);
+            } else if (COUNT) {
+                ++bad;
+            }
         }
-        const int lp = local_pixel(px, p, T);
-        if (lp < 0) {
-            if (COUNT) ++bad;
-            return;
-        }
-        const float ac = clamp_alpha(al);
-        const float a = step_of(ac);
-        const float Ah = frag_absorbance<J>(A2 + lp * LD, clamp_depth(z), a * kLog2e, flags);
-        const float w = ac * ex2(sMp[lp] - Ah);
-        float *q = my + lp;
-        atomicAdd(q, r * w);
-        atomicAdd(q + plane, g * w);
-        atomicAdd(q + 2 * plane, b * w);
-        atomicAdd(q + 3 * plane, w);
-        if (withS) atomicAdd(q + 4 * plane, a);
+        warp_accumulate(mine, lp, c);
     });
+}
+
+// Sum over the warps' copies of pixel lp's accumulators.
+__device__ __forceinline__ float4 sum_warps(const float4 *accw, int npx, int lp) {
+    float4 v = accw[lp];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) {
+        const float4 u = accw[w * npx + lp];
+        v.x += u.x;
+        v.y += u.y;
+        v.z += u.z;
+        v.w += u.w;
+    }
+    return v;
 }
 
 // ---------------------------------------------------------------- composite
@@ -501,15 +644,6 @@ __device__ __forceinline__ void composite_pixel(const Params &p, int64_t gp, flo
     reinterpret_cast<float4 *>(p.out)[gp] = o;
 }
 
-// Sum of the kCopies copies of accumulator plane k of pixel lp.
-__device__ __forceinline__ float sum_copies(const float *acc, int npx, int k, int lp) {
-    const float *q = acc + k * kCopies * npx + lp;
-    float v = q[0];
-#pragma unroll
-    for (int c = 1; c < kCopies; ++c) v += q[c * npx];
-    return v;
-}
-
 // ---------------------------------------------------------------- shared-memory layouts (bytes)
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -518,17 +652,18 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 template <int J> struct Layout {
     static constexpr size_t plane(int npx) { return align16((size_t)npx * Shape<J>::LD * 4); }
     static constexpr size_t words(int npx) { return align16((size_t)npx * 4); }
-    // accumulator planes R, G, B, W (and S), kCopies copies each
-    static constexpr size_t acc(int npx, int planes) { return (size_t)planes * kCopies * words(npx); }
-    static constexpr size_t region(int npx) {
-        return 2 * plane(npx) > plane(npx) + acc(npx, 4) ? 2 * plane(npx) : plane(npx) + acc(npx, 4);
-    }
+    static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 16; }
     // build: F and G bins + nearest-depth words
     static constexpr size_t build(int npx) { return 2 * plane(npx) + words(npx); }
-    // fused: F, G bins, later bin values + accumulators; then S, m_p, depth words
-    static constexpr size_t fused(int npx) { return region(npx) + 3 * words(npx); }
-    // resolve: bin values + R, G, B, W, S accumulators + m_p
-    static constexpr size_t resolve(int npx) { return plane(npx) + acc(npx, 5) + words(npx); }
+    // fused: F and G bins, replaced after the build by the bin values, the
+    // warps' accumulators and the S words; then the nearest-depth words
+    static constexpr size_t region(int npx) {
+        return 2 * plane(npx) > plane(npx) + accw(npx) + words(npx) ? 2 * plane(npx)
+                                                                      : plane(npx) + accw(npx) + words(npx);
+    }
+    static constexpr size_t fused(int npx) { return region(npx) + words(npx); }
+    // resolve: bin values + warps' accumulators + S words
+    static constexpr size_t resolve(int npx) { return plane(npx) + accw(npx) + words(npx); }
 };
 
 }  // namespace wt
