@@ -305,6 +305,18 @@ def run_wt(args):
                          f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
                          f"composite, FP64, single thread, {res['seconds']:.1f} s",
                "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        del coeff, out
+        torch.cuda.empty_cache()
+        serving, pool = {}, None
+        for dname in ("bf16", "f32"):
+            serving[dname], pool = run_serving(args, dname, pool)
+        serving["workload"] = (f"{args.serve_requests} requests, Poisson arrivals mean 2 ms, "
+                               "sizes {360p,720p,1080p,4K}, Poisson(lambda ~ U[2,32]) "
+                               "fragments/pixel, J=4, 40 GB cap, step 8192 tiles")
+        del pool
+        torch.cuda.empty_cache()
     kernel_name = "k_fused" if args.path == "fused" else "k_build + k_resolve"
     path_name = ("wt_build_resolve (fused kernel)" if args.path == "fused"
                  else "wt_build + wt_resolve_composite (two kernels)")
@@ -328,6 +340,7 @@ def run_wt(args):
             "gpu_launches": K * (1 if args.path == "fused" else 2),
             "clocks": clk.summary(),
             "variants": variants,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -368,6 +381,72 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all):
     e2e_ms = max_over_ranks(a.elapsed_time(b) / Ke, world)
     return {"value": frags_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
+
+
+# ---------------------------------------------------------------- serving
+
+SERVE_LAMBDAS = (6.0, 14.0, 22.0, 30.0)
+
+
+def run_serving(args, dtype_name, pool=None):
+    """Continuous-batching serving run: ``args.serve_requests`` frame requests
+    with exponential inter-arrival times (mean 2 ms), resolutions drawn from
+    {640x360, 1280x720, 1920x1080, 3840x2160} and Poisson(lambda) fragments per
+    pixel, lambda ~ U[2, 32] per request (served from a pool of pre-rendered
+    frames at lambda 6/14/22/30, the nearest to the request's lambda), J = 4,
+    40 GB cap.  Latency = GPU completion of a request's last tile (CUDA event)
+    minus its submission time."""
+    import paper_2201_00094_gb300 as wt
+    dev = torch.device("cuda")
+    dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[dtype_name]
+    reqs = synth.serve_request_params(args.serve_requests, seed=args.seed)
+    if pool is None:
+        pool = {}
+        for (w, h) in synth.SERVE_SIZES:
+            for k, lam in enumerate(SERVE_LAMBDAS):
+                pool[(w, h, k)] = synth.serve_frame(w, h, lam, seed=1000 + 7 * k + w, device=dev)
+        torch.cuda.synchronize()
+    srv = wt.Server(J=4, coeff_dtype=dt, max_slots=64, mem_cap_bytes=40 << 30, step_tiles=8192)
+    pending = []
+    lat, frags = [], 0
+    t_start = time.perf_counter()
+    first_submit = None
+    try:
+        for rq in reqs:
+            k = int(np.argmin([abs(rq["lam"] - l) for l in SERVE_LAMBDAS]))
+            fr = pool[(rq["width"], rq["height"], k)]
+            while (time.perf_counter() - t_start) * 1e3 < rq["arrival_ms"]:
+                pass
+            d = wt.make_desc(fr.width, fr.height, 4, dt)
+            f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+            out = torch.empty(fr.P, 4, device=dev)
+            rid = srv.submit(d, f, out, keep=fr)
+            pending.append((rid, fr.n))
+            first_submit = first_submit if first_submit is not None else rid
+            # retire finished requests so that their memory is released
+            while pending and srv.query(pending[0][0]).state == 2:
+                r0, n0 = pending.pop(0)
+                info = srv.query(r0)
+                lat.append((info.done_us - info.submit_us) / 1e3)
+                frags += n0
+                srv.release(r0)
+        last_done = 0.0
+        for rid, n in pending:
+            assert srv.wait(rid, 120_000_000), "serving request timed out"
+            info = srv.query(rid)
+            lat.append((info.done_us - info.submit_us) / 1e3)
+            last_done = max(last_done, info.done_us)
+            frags += n
+            srv.release(rid)
+        makespan_s = time.perf_counter() - t_start
+    finally:
+        srv.close()
+    lat = np.array(lat)
+    return {"requests": len(lat), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "max_ms": round(float(lat.max()), 3),
+            "fragments": int(frags), "fragments_per_s": frags / makespan_s,
+            "makespan_s": round(makespan_s, 3)}, pool
 
 
 # ---------------------------------------------------------------- reference arm
@@ -428,6 +507,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--path", default="fused", choices=["fused", "two_pass"],
                     help="fused kernel (default) or wt_build + wt_resolve_composite")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -226,6 +226,87 @@ wt_status wt_get_error(wt_stream stream, int64_t *bad_count);
 /* (Every call counts the fragments it rejects, so a bad fragment seen by
  * wt_build and then by wt_resolve is counted twice.) */
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of frames on one GPU (no counterpart in the
+ * paper, which renders one frame at a time).
+ *
+ * A server owns a device arena of mem_cap_bytes for the coefficient buffers
+ * (allocated once by wt_serve_create; nothing is allocated per request) and a
+ * scheduler thread.  Requests are admitted in arrival order while fewer than
+ * max_slots are held and the held bytes -- fragments (24 B each) and tile
+ * offsets, coefficients and output, counted per request -- stay under
+ * mem_cap_bytes.  Each scheduling step is one persistent kernel launch over the
+ * tiles of all admitted frames (an equal share of step_tiles each), so frames
+ * that arrive while others are running are processed in the same launches.
+ * The per-tile arithmetic is that of wt_build_resolve.  Kernels never wait on
+ * the host; every host wait is bounded.
+ */
+typedef struct wt_serve_config {
+    int32_t J, coeff_dtype; /* every request must use these ... */
+    uint32_t flags;         /* ... and these reading flags ... */
+    int32_t tile_w, tile_h; /* ... and this tile size */
+    int32_t max_slots;      /* requests held at once (admitted, not released), 1..4096 */
+    int64_t mem_cap_bytes;  /* byte cap for held requests; also the arena size */
+    int64_t step_tiles;     /* tiles per scheduling step (one kernel launch) */
+} wt_serve_config;
+
+typedef struct wt_server wt_server;
+
+typedef struct wt_serve_info {
+    int32_t state;    /* 0 queued, 1 admitted, 2 done */
+    int32_t reserved;
+    double submit_us; /* host clock, microseconds since the server was created */
+    double admit_us;  /* -1 if not admitted yet */
+    double done_us;   /* GPU completion (from a CUDA event), -1 if not done */
+    void *coeff;      /* the request's coefficient buffer in the arena (valid
+                         until wt_serve_release), or NULL while queued */
+} wt_serve_info;
+
+/* Creates a server on the current device.  WT_ERR_CUDA if the arena or the
+ * stream cannot be created. */
+wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **server);
+
+/* Queues a frame.  desc must match the server's J, coeff_dtype, flags and tile
+ * size (else WT_ERR_UNSUPPORTED).  The fragment arrays and out [P * 4] are the
+ * caller's device memory and must stay valid until the request is done.
+ * WT_ERR_NOMEM if the frame alone exceeds the cap.  Thread safe. */
+wt_status wt_serve_submit(wt_server *server, const wt_desc *desc, const wt_frags *frags,
+                          const float bg[3], float *out, int64_t *request_id);
+
+/* Waits until the request is done, at most timeout_us; WT_ERR_TIMEOUT if not. */
+wt_status wt_serve_wait(wt_server *server, int64_t request_id, int64_t timeout_us);
+
+/* State and timestamps of a request (see wt_serve_info). */
+wt_status wt_serve_query(wt_server *server, int64_t request_id, wt_serve_info *info);
+
+/* Gives back a done request's slot, bytes and coefficient buffer.
+ * WT_ERR_ARG if the request is unknown or not done. */
+wt_status wt_serve_release(wt_server *server, int64_t request_id);
+
+/* Held bytes, queued and admitted-unfinished request counts; returns the
+ * server's fault status (WT_OK normally). */
+wt_status wt_serve_stats(wt_server *server, int64_t *used_bytes, int64_t *queued, int64_t *active);
+
+/* Stops the scheduler, waits for the launched work and frees everything. */
+wt_status wt_serve_destroy(wt_server *server);
+
+/* The admission and step-planning policy of the server on its own, with no
+ * GPU: for tests and for callers that drive their own launches.
+ * wt_planner_submit returns a request id > 0 or -WT_ERR_NOMEM;
+ * wt_planner_admit writes the newly admitted ids; wt_planner_plan writes one
+ * step's tile ranges (id, first tile, count) and the ids whose last tiles are
+ * in it (*nfinishing: capacity in, count out); both return their total
+ * count. */
+typedef struct wt_planner wt_planner;
+wt_planner *wt_planner_create(int32_t max_slots, int64_t mem_cap_bytes, int64_t step_tiles);
+int64_t wt_planner_submit(wt_planner *planner, int64_t bytes, int64_t tiles);
+int32_t wt_planner_admit(wt_planner *planner, int64_t *ids, int32_t max_ids);
+int32_t wt_planner_plan(wt_planner *planner, int64_t *ids, int32_t *tile0, int32_t *count,
+                        int32_t max_ranges, int64_t *finishing, int32_t *nfinishing);
+int32_t wt_planner_release(wt_planner *planner, int64_t request_id);
+int64_t wt_planner_used(const wt_planner *planner);
+void wt_planner_destroy(wt_planner *planner);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ __all__ = [
     "DEFAULT_FLAGS", "WtDesc", "WtFrags", "WtError", "lib", "library_path", "make_desc",
     "make_frags", "coeff_torch_dtype", "wt_version", "wt_coeff_bytes", "wt_num_tiles", "wt_build",
     "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
-    "wt_get_error", "wt_backward", "WaveletOIT",
+    "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
+    "WtServeInfo",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -64,6 +65,19 @@ class WtFrags(ctypes.Structure):
                 ("b", ctypes.c_void_p), ("tile_offsets", ctypes.c_void_p)]
 
 
+class WtServeConfig(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int32), ("coeff_dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("max_slots", ctypes.c_int32), ("mem_cap_bytes", ctypes.c_int64),
+                ("step_tiles", ctypes.c_int64)]
+
+
+class WtServeInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double),
+                ("done_us", ctypes.c_double), ("coeff", ctypes.c_void_p)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -95,6 +109,22 @@ def lib() -> ctypes.CDLL:
         "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "wt_serve_create": ([ctypes.POINTER(WtServeConfig), ctypes.POINTER(vp)], ctypes.c_int),
+        "wt_serve_submit": ([vp, D, Fr, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "wt_serve_wait": ([vp, i64, i64], ctypes.c_int),
+        "wt_serve_query": ([vp, i64, ctypes.POINTER(WtServeInfo)], ctypes.c_int),
+        "wt_serve_release": ([vp, i64], ctypes.c_int),
+        "wt_serve_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
+                           ctypes.c_int),
+        "wt_serve_destroy": ([vp], ctypes.c_int),
+        "wt_planner_create": ([ctypes.c_int32, i64, i64], vp),
+        "wt_planner_submit": ([vp, i64, i64], i64),
+        "wt_planner_admit": ([vp, vp, ctypes.c_int32], ctypes.c_int32),
+        "wt_planner_plan": ([vp, vp, vp, vp, ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_int32)],
+                            ctypes.c_int32),
+        "wt_planner_release": ([vp, i64], ctypes.c_int32),
+        "wt_planner_used": ([vp], i64),
+        "wt_planner_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -258,6 +288,108 @@ class WaveletOIT(torch.autograd.Function):
         gc = torch.empty(3, n, device=z.device, dtype=torch.float32)
         wt_backward(ctx.desc, frags, grad_out.contiguous().float(), ga, gc, bg=ctx.bg)
         return None, None, ga, gc[0], gc[1], gc[2], None, None, None
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """Continuous-batching server (wt_serve_* in include/wt.h).  The caller keeps
+    each request's fragment tensors and output tensor alive until it is done."""
+
+    def __init__(self, J: int = 4, coeff_dtype: int = BF16, flags: int = DEFAULT_FLAGS,
+                 max_slots: int = 64, mem_cap_bytes: int = 40 << 30, step_tiles: int = 8192,
+                 tile_w: int = 16, tile_h: int = 16):
+        self.cfg = WtServeConfig(J, coeff_dtype, flags, tile_w, tile_h, max_slots, mem_cap_bytes,
+                                 step_tiles)
+        h = ctypes.c_void_p()
+        _call("wt_serve_create", ctypes.byref(self.cfg), ctypes.byref(h))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, desc: WtDesc, frags: WtFrags, out: torch.Tensor,
+               bg: Sequence[float] = (0.5, 0.5, 0.5), keep=None) -> int:
+        rid = ctypes.c_int64()
+        _call("wt_serve_submit", self._h, ctypes.byref(desc), ctypes.byref(frags), _bg(bg),
+              _dev(out, "out", (torch.float32,)), ctypes.byref(rid))
+        self._keep[rid.value] = (desc, frags, out, keep)
+        return rid.value
+
+    def wait(self, rid: int, timeout_us: int = 10_000_000) -> bool:
+        """True when done; False on timeout."""
+        st = lib().wt_serve_wait(self._h, rid, timeout_us)
+        if st == 4:
+            return False
+        if st != 0:
+            raise WtError("wt_serve_wait", st)
+        return True
+
+    def query(self, rid: int) -> WtServeInfo:
+        info = WtServeInfo()
+        _call("wt_serve_query", self._h, rid, ctypes.byref(info))
+        return info
+
+    def release(self, rid: int) -> None:
+        _call("wt_serve_release", self._h, rid)
+        self._keep.pop(rid, None)
+
+    def stats(self):
+        u, q, a = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        st = lib().wt_serve_stats(self._h, ctypes.byref(u), ctypes.byref(q), ctypes.byref(a))
+        return {"used_bytes": u.value, "queued": q.value, "active": a.value, "status": st}
+
+    def close(self) -> None:
+        if self._h:
+            _call("wt_serve_destroy", self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Planner:
+    """The server's admission / step-planning policy alone (host only)."""
+
+    def __init__(self, max_slots: int, mem_cap_bytes: int, step_tiles: int):
+        self._h = lib().wt_planner_create(max_slots, mem_cap_bytes, step_tiles)
+        if not self._h:
+            raise WtError("wt_planner_create", 1)
+
+    def submit(self, nbytes: int, tiles: int) -> int:
+        return int(lib().wt_planner_submit(self._h, nbytes, tiles))
+
+    def admit(self):
+        buf = (ctypes.c_int64 * 4096)()
+        n = lib().wt_planner_admit(self._h, buf, 4096)
+        return [buf[i] for i in range(min(n, 4096))]
+
+    def plan(self):
+        cap = 8192
+        ids, t0, cnt = (ctypes.c_int64 * cap)(), (ctypes.c_int32 * cap)(), (ctypes.c_int32 * cap)()
+        fin = (ctypes.c_int64 * cap)()
+        nf = ctypes.c_int32(cap)
+        n = lib().wt_planner_plan(self._h, ids, t0, cnt, cap, fin, ctypes.byref(nf))
+        return ([(ids[i], t0[i], cnt[i]) for i in range(n)], [fin[i] for i in range(nf.value)])
+
+    def release(self, rid: int) -> int:
+        return int(lib().wt_planner_release(self._h, rid))
+
+    def used(self) -> int:
+        return int(lib().wt_planner_used(self._h))
+
+    def close(self):
+        if self._h:
+            lib().wt_planner_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def wt_get_error(stream=None) -> int:

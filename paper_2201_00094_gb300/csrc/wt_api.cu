@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(Params p) {
 }
 
 }  // namespace
+
+// Device address of the error word on the current device (for other units).
+unsigned long long *error_word() { return err_word(); }
+
 }  // namespace wt
 
 using namespace wt;

@@ -100,11 +100,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     }
 }
 
-// Steps 2-4 fused: coefficients never leave the SM between build and resolve.
+// Steps 2-4 fused for one tile: the coefficients never leave the SM between
+// build and resolve.  Ends with a barrier, so a persistent caller may reuse the
+// shared memory for its next tile.
 template <int J, typename CT>
-__global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params p) {
+__device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned char *smem) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
     float *sF = reinterpret_cast<float *>(smem);
     float *sG = reinterpret_cast<float *>(smem + Layout<J>::plane(npx));
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params 
     float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
     float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
-    const Tile T = tile_of(p, blockIdx.x, true);
+    const Tile T = tile_of(p, tile, true);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
     __syncthreads();
@@ -145,9 +146,44 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params 
     __syncthreads();
     phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);
     __syncthreads();
-    if (gp < 0) return;
-    const float4 a = sum_warps(accw, npx, lp);
-    composite_pixel(p, gp, a.x, a.y, a.z, a.w, sS[lp]);
+    if (gp >= 0) {
+        const float4 a = sum_warps(accw, npx, lp);
+        composite_pixel(p, gp, a.x, a.y, a.z, a.w, sS[lp]);
+    }
+    __syncthreads();
+}
+
+template <int J, typename CT>
+__global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    fused_tile<J, CT>(p, blockIdx.x, smem);
+}
+
+// Serving: one persistent launch works through the tile tasks of several
+// frames (continuous batching).  The step's task table lists, per admitted
+// frame, a slot and a range of its tiles; tasks are numbered by the running
+// sum of the range lengths, and CTAs claim task numbers from a device counter.
+template <int J, typename CT>
+__global__ void __launch_bounds__(kThreads, MinBlocks<J>::value)
+    k_serve(const Params *__restrict__ slots, const ServeTask *__restrict__ tasks, int ntasks,
+            int64_t total, unsigned long long *counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long claim;
+    for (;;) {
+        if (threadIdx.x == 0) claim = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long k = claim;
+        __syncthreads();
+        if (k >= total) return;
+        int lo = 0, hi = ntasks - 1;  // last range with start <= k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tasks[mid].start <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        const ServeTask t = tasks[lo];
+        fused_tile<J, CT>(slots[t.slot], t.tile0 + (int)(k - t.start), smem);
+    }
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -349,6 +385,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     }
 }
 
+template <int J, typename CT>
+cudaError_t launch_serve_t(const Params *slots, const ServeTask *tasks, int ntasks, int64_t total,
+                           unsigned long long *counter, int npx, int grid, cudaStream_t s) {
+    const size_t bytes = Layout<J>::fused(npx);
+    cudaError_t e = cudaFuncSetAttribute(k_serve<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_serve<J, CT><<<grid, kThreads, bytes, s>>>(slots, tasks, ntasks, total, counter);
+    return cudaGetLastError();
+}
+
+// CTAs of a fused-tile kernel that fit on one SM (persistent grid sizing).
+template <int J, typename CT> int serve_blocks_per_sm(int npx) {
+    int n = 0;
+    const size_t bytes = Layout<J>::fused(npx);
+    if (cudaFuncSetAttribute(k_serve<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_serve<J, CT>, kThreads, bytes) != cudaSuccess) return 0;
+    return n;
+}
+
 template <int J, typename CT> cudaError_t launch_backward_t(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = BackLayout<J>::total(npx);
@@ -466,6 +522,12 @@ cudaError_t launch_absorbance_t(const Params &p, int64_t q, const uint32_t *qpx,
     const TileLaunch kBackward##IDX[5] = {launch_backward_t<1, CT>, launch_backward_t<2, CT>,     \
                                           launch_backward_t<3, CT>, launch_backward_t<4, CT>,     \
                                           launch_backward_t<5, CT>};                              \
+    const ServeLaunch kServe##IDX[5] = {launch_serve_t<1, CT>, launch_serve_t<2, CT>,             \
+                                        launch_serve_t<3, CT>, launch_serve_t<4, CT>,             \
+                                        launch_serve_t<5, CT>};                                   \
+    const ServeOccupancy kServeOcc##IDX[5] = {serve_blocks_per_sm<1, CT>, serve_blocks_per_sm<2, CT>, \
+                                              serve_blocks_per_sm<3, CT>, serve_blocks_per_sm<4, CT>, \
+                                              serve_blocks_per_sm<5, CT>};                        \
     const QueryLaunch kAbsorbance##IDX[5] = {                                                      \
         launch_absorbance_t<1, CT>, launch_absorbance_t<2, CT>, launch_absorbance_t<3, CT>,       \
         launch_absorbance_t<4, CT>, launch_absorbance_t<5, CT>};                                   \

@@ -102,26 +102,25 @@ def test_diff512_batch_finite_differences():
     assert wt.wt_get_error() == 0
     rng = np.random.default_rng(512)
     sample = np.sort(rng.choice(fr.n, 512, replace=False))
-    pix = fr.pixel[torch.from_numpy(sample).to(dev)].long()
-    upix = torch.unique(pix)
-    idx, loc = synth.pixel_subset(fr, upix)
-    h = {k: getattr(fr, k)[idx].cpu().numpy() for k in ("z", "alpha", "r", "g", "b")}
-    loc = loc.cpu().numpy().astype(np.uint32)
-    tgt = target[upix].double().cpu().numpy()
-    pos = {int(i): k for k, i in enumerate(idx.cpu().numpy())}
-    npx = len(upix)
-
-    def loss_of(al, cols):
-        o = oracle.composite(loc, h["z"], al, cols, npx, 4)
-        return ((o[:, :3] - tgt[:, :3]) ** 2).sum()
-
-    ga_s = ga[torch.from_numpy(sample).to(dev)].double().cpu().numpy()
-    gc_s = gc[:, torch.from_numpy(sample).to(dev)].double().cpu().numpy().T
+    st = torch.from_numpy(sample).to(dev)
+    ga_s = ga[st].double().cpu().numpy()
+    gc_s = gc[:, st].double().cpu().numpy().T
     fd_a = np.zeros(512)
     fd_c = np.zeros((512, 3))
-    cols = [h["r"], h["g"], h["b"]]
-    for k, i in enumerate(sample):
-        j = pos[int(i)]
+    pix = fr.pixel[st].long()
+    for k in range(512):
+        # the fragment's own pixel is an exact sub-problem (pixels are independent)
+        idx, _ = synth.pixel_subset(fr, pix[k:k + 1])
+        h = {kk: getattr(fr, kk)[idx].cpu().numpy() for kk in ("z", "alpha", "r", "g", "b")}
+        j = int((idx == int(sample[k])).nonzero()[0, 0])
+        loc = np.zeros(len(idx), np.uint32)
+        tgt = target[pix[k]].double().cpu().numpy()
+
+        def loss_of(al, cols):
+            o = oracle.composite(loc, h["z"], al, cols, 1, 4)
+            return ((o[0, :3] - tgt[:3]) ** 2).sum()
+
+        cols = [h["r"], h["g"], h["b"]]
         hstep = np.float32(2.0 ** -12)
         ap, am = h["alpha"].copy(), h["alpha"].copy()
         ap[j] += hstep

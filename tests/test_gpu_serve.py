@@ -1,0 +1,144 @@
+"""Serving with continuous batching on the GPU: results equal the single-frame
+path, a frame's result is the same alone and in a mix of concurrent frames,
+admission respects the byte cap (bounded waits time out while memory is held),
+and bad requests are refused on the host."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2201_00094_gb300 as wt
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda")
+
+
+def _frame(w, h, lam, seed):
+    return synth.serve_frame(w, h, lam, seed, device=DEV)
+
+
+def _submit(srv, fr, dtype=wt.BF16):
+    d = wt.make_desc(fr.width, fr.height, 4, dtype)
+    f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+    out = torch.full((fr.P, 4), float("nan"), device=DEV)
+    rid = srv.submit(d, f, out, keep=fr)
+    return rid, out
+
+
+def _direct(fr, dtype=wt.BF16):
+    d = wt.make_desc(fr.width, fr.height, 4, dtype)
+    f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+    out = torch.empty(fr.P, 4, device=DEV)
+    wt.wt_build_resolve(d, f, out, None, None)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("dtype", [wt.F32, wt.BF16])
+def test_served_frame_equals_direct_call_and_oracle(dtype):
+    fr = _frame(333, 197, 12.0, seed=1)
+    with wt.Server(J=4, coeff_dtype=dtype, max_slots=4, mem_cap_bytes=1 << 30,
+                   step_tiles=64) as srv:
+        rid, out = _submit(srv, fr, dtype)
+        assert srv.wait(rid, 20_000_000)
+        info = srv.query(rid)
+        assert info.state == 2 and info.done_us >= info.admit_us >= info.submit_us >= 0
+        assert info.coeff
+        srv.release(rid)
+    ref = _direct(fr, dtype)
+    assert (out - ref).abs().max().item() <= 1e-5
+    if dtype == wt.F32:
+        h = fr.to("cpu").numpy()
+        o = oracle.composite(h["pixel"], h["z"], h["alpha"], (h["r"], h["g"], h["b"]), fr.P, 4)
+        assert np.abs(out.cpu().numpy() - o).max() <= 1e-4
+    assert wt.wt_get_error() == 0
+
+
+def test_same_result_alone_and_in_mix():
+    """A frame served alone and the same frame served among 24 concurrent
+    frames of other sizes and depths give the same composite (up to the order
+    of FP32 shared-memory additions)."""
+    probe = _frame(640, 360, 20.0, seed=7)
+    with wt.Server(J=4, coeff_dtype=wt.BF16, max_slots=8, mem_cap_bytes=8 << 30,
+                   step_tiles=2048) as srv:
+        rid, out_alone = _submit(srv, probe)
+        assert srv.wait(rid, 20_000_000)
+        srv.release(rid)
+        others = [_frame(*synth.SERVE_SIZES[k % 3], 2.0 + 4.0 * (k % 8), seed=100 + k)
+                  for k in range(24)]
+        ids = []
+        for k, fr in enumerate(others):
+            ids.append(_submit(srv, fr))
+            if k == 11:
+                pid, out_mix = _submit(srv, probe)   # arrives while others run
+        for rid2, _ in ids:
+            assert srv.wait(rid2, 60_000_000)
+            srv.release(rid2)
+        assert srv.wait(pid, 60_000_000)
+        srv.release(pid)
+        for (rid2, o), fr in zip(ids, others):
+            assert (o - _direct(fr)).abs().max().item() <= 1e-5
+    assert (out_alone - out_mix).abs().max().item() <= 1e-5
+    assert torch.isfinite(out_mix).all()
+
+
+def test_admission_waits_for_memory_and_times_out():
+    a = _frame(512, 512, 8.0, seed=3)
+    b = _frame(512, 512, 8.0, seed=4)
+    cap = a.n * 24 + 512 * 512 * (16 * 2 + 16) + 200_000  # room for one frame only
+    with wt.Server(J=4, coeff_dtype=wt.BF16, max_slots=4, mem_cap_bytes=cap,
+                   step_tiles=256) as srv:
+        ra, oa = _submit(srv, a)
+        rb, ob = _submit(srv, b)
+        assert srv.wait(ra, 20_000_000)
+        # b cannot be admitted while a is held: a bounded wait runs out
+        assert not srv.wait(rb, 200_000)
+        assert srv.query(rb).state == 0
+        assert srv.stats()["queued"] == 1
+        srv.release(ra)
+        assert srv.wait(rb, 20_000_000)
+        srv.release(rb)
+        assert srv.stats()["used_bytes"] == 0
+    assert (ob - _direct(b)).abs().max().item() <= 1e-5
+
+
+def test_refused_requests():
+    fr = _frame(64, 64, 4.0, seed=5)
+    with wt.Server(J=4, coeff_dtype=wt.BF16, max_slots=2, mem_cap_bytes=1 << 20,
+                   step_tiles=64) as srv:
+        f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+        out = torch.empty(fr.P, 4, device=DEV)
+        with pytest.raises(wt.WtError) as e:   # J differs from the server's
+            srv.submit(wt.make_desc(64, 64, 5, wt.BF16), f, out)
+        assert e.value.status == 2
+        with pytest.raises(wt.WtError) as e:   # storage type differs
+            srv.submit(wt.make_desc(64, 64, 4, wt.F32), f, out)
+        assert e.value.status == 2
+        big = _frame(1024, 1024, 4.0, seed=6)
+        fb = wt.make_frags(big.pixel, big.z, big.alpha, big.tile_offsets, big.r, big.g, big.b)
+        with pytest.raises(wt.WtError) as e:   # larger than the whole cap
+            srv.submit(wt.make_desc(1024, 1024, 4, wt.BF16), fb,
+                       torch.empty(big.P, 4, device=DEV))
+        assert e.value.status == 6
+        with pytest.raises(wt.WtError):        # release of an unknown request
+            srv.release(12345)
+
+
+def test_many_small_requests_complete_in_order_of_work():
+    with wt.Server(J=4, coeff_dtype=wt.F16, max_slots=16, mem_cap_bytes=2 << 30,
+                   step_tiles=512) as srv:
+        frames = [_frame(96 + 16 * k, 64 + 8 * k, 4.0 + k, seed=200 + k) for k in range(20)]
+        subs = []
+        for fr in frames:
+            d = wt.make_desc(fr.width, fr.height, 4, wt.F16)
+            f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+            out = torch.empty(fr.P, 4, device=DEV)
+            subs.append((srv.submit(d, f, out, keep=fr), out, fr))
+        for rid, out, fr in subs:
+            assert srv.wait(rid, 30_000_000)
+            srv.release(rid)
+            assert (out - _direct(fr, wt.F16)).abs().max().item() <= 1e-5
