@@ -269,9 +269,13 @@ wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **server);
 /* Queues a frame.  desc must match the server's J, coeff_dtype, flags and tile
  * size (else WT_ERR_UNSUPPORTED).  The fragment arrays and out [P * 4] are the
  * caller's device memory and must stay valid until the request is done.
+ * ready_stream is the stream on which they were produced: the server's work
+ * for the request is ordered after everything enqueued there before this
+ * call.  After wt_serve_wait returns WT_OK, out is complete for every stream.
  * WT_ERR_NOMEM if the frame alone exceeds the cap.  Thread safe. */
 wt_status wt_serve_submit(wt_server *server, const wt_desc *desc, const wt_frags *frags,
-                          const float bg[3], float *out, int64_t *request_id);
+                          const float bg[3], float *out, wt_stream ready_stream,
+                          int64_t *request_id);
 
 /* Waits until the request is done, at most timeout_us; WT_ERR_TIMEOUT if not. */
 wt_status wt_serve_wait(wt_server *server, int64_t request_id, int64_t timeout_us);

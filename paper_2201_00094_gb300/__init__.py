@@ -110,7 +110,7 @@ def lib() -> ctypes.CDLL:
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "wt_serve_create": ([ctypes.POINTER(WtServeConfig), ctypes.POINTER(vp)], ctypes.c_int),
-        "wt_serve_submit": ([vp, D, Fr, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "wt_serve_submit": ([vp, D, Fr, vp, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
         "wt_serve_wait": ([vp, i64, i64], ctypes.c_int),
         "wt_serve_query": ([vp, i64, ctypes.POINTER(WtServeInfo)], ctypes.c_int),
         "wt_serve_release": ([vp, i64], ctypes.c_int),
@@ -307,10 +307,12 @@ class Server:
         self._keep = {}
 
     def submit(self, desc: WtDesc, frags: WtFrags, out: torch.Tensor,
-               bg: Sequence[float] = (0.5, 0.5, 0.5), keep=None) -> int:
+               bg: Sequence[float] = (0.5, 0.5, 0.5), keep=None, stream=None) -> int:
+        """Queues a frame whose inputs and output were produced on `stream`
+        (default: torch's current stream)."""
         rid = ctypes.c_int64()
         _call("wt_serve_submit", self._h, ctypes.byref(desc), ctypes.byref(frags), _bg(bg),
-              _dev(out, "out", (torch.float32,)), ctypes.byref(rid))
+              _dev(out, "out", (torch.float32,)), _stream(stream), ctypes.byref(rid))
         self._keep[rid.value] = (desc, frags, out, keep)
         return rid.value
 

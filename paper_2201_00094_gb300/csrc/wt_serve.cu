@@ -252,6 +252,7 @@ struct ServerImpl {
         void *coeff = nullptr;
         size_t coeff_bytes = 0;
         cudaEvent_t done_ev = nullptr;
+        cudaEvent_t ready_ev = nullptr;  // inputs and output ready on the producer's stream
         bool scheduled = false, done = false;
         double t_submit = 0, t_admit = 0, t_done = 0;
     };
@@ -295,6 +296,11 @@ bool ServerImpl::step_locked(std::unique_lock<std::mutex> &lk) {
         Req &r = reqs[id];
         r.t_admit = now_us();
         r.params.coeff = r.coeff;
+        // the request's work runs after what its producer enqueued before submitting
+        if (cudaStreamWaitEvent(stream, r.ready_ev, 0) != cudaSuccess) {
+            fault = WT_ERR_CUDA;
+            return false;
+        }
         const int slot = planner->slot_of(id);
         h_slots[slot] = r.params;
         if (cudaMemcpyAsync(d_slots + slot, h_slots + slot, sizeof(Params), cudaMemcpyHostToDevice,
@@ -421,7 +427,7 @@ wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **out) {
 }
 
 wt_status wt_serve_submit(wt_server *s, const wt_desc *d, const wt_frags *f, const float bg[3],
-                          float *out, int64_t *request_id) {
+                          float *out, wt_stream ready_stream, int64_t *request_id) {
     if (!s || !d || !f || !bg || !out || !request_id) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     if (d->J != S.cfg.J || d->coeff_dtype != S.cfg.coeff_dtype || d->flags != S.cfg.flags ||
@@ -464,14 +470,22 @@ wt_status wt_serve_submit(wt_server *s, const wt_desc *d, const wt_frags *f, con
     p.err = S.err;
     const int64_t bytes = f->n * 24 + (ntiles(d) + 1) * 8 + (int64_t)r.coeff_bytes + P * 16;
     if (cudaEventCreate(&r.done_ev) != cudaSuccess) return WT_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&r.ready_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(r.ready_ev, reinterpret_cast<cudaStream_t>(ready_stream)) != cudaSuccess) {
+        cudaEventDestroy(r.done_ev);
+        if (r.ready_ev) cudaEventDestroy(r.ready_ev);
+        return WT_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> g(S.mu);
     if (S.fault != WT_OK) {
         cudaEventDestroy(r.done_ev);
+        cudaEventDestroy(r.ready_ev);
         return S.fault;
     }
     const int64_t id = S.planner->submit(bytes, ntiles(d));
     if (id < 0) {
         cudaEventDestroy(r.done_ev);
+        cudaEventDestroy(r.ready_ev);
         return (wt_status)(-id);
     }
     r.t_submit = now_us();
@@ -519,6 +533,7 @@ wt_status wt_serve_release(wt_server *s, int64_t id) {
     S.planner->release(id);
     S.arena.free(it->second.coeff);
     cudaEventDestroy(it->second.done_ev);
+    cudaEventDestroy(it->second.ready_ev);
     S.reqs.erase(it);
     S.cv.notify_all();
     return WT_OK;
@@ -545,8 +560,10 @@ wt_status wt_serve_destroy(wt_server *s) {
     }
     if (S.worker.joinable()) S.worker.join();
     if (S.stream) cudaStreamSynchronize(S.stream);
-    for (auto &kv : S.reqs)
+    for (auto &kv : S.reqs) {
         if (kv.second.done_ev) cudaEventDestroy(kv.second.done_ev);
+        if (kv.second.ready_ev) cudaEventDestroy(kv.second.ready_ev);
+    }
     for (int b = 0; b < ServerImpl::kRing; ++b) {
         if (S.d_tasks[b]) cudaFree(S.d_tasks[b]);
         if (S.h_tasks[b]) cudaFreeHost(S.h_tasks[b]);

@@ -38,6 +38,12 @@ def _direct(fr, dtype=wt.BF16):
     return out
 
 
+# Two runs of the same frame differ only in the order of FP32 shared-memory
+# additions; with 16-bit storage that can move a coefficient by one 16-bit
+# ulp, so those runs are compared at the 16-bit storage tolerance.
+TOL = {wt.F32: 1e-5, wt.BF16: 2e-3, wt.F16: 2e-3}
+
+
 @pytest.mark.parametrize("dtype", [wt.F32, wt.BF16])
 def test_served_frame_equals_direct_call_and_oracle(dtype):
     fr = _frame(333, 197, 12.0, seed=1)
@@ -50,7 +56,7 @@ def test_served_frame_equals_direct_call_and_oracle(dtype):
         assert info.coeff
         srv.release(rid)
     ref = _direct(fr, dtype)
-    assert (out - ref).abs().max().item() <= 1e-5
+    assert (out - ref).abs().max().item() <= TOL[dtype]
     if dtype == wt.F32:
         h = fr.to("cpu").numpy()
         o = oracle.composite(h["pixel"], h["z"], h["alpha"], (h["r"], h["g"], h["b"]), fr.P, 4)
@@ -58,31 +64,31 @@ def test_served_frame_equals_direct_call_and_oracle(dtype):
     assert wt.wt_get_error() == 0
 
 
-def test_same_result_alone_and_in_mix():
+@pytest.mark.parametrize("dtype", [wt.BF16, wt.F32])
+def test_same_result_alone_and_in_mix(dtype):
     """A frame served alone and the same frame served among 24 concurrent
-    frames of other sizes and depths give the same composite (up to the order
-    of FP32 shared-memory additions)."""
+    frames of other sizes and depths give the same composite."""
     probe = _frame(640, 360, 20.0, seed=7)
-    with wt.Server(J=4, coeff_dtype=wt.BF16, max_slots=8, mem_cap_bytes=8 << 30,
+    with wt.Server(J=4, coeff_dtype=dtype, max_slots=8, mem_cap_bytes=8 << 30,
                    step_tiles=2048) as srv:
-        rid, out_alone = _submit(srv, probe)
+        rid, out_alone = _submit(srv, probe, dtype)
         assert srv.wait(rid, 20_000_000)
         srv.release(rid)
         others = [_frame(*synth.SERVE_SIZES[k % 3], 2.0 + 4.0 * (k % 8), seed=100 + k)
                   for k in range(24)]
         ids = []
         for k, fr in enumerate(others):
-            ids.append(_submit(srv, fr))
+            ids.append(_submit(srv, fr, dtype))
             if k == 11:
-                pid, out_mix = _submit(srv, probe)   # arrives while others run
+                pid, out_mix = _submit(srv, probe, dtype)   # arrives while others run
         for rid2, _ in ids:
             assert srv.wait(rid2, 60_000_000)
             srv.release(rid2)
         assert srv.wait(pid, 60_000_000)
         srv.release(pid)
         for (rid2, o), fr in zip(ids, others):
-            assert (o - _direct(fr)).abs().max().item() <= 1e-5
-    assert (out_alone - out_mix).abs().max().item() <= 1e-5
+            assert (o - _direct(fr, dtype)).abs().max().item() <= TOL[dtype]
+    assert (out_alone - out_mix).abs().max().item() <= TOL[dtype]
     assert torch.isfinite(out_mix).all()
 
 
@@ -103,7 +109,7 @@ def test_admission_waits_for_memory_and_times_out():
         assert srv.wait(rb, 20_000_000)
         srv.release(rb)
         assert srv.stats()["used_bytes"] == 0
-    assert (ob - _direct(b)).abs().max().item() <= 1e-5
+    assert (ob - _direct(b)).abs().max().item() <= TOL[wt.BF16]
 
 
 def test_refused_requests():
@@ -141,4 +147,4 @@ def test_many_small_requests_complete_in_order_of_work():
         for rid, out, fr in subs:
             assert srv.wait(rid, 30_000_000)
             srv.release(rid)
-            assert (out - _direct(fr, wt.F16)).abs().max().item() <= 1e-5
+            assert (out - _direct(fr, wt.F16)).abs().max().item() <= TOL[wt.F16]
