@@ -187,6 +187,33 @@ wt_status wt_build_resolve(const wt_desc *desc, const wt_frags *frags, void *coe
                            const float *bg_img, const float bg[3], float *out, wt_stream stream);
 
 /*
+ * wt_build_resolve_batch_static -- wt_build_resolve for a batch of frames in
+ * one launch, allocating nothing.  The paper has no counterpart: it exists for
+ * callers that cannot allocate device memory when they submit work, such as a
+ * renderer that reserves its whole device budget at start-up, or a real-time
+ * loop in which cudaMalloc / cudaFree (which may synchronise the device) would
+ * stall other work.  The scratch the launch needs -- per-frame parameters,
+ * tile ranges and a work counter -- lives in a statically sized device array
+ * of the library (about 13 KB, held by every GPU that loads the library until
+ * the process exits); inputs and outputs are the caller's, and no
+ * coefficients or depth bounds are stored.
+ *   descs, frags  host arrays of nframes entries, 1 <= nframes <= 64 (larger
+ *                 batches return WT_ERR_ARG).  All frames share J,
+ *                 coeff_dtype and tile size (else WT_ERR_UNSUPPORTED);
+ *                 WT_ACCUMULATE is not accepted.
+ *   bgs           host array of nframes * 3 background colours.
+ *   outs          host array of nframes device pointers, out[k] of [P_k * 4].
+ * The first call on a device resolves the scratch's device address with that
+ * device current, so make it before any stream capture.  Every call reuses
+ * the same scratch (each call re-initialises all of it that it uses, the
+ * counter included): calls that overlap on the GPU -- on different streams,
+ * or from different host threads without ordering -- race on it.
+ */
+wt_status wt_build_resolve_batch_static(const wt_desc *descs, const wt_frags *frags,
+                                        const float *bgs, float *const *outs, int32_t nframes,
+                                        wt_stream stream);
+
+/*
  * wt_absorbance -- the evaluation half of §2.3 ("... a logarithmic number of
  * coefficients ... Same applies during evaluation"): A(z) of pixel[q] at depth
  * z[q] for q queries, reading J+1 coefficients per bin.  With alpha non-NULL

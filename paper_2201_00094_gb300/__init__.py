@@ -24,7 +24,7 @@ __all__ = [
     "make_frags", "coeff_torch_dtype", "wt_version", "wt_coeff_bytes", "wt_num_tiles", "wt_build",
     "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
-    "WtServeInfo",
+    "WtServeInfo", "wt_build_resolve_batch_static",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "wt_serve_create": ([ctypes.POINTER(WtServeConfig), ctypes.POINTER(vp)], ctypes.c_int),
         "wt_serve_submit": ([vp, D, Fr, vp, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
@@ -242,6 +243,22 @@ def wt_build_resolve(desc: WtDesc, frags: WtFrags, out: torch.Tensor,
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
           _stream(stream))
+
+
+def wt_build_resolve_batch_static(descs: Sequence[WtDesc], frags: Sequence[WtFrags],
+                                  outs: Sequence[torch.Tensor],
+                                  bgs: Optional[Sequence[Sequence[float]]] = None,
+                                  stream=None) -> None:
+    """wt_build_resolve for up to 64 frames in one launch without any device
+    allocation (for callers that must not allocate when they submit work);
+    see include/wt.h for the limits and the shared-scratch rule."""
+    k = len(descs)
+    da = (WtDesc * max(k, 1))(*descs)
+    fa = (WtFrags * max(k, 1))(*frags)
+    bg = bgs if bgs is not None else [(0.5, 0.5, 0.5)] * k
+    ba = (ctypes.c_float * max(3 * k, 3))(*[float(x) for b in bg for x in b])
+    oa = (ctypes.c_void_p * max(k, 1))(*[_dev(o, "out", (torch.float32,)) for o in outs])
+    _call("wt_build_resolve_batch_static", da, fa, ba, oa, k, _stream(stream))
 
 
 def wt_absorbance(desc: WtDesc, coeff: torch.Tensor, pixel: torch.Tensor, z: torch.Tensor,
