@@ -17,8 +17,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
-    float *sF = reinterpret_cast<float *>(smem);
-    float *sG = reinterpret_cast<float *>(smem + Layout<J>::plane(npx));
+    unsigned *sF = reinterpret_cast<unsigned *>(smem);
+    unsigned *sG = reinterpret_cast<unsigned *>(smem + Layout<J>::plane(npx));
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + 2 * Layout<J>::plane(npx));
     const Tile T = tile_of(p, blockIdx.x, true);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
@@ -107,11 +107,11 @@ template <int J, typename CT>
 __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned char *smem) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
     const int npx = p.g.tile_w * p.g.tile_h;
-    float *sF = reinterpret_cast<float *>(smem);
-    float *sG = reinterpret_cast<float *>(smem + Layout<J>::plane(npx));
+    unsigned *sF = reinterpret_cast<unsigned *>(smem);
+    unsigned *sG = reinterpret_cast<unsigned *>(smem + Layout<J>::plane(npx));
     // after the build: bin values over the F bins, then the warps'
     // accumulators and the S words over the G bins
-    float *vals = sF;
+    float *vals = reinterpret_cast<float *>(smem);
     float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
     float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
@@ -247,9 +247,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t PL = Layout<J>::plane(npx), WD = Layout<J>::words(npx);
-    float *sF = reinterpret_cast<float *>(smem);
-    float *sG = reinterpret_cast<float *>(smem + PL);
-    float *vals = sF;
+    unsigned *sF = reinterpret_cast<unsigned *>(smem);
+    unsigned *sG = reinterpret_cast<unsigned *>(smem + PL);
+    float *vals = reinterpret_cast<float *>(smem);
     float4 *accw = reinterpret_cast<float4 *>(smem + PL);
     float *gam = reinterpret_cast<float *>(smem + PL);  // replaces the accumulators
     unsigned char *wbase = smem + BackLayout<J>::region(npx);

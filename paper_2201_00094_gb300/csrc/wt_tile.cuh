@@ -11,6 +11,12 @@
 // (bin m = floor(C z), fraction f = C z - m):
 //     F_m = sum a_i f_i,      G_m = sum a_i (1 - f_i),
 // and an O(C) tree per pixel turns the bins into the coefficients of §2.3.1.
+// The bins are 32-bit fixed point with a per-pixel power-of-two scale s_p
+// chosen by a counting pass (c_p fragments whose largest step is a_max give
+// c_p a_max s_p <= 2^31, so no bin can overflow), and are added with integer
+// atomics: the sums do not depend on the order of the fragments, so the
+// coefficients -- and everything computed from them in one CTA -- are the
+// same on every run, alone or batched with other frames.
 // For a dyadic interval I with children L, R and u the position normalised to
 // I, F_I = sum_I a u and G_I = sum_I a (1-u) satisfy
 //     t = F_L + G_R,   F_I = t/2 + F_R,   G_I = t/2 + G_L,
@@ -83,7 +89,9 @@ enum : uint32_t { kSelfExclude = 1u, kLinear = 2u, kNormalized = 4u, kAccumulate
 
 template <int J> struct Shape {
     static constexpr int C = 1 << J;
-    static constexpr int LD = C + 4;  // floats per pixel row of bins / bin values (16-byte rows)
+    static constexpr int LD = C + 4;  // words per pixel row of bins / bin values (16-byte rows)
+    // the padding words of a pixel's F row hold its counting-pass results
+    static constexpr int CNT = C, AMAX = C + 1, INV = C + 2;
 };
 
 // ---------------------------------------------------------------- storage
@@ -227,6 +235,26 @@ __device__ __forceinline__ float step_of(float x) {
 }
 
 // ---------------------------------------------------------------- streaming
+
+// Calls body(pixel, alpha) for every fragment of [s, e), 4 per 16-byte load.
+template <class Body>
+__device__ __forceinline__ void for_each_frag2(int64_t s, int64_t e, const Params &p, Body &&body) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int64_t s4 = (s + 3) & ~int64_t(3), e4 = e & ~int64_t(3);
+    if (s4 > e4) s4 = e4 = e;
+    for (int64_t i = s + tid; i < s4; i += nt) body(p.pixel[i], p.alpha[i]);
+    const uint4 *px4 = reinterpret_cast<const uint4 *>(p.pixel);
+    const float4 *a4 = reinterpret_cast<const float4 *>(p.alpha);
+    for (int64_t q = (s4 >> 2) + tid; q < (e4 >> 2); q += nt) {
+        const uint4 pv = px4[q];
+        const float4 av = a4[q];
+        body(pv.x, av.x);
+        body(pv.y, av.y);
+        body(pv.z, av.z);
+        body(pv.w, av.w);
+    }
+    for (int64_t i = e4 + tid; i < e; i += nt) body(p.pixel[i], p.alpha[i]);
+}
 
 // Calls body(pixel, z, alpha) for every fragment of [s, e), 4 per 16-byte load;
 // the loads of the next chunk are issued before the current one is processed.
@@ -417,12 +445,18 @@ template <int J> __device__ __forceinline__ void get_row(const float *row, float
 }
 
 template <int J>
-__device__ __forceinline__ void bins_to_coeffs(const float *Frow, const float *Grow, float (&c)[1 << J],
-                                               float &S) {
+__device__ __forceinline__ void bins_to_coeffs(const unsigned *Frow, const unsigned *Grow,
+                                               float (&c)[1 << J], float &S) {
     constexpr int C = 1 << J;
     float F[C], G[C];
-    get_row<J>(Frow, F);
-    get_row<J>(Grow, G);
+    const float inv = __uint_as_float(Frow[Shape<J>::INV]);  // 1 / s_p, a power of two
+    get_row<J>(reinterpret_cast<const float *>(Frow), F);
+    get_row<J>(reinterpret_cast<const float *>(Grow), G);
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        F[i] = (float)__float_as_uint(F[i]) * inv;
+        G[i] = (float)__float_as_uint(G[i]) * inv;
+    }
     tree_level<J, J - 1>(F, G, c);
     c[0] = G[0];
     S = F[0] + G[0];
@@ -538,11 +572,32 @@ __device__ __forceinline__ void put_bins(float *row, float (&v)[1 << J], float z
 
 // ---------------------------------------------------------------- fragment phases
 
-// Step 2 accumulation: two shared-memory adds into the fragment's bin.
+// Step 2 accumulation.  Pass 0 counts each pixel's fragments and takes its
+// largest clamped alpha (integer atomics on the padding words of its F row);
+// the pixel's scale s_p = 2^(30 - floor(log2(c_p a_max))) then keeps every bin
+// sum below 2^32; pass 1 adds rint(s_p a f) and rint(s_p a (1-f)) to the
+// fragment's bin with integer atomics, and the nearest depth with a red.min.
 template <int J>
-__device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, float *sF, float *sG,
+__device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
                                            unsigned *sZ, unsigned &bad) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+    constexpr int CNT = Shape<J>::CNT, AMAX = Shape<J>::AMAX, INV = Shape<J>::INV;
+    for_each_frag2(T.s, T.e, p, [&](uint32_t px, float al) {
+        if (!(al == al)) return;
+        const int lp = local_pixel(px, p, T);
+        if (lp < 0) return;
+        atomicAdd(&sF[lp * LD + CNT], 1u);
+        atomicMax(&sF[lp * LD + AMAX], __float_as_uint(clamp_alpha(al)));
+    });
+    __syncthreads();
+    for (int lp = threadIdx.x; lp < p.g.tile_w * p.g.tile_h; lp += blockDim.x) {
+        unsigned *row = sF + lp * LD;
+        const float bound = (float)row[CNT] * step_of(__uint_as_float(row[AMAX]));
+        const int e = bound > 0.f ? max(ilogbf(bound), -30) : 0;
+        row[INV] = __float_as_uint(ldexpf(1.f, e - 30));  // 1 / s_p
+        row[AMAX] = __float_as_uint(ldexpf(1.f, 30 - e));  // s_p (the maximum is no longer needed)
+    }
+    __syncthreads();
     for_each_frag3(T.s, T.e, p, [&](uint32_t px, float z, float al) {
         if (!(z == z) || !(al == al)) {
             ++bad;
@@ -553,13 +608,15 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, float
             ++bad;
             return;
         }
+        const float sp = __uint_as_float(sF[lp * LD + AMAX]);
         const float a = step_of(clamp_alpha(al));
         const float zc = clamp_depth(z);
         const float s = zc * (float)C;  // exact: C is a power of two
         const int m = (int)s;
         const float f = s - (float)m;
-        atomicAdd(&sF[lp * LD + m], a * f);
-        atomicAdd(&sG[lp * LD + m], a * (1.f - f));
+        const float as = a * sp;
+        atomicAdd(&sF[lp * LD + m], __float2uint_rn(as * f));
+        atomicAdd(&sG[lp * LD + m], __float2uint_rn(as * (1.f - f)));
         if (a > 0.f) atomicMin(&sZ[lp], __float_as_uint(zc));
     });
 }

@@ -130,8 +130,9 @@ def test_fused_equals_two_pass_full_frame(heavy4k):
     wt.wt_build(d, f, c2, None)
     wt.wt_resolve_composite(d, f, c2, None, o2)
     torch.cuda.synchronize()
-    # same arithmetic up to the order of FP32 shared-memory additions
-    S = c1[:, 0].abs().max().item()
-    assert (c1 - c2).abs().max().item() <= 1e-6 * max(1.0, S)
+    # the coefficients come from order-independent fixed-point bins: identical;
+    # the two-pass resolve sums S with FP32 atomics, so the composite agrees
+    # to FP32 rounding
+    assert torch.equal(c1, c2)
     assert (o1 - o2).abs().max().item() <= 2e-5
     assert math.isfinite(o1.sum().item())

@@ -213,6 +213,23 @@ def test_accumulate_batches_equals_single_build():
     np.testing.assert_allclose(out.cpu().numpy(), r["out"], atol=1e-4)
 
 
+def test_build_is_deterministic_and_order_independent():
+    """Fixed-point bins: the coefficients of a permuted stream are identical."""
+    fr = synth.uniform_frame(48, 40, 24.0, 200, J=5, seed=21)
+    g1 = gpu_run(fr)
+    perm = torch.cat([int(fr.tile_offsets[t]) + torch.randperm(
+        int(fr.tile_offsets[t + 1] - fr.tile_offsets[t]), generator=torch.Generator().manual_seed(t))
+        for t in range(fr.ntiles)])
+    pf = synth.Frame(**{**fr.__dict__, **{k: getattr(fr, k)[perm].contiguous()
+                                           for k in ("pixel", "z", "alpha", "r", "g", "b")}})
+    for kw in (dict(), dict(fused=True)):
+        g2 = gpu_run(pf, **kw)
+        np.testing.assert_array_equal(g1["coeff"], g2["coeff"])
+    g3 = gpu_run(pf, fused=True)
+    g4 = gpu_run(pf, fused=True)
+    np.testing.assert_array_equal(g3["out"], g4["out"])
+
+
 def test_permutation_invariance_on_gpu():
     fr = synth.uniform_frame(32, 32, 10.0, 64, J=5, seed=12)
     g1 = gpu_run(fr)

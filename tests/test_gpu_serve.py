@@ -67,7 +67,9 @@ def test_served_frame_equals_direct_call_and_oracle(dtype):
 @pytest.mark.parametrize("dtype", [wt.BF16, wt.F32])
 def test_same_result_alone_and_in_mix(dtype):
     """A frame served alone and the same frame served among 24 concurrent
-    frames of other sizes and depths give the same composite."""
+    frames of other sizes and depths give the same composite: bit for bit, as
+    the build's fixed-point bins make every tile independent of fragment order
+    and of what else shares the launch."""
     probe = _frame(640, 360, 20.0, seed=7)
     with wt.Server(J=4, coeff_dtype=dtype, max_slots=8, mem_cap_bytes=8 << 30,
                    step_tiles=2048) as srv:
@@ -87,8 +89,8 @@ def test_same_result_alone_and_in_mix(dtype):
         assert srv.wait(pid, 60_000_000)
         srv.release(pid)
         for (rid2, o), fr in zip(ids, others):
-            assert (o - _direct(fr, dtype)).abs().max().item() <= TOL[dtype]
-    assert (out_alone - out_mix).abs().max().item() <= TOL[dtype]
+            assert torch.equal(o, _direct(fr, dtype))
+    assert torch.equal(out_alone, out_mix)
     assert torch.isfinite(out_mix).all()
 
 
