@@ -147,20 +147,33 @@ def barrier(world):
         torch.distributed.barrier()
 
 
+def _agg_device():
+    # NCCL reduces CUDA tensors; gloo (the CPU tests) reduces host tensors
+    return "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(x: float, world: int) -> float:
+    """Timing rule of the multi-GPU run: the slowest rank's time."""
     if world == 1:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_agg_device())
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
 
 
 def sum_over_ranks(x: float, world: int) -> float:
+    """Work of the whole job: every rank renders its own frame (weak scaling)."""
     if world == 1:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_agg_device())
     torch.distributed.all_reduce(t)
     return float(t.item())
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank renders an independent frame: pixels never cross ranks, so the
+    data path needs no collective."""
+    return seed + rank
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -201,7 +214,7 @@ def run_wt(args):
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
     # weak scaling: every rank renders its own independent frame
-    fr = synth.make(args.workload, seed=args.seed + rank, device=dev, **size_kw(args))
+    fr = synth.make(args.workload, seed=rank_seed(args.seed, rank), device=dev, **size_kw(args))
     torch.cuda.synchronize()
     n, P, J = fr.n, fr.P, fr.J
     dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[args.dtype]
