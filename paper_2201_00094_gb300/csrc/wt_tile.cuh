@@ -360,39 +360,29 @@ __device__ __forceinline__ void fill_zero(void *smem, int bytes) {
 }
 
 // Warp-segmented reduction by pixel: adds v into mine[lp] for every lane with
-// lp >= 0.  Called by all 32 lanes together.  Lanes holding the same pixel
-// are grouped; the lowest lane of each group gathers its peers' values one
-// shuffle round at a time (as many rounds as the largest group has extra
-// members, usually 0 or 1) and then updates the warp's own copy, so no two
-// lanes touch one word and no atomic is needed.
-__device__ __forceinline__ void warp_accumulate(float4 *mine, int lp, float4 v) {
+// lp >= 0.  Called by all 32 lanes together.  Each round, every pending lane
+// writes its lane number into its pixel's byte of the warp's owner array; the
+// lanes that read their own number back hold distinct pixels and update the
+// warp's private accumulators with a plain read-modify-write.  Lanes that lost
+// try again in the next round, so a warp needs as many rounds as its most
+// repeated pixel has lanes (usually one or two) and no atomic is used.
+__device__ __forceinline__ void warp_accumulate(float4 *mine, unsigned char *owner, int lp, float4 v) {
     const unsigned lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(0xffffffffu, lp);
-    const bool leader = lane == (unsigned)(__ffs(peers) - 1);
-    unsigned todo = (leader && lp >= 0) ? (peers & ~(1u << lane)) : 0u;
-    while (__any_sync(0xffffffffu, todo != 0u)) {
-        const int src = todo ? __ffs(todo) - 1 : (int)lane;
-        const float x = __shfl_sync(0xffffffffu, v.x, src);
-        const float y = __shfl_sync(0xffffffffu, v.y, src);
-        const float z = __shfl_sync(0xffffffffu, v.z, src);
-        const float w = __shfl_sync(0xffffffffu, v.w, src);
-        if (todo) {
-            v.x += x;
-            v.y += y;
-            v.z += z;
-            v.w += w;
-            todo &= todo - 1;
+    bool pending = lp >= 0;
+    while (__any_sync(0xffffffffu, pending)) {
+        if (pending) owner[lp] = (unsigned char)lane;
+        __syncwarp();
+        if (pending && owner[lp] == (unsigned char)lane) {
+            float4 o = mine[lp];
+            o.x += v.x;
+            o.y += v.y;
+            o.z += v.z;
+            o.w += v.w;
+            mine[lp] = o;
+            pending = false;
         }
+        __syncwarp();
     }
-    if (leader && lp >= 0) {
-        float4 o = mine[lp];
-        o.x += v.x;
-        o.y += v.y;
-        o.z += v.z;
-        o.w += v.w;
-        mine[lp] = o;
-    }
-    __syncwarp();  // the next call's readers see this write
 }
 
 // ---------------------------------------------------------------- error count
@@ -504,9 +494,9 @@ template <int J> __device__ __forceinline__ Pos locate(float s, uint32_t flags) 
         const float pos = s - 0.5f;
         q.lo = min(max((int)floorf(pos), 0), C - 2);
         q.t = fminf(fmaxf(pos - (float)q.lo, 0.f), 1.f);
-        const float B0 = q.lo < q.m ? 0.f : (q.lo == q.m ? 1.f - q.f : 1.f);
-        const float B1 = q.lo + 1 < q.m ? 0.f : (q.lo + 1 == q.m ? 1.f - q.f : 1.f);
-        q.g = fmaf(q.t, B1 - B0, B0);
+        // own bin values at lo, lo+1: (0, 1-f) when lo = m-1, (1-f, 1) when lo = m
+        const float omf = 1.f - q.f;
+        q.g = q.lo < q.m ? q.t * omf : fmaf(q.t, q.f, omf);
     } else {
         q.lo = q.m;
         q.t = 0.f;
@@ -628,10 +618,13 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsig
 // S += a with a shared-memory atomic.
 template <int J, bool COUNT>
 __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
-                                              float4 *accw, float *sS, unsigned &bad) {
+                                              float4 *accw, unsigned char *owners, float *sS,
+                                              unsigned &bad) {
     constexpr int LD = Shape<J>::LD;
     const uint32_t flags = p.flags;
-    float4 *mine = accw + (threadIdx.x >> 5) * (p.g.tile_w * p.g.tile_h);
+    const int npx = p.g.tile_w * p.g.tile_h;
+    float4 *mine = accw + (threadIdx.x >> 5) * npx;
+    unsigned char *owner = owners + (threadIdx.x >> 5) * npx;
     for_each_frag6(T.s, T.e, p,
                    [&](bool valid, uint32_t px, float z, float al, float r, float g, float b) {
         int lp = -1;
@@ -649,7 +642,7 @@ __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, co
                 ++bad;
             }
         }
-        warp_accumulate(mine, lp, c);
+        warp_accumulate(mine, owner, lp, c);
     });
 }
 
@@ -710,17 +703,19 @@ template <int J> struct Layout {
     static constexpr size_t plane(int npx) { return align16((size_t)npx * Shape<J>::LD * 4); }
     static constexpr size_t words(int npx) { return align16((size_t)npx * 4); }
     static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 16; }
+    static constexpr size_t owners(int npx) { return align16((size_t)kWarps * npx); }
     // build: F and G bins + nearest-depth words
     static constexpr size_t build(int npx) { return 2 * plane(npx) + words(npx); }
     // fused: F and G bins, replaced after the build by the bin values, the
     // warps' accumulators and the S words; then the nearest-depth words
     static constexpr size_t region(int npx) {
-        return 2 * plane(npx) > plane(npx) + accw(npx) + words(npx) ? 2 * plane(npx)
-                                                                      : plane(npx) + accw(npx) + words(npx);
+        return 2 * plane(npx) > plane(npx) + accw(npx) + words(npx) + owners(npx)
+                   ? 2 * plane(npx)
+                   : plane(npx) + accw(npx) + words(npx) + owners(npx);
     }
     static constexpr size_t fused(int npx) { return region(npx) + words(npx); }
-    // resolve: bin values + warps' accumulators + S words
-    static constexpr size_t resolve(int npx) { return plane(npx) + accw(npx) + words(npx); }
+    // resolve: bin values + warps' accumulators + S words + owner bytes
+    static constexpr size_t resolve(int npx) { return plane(npx) + accw(npx) + words(npx) + owners(npx); }
 };
 
 }  // namespace wt
