@@ -227,7 +227,7 @@ def run_wt(args):
                 torch.empty(P, 4, device=dev))
 
     coeff, out = buffers(dt)
-    desc = wt.make_desc(fr.width, fr.height, J, dt)
+    desc = wt.make_desc(fr.width, fr.height, J, dt, tile_w=fr.tile_w, tile_h=fr.tile_h)
 
     def step_fused(d=desc, c=coeff, o=out):
         if args.path == "fused":
@@ -275,7 +275,7 @@ def run_wt(args):
     variants = {}
     if not args.no_variants:
         for name, d2 in (("f32", wt.F32), ("bf16", wt.BF16), ("f16", wt.F16)):
-            dsc = wt.make_desc(fr.width, fr.height, J, d2)
+            dsc = wt.make_desc(fr.width, fr.height, J, d2, tile_w=fr.tile_w, tile_h=fr.tile_h)
             c2, o2 = buffers(d2)
             accum_bytes = n * 36 + 2 * P * C * DTYPE_BYTES[d2] + 16 * P
 
@@ -314,7 +314,7 @@ def run_wt(args):
         res = run_oracle_sample(fr, args.cpu_tiles, seed=1234)
         got = out.cpu().numpy()[res["pixel_ids"]]
         cpu = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_tiles} seeded random 16x16 tiles of the same frame "
+               "sample": f"{args.cpu_tiles} seeded random {fr.tile_w}x{fr.tile_h} tiles of the same frame "
                          f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
                          f"composite, FP64, single thread, {res['seconds']:.1f} s",
                "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
@@ -341,7 +341,7 @@ def run_wt(args):
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
                        "fragments_per_gpu": n, "pixels": P, "J": J,
                        "coeff_storage": args.dtype, "path": path_name,
-                       "size_override": args.size or None,
+                       "size_override": args.size or None, "tile": args.tile,
                        "l2": f"inputs larger than L2 ({n * 24 / 1e9:.1f} GB of fragments)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -413,13 +413,16 @@ def run_serving(args, dtype_name, pool=None):
     dev = torch.device("cuda")
     dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[dtype_name]
     reqs = synth.serve_request_params(args.serve_requests, seed=args.seed)
+    tw, th = tile_of(args)
     if pool is None:
         pool = {}
         for (w, h) in synth.SERVE_SIZES:
             for k, lam in enumerate(SERVE_LAMBDAS):
-                pool[(w, h, k)] = synth.serve_frame(w, h, lam, seed=1000 + 7 * k + w, device=dev)
+                pool[(w, h, k)] = synth.serve_frame(w, h, lam, seed=1000 + 7 * k + w, device=dev,
+                                                    tile_w=tw, tile_h=th)
         torch.cuda.synchronize()
-    srv = wt.Server(J=4, coeff_dtype=dt, max_slots=64, mem_cap_bytes=40 << 30, step_tiles=8192)
+    srv = wt.Server(J=4, coeff_dtype=dt, max_slots=64, mem_cap_bytes=40 << 30, step_tiles=8192,
+                    tile_w=tw, tile_h=th)
     pending = []
     lat, frags = [], 0
     t_start = time.perf_counter()
@@ -430,7 +433,7 @@ def run_serving(args, dtype_name, pool=None):
             fr = pool[(rq["width"], rq["height"], k)]
             while (time.perf_counter() - t_start) * 1e3 < rq["arrival_ms"]:
                 pass
-            d = wt.make_desc(fr.width, fr.height, 4, dt)
+            d = wt.make_desc(fr.width, fr.height, 4, dt, tile_w=fr.tile_w, tile_h=fr.tile_h)
             f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
             out = torch.empty(fr.P, 4, device=dev)
             rid = srv.submit(d, f, out, keep=fr)
@@ -489,20 +492,27 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
                    "fragments_per_gpu": fr.n, "pixels": fr.P, "J": fr.J,
-                   "coeff_storage": "f64", "path": "FP64 CPU oracle"},
+                   "coeff_storage": "f64", "path": "FP64 CPU oracle", "tile": args.tile},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step {tiles} seeded random 16x16 tiles of the frame, "
+                         "sample": f"per step {tiles} seeded random {fr.tile_w}x{fr.tile_h} tiles of the frame, "
                                    "build + resolve + composite, FP64, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def tile_of(args):
+    tw, th = (int(x) for x in args.tile.lower().split("x"))
+    return tw, th
+
+
 def size_kw(args):
-    if not args.size:
-        return {}
-    w, h = (int(x) for x in args.size.lower().split("x"))
-    return {"width": w, "height": h}
+    tw, th = tile_of(args)
+    kw = {"tile_w": tw, "tile_h": th}
+    if args.size:
+        w, h = (int(x) for x in args.size.lower().split("x"))
+        kw.update(width=w, height=h)
+    return kw
 
 
 def main():
@@ -512,6 +522,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wt", choices=["wt", "reference"])
     ap.add_argument("--workload", default="heavy4k", choices=sorted(WORKLOADS))
+    ap.add_argument("--tile", default="256x1",
+                    help="screen tile WxH (one CTA each); 256x1 row spans need no division")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--size", default="", help="override the workload's WxH (profiling runs)")

@@ -85,8 +85,7 @@ Params make_params(const wt_desc *d, const wt_frags *f) {
     p.g.tile_h = d->tile_h;
     p.g.ntx = (d->width + d->tile_w - 1) / d->tile_w;
     p.flags = d->flags;
-    // ceil(2^64 / width) for the row division (width == 1 needs none)
-    p.wmagic = d->width > 1 ? ~0ull / (unsigned long long)d->width + 1ull : 0ull;
+    set_row_division(p);
     if (f) {
         p.n = f->n;
         p.pixel = f->pixel;

@@ -59,7 +59,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     float *vals = reinterpret_cast<float *>(smem);
     float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
     float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
-    unsigned char *owners = smem + Layout<J>::plane(npx) + Layout<J>::accw(npx) + Layout<J>::words(npx);
     const Tile T = tile_of(p, blockIdx.x, true);
     const int lp = threadIdx.x;
     int64_t gp = -1;
@@ -75,7 +74,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     fill_zero(accw, (int)(Layout<J>::accw(npx) + Layout<J>::words(npx)));
     __syncthreads();
     unsigned bad = 0;
-    phase_resolve<J, true>(p, T, vals, accw, owners, sS, bad);
+    phase_resolve<J, true>(p, T, vals, accw, sS, bad);
     flush_bad(bad, p.err);
     __syncthreads();
     if (gp < 0) return;
@@ -115,7 +114,6 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     float *vals = reinterpret_cast<float *>(smem);
     float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
     float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
-    unsigned char *owners = smem + Layout<J>::plane(npx) + Layout<J>::accw(npx) + Layout<J>::words(npx);
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
     const Tile T = tile_of(p, tile, true);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
@@ -146,7 +144,7 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     }
     fill_zero(accw, (int)Layout<J>::accw(npx));
     __syncthreads();
-    phase_resolve<J, false>(p, T, vals, accw, owners, nullptr, bad);
+    phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);
     __syncthreads();
     if (gp >= 0) {
         const float4 a = sum_warps(accw, npx, lp);
@@ -202,7 +200,7 @@ template <int J> struct BackLayout {
     static constexpr size_t region(int npx) {
         return 2 * P(npx) > P(npx) + second(npx) ? 2 * P(npx) : P(npx) + second(npx);
     }
-    static constexpr size_t total(int npx) { return region(npx) + 9 * W(npx) + Layout<J>::owners(npx); }
+    static constexpr size_t total(int npx) { return region(npx) + 9 * W(npx); }
 };
 
 // Re-derives everything the adjoint needs about one fragment from its inputs
@@ -260,7 +258,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     float *sU = reinterpret_cast<float *>(wbase + 2 * WD);  // 3 planes
     float *sY = reinterpret_cast<float *>(wbase + 5 * WD);  // 3 planes
     float *sK = reinterpret_cast<float *>(wbase + 8 * WD);
-    unsigned char *owners = wbase + 9 * WD;
     const int wpl = (int)(WD / 4);  // floats per word plane
     const Tile T = tile_of(p, blockIdx.x, true);
     fill_zero(smem, (int)(2 * PL));
@@ -289,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     }
     fill_zero(accw, (int)Layout<J>::accw(npx));
     __syncthreads();
-    phase_resolve<J, false>(p, T, vals, accw, owners, nullptr, bad);  // forward sums, recomputed
+    phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);  // forward sums, recomputed
     __syncthreads();
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (gp >= 0) acc = sum_warps(accw, npx, lp);

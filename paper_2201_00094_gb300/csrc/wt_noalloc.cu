@@ -102,7 +102,7 @@ extern "C" wt_status wt_build_resolve_batch_static(const wt_desc *descs, const w
         p.g.tile_h = d.tile_h;
         p.g.ntx = (d.width + d.tile_w - 1) / d.tile_w;
         p.flags = d.flags;
-        p.wmagic = d.width > 1 ? ~0ull / (unsigned long long)d.width + 1ull : 0ull;
+        set_row_division(p);
         p.n = f.n;
         p.pixel = f.pixel;
         p.z = f.z;

@@ -454,7 +454,7 @@ wt_status wt_serve_submit(wt_server *s, const wt_desc *d, const wt_frags *f, con
     p.g.tile_h = d->tile_h;
     p.g.ntx = (d->width + d->tile_w - 1) / d->tile_w;
     p.flags = d->flags;
-    p.wmagic = d->width > 1 ? ~0ull / (unsigned long long)d->width + 1ull : 0ull;
+    set_row_division(p);
     p.n = f->n;
     p.pixel = f->pixel;
     p.z = f->z;

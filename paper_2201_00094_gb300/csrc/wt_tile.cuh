@@ -42,6 +42,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace wt {
 
 constexpr int kThreads = 256;    // threads per CTA (= max pixels per tile)
@@ -63,7 +65,8 @@ struct Geom {
 struct Params {
     Geom g;
     uint32_t flags;
-    uint64_t wmagic;  // floor((2^64-1) / width) + 1 for the division by width (0 when width == 1)
+    uint32_t wmagic32;  // ceil(2^32 / width) when that divides every in-tile offset exactly, else 0
+    uint64_t wmagic;    // ceil(2^64 / width) (0 when width == 1)
     int64_t n;
     const uint32_t *__restrict__ pixel;
     const float *__restrict__ z;
@@ -174,15 +177,35 @@ __device__ __forceinline__ Tile tile_of(const Params &p, int t, bool count_bad) 
 }
 
 // Local pixel index inside the tile, or -1 when the pixel is not in it.
-// d = pixel - tile origin; its row is d / width, taken as the high word of
-// d * ceil(2^64 / width) (exact for 32-bit d; Granlund & Montgomery 1994).
+// d = pixel - tile origin.  A tile one row high (a span of a row) needs no
+// division.  Otherwise the row is d / width, taken as the high word of
+// d * ceil(2^32 / width) when the host has shown that exact for every
+// d < tile_h * width, else of d * ceil(2^64 / width), exact for any 32-bit d
+// (Granlund & Montgomery 1994).
 __device__ __forceinline__ int local_pixel(uint32_t px, const Params &p, const Tile &T) {
     const uint32_t d = px - T.base;
+    if (p.g.tile_h == 1) return d < (uint32_t)T.tw ? (int)d : -1;
     if (d >= T.lim) return -1;
-    const uint32_t ly = p.wmagic ? (uint32_t)__umul64hi((uint64_t)d, p.wmagic) : d;
+    const uint32_t ly = p.wmagic32 ? __umulhi(d, p.wmagic32)
+                                   : (p.wmagic ? (uint32_t)__umul64hi((uint64_t)d, p.wmagic) : d);
     const uint32_t lx = d - ly * (uint32_t)p.g.width;
     if (lx >= (uint32_t)T.tw) return -1;
     return (int)(ly * (uint32_t)p.g.tile_w + lx);
+}
+
+// Host side: the two magic numbers of the row division for width and tile_h.
+// With m = ceil(2^32 / w) = (2^32 + e) / w, floor(d m / 2^32) = floor(d / w)
+// whenever d e < 2^32, so the 32-bit form is used when (tile_h w - 1) e < 2^32.
+inline void set_row_division(Params &p) {
+    const unsigned long long w = (unsigned long long)p.g.width;
+    p.wmagic = w > 1 ? ~0ull / w + 1ull : 0ull;
+    p.wmagic32 = 0;
+    if (w > 1) {
+        const unsigned long long m = ((1ull << 32) + w - 1) / w;
+        const unsigned long long e = m * w - (1ull << 32);
+        const unsigned long long dmax = (unsigned long long)p.g.tile_h * w - 1;
+        if (m < (1ull << 32) && dmax * e < (1ull << 32)) p.wmagic32 = (uint32_t)m;
+    }
 }
 
 // global pixel id of local pixel lp, or -1 if it lies outside the image
@@ -212,6 +235,19 @@ __device__ __forceinline__ float rcp(float x) {
     return y;
 }
 
+// floor(x) for 0 <= x < 2^23, as an integer and as a float, on the FP32 adder
+// instead of the conversion unit: x + 2^23 rounded toward zero is exactly
+// 2^23 + floor(x) (the representable numbers in [2^23, 2^24) are the
+// integers), whose low mantissa bits are floor(x).
+struct Floor {
+    int i;
+    float f;
+};
+__device__ __forceinline__ Floor floor_small(float x) {
+    const float big = __fadd_rz(x, 8388608.f);
+    return {__float_as_int(big) - 0x4B000000, big - 8388608.f};
+}
+
 // Absorbance step of one interface, a = -ln(1 - x) for x = clamped alpha
 // (v drops by the factor 1 - alpha across it).
 //  x <= 1/2: -ln(1 - x) = 2 atanh(s) with s = x / (2 - x) <= 1/3, summed as
@@ -236,119 +272,83 @@ __device__ __forceinline__ float step_of(float x) {
 
 // ---------------------------------------------------------------- streaming
 
-// Calls body(pixel, alpha) for every fragment of [s, e), 4 per 16-byte load.
-template <class Body>
-__device__ __forceinline__ void for_each_frag2(int64_t s, int64_t e, const Params &p, Body &&body) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    int64_t s4 = (s + 3) & ~int64_t(3), e4 = e & ~int64_t(3);
-    if (s4 > e4) s4 = e4 = e;
-    for (int64_t i = s + tid; i < s4; i += nt) body(p.pixel[i], p.alpha[i]);
-    const uint4 *px4 = reinterpret_cast<const uint4 *>(p.pixel);
-    const float4 *a4 = reinterpret_cast<const float4 *>(p.alpha);
-    for (int64_t q = (s4 >> 2) + tid; q < (e4 >> 2); q += nt) {
-        const uint4 pv = px4[q];
-        const float4 av = a4[q];
-        body(pv.x, av.x);
-        body(pv.y, av.y);
-        body(pv.z, av.z);
-        body(pv.w, av.w);
+// Up to four consecutive fragments held by one thread.  Only the arrays a
+// phase asks for are loaded (the others stay unset and are optimised away).
+enum : int { kWithZ = 1, kWithRGB = 2 };
+template <int N> struct Group {
+    static constexpr int size = N;
+    bool v;  // inside the range (all N fragments or none)
+    uint32_t px[N];
+    float al[N], z[N], r[N], g[N], b[N];
+};
+
+template <int LOAD>
+__device__ __forceinline__ void load_one(Group<1> &G, bool v, int64_t i, const Params &p) {
+    G.v = v;
+    G.px[0] = v ? p.pixel[i] : 0u;
+    G.al[0] = v ? p.alpha[i] : 0.f;
+    if (LOAD & kWithZ) G.z[0] = v ? p.z[i] : 0.f;
+    if (LOAD & kWithRGB) {
+        G.r[0] = v ? p.r[i] : 0.f;
+        G.g[0] = v ? p.gc[i] : 0.f;
+        G.b[0] = v ? p.b[i] : 0.f;
     }
-    for (int64_t i = e4 + tid; i < e; i += nt) body(p.pixel[i], p.alpha[i]);
 }
 
-// Calls body(pixel, z, alpha) for every fragment of [s, e), 4 per 16-byte load;
-// the loads of the next chunk are issued before the current one is processed.
-template <class Body>
-__device__ __forceinline__ void for_each_frag3(int64_t s, int64_t e, const Params &p, Body &&body) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    int64_t s4 = (s + 3) & ~int64_t(3), e4 = e & ~int64_t(3);
-    if (s4 > e4) s4 = e4 = e;
-    for (int64_t i = s + tid; i < s4; i += nt) body(p.pixel[i], p.z[i], p.alpha[i]);
-    const uint4 *px4 = reinterpret_cast<const uint4 *>(p.pixel);
-    const float4 *z4 = reinterpret_cast<const float4 *>(p.z);
-    const float4 *a4 = reinterpret_cast<const float4 *>(p.alpha);
-    {
-        const int64_t qe = e4 >> 2;
-        int64_t q = (s4 >> 2) + tid;
-        uint4 pv = make_uint4(0, 0, 0, 0);
-        float4 zv = make_float4(0.f, 0.f, 0.f, 0.f), av = zv;
-        if (q < qe) {
-            pv = px4[q];
-            zv = z4[q];
-            av = a4[q];
-        }
-        while (q < qe) {
-            const uint4 cp = pv;
-            const float4 cz = zv, ca = av;
-            const int64_t qn = q + nt;
-            if (qn < qe) {  // next chunk in flight while this one is processed
-                pv = px4[qn];
-                zv = z4[qn];
-                av = a4[qn];
-            }
-            body(cp.x, cz.x, ca.x);
-            body(cp.y, cz.y, ca.y);
-            body(cp.z, cz.z, ca.z);
-            body(cp.w, cz.w, ca.w);
-            q = qn;
+template <int LOAD>
+__device__ __forceinline__ void load_four(Group<4> &G, bool v, int64_t q, const Params &p) {
+    uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+    float4 av = make_float4(0.f, 0.f, 0.f, 0.f), zv = av, rv = av, gv = av, bv = av;
+    if (v) {
+        pv = reinterpret_cast<const uint4 *>(p.pixel)[q];
+        av = reinterpret_cast<const float4 *>(p.alpha)[q];
+        if (LOAD & kWithZ) zv = reinterpret_cast<const float4 *>(p.z)[q];
+        if (LOAD & kWithRGB) {
+            rv = reinterpret_cast<const float4 *>(p.r)[q];
+            gv = reinterpret_cast<const float4 *>(p.gc)[q];
+            bv = reinterpret_cast<const float4 *>(p.b)[q];
         }
     }
-    for (int64_t i = e4 + tid; i < e; i += nt) body(p.pixel[i], p.z[i], p.alpha[i]);
+    G.v = v;
+    G.px[0] = pv.x, G.px[1] = pv.y, G.px[2] = pv.z, G.px[3] = pv.w;
+    G.al[0] = av.x, G.al[1] = av.y, G.al[2] = av.z, G.al[3] = av.w;
+    G.z[0] = zv.x, G.z[1] = zv.y, G.z[2] = zv.z, G.z[3] = zv.w;
+    G.r[0] = rv.x, G.r[1] = rv.y, G.r[2] = rv.z, G.r[3] = rv.w;
+    G.g[0] = gv.x, G.g[1] = gv.y, G.g[2] = gv.z, G.g[3] = gv.w;
+    G.b[0] = bv.x, G.b[1] = bv.y, G.b[2] = bv.z, G.b[3] = bv.w;
 }
 
-// With colour: body(valid, pixel, z, alpha, r, g, b).  Trip counts are the
-// same for every lane of the block (lanes past the range get valid = false),
-// so the body may use warp-wide collectives.
-template <class Body>
-__device__ __forceinline__ void for_each_frag6(int64_t s, int64_t e, const Params &p, Body &&body) {
+// Calls body(Group<4>) for the 16-byte-aligned middle of the fragment range
+// [s, e) -- one vector load per array, the next group's loads in flight while
+// the body runs -- and body(Group<1>) for the unaligned head and tail.  Every
+// thread of the block makes the same number of calls (threads past the range
+// get v = false), so the body may use warp-wide collectives.  A body that
+// finishes all of a group's arithmetic before its shared-memory updates lets
+// the four fragments' latencies overlap.
+template <int LOAD, class Body>
+__device__ __forceinline__ void for_each_group(int64_t s, int64_t e, const Params &p, Body &&body) {
     const int tid = threadIdx.x, nt = blockDim.x;
     int64_t s4 = (s + 3) & ~int64_t(3), e4 = e & ~int64_t(3);
     if (s4 > e4) s4 = e4 = e;
     for (int64_t b0 = s; b0 < s4; b0 += nt) {
-        const int64_t i = b0 + tid;
-        const bool v = i < s4;
-        body(v, v ? p.pixel[i] : 0u, v ? p.z[i] : 0.f, v ? p.alpha[i] : 0.f, v ? p.r[i] : 0.f,
-             v ? p.gc[i] : 0.f, v ? p.b[i] : 0.f);
+        Group<1> G;
+        load_one<LOAD>(G, b0 + tid < s4, b0 + tid, p);
+        body(G);
     }
-    const uint4 *px4 = reinterpret_cast<const uint4 *>(p.pixel);
-    const float4 *z4 = reinterpret_cast<const float4 *>(p.z);
-    const float4 *a4 = reinterpret_cast<const float4 *>(p.alpha);
-    const float4 *r4 = reinterpret_cast<const float4 *>(p.r);
-    const float4 *g4 = reinterpret_cast<const float4 *>(p.gc);
-    const float4 *b4 = reinterpret_cast<const float4 *>(p.b);
     const int64_t qe = e4 >> 2;
-    {
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        int64_t q = (s4 >> 2) + tid;
-        bool v = q < qe;
-        uint4 pv = v ? px4[q] : make_uint4(0, 0, 0, 0);
-        float4 zv = v ? z4[q] : zero, av = v ? a4[q] : zero, rv = v ? r4[q] : zero;
-        float4 gv = v ? g4[q] : zero, bv = v ? b4[q] : zero;
-        for (int64_t q0 = s4 >> 2; q0 < qe; q0 += nt) {
-            const uint4 cp = pv;
-            const float4 cz = zv, ca = av, cr = rv, cg = gv, cb = bv;
-            const bool cv = v;
-            q += nt;
-            v = q < qe;
-            if (v) {  // next chunk in flight while this one is processed
-                pv = px4[q];
-                zv = z4[q];
-                av = a4[q];
-                rv = r4[q];
-                gv = g4[q];
-                bv = b4[q];
-            }
-            body(cv, cp.x, cz.x, ca.x, cr.x, cg.x, cb.x);
-            body(cv, cp.y, cz.y, ca.y, cr.y, cg.y, cb.y);
-            body(cv, cp.z, cz.z, ca.z, cr.z, cg.z, cb.z);
-            body(cv, cp.w, cz.w, ca.w, cr.w, cg.w, cb.w);
-        }
+    int64_t q = (s4 >> 2) + tid;
+    Group<4> next;
+    load_four<LOAD>(next, q < qe, q, p);
+    for (int64_t q0 = s4 >> 2; q0 < qe; q0 += nt) {
+        Group<4> cur = next;
+        q += nt;
+        load_four<LOAD>(next, q < qe, q, p);
+        body(cur);
     }
     for (int64_t b0 = e4; b0 < e; b0 += nt) {
-        const int64_t i = b0 + tid;
-        const bool v = i < e;
-        body(v, v ? p.pixel[i] : 0u, v ? p.z[i] : 0.f, v ? p.alpha[i] : 0.f, v ? p.r[i] : 0.f,
-             v ? p.gc[i] : 0.f, v ? p.b[i] : 0.f);
+        Group<1> G;
+        load_one<LOAD>(G, b0 + tid < e, b0 + tid, p);
+        body(G);
     }
 }
 
@@ -360,27 +360,29 @@ __device__ __forceinline__ void fill_zero(void *smem, int bytes) {
 }
 
 // Warp-segmented reduction by pixel: adds v into mine[lp] for every lane with
-// lp >= 0.  Called by all 32 lanes together.  Each round, every pending lane
-// writes its lane number into its pixel's byte of the warp's owner array; the
-// lanes that read their own number back hold distinct pixels and update the
-// warp's private accumulators with a plain read-modify-write.  Lanes that lost
-// try again in the next round, so a warp needs as many rounds as its most
-// repeated pixel has lanes (usually one or two) and no atomic is used.
-__device__ __forceinline__ void warp_accumulate(float4 *mine, unsigned char *owner, int lp, float4 v) {
-    const unsigned lane = threadIdx.x & 31;
-    bool pending = lp >= 0;
-    while (__any_sync(0xffffffffu, pending)) {
-        if (pending) owner[lp] = (unsigned char)lane;
-        __syncwarp();
-        if (pending && owner[lp] == (unsigned char)lane) {
-            float4 o = mine[lp];
-            o.x += v.x;
-            o.y += v.y;
-            o.z += v.z;
-            o.w += v.w;
-            mine[lp] = o;
-            pending = false;
-        }
+// lp >= 0.  Called by all 32 lanes together.  The lanes holding the same pixel
+// are grouped (match.any) and ranked by lane number; in round r the lanes of
+// rank r -- at most one per pixel -- update the warp's private accumulators
+// with a plain read-modify-write.  A warp needs as many rounds as its most
+// repeated pixel has lanes (usually one or two), and no atomic is used.  The
+// order of the additions depends only on the lanes' contents, so the sums are
+// the same on every run.
+__device__ __forceinline__ void accumulate_into(float4 *mine, int lp, float4 v) {
+    float4 o = mine[lp];
+    o.x += v.x;
+    o.y += v.y;
+    o.z += v.z;
+    o.w += v.w;
+    mine[lp] = o;
+}
+__device__ __forceinline__ void warp_accumulate(float4 *mine, int lp, float4 v) {
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const unsigned rank = __popc(__match_any_sync(0xffffffffu, lp) & lt);
+    if (lp >= 0 && rank == 0) accumulate_into(mine, lp, v);
+    __syncwarp();
+    for (unsigned r = 1; __any_sync(0xffffffffu, lp >= 0 && rank >= r); ++r) {
+        if (lp >= 0 && rank == r) accumulate_into(mine, lp, v);
         __syncwarp();
     }
 }
@@ -488,12 +490,16 @@ struct Pos {
 template <int J> __device__ __forceinline__ Pos locate(float s, uint32_t flags) {
     constexpr int C = 1 << J;
     Pos q;
-    q.m = (int)s;
-    q.f = s - (float)q.m;
+    const Floor fm = floor_small(s);
+    q.m = fm.i;
+    q.f = s - fm.f;
     if (flags & kLinear) {
-        const float pos = s - 0.5f;
-        q.lo = min(max((int)floorf(pos), 0), C - 2);
-        q.t = fminf(fmaxf(pos - (float)q.lo, 0.f), 1.f);
+        // pos clamped to [0, C-1]: lo = min(floor(pos), C-2), t = pos - lo,
+        // which is t = 0 left of the first centre and t = 1 right of the last
+        const float pos = fminf(fmaxf(s - 0.5f, 0.f), (float)(C - 1));
+        const Floor fl = floor_small(pos);
+        q.lo = min(fl.i, C - 2);
+        q.t = pos - fminf(fl.f, (float)(C - 2));
         // own bin values at lo, lo+1: (0, 1-f) when lo = m-1, (1-f, 1) when lo = m
         const float omf = 1.f - q.f;
         q.g = q.lo < q.m ? q.t * omf : fmaf(q.t, q.f, omf);
@@ -572,12 +578,17 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsig
                                            unsigned *sZ, unsigned &bad) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
     constexpr int CNT = Shape<J>::CNT, AMAX = Shape<J>::AMAX, INV = Shape<J>::INV;
-    for_each_frag2(T.s, T.e, p, [&](uint32_t px, float al) {
-        if (!(al == al)) return;
-        const int lp = local_pixel(px, p, T);
-        if (lp < 0) return;
-        atomicAdd(&sF[lp * LD + CNT], 1u);
-        atomicMax(&sF[lp * LD + AMAX], __float_as_uint(clamp_alpha(al)));
+    for_each_group<0>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int lp = G.v && G.al[k] == G.al[k] ? local_pixel(G.px[k], p, T) : -1;
+            if (lp >= 0) {
+                unsigned *row = sF + lp * LD;
+                atomicAdd(&row[CNT], 1u);
+                atomicMax(&row[AMAX], __float_as_uint(clamp_alpha(G.al[k])));
+            }
+        }
     });
     __syncthreads();
     for (int lp = threadIdx.x; lp < p.g.tile_w * p.g.tile_h; lp += blockDim.x) {
@@ -588,26 +599,34 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsig
         row[AMAX] = __float_as_uint(ldexpf(1.f, 30 - e));  // s_p (the maximum is no longer needed)
     }
     __syncthreads();
-    for_each_frag3(T.s, T.e, p, [&](uint32_t px, float z, float al) {
-        if (!(z == z) || !(al == al)) {
-            ++bad;
-            return;
+    for_each_group<kWithZ>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+        int lp[N];
+        float sp[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            lp[k] = -1;
+            if (G.v) {
+                if (G.z[k] == G.z[k] && G.al[k] == G.al[k]) lp[k] = local_pixel(G.px[k], p, T);
+                if (lp[k] < 0) ++bad;
+            }
         }
-        const int lp = local_pixel(px, p, T);
-        if (lp < 0) {
-            ++bad;
-            return;
+        // the group's scale reads, then its arithmetic, then its atomics
+#pragma unroll
+        for (int k = 0; k < N; ++k) sp[k] = lp[k] >= 0 ? __uint_as_float(sF[lp[k] * LD + AMAX]) : 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if (lp[k] < 0) continue;
+            const float a = step_of(clamp_alpha(G.al[k]));
+            const float zc = clamp_depth(G.z[k]);
+            const float s = zc * (float)C;  // exact: C is a power of two
+            const Floor m = floor_small(s);
+            const float f = s - m.f;
+            const float as = a * sp[k];
+            atomicAdd(&sF[lp[k] * LD + m.i], __float2uint_rn(as * f));
+            atomicAdd(&sG[lp[k] * LD + m.i], __float2uint_rn(as * (1.f - f)));
+            if (a > 0.f) atomicMin(&sZ[lp[k]], __float_as_uint(zc));
         }
-        const float sp = __uint_as_float(sF[lp * LD + AMAX]);
-        const float a = step_of(clamp_alpha(al));
-        const float zc = clamp_depth(z);
-        const float s = zc * (float)C;  // exact: C is a power of two
-        const int m = (int)s;
-        const float f = s - (float)m;
-        const float as = a * sp;
-        atomicAdd(&sF[lp * LD + m], __float2uint_rn(as * f));
-        atomicAdd(&sG[lp * LD + m], __float2uint_rn(as * (1.f - f)));
-        if (a > 0.f) atomicMin(&sZ[lp], __float_as_uint(zc));
     });
 }
 
@@ -618,31 +637,30 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsig
 // S += a with a shared-memory atomic.
 template <int J, bool COUNT>
 __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
-                                              float4 *accw, unsigned char *owners, float *sS,
+                                              float4 *accw, float *sS,
                                               unsigned &bad) {
     constexpr int LD = Shape<J>::LD;
     const uint32_t flags = p.flags;
     const int npx = p.g.tile_w * p.g.tile_h;
     float4 *mine = accw + (threadIdx.x >> 5) * npx;
-    unsigned char *owner = owners + (threadIdx.x >> 5) * npx;
-    for_each_frag6(T.s, T.e, p,
-                   [&](bool valid, uint32_t px, float z, float al, float r, float g, float b) {
-        int lp = -1;
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) {
-            if (z == z && al == al) lp = local_pixel(px, p, T);
-            if (lp >= 0) {
-                const float ac = clamp_alpha(al);
-                const float a = step_of(ac);
-                const float Ah = frag_absorbance<J>(A2 + lp * LD, clamp_depth(z), a * kLog2e, flags);
-                const float w = ac * ex2(-Ah);
-                c = make_float4(r * w, g * w, b * w, w);
-                if (sS) atomicAdd(&sS[lp], a);
-            } else if (COUNT) {
-                ++bad;
-            }
+    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int lp = G.v && G.z[k] == G.z[k] && G.al[k] == G.al[k] ? local_pixel(G.px[k], p, T) : -1;
+            if (COUNT && G.v && lp < 0) ++bad;
+            // a lane without a valid fragment evaluates pixel 0 and adds nothing
+            const bool ok = lp >= 0;
+            const int l = ok ? lp : 0;
+            const float ac = ok ? clamp_alpha(G.al[k]) : 0.f;
+            const float a = step_of(ac);
+            const float Ah = frag_absorbance<J>(A2 + l * LD, clamp_depth(G.z[k]), a * kLog2e, flags);
+            const float w = ac * ex2(-Ah);
+            const float4 c = ok ? make_float4(G.r[k] * w, G.g[k] * w, G.b[k] * w, w)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sS && ok) atomicAdd(&sS[l], a);
+            warp_accumulate(mine, lp, c);
         }
-        warp_accumulate(mine, owner, lp, c);
     });
 }
 
@@ -703,19 +721,18 @@ template <int J> struct Layout {
     static constexpr size_t plane(int npx) { return align16((size_t)npx * Shape<J>::LD * 4); }
     static constexpr size_t words(int npx) { return align16((size_t)npx * 4); }
     static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 16; }
-    static constexpr size_t owners(int npx) { return align16((size_t)kWarps * npx); }
     // build: F and G bins + nearest-depth words
     static constexpr size_t build(int npx) { return 2 * plane(npx) + words(npx); }
     // fused: F and G bins, replaced after the build by the bin values, the
     // warps' accumulators and the S words; then the nearest-depth words
     static constexpr size_t region(int npx) {
-        return 2 * plane(npx) > plane(npx) + accw(npx) + words(npx) + owners(npx)
+        return 2 * plane(npx) > plane(npx) + accw(npx) + words(npx)
                    ? 2 * plane(npx)
-                   : plane(npx) + accw(npx) + words(npx) + owners(npx);
+                   : plane(npx) + accw(npx) + words(npx);
     }
     static constexpr size_t fused(int npx) { return region(npx) + words(npx); }
-    // resolve: bin values + warps' accumulators + S words + owner bytes
-    static constexpr size_t resolve(int npx) { return plane(npx) + accw(npx) + words(npx) + owners(npx); }
+    // resolve: bin values + warps' accumulators + S words
+    static constexpr size_t resolve(int npx) { return plane(npx) + accw(npx) + words(npx); }
 };
 
 }  // namespace wt

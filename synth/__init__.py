@@ -164,8 +164,9 @@ def uniform_frame(width, height, lam, cap=None, alpha_range=(0.05, 0.6), J=4, se
                    tile_w, tile_h)
 
 
-def plain64(seed=0, device="cpu"):
-    return uniform_frame(64, 64, 4.0, 16, (0.05, 0.6), 4, seed, device, name="plain64")
+def plain64(seed=0, device="cpu", tile_w=TILE, tile_h=TILE):
+    return uniform_frame(64, 64, 4.0, 16, (0.05, 0.6), 4, seed, device, tile_w, tile_h,
+                         name="plain64")
 
 
 def _value_noise(width, height, cell, g, device):
@@ -177,7 +178,7 @@ def _value_noise(width, height, cell, g, device):
     return up[0, 0, :height, :width].reshape(-1)
 
 
-def smoke1080(seed=0, device="cpu", width=1920, height=1080, J=4):
+def smoke1080(seed=0, device="cpu", width=1920, height=1080, J=4, tile_w=TILE, tile_h=TILE):
     g = _gen(device, seed)
     P = width * height
     noise = _value_noise(width, height, 64, g, device)
@@ -187,7 +188,7 @@ def smoke1080(seed=0, device="cpu", width=1920, height=1080, J=4):
     c_smoke = _lognormal_counts(P, 32.0, 512, g, device)
     c_surf = torch.randint(0, 5, (P,), generator=g, device=device, dtype=torch.int32)
     counts = torch.where(smoke, c_smoke, c_surf)
-    pixel, offsets = assemble(width, height, counts, g, device)
+    pixel, offsets = assemble(width, height, counts, g, device, tile_w, tile_h)
     n = pixel.numel()
     is_smoke = smoke[pixel.to(torch.int64)]
     slab = torch.randint(0, 3, (n,), generator=g, device=device)
@@ -199,14 +200,15 @@ def smoke1080(seed=0, device="cpu", width=1920, height=1080, J=4):
     a_surf = _uniform(n, 0.3, 0.9, g, device)
     alpha = torch.where(is_smoke, a_smoke, a_surf)
     return _finish("smoke1080", width, height, J, pixel, offsets, z, alpha, g, device, counts,
-                   TILE, TILE)
+                   tile_w, tile_h)
 
 
-def heavy4k(seed=0, device="cpu", width=3840, height=2160, J=5, mean=24.0, cap=1024):
+def heavy4k(seed=0, device="cpu", width=3840, height=2160, J=5, mean=24.0, cap=1024,
+            tile_w=TILE, tile_h=TILE):
     g = _gen(device, seed)
     P = width * height
     counts = _lognormal_counts(P, mean, cap, g, device)
-    pixel, offsets = assemble(width, height, counts, g, device)
+    pixel, offsets = assemble(width, height, counts, g, device, tile_w, tile_h)
     n = pixel.numel()
     slab = torch.randint(0, 5, (n,), generator=g, device=device)
     means = torch.tensor([0.1, 0.3, 0.5, 0.7, 0.9], device=device)[slab]
@@ -217,7 +219,7 @@ def heavy4k(seed=0, device="cpu", width=3840, height=2160, J=5, mean=24.0, cap=1
     del z_slab, z_uni, pick_uni, means, slab
     alpha = _uniform(n, 0.01, 0.4, g, device)
     return _finish("heavy4k", width, height, J, pixel, offsets, z, alpha, g, device, counts,
-                   TILE, TILE)
+                   tile_w, tile_h)
 
 
 def diff512(seed=0, device="cpu", width=512, height=512, J=4):
@@ -239,8 +241,9 @@ def serve_request_params(num, seed=0, mean_gap_ms=2.0):
             for i in range(num)]
 
 
-def serve_frame(width, height, lam, seed, device="cpu", J=4):
-    return uniform_frame(width, height, lam, None, (0.02, 0.6), J, seed, device, name="serve")
+def serve_frame(width, height, lam, seed, device="cpu", J=4, tile_w=TILE, tile_h=TILE):
+    return uniform_frame(width, height, lam, None, (0.02, 0.6), J, seed, device, tile_w, tile_h,
+                         name="serve")
 
 
 WORKLOADS = {"plain64": plain64, "smoke1080": smoke1080, "heavy4k": heavy4k, "diff512": diff512}

@@ -54,6 +54,29 @@ def test_ragged_tiles_every_J(J, tile):
     np.testing.assert_allclose(gf["out"], r["out"], atol=1e-4, rtol=0)
 
 
+def test_row_span_tiles():
+    """Tiles one row high (256 x 1, the benchmark's shape) need no division."""
+    fr = synth.uniform_frame(611, 23, 6.0, 40, J=5, seed=611, tile_w=256, tile_h=1)
+    r = oracle_run(fr)
+    for fused in (False, True):
+        g = gpu_run(fr, fused=fused)
+        assert g["bad"] == 0
+        np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
+
+
+def test_wide_image_general_row_division():
+    """At width 30000 with 16-row tiles the 32-bit reciprocal of the width is
+    not exact for every in-tile offset, so the 64-bit one is used."""
+    w = 30000
+    m = -(-(1 << 32) // w)
+    assert (16 * w - 1) * (m * w - (1 << 32)) >= 1 << 32
+    fr = synth.uniform_frame(w, 20, 0.3, 8, J=3, seed=30000)
+    r = oracle_run(fr)
+    g = gpu_run(fr, fused=True)
+    assert g["bad"] == 0
+    np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
+
+
 @pytest.mark.parametrize("flags", ALL_FLAGS)
 def test_every_reading_flag(flags):
     fr = synth.uniform_frame(40, 24, 8.0, 64, J=4, seed=100 + flags)
