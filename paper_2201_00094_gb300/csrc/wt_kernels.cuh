@@ -25,15 +25,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;  // +inf
     __syncthreads();
     unsigned bad = 0;
-    phase_bins<J>(p, T, sF, sG, sZ, bad);
+    const bool scaled = phase_bins<J>(p, T, sF, sG, sZ, bad);
     flush_bad(bad, p.err);
-    __syncthreads();
     const int lp = threadIdx.x;
     if (lp >= npx) return;
     const int64_t gp = global_pixel(p, T, lp);
     if (gp < 0) return;
     float c[C], S;
-    bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S);
+    bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
     CT *dst = static_cast<CT *>(p.coeff) + gp * C;
     const bool acc = (p.flags & kAccumulate) != 0;
     if (acc) {
@@ -49,16 +48,17 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
         p.zmin[gp] = v;
     }
 }
+}
 
 // §2.1 step 3 (+ step 4 when COMPOSITE): resolve against stored coefficients.
 template <int J, typename CT, bool COMPOSITE>
 __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Params p) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+    constexpr int C = Shape<J>::C, LDV = Shape<J>::LDV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
     float *vals = reinterpret_cast<float *>(smem);
-    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
-    float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
+    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::vplane(npx));
+    float *sS = reinterpret_cast<float *>(smem + Layout<J>::vplane(npx) + Layout<J>::accw(npx));
     const Tile T = tile_of(p, blockIdx.x, true);
     const int lp = threadIdx.x;
     int64_t gp = -1;
@@ -66,10 +66,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     if (gp >= 0) {
         float v[C];
         load_row<CT, C>(static_cast<const CT *>(p.coeff) + gp * C, v);
-        coeffs_to_bins<J>(v);
-#pragma unroll
-        for (int i = 0; i < C; ++i) v[i] *= kLog2e;
-        put_bins<J>(vals + lp * LD, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000), p.flags);
+        coeffs_to_bins<J>(v, kLog2e);
+        put_bins<J>(vals + lp * LDV, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000), p.flags);
     }
     fill_zero(accw, (int)(Layout<J>::accw(npx) + Layout<J>::words(npx)));
     __syncthreads();
@@ -105,44 +103,51 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
 // shared memory for its next tile.
 template <int J, typename CT>
 __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned char *smem) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
     const int npx = p.g.tile_w * p.g.tile_h;
     unsigned *sF = reinterpret_cast<unsigned *>(smem);
     unsigned *sG = reinterpret_cast<unsigned *>(smem + Layout<J>::plane(npx));
     // after the build: bin values over the F bins, then the warps'
     // accumulators and the S words over the G bins
     float *vals = reinterpret_cast<float *>(smem);
-    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::plane(npx));
-    float *sS = reinterpret_cast<float *>(smem + Layout<J>::plane(npx) + Layout<J>::accw(npx));
+    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::vplane(npx));
+    float *sS = reinterpret_cast<float *>(smem + Layout<J>::vplane(npx) + Layout<J>::accw(npx));
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
     const Tile T = tile_of(p, tile, true);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
     __syncthreads();
     unsigned bad = 0;
-    phase_bins<J>(p, T, sF, sG, sZ, bad);
+    const bool scaled = phase_bins<J>(p, T, sF, sG, sZ, bad);
     flush_bad(bad, p.err);
-    __syncthreads();
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
+    // the coefficient rows go out through a staging copy over the (not yet
+    // used) accumulator area when they are whole 16-byte chunks
+    CT *coeff = static_cast<CT *>(p.coeff);
+    const bool stage = Staged<CT, C>::ok && coeff != nullptr;
     float v[C], S = 0.f;
     if (gp >= 0) {
-        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S);
+        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S, scaled);
 #pragma unroll
         for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(Cvt<CT>::to(v[i]));  // storage precision
-        if (p.coeff) store_row<CT, C>(static_cast<CT *>(p.coeff) + gp * C, v);
+        if (coeff && !stage) store_row<CT, C>(coeff + gp * C, v);
         if (p.zmin) p.zmin[gp] = __uint_as_float(sZ[lp]);
-        coeffs_to_bins<J>(v);
-#pragma unroll
-        for (int i = 0; i < C; ++i) v[i] *= kLog2e;
     }
     __syncthreads();  // every bin row has been read
     if (gp >= 0) {
-        put_bins<J>(vals + lp * LD, v, __uint_as_float(sZ[lp]), p.flags);
+        if (stage) stage_row<CT, C>(reinterpret_cast<uint4 *>(accw), lp, v);
+        coeffs_to_bins<J>(v, kLog2e);
+        put_bins<J>(vals + lp * LDV, v, __uint_as_float(sZ[lp]), p.flags);
         sS[lp] = S;
     }
-    fill_zero(accw, (int)Layout<J>::accw(npx));
+    if (stage) {
+        __syncthreads();  // staged rows complete
+        copy_staged<CT, C>(p, T, reinterpret_cast<uint4 *>(accw), (int)Layout<J>::accw(npx), coeff);
+    } else {
+        fill_zero(accw, (int)Layout<J>::accw(npx));
+    }
     __syncthreads();
     phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);
     __syncthreads();
@@ -193,12 +198,13 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value)
 // per-pixel words (depth, S, u[3], ybar[3], const).
 template <int J> struct BackLayout {
     static constexpr size_t P(int npx) { return Layout<J>::plane(npx); }
+    static constexpr size_t V(int npx) { return Layout<J>::vplane(npx); }
     static constexpr size_t W(int npx) { return Layout<J>::words(npx); }
     static constexpr size_t second(int npx) {
         return Layout<J>::accw(npx) > P(npx) ? Layout<J>::accw(npx) : P(npx);
     }
     static constexpr size_t region(int npx) {
-        return 2 * P(npx) > P(npx) + second(npx) ? 2 * P(npx) : P(npx) + second(npx);
+        return 2 * P(npx) > V(npx) + second(npx) ? 2 * P(npx) : V(npx) + second(npx);
     }
     static constexpr size_t total(int npx) { return region(npx) + 9 * W(npx); }
 };
@@ -222,7 +228,7 @@ __device__ __forceinline__ FragState<J> frag_state(const Params &p, const Tile &
     st.ac = clamp_alpha(al);
     st.a = step_of(st.ac);
     st.q = locate<J>(clamp_depth(z) * (float)(1 << J), p.flags);
-    const float full = recon_at<J>(vals + st.lp * Shape<J>::LD, st.q, p.flags);
+    const float full = recon_at<J>(vals + st.lp * Shape<J>::LDV, st.q, p.flags);
     const float Ah = (p.flags & kSelfExclude) ? fmaxf(full - st.a * kLog2e * st.q.g, 0.f) : full;
     st.w = st.ac * ex2(-Ah);
     return st;
@@ -243,15 +249,15 @@ __device__ __forceinline__ FragState<J> frag_state(const Params &p, const Tile &
 // Coefficients are rebuilt here (never stored between the passes).
 template <int J, typename CT>
 __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
-    const size_t PL = Layout<J>::plane(npx), WD = Layout<J>::words(npx);
+    const size_t PL = Layout<J>::plane(npx), VL = Layout<J>::vplane(npx), WD = Layout<J>::words(npx);
     unsigned *sF = reinterpret_cast<unsigned *>(smem);
     unsigned *sG = reinterpret_cast<unsigned *>(smem + PL);
     float *vals = reinterpret_cast<float *>(smem);
-    float4 *accw = reinterpret_cast<float4 *>(smem + PL);
-    float *gam = reinterpret_cast<float *>(smem + PL);  // replaces the accumulators
+    float4 *accw = reinterpret_cast<float4 *>(smem + VL);
+    float *gam = reinterpret_cast<float *>(smem + VL);  // replaces the accumulators
     unsigned char *wbase = smem + BackLayout<J>::region(npx);
     unsigned *sZ = reinterpret_cast<unsigned *>(wbase);
     float *sS = reinterpret_cast<float *>(wbase + WD);
@@ -264,24 +270,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
     __syncthreads();
     unsigned bad = 0;
-    phase_bins<J>(p, T, sF, sG, sZ, bad);
+    const bool scaled = phase_bins<J>(p, T, sF, sG, sZ, bad);
     flush_bad(bad, p.err);
-    __syncthreads();
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
     float v[C], S = 0.f;
     if (gp >= 0) {
-        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S);
+        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S, scaled);
 #pragma unroll
         for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(Cvt<CT>::to(v[i]));
-        coeffs_to_bins<J>(v);
-#pragma unroll
-        for (int i = 0; i < C; ++i) v[i] *= kLog2e;
+        coeffs_to_bins<J>(v, kLog2e);
     }
     __syncthreads();
     if (gp >= 0) {
-        put_bins<J>(vals + lp * LD, v, __uint_as_float(sZ[lp]), p.flags);
+        put_bins<J>(vals + lp * LDV, v, __uint_as_float(sZ[lp]), p.flags);
         sS[lp] = S;
     }
     fill_zero(accw, (int)Layout<J>::accw(npx));

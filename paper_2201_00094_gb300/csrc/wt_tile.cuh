@@ -11,11 +11,10 @@
 // (bin m = floor(C z), fraction f = C z - m):
 //     F_m = sum a_i f_i,      G_m = sum a_i (1 - f_i),
 // and an O(C) tree per pixel turns the bins into the coefficients of §2.3.1.
-// The bins are 32-bit fixed point with a per-pixel power-of-two scale s_p
-// chosen by a counting pass (c_p fragments whose largest step is a_max give
-// c_p a_max s_p <= 2^31, so no bin can overflow), and are added with integer
-// atomics: the sums do not depend on the order of the fragments, so the
-// coefficients -- and everything computed from them in one CTA -- are the
+// The bins are 32-bit fixed point (scale 2^27; a tile whose bins would wrap is
+// rebuilt with per-pixel scales from a counting pass) and are added with
+// integer atomics: the sums do not depend on the order of the fragments, so
+// the coefficients -- and everything computed from them in one CTA -- are the
 // same on every run, alone or batched with other frames.
 // For a dyadic interval I with children L, R and u the position normalised to
 // I, F_I = sum_I a u and G_I = sum_I a (1-u) satisfy
@@ -28,13 +27,12 @@
 // values at the bin centres (§2.3.2), kept in shared memory pre-multiplied by
 // log2(e), so a fragment's transmittance is one ex2 instruction.
 //
-// The build's bins take FP32 shared-memory atomic adds (separate F and G
-// planes, so a warp's lanes spread over the banks).  The resolve's per-pixel
-// sums use a warp-segmented reduction instead of atomics: the lanes of a warp
-// that hold the same pixel are grouped (match.any), the group's leader adds
-// its peers' values through shuffles and applies one plain read-modify-write
-// to the warp's private copy of the accumulators; the copies are summed per
-// pixel at the end of the tile.
+// The build's F and G bins live in separate shared planes, so a warp's lanes
+// spread over the banks.  The resolve's per-pixel sums use a warp-segmented
+// reduction instead of atomics: the lanes of a warp that hold the same pixel
+// are ranked (match.any) and update the warp's private copy of the
+// accumulators in rank order with plain read-modify-writes; the copies are
+// summed per pixel at the end of the tile.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -49,13 +47,14 @@ namespace wt {
 constexpr int kThreads = 256;    // threads per CTA (= max pixels per tile)
 constexpr int kMaxTilePx = 256;
 constexpr int kWarps = kThreads / 32;  // warp-private copies of the per-pixel accumulators
-constexpr int kCasLimit = 1 << 20;  // bound on CAS retries (never reached in practice)
 // alpha is clamped to [0, 1 - 2^-20] and z to [0, 1 - 2^-24] (exact in FP32)
 constexpr float kAlphaMax = 0.99999904632568359375f;
 constexpr float kZMax = 0.999999940395355224609375f;
 constexpr float kLog2e = 1.44269504088896340736f;
 // the largest step after the clamp is -ln(2^-20) = 20 ln 2, i.e. 20 in log2 units
 constexpr float kStepCapLog2 = 20.0f;
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 struct Geom {
     int width, height, tile_w, tile_h, ntx;
@@ -92,10 +91,26 @@ enum : uint32_t { kSelfExclude = 1u, kLinear = 2u, kNormalized = 4u, kAccumulate
 
 template <int J> struct Shape {
     static constexpr int C = 1 << J;
-    static constexpr int LD = C + 4;  // words per pixel row of bins / bin values (16-byte rows)
+    static constexpr int LD = C + 4;  // words per pixel row of bins (16-byte rows)
     // the padding words of a pixel's F row hold its counting-pass results
     static constexpr int CNT = C, AMAX = C + 1, INV = C + 2;
+    // Row of bin values (16-byte rows): word V0 + m holds A_m, and the row is
+    // padded on both sides with copies of the end values (word V0 - 1 = A_0,
+    // word V0 + C = A_{C-1}), so the linear reconstruction reads entries
+    // lo, lo + 1 of the padded sequence at words V0 - 1 + lo for every
+    // lo in [0, C] with no clamping.
+    static constexpr int V0 = 4, LDV = C + 8;
 };
+
+// The build's bins are 32-bit fixed point, F and G scaled by 2^27: one
+// fragment adds at most 20 ln 2 * 2^27 < 2^31, and a bin holds up to 32
+// absorbance units before its word wraps.  A wrap is detected from the atomic's
+// return value; the tile is then rebuilt with per-pixel scales (a counting pass
+// bounds every pixel's sums), so the bins never overflow.  Tiles holding a step
+// below 2^-7 are rebuilt the same way, so every step keeps a relative
+// resolution of 2^-21 or better.
+constexpr float kBinScale = 134217728.f;              // 2^27
+constexpr float kBinInv = 7.450580596923828125e-9f;  // 2^-27
 
 // ---------------------------------------------------------------- storage
 
@@ -146,6 +161,46 @@ __device__ __forceinline__ void load_row(const CT *src, float (&v)[C]) {
     } else {
 #pragma unroll
         for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(src[i]);
+    }
+}
+
+// Coefficient rows of a tile staged in shared memory, so that they reach
+// global memory in coalesced 16-byte vectors (a thread's own 128-byte row
+// written directly would touch 32 cache lines per warp instruction).  A row of
+// K = C * sizeof(CT) / 16 chunks is staged at chunks lp*K .. lp*K + K-1 with
+// chunk q at position q ^ sw(lp): the eight lanes of a quarter warp then
+// write eight distinct bank groups.
+template <typename CT, int C> struct Staged {
+    static constexpr bool ok = (C * (int)sizeof(CT)) % 16 == 0;
+    static constexpr int K = ok ? C * (int)sizeof(CT) / 16 : 1;  // (unused when not ok)
+    static __device__ __forceinline__ int sw(int lp) { return (lp / (K >= 8 ? 1 : 8 / K)) & (K - 1); }
+};
+
+template <typename CT, int C>
+__device__ __forceinline__ void stage_row(uint4 *stage, int lp, const float (&v)[C]) {
+    using S = Staged<CT, C>;
+    constexpr int PER = 16 / sizeof(CT);
+    const int sw = S::sw(lp);
+#pragma unroll
+    for (int q = 0; q < S::K; ++q) {
+        union { uint4 u; CT e[PER]; } pk;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) pk.e[i] = Cvt<CT>::to(v[q * PER + i]);
+        stage[lp * S::K + (q ^ sw)] = pk.u;
+    }
+}
+
+template <typename CT, int C>
+__device__ __forceinline__ void unstage_row(const uint4 *stage, int lp, float (&v)[C]) {
+    using S = Staged<CT, C>;
+    constexpr int PER = 16 / sizeof(CT);
+    const int sw = S::sw(lp);
+#pragma unroll
+    for (int q = 0; q < S::K; ++q) {
+        union { uint4 u; CT e[PER]; } pk;
+        pk.u = stage[lp * S::K + (q ^ sw)];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) v[q * PER + i] = Cvt<CT>::from(pk.e[i]);
     }
 }
 
@@ -213,6 +268,54 @@ __device__ __forceinline__ int64_t global_pixel(const Params &p, const Tile &T, 
     const int lx = lp % p.g.tile_w, ly = lp / p.g.tile_w;
     if (lx >= T.tw || ly >= T.th) return -1;
     return (int64_t)(T.ty0 + ly) * p.g.width + T.tx0 + lx;
+}
+
+// Copies the staged coefficient rows of a tile to global memory (consecutive
+// threads take consecutive 16-byte chunks: a tile row's pixels are contiguous
+// in the pixel-major coefficient array) and clears the staging area, whose
+// `bytes` bytes are reused as zeroed accumulators afterwards.
+template <typename CT, int C>
+__device__ __forceinline__ void copy_staged(const Params &p, const Tile &T, uint4 *stage, int bytes,
+                                            CT *coeff) {
+    using S = Staged<CT, C>;
+    const int npx = p.g.tile_w * p.g.tile_h;
+    const int nchunk = npx * S::K;
+    for (int c = threadIdx.x; c < bytes / 16; c += blockDim.x) {
+        if (c < nchunk) {
+            const int lp = c / S::K, q = (c % S::K) ^ S::sw(lp);
+            int lx = lp, ly = 0;
+            if (p.g.tile_h != 1) {
+                lx = lp % p.g.tile_w;
+                ly = lp / p.g.tile_w;
+            }
+            if (lx < T.tw && ly < T.th) {
+                const int64_t gp = (int64_t)(T.ty0 + ly) * p.g.width + T.tx0 + lx;
+                reinterpret_cast<uint4 *>(coeff + gp * C)[q] = stage[c];
+            }
+        }
+        stage[c] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// The reverse of copy_staged: a tile's coefficient rows read from global
+// memory in coalesced 16-byte chunks into their staged positions.
+template <typename CT, int C>
+__device__ __forceinline__ void load_staged(const Params &p, const Tile &T, uint4 *stage,
+                                            const CT *coeff) {
+    using S = Staged<CT, C>;
+    const int nchunk = p.g.tile_w * p.g.tile_h * S::K;
+    for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
+        const int lp = c / S::K, q = (c % S::K) ^ S::sw(lp);
+        int lx = lp, ly = 0;
+        if (p.g.tile_h != 1) {
+            lx = lp % p.g.tile_w;
+            ly = lp / p.g.tile_w;
+        }
+        if (lx < T.tw && ly < T.th) {
+            const int64_t gp = (int64_t)(T.ty0 + ly) * p.g.width + T.tx0 + lx;
+            stage[c] = reinterpret_cast<const uint4 *>(coeff + gp * C)[q];
+        }
+    }
 }
 
 // ---------------------------------------------------------------- conditioning
@@ -438,10 +541,11 @@ template <int J> __device__ __forceinline__ void get_row(const float *row, float
 
 template <int J>
 __device__ __forceinline__ void bins_to_coeffs(const unsigned *Frow, const unsigned *Grow,
-                                               float (&c)[1 << J], float &S) {
+                                               float (&c)[1 << J], float &S, bool scaled) {
     constexpr int C = 1 << J;
     float F[C], G[C];
-    const float inv = __uint_as_float(Frow[Shape<J>::INV]);  // 1 / s_p, a power of two
+    // 1 / s_p (a power of two) when the tile took per-pixel scales, else 2^-27
+    const float inv = scaled ? __uint_as_float(Frow[Shape<J>::INV]) : kBinInv;
     get_row<J>(reinterpret_cast<const float *>(Frow), F);
     get_row<J>(reinterpret_cast<const float *>(Grow), G);
 #pragma unroll
@@ -457,24 +561,26 @@ __device__ __forceinline__ void bins_to_coeffs(const unsigned *Frow, const unsig
 // One level of the synthesis: values on the 2^n intervals of level n in
 // v[0 .. 2^n) become values on the 2^{n+1} intervals of level n+1.
 template <int J, int n>
-__device__ __forceinline__ void synth_level(float (&v)[1 << J], const float (&c)[1 << J]) {
+__device__ __forceinline__ void synth_level(float (&v)[1 << J], const float (&c)[1 << J], float scale) {
 #pragma unroll
     for (int k = (1 << n) - 1; k >= 0; --k) {
-        const float d = sqrt2_pow(n) * c[(1 << n) + k];
+        const float d = (sqrt2_pow(n) * scale) * c[(1 << n) + k];
         const float base = v[k];
         v[2 * k + 1] = base - d;
         v[2 * k] = base + d;
     }
-    if constexpr (n + 1 < J) synth_level<J, n + 1>(v, c);
+    if constexpr (n + 1 < J) synth_level<J, n + 1>(v, c, scale);
 }
 
 // Haar synthesis at the bin centres, in place: values of the Haar series on
-// each finest bin, A_m = chi_00 + sum_n (+-) 2^{n/2} X_{n, m >> (J-n)}.
-template <int J> __device__ __forceinline__ void coeffs_to_bins(float (&v)[1 << J]) {
+// each finest bin, A_m = chi_00 + sum_n (+-) 2^{n/2} X_{n, m >> (J-n)},
+// multiplied by scale (a constant folded into the level factors).
+template <int J> __device__ __forceinline__ void coeffs_to_bins(float (&v)[1 << J], float scale = 1.f) {
     float c[1 << J];
 #pragma unroll
     for (int i = 0; i < (1 << J); ++i) c[i] = v[i];
-    synth_level<J, 0>(v, c);
+    v[0] = c[0] * scale;
+    if constexpr (J > 0) synth_level<J, 0>(v, c, scale);
 }
 
 // Where a depth falls for the reconstruction of §2.3.2, from s = C z:
@@ -483,6 +589,7 @@ template <int J> __device__ __forceinline__ void coeffs_to_bins(float (&v)[1 << 
 // reconstructed at its own depth (its bin values are 0 before bin m, 1-f in
 // it and 1 after it).  Linear: position pos = s - 1/2 in centre units,
 // clamped so that the outer half-bins are constant.  Staircase: the bin value.
+// (The adjoint uses every field; the forward resolve uses absorbance_at.)
 struct Pos {
     int m, lo;
     float f, t, g;
@@ -511,50 +618,81 @@ template <int J> __device__ __forceinline__ Pos locate(float s, uint32_t flags) 
     return q;
 }
 
-// Reconstruction at a located depth from one pixel's bin values.
+// Reconstruction at a located depth from one pixel's row of bin values.
 template <int J>
-__device__ __forceinline__ float recon_at(const float *A, const Pos &q, uint32_t flags) {
+__device__ __forceinline__ float recon_at(const float *row, const Pos &q, uint32_t flags) {
+    const float *A = row + Shape<J>::V0;
     if (!(flags & kLinear)) return A[q.m];
     const float A0 = A[q.lo], A1 = A[q.lo + 1];
     return fmaf(q.t, A1 - A0, A0);
 }
 
-// Absorbance in front of a fragment, in the units of A (a2 = its step in
-// those units); the own step is removed under self-exclusion.
+// Absorbance in front of a fragment at clamped depth zc from its pixel's row
+// of bin values, in the row's units; a2 is the fragment's own step in those
+// units, removed under self-exclusion (pass 0 for the reconstruction alone).
+//
+// Linear interpolation: with s = C zc, the bin boundary nearest to s is
+// lo = floor(s + 1/2) in [0, C] and u = s - lo in [-1/2, 1/2) is the signed
+// distance to it.  The reconstruction runs between the centres on either side
+// of that boundary -- entries lo, lo+1 of the padded row, weight t = u + 1/2 --
+// and is constant in the outer half-bins, where both entries hold the end value.
+// The own unit step reconstructed at its own depth (bin values 0, 1-f, 1 before,
+// in and after its bin m, f = s - m) is then
+//     g = 1/2 + u (1/2 - |u|)                  between the outer half-bins,
+//     g = 1 - u  (lo = 0),   g = -u  (lo = C)  in the first / last half-bin,
+// i.e. (1-f)(f+1/2) for f < 1/2 and 1 - 3f/2 + f^2 for f >= 1/2 inside.
+// Staircase: the value of bin m, own step 1 - f.
 template <int J>
-__device__ __forceinline__ float frag_absorbance(const float *A, float zc, float a2, uint32_t flags) {
-    const Pos q = locate<J>(zc * (float)(1 << J), flags);
-    const float full = recon_at<J>(A, q, flags);
-    return (flags & kSelfExclude) ? fmaxf(full - a2 * q.g, 0.f) : full;
+__device__ __forceinline__ float absorbance_at(const float *row, float zc, float a2, uint32_t flags) {
+    constexpr int C = 1 << J;
+    const float s = zc * (float)C;  // exact: C is a power of two
+    float A, g;
+    if (flags & kLinear) {
+        const Floor b = floor_small(s + 0.5f);
+        const float u = s - b.f;  // exact
+        const float *e = row + (Shape<J>::V0 - 1) + b.i;
+        const float A0 = e[0], A1 = e[1];
+        A = fmaf(u + 0.5f, A1 - A0, A0);
+        const float inner = fmaf(u, 0.5f - fabsf(u), 0.5f);
+        const float outer = (b.i == 0 ? 1.f : 0.f) - u;
+        g = (unsigned)(b.i - 1) < (unsigned)(C - 1) ? inner : outer;
+    } else {
+        const Floor m = floor_small(s);
+        A = row[Shape<J>::V0 + m.i];
+        g = 1.f - (s - m.f);
+    }
+    return (flags & kSelfExclude) ? fmaxf(fmaf(-a2, g, A), 0.f) : A;
 }
 
 // Per-pixel weight offset m_p (log2 units): every fragment's absorbance is
 // >= m_p and the nearest one's is <= m_p + 20, so 2^(m_p - A_i) never
 // overflows and the largest weight never underflows.
 template <int J>
-__device__ __forceinline__ float weight_offset(const float *A2, float zmin, uint32_t flags) {
+__device__ __forceinline__ float weight_offset(const float *row, float zmin, uint32_t flags) {
     if (!(zmin < 1.f)) return 0.f;  // +inf: no fragment with alpha > 0
-    const float full = frag_absorbance<J>(A2, clamp_depth(zmin), 0.f, flags & kLinear);
+    const float full = absorbance_at<J>(row, clamp_depth(zmin), 0.f, flags & kLinear);
     return fmaxf(full - kStepCapLog2, 0.f);
 }
 
-// Stores one pixel's bin values (log2 units) into its shared row and, in the
-// normalised resolve, folds in the weight offset: the row becomes A' = A - m_p
-// with m_p from the pixel's nearest depth (every fragment then has A' >= 0 up
-// to rounding, which the self-excluded clamp at 0 absorbs).
+// Stores one pixel's bin values (log2 units) into its padded shared row and,
+// in the normalised resolve, folds in the weight offset: the row becomes
+// A' = A - m_p with m_p from the pixel's nearest depth (every fragment then has
+// A' >= 0 up to rounding, which the self-excluded clamp at 0 absorbs).
 template <int J>
 __device__ __forceinline__ void put_bins(float *row, float (&v)[1 << J], float zmin, uint32_t flags) {
-    constexpr int C = 1 << J;
+    constexpr int C = 1 << J, V0 = Shape<J>::V0;
     auto put = [&]() {
         if constexpr (C % 4 == 0) {
 #pragma unroll
             for (int q = 0; q < C / 4; ++q)
-                reinterpret_cast<float4 *>(row)[q] =
+                reinterpret_cast<float4 *>(row + V0)[q] =
                     make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         } else {
 #pragma unroll
-            for (int i = 0; i < C; ++i) row[i] = v[i];
+            for (int i = 0; i < C; ++i) row[V0 + i] = v[i];
         }
+        row[V0 - 1] = v[0];
+        row[V0 + C] = v[C - 1];
     };
     put();
     if (!(flags & kNormalized)) return;
@@ -568,15 +706,62 @@ __device__ __forceinline__ void put_bins(float *row, float (&v)[1 << J], float z
 
 // ---------------------------------------------------------------- fragment phases
 
-// Step 2 accumulation.  Pass 0 counts each pixel's fragments and takes its
-// largest clamped alpha (integer atomics on the padding words of its F row);
-// the pixel's scale s_p = 2^(30 - floor(log2(c_p a_max))) then keeps every bin
-// sum below 2^32; pass 1 adds rint(s_p a f) and rint(s_p a (1-f)) to the
-// fragment's bin with integer atomics, and the nearest depth with a red.min.
+// Step 2 accumulation, one pass over the fragments with bins scaled by a
+// fixed 2^27 (SCALED = false) or by per-pixel scales s_p (SCALED = true, after
+// count_pass).  Each fragment adds rint(s a f) and rint(s a (1-f)) to its bin
+// with integer atomics and its depth to the pixel's nearest depth with a
+// red.min.  Under the fixed scale the pass reports whether the tile needs the
+// per-pixel scales: a bin word wrapped (seen from the atomics' return values),
+// or a fragment's step is below 2^-7, where the fixed scale would round it by
+// more than 2^-21 of itself.  Invalid fragments are counted in bad when COUNT.
+template <int J, bool SCALED, bool COUNT>
+__device__ __forceinline__ bool bins_pass(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
+                                          unsigned *sZ, unsigned &bad) {
+    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, AMAX = Shape<J>::AMAX;
+    constexpr float kFineStep = 1048576.f;  // 2^20: a step of 2^-7 under the fixed scale
+    bool retry = false;
+    for_each_group<kWithZ>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+        int lp[N];
+        float sp[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            lp[k] = -1;
+            if (G.v) {
+                if (G.z[k] == G.z[k] && G.al[k] == G.al[k]) lp[k] = local_pixel(G.px[k], p, T);
+                if (COUNT && lp[k] < 0) ++bad;
+            }
+        }
+        // the group's scale reads, then its arithmetic, then its atomics
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            sp[k] = SCALED ? (lp[k] >= 0 ? __uint_as_float(sF[lp[k] * LD + AMAX]) : 0.f) : kBinScale;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if (lp[k] < 0) continue;
+            const float a = step_of(clamp_alpha(G.al[k]));
+            const float zc = clamp_depth(G.z[k]);
+            const float s = zc * (float)C;  // exact: C is a power of two
+            const Floor m = floor_small(s);
+            const float f = s - m.f;
+            const float as = a * sp[k];
+            const unsigned vF = __float2uint_rn(as * f), vG = __float2uint_rn(as * (1.f - f));
+            const unsigned oF = atomicAdd(&sF[lp[k] * LD + m.i], vF);
+            const unsigned oG = atomicAdd(&sG[lp[k] * LD + m.i], vG);
+            if (!SCALED) retry |= (oF + vF < oF) | (oG + vG < oG) | (as < kFineStep && a > 0.f);
+            if (a > 0.f) atomicMin(&sZ[lp[k]], __float_as_uint(zc));
+        }
+    });
+    return retry;
+}
+
+// Counting pass of the fallback: each pixel's fragment count c_p and largest
+// clamped alpha (integer atomics on the padding words of its F row), then its
+// scale s_p = 2^(30 - floor(log2(c_p a_max))), which keeps every bin sum below
+// 2^32.  Ends with a barrier.
 template <int J>
-__device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
-                                           unsigned *sZ, unsigned &bad) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+__device__ __forceinline__ void count_pass(const Params &p, const Tile &T, unsigned *sF) {
+    constexpr int LD = Shape<J>::LD;
     constexpr int CNT = Shape<J>::CNT, AMAX = Shape<J>::AMAX, INV = Shape<J>::INV;
     for_each_group<0>(T.s, T.e, p, [&](auto &G) {
         constexpr int N = std::remove_reference_t<decltype(G)>::size;
@@ -599,47 +784,41 @@ __device__ __forceinline__ void phase_bins(const Params &p, const Tile &T, unsig
         row[AMAX] = __float_as_uint(ldexpf(1.f, 30 - e));  // s_p (the maximum is no longer needed)
     }
     __syncthreads();
-    for_each_group<kWithZ>(T.s, T.e, p, [&](auto &G) {
-        constexpr int N = std::remove_reference_t<decltype(G)>::size;
-        int lp[N];
-        float sp[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            lp[k] = -1;
-            if (G.v) {
-                if (G.z[k] == G.z[k] && G.al[k] == G.al[k]) lp[k] = local_pixel(G.px[k], p, T);
-                if (lp[k] < 0) ++bad;
-            }
-        }
-        // the group's scale reads, then its arithmetic, then its atomics
-#pragma unroll
-        for (int k = 0; k < N; ++k) sp[k] = lp[k] >= 0 ? __uint_as_float(sF[lp[k] * LD + AMAX]) : 0.f;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            if (lp[k] < 0) continue;
-            const float a = step_of(clamp_alpha(G.al[k]));
-            const float zc = clamp_depth(G.z[k]);
-            const float s = zc * (float)C;  // exact: C is a power of two
-            const Floor m = floor_small(s);
-            const float f = s - m.f;
-            const float as = a * sp[k];
-            atomicAdd(&sF[lp[k] * LD + m.i], __float2uint_rn(as * f));
-            atomicAdd(&sG[lp[k] * LD + m.i], __float2uint_rn(as * (1.f - f)));
-            if (a > 0.f) atomicMin(&sZ[lp[k]], __float_as_uint(zc));
-        }
-    });
 }
 
-// Step 3 (§2.1).  A2 holds each pixel's bin values in log2 units minus the
-// pixel's weight offset m_p, so v_i = 2^(m_p - A_i) = 2^-A'_i and
+// Step 2 accumulation of one tile into its F and G bins (zeroed by the
+// caller, nearest-depth words set to +inf).  The fixed-scale pass is tried
+// first; if it reports a wrapped bin or a step too small for the fixed scale,
+// the bins are cleared and rebuilt with per-pixel scales.  Returns whether the
+// per-pixel scales were used (the INV word of each pixel's F row then holds
+// 1 / s_p).  Ends with a barrier.
+template <int J>
+__device__ __forceinline__ bool phase_bins(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
+                                           unsigned *sZ, unsigned &bad) {
+    const bool retry = bins_pass<J, false, true>(p, T, sF, sG, sZ, bad);
+    if (!__syncthreads_or(retry)) return false;
+    const int npx = p.g.tile_w * p.g.tile_h;
+    fill_zero(sF, (int)(2 * align16((size_t)npx * Shape<J>::LD * 4)));  // F and G planes are adjacent
+    __syncthreads();
+    count_pass<J>(p, T, sF);
+    bins_pass<J, true, false>(p, T, sF, sG, sZ, bad);  // the nearest depths are already final
+    __syncthreads();
+    return true;
+}
+
+// Step 3 (§2.1).  Each pixel's row holds its bin values in log2 units minus
+// the pixel's weight offset m_p, so v_i = 2^(m_p - A_i) = 2^-A'_i and
 // w_i = alpha_i v_i; per pixel (R, G, B, W) += (c w, w) through the
 // warp-segmented reduction into this warp's copy, and, when sS is given,
-// S += a with a shared-memory atomic.
+// S += a with a shared-memory atomic.  The own step removed under
+// self-exclusion is -log2(1 - alpha), taken from the hardware log2 (its
+// absolute error, ~2^-22, moves one fragment's exponent only), except when
+// S needs the accurate step.
 template <int J, bool COUNT>
 __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
                                               float4 *accw, float *sS,
                                               unsigned &bad) {
-    constexpr int LD = Shape<J>::LD;
+    constexpr int LDV = Shape<J>::LDV;
     const uint32_t flags = p.flags;
     const int npx = p.g.tile_w * p.g.tile_h;
     float4 *mine = accw + (threadIdx.x >> 5) * npx;
@@ -650,16 +829,19 @@ __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, co
             const int lp = G.v && G.z[k] == G.z[k] && G.al[k] == G.al[k] ? local_pixel(G.px[k], p, T) : -1;
             if (COUNT && G.v && lp < 0) ++bad;
             // a lane without a valid fragment evaluates pixel 0 and adds nothing
-            const bool ok = lp >= 0;
-            const int l = ok ? lp : 0;
-            const float ac = ok ? clamp_alpha(G.al[k]) : 0.f;
-            const float a = step_of(ac);
-            const float Ah = frag_absorbance<J>(A2 + l * LD, clamp_depth(G.z[k]), a * kLog2e, flags);
+            const int l = lp >= 0 ? lp : 0;
+            const float ac = clamp_alpha(G.al[k]);  // 0 for NaN
+            float a = 0.f, a2;
+            if (sS) {
+                a = step_of(ac);
+                a2 = a * kLog2e;
+            } else {
+                a2 = -lg2(1.f - ac);
+            }
+            const float Ah = absorbance_at<J>(A2 + l * LDV, clamp_depth(G.z[k]), a2, flags);
             const float w = ac * ex2(-Ah);
-            const float4 c = ok ? make_float4(G.r[k] * w, G.g[k] * w, G.b[k] * w, w)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sS && ok) atomicAdd(&sS[l], a);
-            warp_accumulate(mine, lp, c);
+            if (sS && lp >= 0) atomicAdd(&sS[l], a);
+            warp_accumulate(mine, lp, make_float4(G.r[k] * w, G.g[k] * w, G.b[k] * w, w));
         }
     });
 }
@@ -714,11 +896,10 @@ __device__ __forceinline__ void composite_pixel(const Params &p, int64_t gp, flo
 
 // ---------------------------------------------------------------- shared-memory layouts (bytes)
 
-__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
 // Every region starts on a 16-byte boundary (float4 row reads and writes).
 template <int J> struct Layout {
     static constexpr size_t plane(int npx) { return align16((size_t)npx * Shape<J>::LD * 4); }
+    static constexpr size_t vplane(int npx) { return align16((size_t)npx * Shape<J>::LDV * 4); }
     static constexpr size_t words(int npx) { return align16((size_t)npx * 4); }
     static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 16; }
     // build: F and G bins + nearest-depth words
@@ -726,13 +907,13 @@ template <int J> struct Layout {
     // fused: F and G bins, replaced after the build by the bin values, the
     // warps' accumulators and the S words; then the nearest-depth words
     static constexpr size_t region(int npx) {
-        return 2 * plane(npx) > plane(npx) + accw(npx) + words(npx)
+        return 2 * plane(npx) > vplane(npx) + accw(npx) + words(npx)
                    ? 2 * plane(npx)
-                   : plane(npx) + accw(npx) + words(npx);
+                   : vplane(npx) + accw(npx) + words(npx);
     }
     static constexpr size_t fused(int npx) { return region(npx) + words(npx); }
     // resolve: bin values + warps' accumulators + S words
-    static constexpr size_t resolve(int npx) { return plane(npx) + accw(npx) + words(npx); }
+    static constexpr size_t resolve(int npx) { return vplane(npx) + accw(npx) + words(npx); }
 };
 
 }  // namespace wt
