@@ -28,26 +28,37 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
     const bool scaled = phase_bins<J>(p, T, sF, sG, sZ, bad);
     flush_bad(bad, p.err);
     const int lp = threadIdx.x;
-    if (lp >= npx) return;
-    const int64_t gp = global_pixel(p, T, lp);
-    if (gp < 0) return;
-    float c[C], S;
-    bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
-    CT *dst = static_cast<CT *>(p.coeff) + gp * C;
+    int64_t gp = -1;
+    if (lp < npx) gp = global_pixel(p, T, lp);
+    CT *coeff = static_cast<CT *>(p.coeff);
     const bool acc = (p.flags & kAccumulate) != 0;
-    if (acc) {
-        float old[C];
-        load_row<CT, C>(dst, old);
+    // rows of whole 16-byte chunks go out through a staging copy over the F
+    // bins (coalesced stores); accumulation adds to the stored rows directly
+    const bool stage = Staged<CT, C>::ok && !acc;
+    float c[C], S;
+    if (gp >= 0) {
+        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
+        CT *dst = coeff + gp * C;
+        if (acc) {
+            float old[C];
+            load_row<CT, C>(dst, old);
 #pragma unroll
-        for (int i = 0; i < C; ++i) c[i] += old[i];
+            for (int i = 0; i < C; ++i) c[i] += old[i];
+        }
+        if (!stage) store_row<CT, C>(dst, c);
+        if (p.zmin) {
+            float v = __uint_as_float(sZ[lp]);
+            if (acc) v = fminf(v, p.zmin[gp]);
+            p.zmin[gp] = v;
+        }
     }
-    store_row<CT, C>(dst, c);
-    if (p.zmin) {
-        float v = __uint_as_float(sZ[lp]);
-        if (acc) v = fminf(v, p.zmin[gp]);
-        p.zmin[gp] = v;
+    if (stage) {
+        uint4 *st = reinterpret_cast<uint4 *>(smem);
+        __syncthreads();  // every bin row has been read
+        if (gp >= 0) stage_row<CT, C>(st, lp, c);
+        __syncthreads();
+        copy_staged<CT, C>(p, T, st, npx * Staged<CT, C>::K * 16, coeff);
     }
-}
 }
 
 // §2.1 step 3 (+ step 4 when COMPOSITE): resolve against stored coefficients.
@@ -63,12 +74,22 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
+    // rows of whole 16-byte chunks come in through a staging copy over the
+    // (not yet used) accumulator area (coalesced loads)
+    const CT *coeff = static_cast<const CT *>(p.coeff);
+    uint4 *st = reinterpret_cast<uint4 *>(accw);
+    if (Staged<CT, C>::ok) {
+        load_staged<CT, C>(p, T, st, coeff);
+        __syncthreads();
+    }
     if (gp >= 0) {
         float v[C];
-        load_row<CT, C>(static_cast<const CT *>(p.coeff) + gp * C, v);
+        if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v);
+        else load_row<CT, C>(coeff + gp * C, v);
         coeffs_to_bins<J>(v, kLog2e);
         put_bins<J>(vals + lp * LDV, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000), p.flags);
     }
+    if (Staged<CT, C>::ok) __syncthreads();  // staged rows consumed
     fill_zero(accw, (int)(Layout<J>::accw(npx) + Layout<J>::words(npx)));
     __syncthreads();
     unsigned bad = 0;
