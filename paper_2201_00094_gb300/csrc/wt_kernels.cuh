@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
     unsigned *sG = reinterpret_cast<unsigned *>(smem + Layout<J>::plane(npx));
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + 2 * Layout<J>::plane(npx));
     const Tile T = tile_of(p, blockIdx.x, true);
+    prefetch_tile<kWithZ>(p, T);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;  // +inf
     __syncthreads();
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
     float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::vplane(npx));
     float *sS = reinterpret_cast<float *>(smem + Layout<J>::vplane(npx) + Layout<J>::accw(npx));
     const Tile T = tile_of(p, blockIdx.x, true);
+    prefetch_tile<kWithZ | kWithRGB>(p, T);
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
 // Steps 2-4 fused for one tile: the coefficients never leave the SM between
 // build and resolve.  Ends with a barrier, so a persistent caller may reuse the
 // shared memory for its next tile.
-template <int J, typename CT>
+template <int J, typename CT, bool DEF = false>
 __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned char *smem) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
     const int npx = p.g.tile_w * p.g.tile_h;
@@ -135,6 +137,7 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     float *sS = reinterpret_cast<float *>(smem + Layout<J>::vplane(npx) + Layout<J>::accw(npx));
     unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
     const Tile T = tile_of(p, tile, true);
+    prefetch_tile<kWithZ | kWithRGB>(p, T);
     fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
     __syncthreads();
@@ -160,7 +163,7 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     if (gp >= 0) {
         if (stage) stage_row<CT, C>(reinterpret_cast<uint4 *>(accw), lp, v);
         coeffs_to_bins<J>(v, kLog2e);
-        put_bins<J>(vals + lp * LDV, v, __uint_as_float(sZ[lp]), p.flags);
+        put_bins<J>(vals + lp * LDV, v, __uint_as_float(sZ[lp]), DEF ? kDefaultFlags : p.flags);
         sS[lp] = S;
     }
     if (stage) {
@@ -170,7 +173,7 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
         fill_zero(accw, (int)Layout<J>::accw(npx));
     }
     __syncthreads();
-    phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);
+    phase_resolve<J, false, DEF>(p, T, vals, accw, nullptr, bad);
     __syncthreads();
     if (gp >= 0) {
         const float4 a = sum_warps(accw, npx, lp);
@@ -179,10 +182,12 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     __syncthreads();
 }
 
-template <int J, typename CT>
+// DEF: compiled for the default flags (p.flags == kDefaultFlags), so the
+// per-fragment reconstruction carries no flag tests.
+template <int J, typename CT, bool DEF>
 __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    fused_tile<J, CT>(p, blockIdx.x, smem);
+    fused_tile<J, CT, DEF>(p, blockIdx.x, smem);
 }
 
 // Serving: one persistent launch works through the tile tasks of several
@@ -508,13 +513,18 @@ cudaError_t launch_resolve_t(const Params &p, int ntiles, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int J, typename CT> cudaError_t launch_fused_t(const Params &p, int ntiles, cudaStream_t s) {
+template <int J, typename CT, bool DEF> cudaError_t launch_fused_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::fused(npx);
-    cudaError_t e = cudaFuncSetAttribute(k_fused<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fused<J, CT, DEF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_fused<J, CT><<<ntiles, kThreads, bytes, s>>>(p);
+    k_fused<J, CT, DEF><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
+}
+template <int J, typename CT> cudaError_t launch_fused_t(const Params &p, int ntiles, cudaStream_t s) {
+    return p.flags == kDefaultFlags ? launch_fused_k<J, CT, true>(p, ntiles, s)
+                                    : launch_fused_k<J, CT, false>(p, ntiles, s);
 }
 
 template <int J, typename CT>

@@ -88,6 +88,8 @@ struct Params {
 };
 
 enum : uint32_t { kSelfExclude = 1u, kLinear = 2u, kNormalized = 4u, kAccumulate = 8u };
+// the default method: self-excluded, linearly interpolated, normalised resolve
+constexpr uint32_t kDefaultFlags = kSelfExclude | kLinear | kNormalized;
 
 template <int J> struct Shape {
     static constexpr int C = 1 << J;
@@ -423,35 +425,58 @@ __device__ __forceinline__ void load_four(Group<4> &G, bool v, int64_t q, const 
 
 // Calls body(Group<4>) for the 16-byte-aligned middle of the fragment range
 // [s, e) -- one vector load per array, the next group's loads in flight while
-// the body runs -- and body(Group<1>) for the unaligned head and tail.  Every
-// thread of the block makes the same number of calls (threads past the range
-// get v = false), so the body may use warp-wide collectives.  A body that
-// finishes all of a group's arithmetic before its shared-memory updates lets
-// the four fragments' latencies overlap.
+// the body runs -- and body(Group<1>) once, in the
+// block's last warp, for the unaligned head and tail (at most 3 + 3
+// fragments).  Every lane of a warp makes the same calls (lanes past the range
+// get v = false) and a warp stops as soon as its first lane is past the range,
+// so the body may use warp-wide collectives but no block-wide barrier.  A body
+// that finishes all of a group's arithmetic before its shared-memory updates
+// lets the four fragments' latencies overlap.
 template <int LOAD, class Body>
 __device__ __forceinline__ void for_each_group(int64_t s, int64_t e, const Params &p, Body &&body) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     int64_t s4 = (s + 3) & ~int64_t(3), e4 = e & ~int64_t(3);
     if (s4 > e4) s4 = e4 = e;
-    for (int64_t b0 = s; b0 < s4; b0 += nt) {
+    const int nh = (int)(s4 - s), ne = nh + (int)(e - e4);
+    if (ne > 0 && (tid >> 5) == (nt >> 5) - 1) {
         Group<1> G;
-        load_one<LOAD>(G, b0 + tid < s4, b0 + tid, p);
+        load_one<LOAD>(G, lane < ne, lane < nh ? s + lane : e4 + (lane - nh), p);
         body(G);
     }
     const int64_t qe = e4 >> 2;
-    int64_t q = (s4 >> 2) + tid;
+    int64_t q = (s4 >> 2) + tid;  // the warp's first lane is at q - lane
     Group<4> next;
     load_four<LOAD>(next, q < qe, q, p);
-    for (int64_t q0 = s4 >> 2; q0 < qe; q0 += nt) {
+    while (q - lane < qe) {
         Group<4> cur = next;
         q += nt;
         load_four<LOAD>(next, q < qe, q, p);
         body(cur);
     }
-    for (int64_t b0 = e4; b0 < e; b0 += nt) {
-        Group<1> G;
-        load_one<LOAD>(G, b0 + tid < e, b0 + tid, p);
-        body(G);
+}
+
+// L2 prefetch (bulk, asynchronous) of the 16-byte-aligned interior of the
+// 4-byte-element range a[s, e), in pieces of at most 32 KB: the tile's
+// fragment arrays stream into L2 while the block works on them, instead of
+// arriving one register group at a time.  Addresses stay inside [s, e).
+__device__ __forceinline__ void l2_prefetch_range(const void *a, int64_t s, int64_t e) {
+    const int64_t b0 = (s * 4 + 15) & ~int64_t(15), b1 = (e * 4) & ~int64_t(15);
+    for (int64_t b = b0; b < b1; b += 32768) {
+        const unsigned n = (unsigned)(b1 - b < 32768 ? b1 - b : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a) + b),
+                     "r"(n)
+                     : "memory");
+    }
+}
+template <int LOAD> __device__ __forceinline__ void prefetch_tile(const Params &p, const Tile &T) {
+    if (threadIdx.x != 0) return;
+    l2_prefetch_range(p.pixel, T.s, T.e);
+    l2_prefetch_range(p.alpha, T.s, T.e);
+    if (LOAD & kWithZ) l2_prefetch_range(p.z, T.s, T.e);
+    if (LOAD & kWithRGB) {
+        l2_prefetch_range(p.r, T.s, T.e);
+        l2_prefetch_range(p.gc, T.s, T.e);
+        l2_prefetch_range(p.b, T.s, T.e);
     }
 }
 
@@ -508,17 +533,19 @@ __device__ __forceinline__ constexpr float half_inv_sqrt2_pow(int n) { return 0.
 // One level of the bins -> coefficients tree (children at level n+1 in
 // F, G[0 .. 2^{n+1}), parents written to F, G[0 .. 2^n)).
 template <int J, int n>
-__device__ __forceinline__ void tree_level(float (&F)[1 << J], float (&G)[1 << J], float (&c)[1 << J]) {
+__device__ __forceinline__ void tree_level(float (&F)[1 << J], float (&G)[1 << J], float (&c)[1 << J],
+                                           float inv) {
+    const float h = -half_inv_sqrt2_pow(n) * inv;
 #pragma unroll
     for (int k = 0; k < (1 << n); ++k) {
         const float t = F[2 * k] + G[2 * k + 1];
-        c[(1 << n) + k] = -half_inv_sqrt2_pow(n) * t;
+        c[(1 << n) + k] = h * t;
         const float Fp = fmaf(0.5f, t, F[2 * k + 1]);
         const float Gp = fmaf(0.5f, t, G[2 * k]);
         F[k] = Fp;
         G[k] = Gp;
     }
-    if constexpr (n > 0) tree_level<J, n - 1>(F, G, c);
+    if constexpr (n > 0) tree_level<J, n - 1>(F, G, c, inv);
 }
 
 // Bins (F, G) of one pixel -> Haar coefficients in heap order, and S = sum a.
@@ -548,14 +575,16 @@ __device__ __forceinline__ void bins_to_coeffs(const unsigned *Frow, const unsig
     const float inv = scaled ? __uint_as_float(Frow[Shape<J>::INV]) : kBinInv;
     get_row<J>(reinterpret_cast<const float *>(Frow), F);
     get_row<J>(reinterpret_cast<const float *>(Grow), G);
+    // the tree runs on the integer sums (exact as floats up to 2^24, rounded
+    // once above) and the scale enters through the level constants
 #pragma unroll
     for (int i = 0; i < C; ++i) {
-        F[i] = (float)__float_as_uint(F[i]) * inv;
-        G[i] = (float)__float_as_uint(G[i]) * inv;
+        F[i] = (float)__float_as_uint(F[i]);
+        G[i] = (float)__float_as_uint(G[i]);
     }
-    tree_level<J, J - 1>(F, G, c);
-    c[0] = G[0];
-    S = F[0] + G[0];
+    tree_level<J, J - 1>(F, G, c, inv);
+    c[0] = G[0] * inv;
+    S = (F[0] + G[0]) * inv;
 }
 
 // One level of the synthesis: values on the 2^n intervals of level n in
@@ -814,12 +843,12 @@ __device__ __forceinline__ bool phase_bins(const Params &p, const Tile &T, unsig
 // self-exclusion is -log2(1 - alpha), taken from the hardware log2 (its
 // absolute error, ~2^-22, moves one fragment's exponent only), except when
 // S needs the accurate step.
-template <int J, bool COUNT>
+template <int J, bool COUNT, bool DEF = false>
 __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
                                               float4 *accw, float *sS,
                                               unsigned &bad) {
     constexpr int LDV = Shape<J>::LDV;
-    const uint32_t flags = p.flags;
+    const uint32_t flags = DEF ? kDefaultFlags : p.flags;  // DEF: p.flags is the default
     const int npx = p.g.tile_w * p.g.tile_h;
     float4 *mine = accw + (threadIdx.x >> 5) * npx;
     for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
@@ -871,12 +900,13 @@ __device__ __forceinline__ void composite_pixel(const Params &p, int64_t gp, flo
         bg1 = p.bg_img[3 * gp + 1];
         bg2 = p.bg_img[3 * gp + 2];
     }
-    const float T = expf(-S);
-    const float cover = -expm1f(-S);  // 1 - T without cancellation
+    const float T = ex2(-S * kLog2e);
+    // 1 - T; for small S the series S (1 - S/2) (error below S^3/6 < 3e-10)
+    const float cover = S < 0.0009765625f ? S * fmaf(-0.5f, S, 1.f) : 1.f - T;
     float4 o;
     if (p.flags & kNormalized) {
         if (W > 0.f) {
-            const float k = cover / W;
+            const float k = W >= 1.17549435e-38f ? cover * rcp(W) : cover / W;  // (subnormal W)
             o.x = fmaf(R, k, bg0 * T);
             o.y = fmaf(G, k, bg1 * T);
             o.z = fmaf(B, k, bg2 * T);
