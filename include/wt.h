@@ -243,6 +243,61 @@ wt_status wt_backward(const wt_desc *desc, const wt_frags *frags, const float *b
                       const float bg[3], const float *grad_out, float *grad_alpha,
                       float *grad_rgb, wt_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Before the build: grouping an unordered stream by tile, and the per-pixel
+ * depth bounds of §2.1 step 1 ("tight per-pixel depth bounds" of the
+ * transparent surfaces, into which depth is normalised before the build).
+ */
+
+/* Bytes of device workspace wt_bin needs for this descriptor (tile counts and
+ * cursors, about 12 bytes per tile); 0 if the descriptor is invalid.  Only the
+ * descriptor's width, height, tile_w and tile_h are used. */
+size_t wt_bin_workspace_bytes(const wt_desc *desc);
+
+/*
+ * wt_bin -- groups an unordered fragment stream by tile (row-major tiles of
+ * desc) into caller-allocated output arrays, a counting sort by tile id:
+ *   in          n fragments in any order; in->tile_offsets is ignored (may be
+ *               NULL); in->r/g/b may all be NULL (then r/g/b_out are unused).
+ *   *_out       [n] device arrays (at least in->n elements each), written with
+ *               the kept fragments grouped by tile; they must not overlap in.
+ *   tile_offsets_out [ntiles + 1] int64, written: tile t owns
+ *               [tile_offsets_out[t], tile_offsets_out[t+1]); the last entry
+ *               is the number of kept fragments.
+ *   workspace   wt_bin_workspace_bytes(desc) bytes of device memory, 256-byte
+ *               aligned, owned by the caller (overwritten).
+ * Fragments whose pixel id is >= width*height are dropped and counted in the
+ * error word.  The order of the fragments inside a tile is unspecified (it
+ * follows the atomics that hand out the slots): the build does not depend on
+ * it, the resolve's FP32 sums may change in their last bits between runs.
+ */
+wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
+                 float *alpha_out, float *r_out, float *g_out, float *b_out,
+                 int64_t *tile_offsets_out, void *workspace, wt_stream stream);
+
+/*
+ * wt_depth_bounds -- §2.1 step 1: per-pixel depth bounds of the transparent
+ * fragments of a tile-grouped stream.
+ *   zlo, zhi  [width*height] float, written: the smallest and largest raw depth
+ *             of the pixel's fragments (NaN z or alpha and misfiled fragments
+ *             excluded and counted); +inf / -inf for a pixel without any.
+ * Only the descriptor's geometry is used.
+ */
+wt_status wt_depth_bounds(const wt_desc *desc, const wt_frags *frags, float *zlo, float *zhi,
+                          wt_stream stream);
+
+/*
+ * wt_normalize_depth -- maps every fragment's raw depth into its pixel's
+ * bounds: z_out = (z - zlo[p]) / (zhi[p] - zlo[p]) (FP32, IEEE division), and
+ * 0 when the pixel's range is 0 or not finite.  The nearest fragment goes to 0
+ * and the farthest to 1 (which the build clamps into the last bin).  Fragments
+ * with a pixel id >= width*height or a NaN depth get NaN (the build then
+ * rejects and counts them).  z_out may be frags->z (in place); the tile
+ * grouping is not needed.
+ */
+wt_status wt_normalize_depth(const wt_desc *desc, const wt_frags *frags, const float *zlo,
+                             const float *zhi, float *z_out, wt_stream stream);
+
 /*
  * wt_get_error -- synchronises `stream`, then returns in *bad_count the
  * number of fragments (or queries, or tile ranges) rejected by any call on the

@@ -69,6 +69,8 @@ def _load():
     lib.wto_resolve.argtypes = [i64, P, P, P, P, P, P, i64, i32, u32, P, P, P, P, P]
     lib.wto_abuffer.argtypes = [i64, P, P, P, P, P, P, i64, P, P, P]
     lib.wto_grad.argtypes = [i64, P, P, P, P, P, P, i64, i32, u32, P, P, P, P, P]
+    lib.wto_depth_bounds.argtypes = [i64, P, P, P, i64, P, P]
+    lib.wto_normalize_depth.argtypes = [i64, P, P, i64, P, P, P]
     for f in ("wto_build", "wto_build_binned", "wto_fragment_absorbance", "wto_absorbance_at",
               "wto_resolve", "wto_abuffer", "wto_grad"):
         getattr(lib, f).restype = ctypes.c_int
@@ -202,3 +204,45 @@ def _split_rgb(rgb):
         return tuple(_f32(c) for c in rgb)
     a = np.asarray(rgb, dtype=np.float32)
     return _f32(a[:, 0]), _f32(a[:, 1]), _f32(a[:, 2])
+
+
+def depth_bounds(pixel, z, alpha, P: int):
+    """Per-pixel (min, max) depth of the pixel's fragments (§2.1 step 1)."""
+    pixel, z, alpha = _u32(pixel), _f32(z), _f32(alpha)
+    lo, hi = np.empty(P), np.empty(P)
+    _check(_load().wto_depth_bounds(len(pixel), _ptr(pixel), _ptr(z), _ptr(alpha), P, _ptr(lo), _ptr(hi)),
+           "wto_depth_bounds")
+    return lo, hi
+
+
+def normalize_depth(pixel, z, P: int, zlo, zhi) -> np.ndarray:
+    """Depth mapped into its pixel's bounds, (z - lo) / (hi - lo)."""
+    pixel, z = _u32(pixel), _f32(z)
+    zlo, zhi = _f64(zlo), _f64(zhi)
+    out = np.empty(len(pixel))
+    _check(_load().wto_normalize_depth(len(pixel), _ptr(pixel), _ptr(z), P, _ptr(zlo), _ptr(zhi), _ptr(out)),
+           "wto_normalize_depth")
+    return out
+
+
+def tile_of_pixels(pixel, width: int, height: int, tile_w: int, tile_h: int) -> np.ndarray:
+    """Row-major tile id of each pixel id (y * width + x); -1 outside the image."""
+    pixel = np.asarray(pixel, dtype=np.int64)
+    ntx = -(-width // tile_w)
+    y, x = pixel // width, pixel % width
+    t = (y // tile_h) * ntx + x // tile_w
+    return np.where(pixel < width * height, t, -1)
+
+
+def bin_by_tile(pixel, width: int, height: int, tile_w: int, tile_h: int):
+    """Fragments grouped by tile: a stable counting sort by tile id (the
+    library sort stands in for the counting).  Returns (order, tile_offsets):
+    kept fragment indices in tile order, and [ntiles + 1] offsets; fragments
+    outside the image are dropped."""
+    t = tile_of_pixels(pixel, width, height, tile_w, tile_h)
+    ntiles = -(-width // tile_w) * -(-height // tile_h)
+    keep = np.nonzero(t >= 0)[0]
+    order = keep[np.argsort(t[keep], kind="stable")]
+    counts = np.bincount(t[keep], minlength=ntiles)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return order, offsets

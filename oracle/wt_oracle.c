@@ -523,3 +523,44 @@ done:
     oa_ungroup(&grp);
     return st;
 }
+
+/*
+ * §2.1 step 1: the tight per-pixel depth bounds of the transparent surfaces,
+ * taken literally as the smallest and largest depth of the pixel's fragments
+ * (fragments with a NaN depth or opacity, or a pixel id outside the image,
+ * are left out); +inf / -inf for a pixel without fragments.
+ */
+int wto_depth_bounds(int64_t n, const uint32_t *pixel, const float *z, const float *alpha, int64_t P,
+                     double *zlo, double *zhi) {
+    if (n < 0 || P < 1 || !zlo || !zhi || (n > 0 && (!pixel || !z || !alpha))) return WTO_ERR_ARG;
+    for (int64_t p = 0; p < P; ++p) {
+        zlo[p] = INFINITY;
+        zhi[p] = -INFINITY;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if ((int64_t)pixel[i] >= P || isnan(z[i]) || isnan(alpha[i])) continue;
+        double d = (double)z[i];
+        if (d < zlo[pixel[i]]) zlo[pixel[i]] = d;
+        if (d > zhi[pixel[i]]) zhi[pixel[i]] = d;
+    }
+    return WTO_OK;
+}
+
+/*
+ * Depth normalised into the pixel's bounds: (z - lo) / (hi - lo), so that the
+ * nearest fragment sits at 0 and the farthest at 1; 0 when the pixel's range
+ * is empty or not finite; NaN for a bad pixel id or a NaN depth.
+ */
+int wto_normalize_depth(int64_t n, const uint32_t *pixel, const float *z, int64_t P, const double *zlo,
+                        const double *zhi, double *z_out) {
+    if (n < 0 || P < 1 || !zlo || !zhi || (n > 0 && (!pixel || !z || !z_out))) return WTO_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if ((int64_t)pixel[i] >= P || isnan(z[i])) {
+            z_out[i] = NAN;
+            continue;
+        }
+        double lo = zlo[pixel[i]], range = zhi[pixel[i]] - lo;
+        z_out[i] = (range > 0.0 && isfinite(range)) ? ((double)z[i] - lo) / range : 0.0;
+    }
+    return WTO_OK;
+}

@@ -50,6 +50,13 @@ int wto_grad(int64_t n, const uint32_t *pixel, const float *z, const float *alph
              const double *bg, const double *bg_img, const double *gout,
              double *grad_alpha, double *grad_rgb);
 
+/* §2.1 step 1: per-pixel depth bounds (min / max depth of the pixel's fragments) */
+int wto_depth_bounds(int64_t n, const uint32_t *pixel, const float *z, const float *alpha, int64_t P,
+                     double *zlo, double *zhi);
+/* depth mapped into the pixel's bounds: (z - lo) / (hi - lo), 0 for an empty range */
+int wto_normalize_depth(int64_t n, const uint32_t *pixel, const float *z, int64_t P, const double *zlo,
+                        const double *zhi, double *z_out);
+
 #ifdef __cplusplus
 }
 #endif

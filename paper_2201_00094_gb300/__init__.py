@@ -24,7 +24,8 @@ __all__ = [
     "make_frags", "coeff_torch_dtype", "wt_version", "wt_coeff_bytes", "wt_num_tiles", "wt_build",
     "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
-    "WtServeInfo", "wt_build_resolve_batch_static",
+    "WtServeInfo", "wt_build_resolve_batch_static", "wt_bin_workspace_bytes", "wt_bin",
+    "wt_depth_bounds", "wt_normalize_depth",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -110,6 +111,10 @@ def lib() -> ctypes.CDLL:
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "wt_bin_workspace_bytes": ([D], ctypes.c_size_t),
+        "wt_bin": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_depth_bounds": ([D, Fr, vp, vp, vp], ctypes.c_int),
+        "wt_normalize_depth": ([D, Fr, vp, vp, vp, vp], ctypes.c_int),
         "wt_serve_create": ([ctypes.POINTER(WtServeConfig), ctypes.POINTER(vp)], ctypes.c_int),
         "wt_serve_submit": ([vp, D, Fr, vp, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
         "wt_serve_wait": ([vp, i64, i64], ctypes.c_int),
@@ -267,6 +272,56 @@ def wt_absorbance(desc: WtDesc, coeff: torch.Tensor, pixel: torch.Tensor, z: tor
           _dev(pixel, "pixel", (torch.int32, torch.uint32)), _dev(z, "z", (torch.float32,)),
           _dev(alpha, "alpha", (torch.float32,)), _dev(A_out, "A_out", (torch.float32,)),
           _stream(stream))
+
+
+def wt_bin_workspace_bytes(desc: WtDesc) -> int:
+    return int(lib().wt_bin_workspace_bytes(ctypes.byref(desc)))
+
+
+def wt_bin(desc: WtDesc, pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tensor,
+           r: Optional[torch.Tensor] = None, g: Optional[torch.Tensor] = None,
+           b: Optional[torch.Tensor] = None, out: Optional[dict] = None,
+           workspace: Optional[torch.Tensor] = None, stream=None) -> dict:
+    """Groups an unordered fragment stream by tile (wt_bin).  Returns a dict of
+    the output tensors (pixel, z, alpha, r, g, b, tile_offsets); pass ``out``
+    (same keys) and ``workspace`` (uint8, wt_bin_workspace_bytes) to reuse
+    buffers.  The number of kept fragments is tile_offsets[-1]."""
+    n = int(pixel.numel())
+    dev = pixel.device
+    rgb = r is not None
+    if out is None:
+        out = {"pixel": torch.empty(n, dtype=pixel.dtype, device=dev),
+               "z": torch.empty(n, device=dev), "alpha": torch.empty(n, device=dev),
+               "tile_offsets": torch.empty(wt_num_tiles(desc) + 1, dtype=torch.int64, device=dev)}
+        if rgb:
+            for k in ("r", "g", "b"):
+                out[k] = torch.empty(n, device=dev)
+    if workspace is None:
+        workspace = torch.empty(max(1, wt_bin_workspace_bytes(desc)), dtype=torch.uint8, device=dev)
+    fin = WtFrags(n, _dev(pixel, "pixel", (torch.int32, torch.uint32)), _dev(z, "z", (torch.float32,)),
+                  _dev(alpha, "alpha", (torch.float32,)), _dev(r, "r", (torch.float32,)),
+                  _dev(g, "g", (torch.float32,)), _dev(b, "b", (torch.float32,)), None)
+    _call("wt_bin", ctypes.byref(desc), ctypes.byref(fin),
+          _dev(out["pixel"], "pixel_out", (torch.int32, torch.uint32)),
+          _dev(out["z"], "z_out", (torch.float32,)), _dev(out["alpha"], "alpha_out", (torch.float32,)),
+          _dev(out.get("r"), "r_out", (torch.float32,)), _dev(out.get("g"), "g_out", (torch.float32,)),
+          _dev(out.get("b"), "b_out", (torch.float32,)),
+          _dev(out["tile_offsets"], "tile_offsets_out", (torch.int64,)),
+          _dev(workspace, "workspace", (torch.uint8,)), _stream(stream))
+    return out
+
+
+def wt_depth_bounds(desc: WtDesc, frags: WtFrags, zlo: torch.Tensor, zhi: torch.Tensor,
+                    stream=None) -> None:
+    _call("wt_depth_bounds", ctypes.byref(desc), ctypes.byref(frags),
+          _dev(zlo, "zlo", (torch.float32,)), _dev(zhi, "zhi", (torch.float32,)), _stream(stream))
+
+
+def wt_normalize_depth(desc: WtDesc, frags: WtFrags, zlo: torch.Tensor, zhi: torch.Tensor,
+                       z_out: torch.Tensor, stream=None) -> None:
+    _call("wt_normalize_depth", ctypes.byref(desc), ctypes.byref(frags),
+          _dev(zlo, "zlo", (torch.float32,)), _dev(zhi, "zhi", (torch.float32,)),
+          _dev(z_out, "z_out", (torch.float32,)), _stream(stream))
 
 
 def wt_backward(desc: WtDesc, frags: WtFrags, grad_out: torch.Tensor, grad_alpha: torch.Tensor,

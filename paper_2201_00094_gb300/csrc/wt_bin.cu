@@ -1,0 +1,287 @@
+// Steps before the coefficient build: grouping an unordered fragment stream
+// by screen tile, and the per-pixel depth bounds of §2.1 step 1 with the
+// normalisation of depth into them.
+//
+// Binning is a counting sort by tile id (row-major tiles of the descriptor):
+// a histogram pass with global integer atomics, one exclusive scan of the
+// tile counts into tile_offsets, and a scatter pass in which every fragment
+// takes the next slot of its tile with a 64-bit atomic.  Fragments whose
+// pixel id is outside the image are dropped and counted.  The order of the
+// fragments inside a tile is that of the atomics: the build does not depend on
+// it (its sums are integer), the resolve's FP32 sums may differ in the last
+// bits between runs.
+//
+// Depth bounds run per tile over a tile-grouped stream: shared-memory min/max
+// per pixel, one store per pixel.  Depth is compared through an order-
+// preserving map of the float bits to unsigned integers, so negative depths
+// order correctly.
+#include "wt.h"
+#include "wt_internal.h"
+#include "wt_tile.cuh"
+
+namespace wt {
+
+unsigned long long *error_word();  // wt_api.cu
+
+namespace {
+
+struct BinGeom {
+    int width, height, tile_w, tile_h, ntx;
+    int64_t P;
+};
+
+// Row-major tile index of a pixel id, or -1 outside the image.
+__device__ __forceinline__ int64_t tile_index(uint32_t px, const BinGeom &g) {
+    if ((int64_t)px >= g.P) return -1;
+    const uint32_t y = px / (uint32_t)g.width, x = px - y * (uint32_t)g.width;
+    return (int64_t)(y / (uint32_t)g.tile_h) * g.ntx + x / (uint32_t)g.tile_w;
+}
+
+__global__ void __launch_bounds__(256) k_bin_count(BinGeom g, int64_t n, const uint32_t *__restrict__ pixel,
+                                                   unsigned *__restrict__ counts, unsigned long long *err) {
+    unsigned bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = tile_index(pixel[i], g);
+        if (t < 0) ++bad;
+        else atomicAdd(&counts[t], 1u);
+    }
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(err, (unsigned long long)bad);
+}
+
+// One block: exclusive scan of the tile counts into offsets[0 .. ntiles] and
+// the scatter cursors.  Each thread scans a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_bin_scan(const unsigned *__restrict__ counts, int64_t ntiles,
+                                                   int64_t *__restrict__ offsets,
+                                                   unsigned long long *__restrict__ cursor) {
+    __shared__ unsigned long long part[1024];
+    const int64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = min(ntiles, b + per);
+    unsigned long long sum = 0;
+    for (int64_t t = b; t < e; ++t) sum += counts[t];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {  // inclusive Hillis-Steele scan of the chunk sums
+        const unsigned long long v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - sum;  // exclusive start of this chunk
+    for (int64_t t = b; t < e; ++t) {
+        offsets[t] = (int64_t)run;
+        cursor[t] = run;
+        run += counts[t];
+    }
+    if (threadIdx.x == blockDim.x - 1) offsets[ntiles] = (int64_t)part[threadIdx.x];
+}
+
+struct BinArrays {
+    const uint32_t *pixel;
+    const float *z, *alpha, *r, *g, *b;
+    uint32_t *opixel;
+    float *oz, *oalpha, *or_, *og, *ob;
+};
+
+__global__ void __launch_bounds__(256) k_bin_scatter(BinGeom g, int64_t n, BinArrays a,
+                                                     unsigned long long *__restrict__ cursor) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t px = a.pixel[i];
+        const int64_t t = tile_index(px, g);
+        if (t < 0) continue;
+        const int64_t slot = (int64_t)atomicAdd(&cursor[t], 1ull);
+        a.opixel[slot] = px;
+        a.oz[slot] = a.z[i];
+        a.oalpha[slot] = a.alpha[i];
+        if (a.r) {
+            a.or_[slot] = a.r[i];
+            a.og[slot] = a.g[i];
+            a.ob[slot] = a.b[i];
+        }
+    }
+}
+
+// order-preserving map of float bits to unsigned (and back)
+__device__ __forceinline__ unsigned order_key(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_key(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Per-pixel min and max depth of a tile's valid fragments (z and alpha not
+// NaN, pixel inside the tile); +inf / -inf for pixels with none.
+__global__ void __launch_bounds__(kThreads) k_depth_bounds(Params p, float *__restrict__ zlo,
+                                                           float *__restrict__ zhi) {
+    __shared__ unsigned slo[kMaxTilePx], shi[kMaxTilePx];
+    const int npx = p.g.tile_w * p.g.tile_h;
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) {
+        slo[i] = order_key(__int_as_float(0x7f800000));
+        shi[i] = order_key(__int_as_float(0xff800000));
+    }
+    const Tile T = tile_of(p, blockIdx.x, true);
+    __syncthreads();
+    unsigned bad = 0;
+    for_each_group<kWithZ>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if (!G.v) continue;
+            const int lp = G.z[k] == G.z[k] && G.al[k] == G.al[k] ? local_pixel(G.px[k], p, T) : -1;
+            if (lp < 0) {
+                ++bad;
+                continue;
+            }
+            const unsigned key = order_key(G.z[k]);
+            atomicMin(&slo[lp], key);
+            atomicMax(&shi[lp], key);
+        }
+    });
+    flush_bad(bad, p.err);
+    __syncthreads();
+    const int lp = threadIdx.x;
+    if (lp >= npx) return;
+    const int64_t gp = global_pixel(p, T, lp);
+    if (gp < 0) return;
+    zlo[gp] = from_key(slo[lp]);
+    zhi[gp] = from_key(shi[lp]);
+}
+
+// z_out = (z - zlo_p) / (zhi_p - zlo_p) for the fragment's pixel p, 0 when the
+// range is empty or not finite; fragments with a bad pixel id or NaN keep NaN.
+__global__ void __launch_bounds__(256) k_normalize_depth(int64_t n, int64_t P, const uint32_t *__restrict__ pixel,
+                                                         const float *z, const float *__restrict__ zlo,
+                                                         const float *__restrict__ zhi, float *z_out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t px = pixel[i];
+        const float zi = z[i];
+        float o = __int_as_float(0x7fc00000);
+        if ((int64_t)px < P && zi == zi) {
+            const float lo = zlo[px], range = zhi[px] - lo;
+            o = range > 0.f && range < __int_as_float(0x7f800000) ? (zi - lo) / range : 0.f;
+        }
+        z_out[i] = o;
+    }
+}
+
+int grid_for(int64_t n) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + 255) / 256;
+    const int64_t cap = (int64_t)sms * 8;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+bool aligned_to(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+wt_status check_geom(const wt_desc *d) {
+    if (!d || d->width < 1 || d->height < 1 || d->tile_w < 1 || d->tile_h < 1) return WT_ERR_ARG;
+    if ((int64_t)d->width * d->height >= (int64_t(1) << 31)) return WT_ERR_ARG;
+    if ((int64_t)d->tile_w * d->tile_h > kMaxTilePx) return WT_ERR_ARG;
+    return WT_OK;
+}
+
+BinGeom bin_geom(const wt_desc *d) {
+    BinGeom g;
+    g.width = d->width;
+    g.height = d->height;
+    g.tile_w = d->tile_w;
+    g.tile_h = d->tile_h;
+    g.ntx = (d->width + d->tile_w - 1) / d->tile_w;
+    g.P = (int64_t)d->width * d->height;
+    return g;
+}
+
+int64_t tiles_of(const wt_desc *d) {
+    return (int64_t)((d->width + d->tile_w - 1) / d->tile_w) * ((d->height + d->tile_h - 1) / d->tile_h);
+}
+
+size_t ws_counts(int64_t ntiles) { return ((size_t)ntiles * 4 + 255) & ~size_t(255); }
+
+}  // namespace
+}  // namespace wt
+
+using namespace wt;
+
+extern "C" size_t wt_bin_workspace_bytes(const wt_desc *desc) {
+    if (check_geom(desc) != WT_OK) return 0;
+    const int64_t nt = tiles_of(desc);
+    return ws_counts(nt) + (size_t)nt * 8;
+}
+
+extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
+                            float *alpha_out, float *r_out, float *g_out, float *b_out,
+                            int64_t *tile_offsets_out, void *workspace, wt_stream stream) {
+    wt_status st = check_geom(desc);
+    if (st != WT_OK) return st;
+    if (!in || in->n < 0 || !tile_offsets_out || !workspace) return WT_ERR_ARG;
+    if (!aligned_to(workspace, 256) || !aligned_to(tile_offsets_out, 8)) return WT_ERR_ARG;
+    const bool rgb = in->r != nullptr;
+    if (rgb != (in->g != nullptr) || rgb != (in->b != nullptr)) return WT_ERR_ARG;
+    if (in->n > 0) {
+        const void *need[6] = {in->pixel, in->z, in->alpha, pixel_out, z_out, alpha_out};
+        for (const void *p : need)
+            if (!p) return WT_ERR_ARG;
+        if (rgb && (!r_out || !g_out || !b_out)) return WT_ERR_ARG;
+    }
+    unsigned long long *err = error_word();
+    if (!err) return WT_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t nt = tiles_of(desc);
+    unsigned *counts = static_cast<unsigned *>(workspace);
+    unsigned long long *cursor =
+        reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + ws_counts(nt));
+    const BinGeom g = bin_geom(desc);
+    if (cudaMemsetAsync(counts, 0, (size_t)nt * 4, s) != cudaSuccess) return WT_ERR_CUDA;
+    if (in->n > 0) k_bin_count<<<grid_for(in->n), 256, 0, s>>>(g, in->n, in->pixel, counts, err);
+    k_bin_scan<<<1, 1024, 0, s>>>(counts, nt, tile_offsets_out, cursor);
+    if (in->n > 0) {
+        BinArrays a{in->pixel, in->z, in->alpha, in->r, in->g, in->b,
+                    pixel_out, z_out, alpha_out, r_out, g_out, b_out};
+        if (!rgb) a.r = a.g = a.b = nullptr;
+        k_bin_scatter<<<grid_for(in->n), 256, 0, s>>>(g, in->n, a, cursor);
+    }
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+extern "C" wt_status wt_depth_bounds(const wt_desc *desc, const wt_frags *frags, float *zlo, float *zhi,
+                                     wt_stream stream) {
+    wt_status st = check_geom(desc);
+    if (st != WT_OK) return st;
+    if (!frags || frags->n < 0 || !frags->tile_offsets || !zlo || !zhi) return WT_ERR_ARG;
+    if (!aligned_to(frags->tile_offsets, 8)) return WT_ERR_ARG;
+    const void *req[3] = {frags->pixel, frags->z, frags->alpha};
+    for (const void *p : req)
+        if ((frags->n > 0 && !p) || !aligned_to(p, 16)) return WT_ERR_ARG;
+    unsigned long long *err = error_word();
+    if (!err) return WT_ERR_CUDA;
+    Params p{};
+    p.g.width = desc->width;
+    p.g.height = desc->height;
+    p.g.tile_w = desc->tile_w;
+    p.g.tile_h = desc->tile_h;
+    p.g.ntx = (desc->width + desc->tile_w - 1) / desc->tile_w;
+    set_row_division(p);
+    p.n = frags->n;
+    p.pixel = frags->pixel;
+    p.z = frags->z;
+    p.alpha = frags->alpha;
+    p.off = frags->tile_offsets;
+    p.err = err;
+    const int64_t nt = tiles_of(desc);
+    k_depth_bounds<<<(unsigned)nt, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(p, zlo, zhi);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+extern "C" wt_status wt_normalize_depth(const wt_desc *desc, const wt_frags *frags, const float *zlo,
+                                        const float *zhi, float *z_out, wt_stream stream) {
+    wt_status st = check_geom(desc);
+    if (st != WT_OK) return st;
+    if (!frags || frags->n < 0 || !zlo || !zhi) return WT_ERR_ARG;
+    if (frags->n > 0 && (!frags->pixel || !frags->z || !z_out)) return WT_ERR_ARG;
+    if (frags->n == 0) return WT_OK;
+    k_normalize_depth<<<grid_for(frags->n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        frags->n, (int64_t)desc->width * desc->height, frags->pixel, frags->z, zlo, zhi, z_out);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}

@@ -351,32 +351,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     fill_zero(gam, (int)PL);
     __syncthreads();
     const uint32_t flags = p.flags;
-    const int tid = threadIdx.x, nt = blockDim.x;
     // pass 3: colour gradients and the scatter of gamma into the bins
-    for (int64_t i = T.s + tid; i < T.e; i += nt) {
-        const FragState<J> st = frag_state<J>(p, T, vals, p.pixel[i], p.z[i], p.alpha[i]);
-        if (st.lp < 0) {
-            p.grgb[i] = 0.f;
-            p.grgb[p.n + i] = 0.f;
-            p.grgb[2 * p.n + i] = 0.f;
-            continue;
+    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+        float gr[3][N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            gr[0][k] = gr[1][k] = gr[2][k] = 0.f;
+            if (!G.v) continue;
+            const FragState<J> st = frag_state<J>(p, T, vals, G.px[k], G.z[k], G.al[k]);
+            if (st.lp < 0) continue;
+            const float c[3] = {G.r[k], G.g[k], G.b[k]};
+            float beta = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float u = sU[ch * wpl + st.lp];
+                beta = fmaf(u, c[ch] - sY[ch * wpl + st.lp], beta);
+                gr[ch][k] = u * st.w;
+            }
+            const float gamma = -beta * st.w;
+            float *row = gam + st.lp * LD;
+            if (flags & kLinear) {
+                atomicAdd(&row[st.q.lo], gamma * (1.f - st.q.t));
+                atomicAdd(&row[st.q.lo + 1], gamma * st.q.t);
+            } else {
+                atomicAdd(&row[st.q.m], gamma);
+            }
         }
-        const float c[3] = {p.r[i], p.gc[i], p.b[i]};
-        float beta = 0.f;
-        for (int ch = 0; ch < 3; ++ch) {
-            const float u = sU[ch * wpl + st.lp];
-            beta = fmaf(u, c[ch] - sY[ch * wpl + st.lp], beta);
-            p.grgb[ch * p.n + i] = u * st.w;
+        if (G.v) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) store_group<N>(p.grgb + ch * p.n, G.i0, gr[ch]);
         }
-        const float gamma = -beta * st.w;
-        float *row = gam + st.lp * LD;
-        if (flags & kLinear) {
-            atomicAdd(&row[st.q.lo], gamma * (1.f - st.q.t));
-            atomicAdd(&row[st.q.lo + 1], gamma * st.q.t);
-        } else {
-            atomicAdd(&row[st.q.m], gamma);
-        }
-    }
+    });
     __syncthreads();
     if (gp >= 0) {  // inclusive suffix sums Q_m, with Q_C = 0
         float *row = gam + lp * LD;
@@ -389,29 +395,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     }
     __syncthreads();
     // pass 4: opacity gradients
-    for (int64_t i = T.s + tid; i < T.e; i += nt) {
-        const float al = p.alpha[i];
-        const FragState<J> st = frag_state<J>(p, T, vals, p.pixel[i], p.z[i], al);
-        if (st.lp < 0) {
-            p.galpha[i] = 0.f;
-            continue;
+    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+        float ga[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            ga[k] = 0.f;
+            if (!G.v) continue;
+            const float al = G.al[k];
+            const FragState<J> st = frag_state<J>(p, T, vals, G.px[k], G.z[k], al);
+            if (st.lp < 0) continue;
+            const float c[3] = {G.r[k], G.g[k], G.b[k]};
+            float beta = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                beta = fmaf(sU[ch * wpl + st.lp], c[ch] - sY[ch * wpl + st.lp], beta);
+            const float gamma = -beta * st.w;
+            const float *Q = gam + st.lp * LD;
+            float da = fmaf(st.q.f, Q[st.q.m + 1], (1.f - st.q.f) * Q[st.q.m]);
+            if (flags & kSelfExclude) da -= gamma * st.q.g;
+            da += sK[st.lp];
+            if (al > 0.f && al < kAlphaMax) {
+                const float direct = st.ac > 0.f ? beta * (st.w / st.ac) : 0.f;
+                ga[k] = direct + da / (1.f - al);
+            }
         }
-        const float c[3] = {p.r[i], p.gc[i], p.b[i]};
-        float beta = 0.f;
-        for (int ch = 0; ch < 3; ++ch)
-            beta = fmaf(sU[ch * wpl + st.lp], c[ch] - sY[ch * wpl + st.lp], beta);
-        const float gamma = -beta * st.w;
-        const float *Q = gam + st.lp * LD;
-        float da = fmaf(st.q.f, Q[st.q.m + 1], (1.f - st.q.f) * Q[st.q.m]);
-        if (flags & kSelfExclude) da -= gamma * st.q.g;
-        da += sK[st.lp];
-        float g = 0.f;
-        if (al > 0.f && al < kAlphaMax) {
-            const float direct = st.ac > 0.f ? beta * (st.w / st.ac) : 0.f;
-            g = direct + da / (1.f - al);
-        }
-        p.galpha[i] = g;
-    }
+        if (G.v) store_group<N>(p.galpha, G.i0, ga);
+    });
 }
 
 template <int J, typename CT>

@@ -382,7 +382,8 @@ __device__ __forceinline__ float step_of(float x) {
 enum : int { kWithZ = 1, kWithRGB = 2 };
 template <int N> struct Group {
     static constexpr int size = N;
-    bool v;  // inside the range (all N fragments or none)
+    bool v;      // inside the range (all N fragments or none)
+    int64_t i0;  // index of the first fragment
     uint32_t px[N];
     float al[N], z[N], r[N], g[N], b[N];
 };
@@ -390,6 +391,7 @@ template <int N> struct Group {
 template <int LOAD>
 __device__ __forceinline__ void load_one(Group<1> &G, bool v, int64_t i, const Params &p) {
     G.v = v;
+    G.i0 = i;
     G.px[0] = v ? p.pixel[i] : 0u;
     G.al[0] = v ? p.alpha[i] : 0.f;
     if (LOAD & kWithZ) G.z[0] = v ? p.z[i] : 0.f;
@@ -415,6 +417,7 @@ __device__ __forceinline__ void load_four(Group<4> &G, bool v, int64_t q, const 
         }
     }
     G.v = v;
+    G.i0 = 4 * q;
     G.px[0] = pv.x, G.px[1] = pv.y, G.px[2] = pv.z, G.px[3] = pv.w;
     G.al[0] = av.x, G.al[1] = av.y, G.al[2] = av.z, G.al[3] = av.w;
     G.z[0] = zv.x, G.z[1] = zv.y, G.z[2] = zv.z, G.z[3] = zv.w;
@@ -478,6 +481,19 @@ template <int LOAD> __device__ __forceinline__ void prefetch_tile(const Params &
         l2_prefetch_range(p.gc, T.s, T.e);
         l2_prefetch_range(p.b, T.s, T.e);
     }
+}
+
+// Stores a group's N per-fragment results at dst[i0 ..], as one 16-byte
+// vector when N = 4 and the address allows it.
+template <int N> __device__ __forceinline__ void store_group(float *dst, int64_t i0, const float (&v)[N]) {
+    if constexpr (N == 4) {
+        if ((reinterpret_cast<uintptr_t>(dst + i0) & 15) == 0) {
+            *reinterpret_cast<float4 *>(dst + i0) = make_float4(v[0], v[1], v[2], v[3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[i0 + k] = v[k];
 }
 
 // ---------------------------------------------------------------- shared-memory updates

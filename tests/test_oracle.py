@@ -383,3 +383,71 @@ def test_gradient_matches_finite_differences(flags):
             cm[i, ch] -= h
             fd = (loss(al, cp) - loss(al, cm)) / (float(cp[i, ch]) - float(cm[i, ch]))
             assert gc[i, ch] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+# ---------------------------------------------------------------- §2.1 step 1 and tile binning
+
+def test_depth_bounds_hand_example():
+    """Bounds of a pixel are its nearest and farthest fragment; an empty pixel
+    has (+inf, -inf); NaN fragments and bad pixel ids are left out; negative
+    depths order correctly."""
+    pixel = np.array([0, 0, 0, 2, 0, 3, 2], dtype=np.uint32)
+    z = np.array([0.3, 0.1, 0.7, -2.5, np.nan, 0.5, -2.0], dtype=np.float32)
+    alpha = np.array([0.5, 0.5, 0.5, 0.2, 0.5, 0.5, np.nan], dtype=np.float32)
+    lo, hi = o.depth_bounds(pixel, z, alpha, 3)  # pixel 3 is outside P = 3
+    assert lo[0] == np.float32(0.1) and hi[0] == np.float32(0.7)
+    assert lo[1] == np.inf and hi[1] == -np.inf
+    assert lo[2] == np.float32(-2.5) and hi[2] == np.float32(-2.5)
+
+
+def test_normalize_depth_maps_bounds_to_unit_interval():
+    pixel = np.array([0, 0, 0, 2, 5, 1], dtype=np.uint32)
+    z = np.array([0.3, 0.1, 0.7, -2.5, 0.2, np.nan], dtype=np.float32)
+    alpha = np.full(6, 0.5, dtype=np.float32)
+    lo, hi = o.depth_bounds(pixel, z, alpha, 3)
+    zn = o.normalize_depth(pixel, z, 3, lo, hi)
+    f = z.astype(np.float64)
+    assert zn[1] == 0.0 and zn[2] == 1.0
+    assert zn[0] == pytest.approx((f[0] - f[1]) / (f[2] - f[1]), rel=1e-15)
+    assert zn[3] == 0.0                      # a single fragment: empty range
+    assert np.isnan(zn[4]) and np.isnan(zn[5])  # bad pixel id, NaN depth
+
+
+def test_normalize_depth_undoes_an_affine_depth_map():
+    """Depths that fill [0, 1] in every pixel, mapped affinely into arbitrary
+    per-pixel ranges, come back to themselves."""
+    rng = np.random.default_rng(5)
+    P = 50
+    pixel = np.repeat(np.arange(P), 6).astype(np.uint32)
+    u = rng.random(len(pixel))
+    u[::6], u[1::6] = 0.0, 1.0
+    lo_p, span_p = rng.uniform(-5, 5, P), rng.uniform(0.5, 8, P)
+    z = (lo_p[pixel] + u * span_p[pixel]).astype(np.float32)
+    lo, hi = o.depth_bounds(pixel, z, np.full(len(z), 0.3, np.float32), P)
+    zn = o.normalize_depth(pixel, z, P, lo, hi)
+    np.testing.assert_allclose(zn, u, atol=1e-6)
+
+
+def test_tile_ids_hand_computed():
+    """53 x 37 image in 7 x 3 tiles: 8 tiles per row, 13 rows of tiles."""
+    W, H = 53, 37
+    cases = {(0, 0): 0, (6, 2): 0, (7, 0): 1, (0, 3): 8, (52, 0): 7, (52, 36): 103, (13, 5): 8 + 1}
+    px = np.array([y * W + x for (x, y) in cases], dtype=np.int64)
+    got = o.tile_of_pixels(np.append(px, W * H), W, H, 7, 3)
+    assert list(got[:-1]) == list(cases.values())
+    assert got[-1] == -1
+
+
+def test_bin_by_tile_groups_and_keeps_order():
+    rng = np.random.default_rng(6)
+    W, H, tw, th = 53, 37, 7, 3
+    pixel = rng.integers(0, W * H + 20, size=5000)  # a few outside the image
+    order, off = o.bin_by_tile(pixel, W, H, tw, th)
+    assert off[0] == 0 and off[-1] == np.sum(pixel < W * H) == len(order)
+    assert np.all(np.diff(off) >= 0)
+    ntx = -(-W // tw)
+    for t in range(len(off) - 1):
+        idx = order[off[t]:off[t + 1]]
+        assert np.all(np.diff(idx) > 0)  # stable: input order inside a tile
+        x, y = pixel[idx] % W, pixel[idx] // W
+        assert np.all(x // tw == t % ntx) and np.all(y // th == t // ntx)
