@@ -263,13 +263,16 @@ def run_wt(args):
     value = frags_all * K / (total_ms / 1e3)
 
     s = DTYPE_BYTES[dt]
-    if args.path == "fused":
-        alg_bytes = n * 24 + P * C * s + 16 * P  # fragments once, coefficients + RGBA written
-    else:
-        alg_bytes = n * 36 + 2 * P * C * s + 16 * P  # two passes over the fragments
+    # Algorithmic bytes of one frame of the method (two passes over the
+    # fragments, coefficients written once and read once, RGBA written once):
+    # 36 n + 2 P C s + 16 P.  The fused kernel's own minimum is 24 n + P C s + 16 P
+    # (fragments read once, coefficients written once); both are reported.
+    method_bytes = n * 36 + 2 * P * C * s + 16 * P
+    fused_min_bytes = n * 24 + P * C * s + 16 * P
+    alg_bytes = method_bytes
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic("k_fused", args.workload, args.dtype)
+    traffic = profiled_traffic("k_fused", args.workload, args.dtype) if args.path == "fused" else None
 
     # ---- variants (not part of `value`): two-pass path and 16-bit storage
     variants = {}
@@ -318,9 +321,18 @@ def run_wt(args):
                          f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
                          f"composite, FP64, single thread, {res['seconds']:.1f} s",
                "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
+    preprocess = None
+    if rank == 0 and world == 1 and not args.no_preprocess:
+        preprocess = run_preprocess(wt, fr, desc, stream)
+    backward = None
+    if rank == 0 and world == 1 and not args.no_backward:
+        del coeff, out
+        torch.cuda.empty_cache()
+        backward = run_backward(wt, args)
+        coeff, out = None, None
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
-        del coeff, out
+        coeff = out = None
         torch.cuda.empty_cache()
         serving, pool = {}, None
         for dname in ("bf16", "f32"):
@@ -346,18 +358,121 @@ def run_wt(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(achieved / hbm, 4),
                          "traffic": traffic, "kernel": kernel_name,
-                         "alg_bytes_per_launch": alg_bytes, "launch_ms": round(launch_ms, 4),
+                         "alg_bytes_per_launch": alg_bytes,
+                         "alg_bytes_definition": "36 n + 2 P C s + 16 P (the method's two passes)",
+                         "fused_min_bytes_per_launch": fused_min_bytes,
+                         "frac_of_fused_min_bytes": round(fused_min_bytes / (launch_ms / 1e3) / 1e9 / hbm, 4),
+                         "dram_frac_measured": (round(traffic / (launch_ms / 1e3) / 1e9 / hbm, 4)
+                                                if traffic else None),
+                         "launch_ms": round(launch_ms, 4),
                          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": K * (1 if args.path == "fused" else 2),
             "clocks": clk.summary(),
             "variants": variants,
+            "preprocess": preprocess,
+            "backward": backward,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_preprocess(wt, fr, desc, stream):
+    """The steps before the build on the same frame: grouping the frame's
+    fragments, put in a seeded random order, by tile (wt_bin), and the
+    per-pixel depth bounds of §2.1 step 1 with the normalisation of depth into
+    them (wt_depth_bounds, wt_normalize_depth).  Bytes per fragment: binning
+    reads the pixel id twice and the six arrays once and writes them once
+    (52 B; its 32-byte staging records add 64 B of workspace traffic); bounds
+    read pixel, z, alpha (12 B); normalisation reads pixel and z and writes z
+    (12 B)."""
+    dev = fr.pixel.device
+    n, P = fr.n, fr.P
+    g = torch.Generator(device=dev)
+    g.manual_seed(4321)
+    perm = torch.randperm(n, device=dev, generator=g)
+    src = {k: getattr(fr, k)[perm].contiguous() for k in ("pixel", "z", "alpha", "r", "g", "b")}
+    del perm
+    out = {k: torch.empty_like(v) for k, v in src.items()}
+    out["tile_offsets"] = torch.empty_like(fr.tile_offsets)
+    ws = torch.empty(max(1, wt.wt_bin_workspace_bytes(desc, n)), dtype=torch.uint8, device=dev)
+    zlo, zhi = torch.empty(P, device=dev), torch.empty(P, device=dev)
+    zn = torch.empty(n, device=dev)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    bin_ms = timed(lambda: wt.wt_bin(desc, src["pixel"], src["z"], src["alpha"], src["r"], src["g"],
+                                     src["b"], out=out, workspace=ws, stream=stream))
+    frags = wt.make_frags(out["pixel"], out["z"], out["alpha"], out["tile_offsets"])
+    bounds_ms = timed(lambda: wt.wt_depth_bounds(desc, frags, zlo, zhi, stream=stream))
+    norm_ms = timed(lambda: wt.wt_normalize_depth(desc, frags, zlo, zhi, zn, stream=stream))
+    assert wt.wt_get_error(stream) == 0
+    assert torch.equal(out["tile_offsets"], fr.tile_offsets)
+    hbm, _ = peaks()
+    res = {}
+    for name, ms, per in (("bin", bin_ms, 52), ("depth_bounds", bounds_ms, 12), ("normalize_depth", norm_ms, 12)):
+        gbs = n * per / (ms / 1e3) / 1e9
+        res[name] = {"ms": round(ms, 4), "fragments_per_s": n / (ms / 1e3), "alg_bytes_per_fragment": per,
+                     "alg_GBps": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm, 4)}
+    res["input"] = "the bench frame's fragments in a seeded random order"
+    del src, out, ws, zlo, zhi, zn
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_backward(wt, args):
+    """Adjoint of build + resolve + composite (wt_backward) on the
+    differentiation workload: 16 frames of 512x512 stacked as 512x8192 (pixels
+    are independent), Poisson(32) fragments per pixel capped at 256,
+    alpha U[.05,.5], J = 4, FP32, with a seeded dL/d(out).  The forward (fused)
+    call on the same frame is timed beside it."""
+    dev = torch.device("cuda")
+    tw, th = tile_of(args)
+    fr = synth.uniform_frame(512, 8192, 32.0, 256, (0.05, 0.5), 4, args.seed, dev, name="diff512",
+                             tile_w=tw, tile_h=th)
+    n, P = fr.n, fr.P
+    desc = wt.make_desc(fr.width, fr.height, fr.J, wt.F32, tile_w=fr.tile_w, tile_h=fr.tile_h)
+    frags = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+    g = torch.Generator(device=dev)
+    g.manual_seed(args.seed + 17)
+    grad_out = torch.rand(P, 4, device=dev, generator=g) - 0.5
+    grad_alpha = torch.empty(n, device=dev)
+    grad_rgb = torch.empty(3, n, device=dev)
+    out = torch.empty(P, 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    fwd_ms = timed(lambda: wt.wt_build_resolve(desc, frags, out, None, None, bg=fr.bg, stream=stream))
+    bwd_ms = timed(lambda: wt.wt_backward(desc, frags, grad_out, grad_alpha, grad_rgb, bg=fr.bg,
+                                          stream=stream))
+    assert wt.wt_get_error(stream) == 0
+    return {"workload": "16 x 512x512 stacked as 512x8192, Poisson(32) cap 256, alpha U[.05,.5], J=4, FP32",
+            "fragments": n, "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "backward_fragments_per_s": n / (bwd_ms / 1e3),
+            "backward_bytes_per_fragment": 24 + 16,
+            "backward_GBps_of_fragment_io": round(n * 40 / (bwd_ms / 1e3) / 1e9, 1)}
 
 
 def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all):
@@ -522,8 +637,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wt", choices=["wt", "reference"])
     ap.add_argument("--workload", default="heavy4k", choices=sorted(WORKLOADS))
-    ap.add_argument("--tile", default="256x1",
-                    help="screen tile WxH (one CTA each); 256x1 row spans need no division")
+    ap.add_argument("--tile", default="192x1",
+                    help="screen tile WxH (one CTA each); row spans need no division, and at J = 5 "
+                         "tiles of <= 192 pixels fit four CTAs per SM")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--size", default="", help="override the workload's WxH (profiling runs)")
@@ -533,6 +649,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-preprocess", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--path", default="fused", choices=["fused", "two_pass"],
                     help="fused kernel (default) or wt_build + wt_resolve_composite")

@@ -249,10 +249,11 @@ wt_status wt_backward(const wt_desc *desc, const wt_frags *frags, const float *b
  * transparent surfaces, into which depth is normalised before the build).
  */
 
-/* Bytes of device workspace wt_bin needs for this descriptor (tile counts and
- * cursors, about 12 bytes per tile); 0 if the descriptor is invalid.  Only the
- * descriptor's width, height, tile_w and tile_h are used. */
-size_t wt_bin_workspace_bytes(const wt_desc *desc);
+/* Bytes of device workspace wt_bin needs for n fragments with this
+ * descriptor: tile counts and cursors (about 12 bytes per tile) and a staging
+ * record of 32 bytes per fragment; 0 if the descriptor is invalid or n < 0.
+ * Only the descriptor's width, height, tile_w and tile_h are used. */
+size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n);
 
 /*
  * wt_bin -- groups an unordered fragment stream by tile (row-major tiles of
@@ -264,8 +265,9 @@ size_t wt_bin_workspace_bytes(const wt_desc *desc);
  *   tile_offsets_out [ntiles + 1] int64, written: tile t owns
  *               [tile_offsets_out[t], tile_offsets_out[t+1]); the last entry
  *               is the number of kept fragments.
- *   workspace   wt_bin_workspace_bytes(desc) bytes of device memory, 256-byte
- *               aligned, owned by the caller (overwritten).
+ *   workspace   device memory of workspace_bytes >= wt_bin_workspace_bytes(desc,
+ *               in->n) bytes (else WT_ERR_ARG), 256-byte aligned, owned by the
+ *               caller (overwritten).
  * Fragments whose pixel id is >= width*height are dropped and counted in the
  * error word.  The order of the fragments inside a tile is unspecified (it
  * follows the atomics that hand out the slots): the build does not depend on
@@ -273,7 +275,8 @@ size_t wt_bin_workspace_bytes(const wt_desc *desc);
  */
 wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
                  float *alpha_out, float *r_out, float *g_out, float *b_out,
-                 int64_t *tile_offsets_out, void *workspace, wt_stream stream);
+                 int64_t *tile_offsets_out, void *workspace, size_t workspace_bytes,
+                 wt_stream stream);
 
 /*
  * wt_depth_bounds -- §2.1 step 1: per-pixel depth bounds of the transparent

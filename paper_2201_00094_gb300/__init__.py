@@ -111,8 +111,8 @@ def lib() -> ctypes.CDLL:
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
-        "wt_bin_workspace_bytes": ([D], ctypes.c_size_t),
-        "wt_bin": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_bin_workspace_bytes": ([D, i64], ctypes.c_size_t),
+        "wt_bin": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
         "wt_depth_bounds": ([D, Fr, vp, vp, vp], ctypes.c_int),
         "wt_normalize_depth": ([D, Fr, vp, vp, vp, vp], ctypes.c_int),
         "wt_serve_create": ([ctypes.POINTER(WtServeConfig), ctypes.POINTER(vp)], ctypes.c_int),
@@ -274,8 +274,8 @@ def wt_absorbance(desc: WtDesc, coeff: torch.Tensor, pixel: torch.Tensor, z: tor
           _stream(stream))
 
 
-def wt_bin_workspace_bytes(desc: WtDesc) -> int:
-    return int(lib().wt_bin_workspace_bytes(ctypes.byref(desc)))
+def wt_bin_workspace_bytes(desc: WtDesc, n: int) -> int:
+    return int(lib().wt_bin_workspace_bytes(ctypes.byref(desc), int(n)))
 
 
 def wt_bin(desc: WtDesc, pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tensor,
@@ -284,8 +284,8 @@ def wt_bin(desc: WtDesc, pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tens
            workspace: Optional[torch.Tensor] = None, stream=None) -> dict:
     """Groups an unordered fragment stream by tile (wt_bin).  Returns a dict of
     the output tensors (pixel, z, alpha, r, g, b, tile_offsets); pass ``out``
-    (same keys) and ``workspace`` (uint8, wt_bin_workspace_bytes) to reuse
-    buffers.  The number of kept fragments is tile_offsets[-1]."""
+    (same keys) and ``workspace`` (uint8, wt_bin_workspace_bytes(desc, n)) to
+    reuse buffers.  The number of kept fragments is tile_offsets[-1]."""
     n = int(pixel.numel())
     dev = pixel.device
     rgb = r is not None
@@ -297,7 +297,7 @@ def wt_bin(desc: WtDesc, pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tens
             for k in ("r", "g", "b"):
                 out[k] = torch.empty(n, device=dev)
     if workspace is None:
-        workspace = torch.empty(max(1, wt_bin_workspace_bytes(desc)), dtype=torch.uint8, device=dev)
+        workspace = torch.empty(max(1, wt_bin_workspace_bytes(desc, n)), dtype=torch.uint8, device=dev)
     fin = WtFrags(n, _dev(pixel, "pixel", (torch.int32, torch.uint32)), _dev(z, "z", (torch.float32,)),
                   _dev(alpha, "alpha", (torch.float32,)), _dev(r, "r", (torch.float32,)),
                   _dev(g, "g", (torch.float32,)), _dev(b, "b", (torch.float32,)), None)
@@ -307,7 +307,7 @@ def wt_bin(desc: WtDesc, pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tens
           _dev(out.get("r"), "r_out", (torch.float32,)), _dev(out.get("g"), "g_out", (torch.float32,)),
           _dev(out.get("b"), "b_out", (torch.float32,)),
           _dev(out["tile_offsets"], "tile_offsets_out", (torch.int64,)),
-          _dev(workspace, "workspace", (torch.uint8,)), _stream(stream))
+          _dev(workspace, "workspace", (torch.uint8,)), int(workspace.numel()), _stream(stream))
     return out
 
 

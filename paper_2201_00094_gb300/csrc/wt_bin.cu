@@ -4,9 +4,11 @@
 //
 // Binning is a counting sort by tile id (row-major tiles of the descriptor):
 // a histogram pass with global integer atomics, one exclusive scan of the
-// tile counts into tile_offsets, and a scatter pass in which every fragment
-// takes the next slot of its tile with a 64-bit atomic.  Fragments whose
-// pixel id is outside the image are dropped and counted.  The order of the
+// tile counts into tile_offsets, a scatter pass in which every fragment takes
+// the next slot of its tile with a 64-bit atomic and is staged there as one
+// record, and a pass that unpacks the records in order into the output
+// arrays.  Fragments whose pixel id is outside the image are dropped and
+// counted.  The order of the
 // fragments inside a tile is that of the atomics: the build does not depend on
 // it (its sums are integer), the resolve's FP32 sums may differ in the last
 // bits between runs.
@@ -76,27 +78,54 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const unsigned *__restrict__ 
     if (threadIdx.x == blockDim.x - 1) offsets[ntiles] = (int64_t)part[threadIdx.x];
 }
 
-struct BinArrays {
+// The scatter writes each kept fragment as one record into its tile's next
+// slot of a staging array -- 32 bytes (pixel, z, alpha, r, g, b) or 16 bytes
+// (pixel, z, alpha) -- so that every slot is one whole-sector store, however
+// scattered the slots are; a second pass copies the records out to the
+// structure-of-arrays output in order, with coalesced loads and stores.
+struct BinIn {
     const uint32_t *pixel;
     const float *z, *alpha, *r, *g, *b;
-    uint32_t *opixel;
-    float *oz, *oalpha, *or_, *og, *ob;
+};
+struct BinOut {
+    uint32_t *pixel;
+    float *z, *alpha, *r, *g, *b;
 };
 
-__global__ void __launch_bounds__(256) k_bin_scatter(BinGeom g, int64_t n, BinArrays a,
+template <bool RGB>
+__global__ void __launch_bounds__(256) k_bin_scatter(BinGeom g, int64_t n, BinIn a, uint4 *__restrict__ stage,
                                                      unsigned long long *__restrict__ cursor) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t px = a.pixel[i];
         const int64_t t = tile_index(px, g);
         if (t < 0) continue;
         const int64_t slot = (int64_t)atomicAdd(&cursor[t], 1ull);
-        a.opixel[slot] = px;
-        a.oz[slot] = a.z[i];
-        a.oalpha[slot] = a.alpha[i];
-        if (a.r) {
-            a.or_[slot] = a.r[i];
-            a.og[slot] = a.g[i];
-            a.ob[slot] = a.b[i];
+        const uint4 r0 = make_uint4(px, __float_as_uint(a.z[i]), __float_as_uint(a.alpha[i]),
+                                    RGB ? __float_as_uint(a.r[i]) : 0u);
+        if (RGB) {
+            stage[2 * slot] = r0;
+            stage[2 * slot + 1] = make_uint4(__float_as_uint(a.g[i]), __float_as_uint(a.b[i]), 0u, 0u);
+        } else {
+            stage[slot] = r0;
+        }
+    }
+}
+
+template <bool RGB>
+__global__ void __launch_bounds__(256) k_bin_unpack(int64_t n, const int64_t *__restrict__ kept_at,
+                                                    const uint4 *__restrict__ stage, BinOut o) {
+    const int64_t kept = *kept_at;  // tile_offsets[ntiles]
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kept && i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 r0 = stage[RGB ? 2 * i : i];
+        o.pixel[i] = r0.x;
+        o.z[i] = __uint_as_float(r0.y);
+        o.alpha[i] = __uint_as_float(r0.z);
+        if (RGB) {
+            const uint4 r1 = stage[2 * i + 1];
+            o.r[i] = __uint_as_float(r0.w);
+            o.g[i] = __uint_as_float(r1.x);
+            o.b[i] = __uint_as_float(r1.y);
         }
     }
 }
@@ -204,19 +233,21 @@ size_t ws_counts(int64_t ntiles) { return ((size_t)ntiles * 4 + 255) & ~size_t(2
 
 using namespace wt;
 
-extern "C" size_t wt_bin_workspace_bytes(const wt_desc *desc) {
-    if (check_geom(desc) != WT_OK) return 0;
+extern "C" size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n) {
+    if (check_geom(desc) != WT_OK || n < 0) return 0;
     const int64_t nt = tiles_of(desc);
-    return ws_counts(nt) + (size_t)nt * 8;
+    return ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)) + (size_t)n * 32;
 }
 
 extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
                             float *alpha_out, float *r_out, float *g_out, float *b_out,
-                            int64_t *tile_offsets_out, void *workspace, wt_stream stream) {
+                            int64_t *tile_offsets_out, void *workspace, size_t workspace_bytes,
+                            wt_stream stream) {
     wt_status st = check_geom(desc);
     if (st != WT_OK) return st;
     if (!in || in->n < 0 || !tile_offsets_out || !workspace) return WT_ERR_ARG;
     if (!aligned_to(workspace, 256) || !aligned_to(tile_offsets_out, 8)) return WT_ERR_ARG;
+    if (workspace_bytes < wt_bin_workspace_bytes(desc, in->n)) return WT_ERR_ARG;
     const bool rgb = in->r != nullptr;
     if (rgb != (in->g != nullptr) || rgb != (in->b != nullptr)) return WT_ERR_ARG;
     if (in->n > 0) {
@@ -229,18 +260,25 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
     if (!err) return WT_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t nt = tiles_of(desc);
-    unsigned *counts = static_cast<unsigned *>(workspace);
-    unsigned long long *cursor =
-        reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + ws_counts(nt));
+    char *ws = static_cast<char *>(workspace);
+    unsigned *counts = reinterpret_cast<unsigned *>(ws);
+    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + ws_counts(nt));
+    uint4 *stage = reinterpret_cast<uint4 *>(ws + ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)));
     const BinGeom g = bin_geom(desc);
     if (cudaMemsetAsync(counts, 0, (size_t)nt * 4, s) != cudaSuccess) return WT_ERR_CUDA;
     if (in->n > 0) k_bin_count<<<grid_for(in->n), 256, 0, s>>>(g, in->n, in->pixel, counts, err);
     k_bin_scan<<<1, 1024, 0, s>>>(counts, nt, tile_offsets_out, cursor);
     if (in->n > 0) {
-        BinArrays a{in->pixel, in->z, in->alpha, in->r, in->g, in->b,
-                    pixel_out, z_out, alpha_out, r_out, g_out, b_out};
-        if (!rgb) a.r = a.g = a.b = nullptr;
-        k_bin_scatter<<<grid_for(in->n), 256, 0, s>>>(g, in->n, a, cursor);
+        const BinIn a{in->pixel, in->z, in->alpha, in->r, in->g, in->b};
+        const BinOut o{pixel_out, z_out, alpha_out, r_out, g_out, b_out};
+        const int grid = grid_for(in->n);
+        if (rgb) {
+            k_bin_scatter<true><<<grid, 256, 0, s>>>(g, in->n, a, stage, cursor);
+            k_bin_unpack<true><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
+        } else {
+            k_bin_scatter<false><<<grid, 256, 0, s>>>(g, in->n, a, stage, cursor);
+            k_bin_unpack<false><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
+        }
     }
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }

@@ -183,9 +183,11 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
 }
 
 // DEF: compiled for the default flags (p.flags == kDefaultFlags), so the
-// per-fragment reconstruction carries no flag tests.
-template <int J, typename CT, bool DEF>
-__global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_fused(Params p) {
+// per-fragment reconstruction carries no flag tests.  MB: blocks per SM the
+// registers are budgeted for; at J = 5 a tile of at most 192 pixels leaves
+// room for four blocks' shared memory, so that launch caps registers at 64.
+template <int J, typename CT, bool DEF, int MB>
+__global__ void __launch_bounds__(kThreads, MB) k_fused(Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     fused_tile<J, CT, DEF>(p, blockIdx.x, smem);
 }
@@ -523,18 +525,26 @@ cudaError_t launch_resolve_t(const Params &p, int ntiles, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int J, typename CT, bool DEF> cudaError_t launch_fused_k(const Params &p, int ntiles, cudaStream_t s) {
+template <int J, typename CT, bool DEF, int MB>
+cudaError_t launch_fused_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::fused(npx);
     cudaError_t e =
-        cudaFuncSetAttribute(k_fused<J, CT, DEF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaFuncSetAttribute(k_fused<J, CT, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_fused<J, CT, DEF><<<ntiles, kThreads, bytes, s>>>(p);
+    k_fused<J, CT, DEF, MB><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
 }
+// Tiles of at most this many pixels fit four fused blocks per SM at J = 5.
+constexpr int kFourBlockTilePx = 192;
 template <int J, typename CT> cudaError_t launch_fused_t(const Params &p, int ntiles, cudaStream_t s) {
-    return p.flags == kDefaultFlags ? launch_fused_k<J, CT, true>(p, ntiles, s)
-                                    : launch_fused_k<J, CT, false>(p, ntiles, s);
+    const bool def = p.flags == kDefaultFlags;
+    if constexpr (MinBlocks<J>::value < 4) {
+        if (p.g.tile_w * p.g.tile_h <= kFourBlockTilePx)
+            return def ? launch_fused_k<J, CT, true, 4>(p, ntiles, s) : launch_fused_k<J, CT, false, 4>(p, ntiles, s);
+    }
+    return def ? launch_fused_k<J, CT, true, MinBlocks<J>::value>(p, ntiles, s)
+               : launch_fused_k<J, CT, false, MinBlocks<J>::value>(p, ntiles, s);
 }
 
 template <int J, typename CT>
