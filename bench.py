@@ -475,9 +475,14 @@ def run_backward(wt, args):
             "backward_GBps_of_fragment_io": round(n * 40 / (bwd_ms / 1e3) / 1e9, 1)}
 
 
-def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all):
+def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all, nchunks=8):
     """Same metric through the C ABI with the fragment stream copied from
-    pinned host memory and the composite copied back, every step."""
+    pinned host memory and the composite copied back, every step.  The frame
+    goes up in `nchunks` ranges of whole tile rows: chunk c's arrays are copied
+    on an upload stream while wt_build_resolve_tiles works on chunk c-1, and
+    each chunk's rows of the composite go back on a download stream as soon as
+    they are done.  The host link's own rate (the same bytes copied with
+    nothing else running) is reported beside it."""
     dev = out.device
     P = fr.P
     host = {k: getattr(fr, k).cpu().pin_memory() for k in ("pixel", "z", "alpha", "r", "g", "b",
@@ -488,16 +493,44 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all):
     dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
     frags_e2e = wt.make_frags(dev_bufs["pixel"], dev_bufs["z"], dev_bufs["alpha"],
                               dev_bufs["tile_offsets"], dev_bufs["r"], dev_bufs["g"], dev_bufs["b"])
+    off = host["tile_offsets"].numpy()
+    ntx = -(-fr.width // fr.tile_w)
+    nty = -(-fr.height // fr.tile_h)
+    rows = np.linspace(0, nty, min(nchunks, nty) + 1).round().astype(np.int64)
+    chunks = []
+    for r0, r1 in zip(rows[:-1], rows[1:]):
+        if r1 > r0:
+            t0, t1 = r0 * ntx, r1 * ntx
+            chunks.append((int(t0), int(t1), int(off[t0]), int(off[t1]),
+                           int(r0 * fr.tile_h * fr.width), int(min(r1 * fr.tile_h, fr.height) * fr.width)))
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    arrays = ("pixel", "z", "alpha", "r", "g", "b")
 
     def step_e2e():
-        for k, v in host.items():
-            dev_bufs[k].copy_(v, non_blocking=True)
-        wt.wt_build_resolve(desc, frags_e2e, out, coeff, None, bg=fr.bg, stream=stream)
-        out_host.copy_(out, non_blocking=True)
+        up.wait_stream(stream)  # the previous step's kernels are done with the buffers
+        with torch.cuda.stream(up):
+            dev_bufs["tile_offsets"].copy_(host["tile_offsets"], non_blocking=True)
+        for (t0, t1, f0, f1, p0, p1) in chunks:
+            with torch.cuda.stream(up):
+                for k in arrays:
+                    dev_bufs[k][f0:f1].copy_(host[k][f0:f1], non_blocking=True)
+            stream.wait_stream(up)
+            wt.wt_build_resolve_tiles(desc, frags_e2e, t0, t1 - t0, out, coeff, stream=stream)
+            down.wait_stream(stream)
+            with torch.cuda.stream(down):
+                out_host[p0:p1].copy_(out[p0:p1], non_blocking=True)
+        stream.wait_stream(down)
+
+    def copies_only():
+        with torch.cuda.stream(up):
+            for k in host:
+                dev_bufs[k].copy_(host[k], non_blocking=True)
+        stream.wait_stream(up)
 
     for _ in range(2):
         step_e2e()
     torch.cuda.synchronize()
+    assert wt.wt_get_error(stream) == 0
     Ke = max(3, min(K, 10))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
@@ -507,8 +540,15 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all):
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(a.elapsed_time(b) / Ke, world)
+    a.record(stream)
+    for _ in range(3):
+        copies_only()
+    b.record(stream)
+    torch.cuda.synchronize()
+    link_ms = a.elapsed_time(b) / 3
     return {"value": frags_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "chunks": len(chunks),
+            "h2d_alone_ms": round(link_ms, 3), "h2d_alone_GBps": round(h2d / (link_ms / 1e3) / 1e9, 1)}
 
 
 # ---------------------------------------------------------------- serving

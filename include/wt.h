@@ -187,6 +187,20 @@ wt_status wt_build_resolve(const wt_desc *desc, const wt_frags *frags, void *coe
                            const float *bg_img, const float bg[3], float *out, wt_stream stream);
 
 /*
+ * wt_build_resolve_tiles -- wt_build_resolve for the tiles
+ * [first_tile, first_tile + num_tiles) only (tiles are independent, §2.1: the
+ * method keeps constant state per pixel).  Only those tiles' fragment ranges
+ * are read and only their pixels of coeff, zmin and out are written, so a
+ * caller can stream a frame in pieces, for example overlapping the upload of
+ * the next range of tiles with the work on this one.  frags->tile_offsets
+ * must still cover every tile.  A range outside [0, ntiles] is WT_ERR_ARG;
+ * num_tiles = 0 launches nothing.
+ */
+wt_status wt_build_resolve_tiles(const wt_desc *desc, const wt_frags *frags, int64_t first_tile,
+                                 int64_t num_tiles, void *coeff, float *zmin, const float *bg_img,
+                                 const float bg[3], float *out, wt_stream stream);
+
+/*
  * wt_build_resolve_batch_static -- wt_build_resolve for a batch of frames in
  * one launch, allocating nothing.  The paper has no counterpart: it exists for
  * callers that cannot allocate device memory when they submit work, such as a

@@ -225,22 +225,34 @@ wt_status wt_resolve_composite(const wt_desc *d, const wt_frags *f, const void *
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
-wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin,
-                           const float *bg_img, const float bg[3], float *out, wt_stream stream) {
+wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t first_tile, int64_t num_tiles,
+                                 void *coeff, float *zmin, const float *bg_img, const float bg[3], float *out,
+                                 wt_stream stream) {
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
     if ((st = check_frags(f, true)) != WT_OK) return st;
     if ((coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16) || (zmin && !aligned(zmin, 4)))
         return WT_ERR_ARG;
+    const int64_t nt = ntiles_of(d);
+    if (first_tile < 0 || num_tiles < 0 || first_tile + num_tiles > nt) return WT_ERR_ARG;
+    if (num_tiles == 0) return WT_OK;
     Params p = make_params(d, f);
+    p.tile0 = (int32_t)first_tile;
     p.coeff = coeff;
     p.zmin = zmin;
     p.out = out;
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
     const TileLaunch *t = table(kFused0, kFused1, kFused2, d->coeff_dtype);
-    return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
+    return finish(t[d->J - 1](p, (int)num_tiles, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin,
+                           const float *bg_img, const float bg[3], float *out, wt_stream stream) {
+    wt_status st = check_desc(d);
+    if (st != WT_OK) return st;
+    return wt_build_resolve_tiles(d, f, 0, ntiles_of(d), coeff, zmin, bg_img, bg, out, stream);
 }
 
 wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, const float bg[3],

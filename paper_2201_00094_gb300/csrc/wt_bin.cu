@@ -3,11 +3,12 @@
 // normalisation of depth into them.
 //
 // Binning is a counting sort by tile id (row-major tiles of the descriptor):
-// a histogram pass with global integer atomics, one exclusive scan of the
-// tile counts into tile_offsets, a scatter pass in which every fragment takes
-// the next slot of its tile with a 64-bit atomic and is staged there as one
-// record, and a pass that unpacks the records in order into the output
-// arrays.  Fragments whose pixel id is outside the image are dropped and
+// a histogram pass, one exclusive scan of the tile counts into tile_offsets, a
+// scatter pass in which every fragment takes the next slot of its tile and is
+// staged there as one record, and a pass that unpacks the records in order
+// into the output arrays.  When the tile counters fit in shared memory, each
+// block counts and ranks its own chunk of the stream with shared atomics;
+// otherwise the counts and slots come from global atomics.  Fragments whose pixel id is outside the image are dropped and
 // counted.  The order of the
 // fragments inside a tile is that of the atomics: the build does not depend on
 // it (its sums are integer), the resolve's FP32 sums may differ in the last
@@ -130,6 +131,77 @@ __global__ void __launch_bounds__(256) k_bin_unpack(int64_t n, const int64_t *__
     }
 }
 
+// Binning with per-block shared-memory counters, for descriptors whose tile
+// count fits in shared memory: one block per SM owns a contiguous chunk of the
+// stream.  Pass 1 counts the chunk's fragments per tile with shared atomics
+// and stores the block's counts; a pass over the tiles turns them into each
+// block's starting rank inside every tile (blocks in order) and the tile
+// totals; pass 2 hands out ranks with shared atomics again, so no global
+// atomic is issued per fragment.
+constexpr int kBinThreads = 1024;
+
+__global__ void __launch_bounds__(kBinThreads) k_bin_count_local(BinGeom g, int64_t n, int64_t chunk,
+                                                                 int64_t ntiles, const uint32_t *__restrict__ pixel,
+                                                                 unsigned *__restrict__ H, unsigned long long *err) {
+    extern __shared__ unsigned hist[];
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0u;
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * chunk, e = min(n, s + chunk);
+    unsigned bad = 0;
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+        const int64_t t = tile_index(pixel[i], g);
+        if (t < 0) ++bad;
+        else atomicAdd(&hist[t], 1u);
+    }
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(err, (unsigned long long)bad);
+    __syncthreads();
+    unsigned *row = H + (int64_t)blockIdx.x * ntiles;
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = hist[t];
+}
+
+// Per tile: each block's count becomes the number of the tile's fragments in
+// earlier blocks; the tile's total goes to counts[t].
+__global__ void __launch_bounds__(256) k_bin_block_ranks(int nblocks, int64_t ntiles, unsigned *__restrict__ H,
+                                                         unsigned *__restrict__ counts) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    unsigned run = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        const unsigned h = H[(int64_t)b * ntiles + t];
+        H[(int64_t)b * ntiles + t] = run;
+        run += h;
+    }
+    counts[t] = run;
+}
+
+template <bool RGB>
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter_local(BinGeom g, int64_t n, int64_t chunk,
+                                                                   int64_t ntiles, BinIn a,
+                                                                   const unsigned *__restrict__ H,
+                                                                   const int64_t *__restrict__ offsets,
+                                                                   uint4 *__restrict__ stage) {
+    extern __shared__ unsigned cur[];
+    const unsigned *row = H + (int64_t)blockIdx.x * ntiles;
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) cur[t] = row[t];
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * chunk, e = min(n, s + chunk);
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+        const uint32_t px = a.pixel[i];
+        const int64_t t = tile_index(px, g);
+        if (t < 0) continue;
+        const int64_t slot = offsets[t] + atomicAdd(&cur[t], 1u);
+        const uint4 r0 = make_uint4(px, __float_as_uint(a.z[i]), __float_as_uint(a.alpha[i]),
+                                    RGB ? __float_as_uint(a.r[i]) : 0u);
+        if (RGB) {
+            stage[2 * slot] = r0;
+            stage[2 * slot + 1] = make_uint4(__float_as_uint(a.g[i]), __float_as_uint(a.b[i]), 0u, 0u);
+        } else {
+            stage[slot] = r0;
+        }
+    }
+}
+
 // order-preserving map of float bits to unsigned (and back)
 __device__ __forceinline__ unsigned order_key(float x) {
     const unsigned u = __float_as_uint(x);
@@ -228,6 +300,20 @@ int64_t tiles_of(const wt_desc *d) {
 
 size_t ws_counts(int64_t ntiles) { return ((size_t)ntiles * 4 + 255) & ~size_t(255); }
 
+int num_sms() {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Tile counters that fit one block's shared memory (the per-block path).
+bool local_bins(int64_t ntiles) { return ntiles * 4 <= 200 * 1024; }
+
+// Bytes of the per-block count matrix (one row of ntiles per block).
+size_t ws_blocks(int64_t ntiles) {
+    return local_bins(ntiles) ? (((size_t)num_sms() * ntiles * 4 + 255) & ~size_t(255)) : 0;
+}
+
 }  // namespace
 }  // namespace wt
 
@@ -236,7 +322,7 @@ using namespace wt;
 extern "C" size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n) {
     if (check_geom(desc) != WT_OK || n < 0) return 0;
     const int64_t nt = tiles_of(desc);
-    return ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)) + (size_t)n * 32;
+    return ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)) + ws_blocks(nt) + (size_t)n * 32;
 }
 
 extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
@@ -263,15 +349,40 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
     char *ws = static_cast<char *>(workspace);
     unsigned *counts = reinterpret_cast<unsigned *>(ws);
     unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + ws_counts(nt));
-    uint4 *stage = reinterpret_cast<uint4 *>(ws + ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)));
+    const size_t blocks_bytes = ws_blocks(nt);
+    unsigned *H = reinterpret_cast<unsigned *>(ws + ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)));
+    uint4 *stage = reinterpret_cast<uint4 *>(reinterpret_cast<char *>(H) + blocks_bytes);
     const BinGeom g = bin_geom(desc);
+    const BinIn a{in->pixel, in->z, in->alpha, in->r, in->g, in->b};
+    const BinOut o{pixel_out, z_out, alpha_out, r_out, g_out, b_out};
+    const int grid = grid_for(in->n);
+    if (blocks_bytes && in->n > 0) {
+        // per-block shared-memory counters
+        const int nb = num_sms();
+        const int64_t chunk = (in->n + nb - 1) / nb;
+        const size_t smem = (size_t)nt * 4;
+        cudaError_t e = cudaFuncSetAttribute(k_bin_count_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(rgb ? (const void *)k_bin_scatter_local<true> : (const void *)k_bin_scatter_local<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return WT_ERR_CUDA;
+        k_bin_count_local<<<nb, kBinThreads, smem, s>>>(g, in->n, chunk, nt, in->pixel, H, err);
+        k_bin_block_ranks<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(nb, nt, H, counts);
+        k_bin_scan<<<1, 1024, 0, s>>>(counts, nt, tile_offsets_out, cursor);
+        if (rgb) {
+            k_bin_scatter_local<true><<<nb, kBinThreads, smem, s>>>(g, in->n, chunk, nt, a, H, tile_offsets_out, stage);
+            k_bin_unpack<true><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
+        } else {
+            k_bin_scatter_local<false><<<nb, kBinThreads, smem, s>>>(g, in->n, chunk, nt, a, H, tile_offsets_out, stage);
+            k_bin_unpack<false><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
+        }
+        return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+    }
+    // global atomics (tile counts too large for shared memory, or no fragments)
     if (cudaMemsetAsync(counts, 0, (size_t)nt * 4, s) != cudaSuccess) return WT_ERR_CUDA;
-    if (in->n > 0) k_bin_count<<<grid_for(in->n), 256, 0, s>>>(g, in->n, in->pixel, counts, err);
+    if (in->n > 0) k_bin_count<<<grid, 256, 0, s>>>(g, in->n, in->pixel, counts, err);
     k_bin_scan<<<1, 1024, 0, s>>>(counts, nt, tile_offsets_out, cursor);
     if (in->n > 0) {
-        const BinIn a{in->pixel, in->z, in->alpha, in->r, in->g, in->b};
-        const BinOut o{pixel_out, z_out, alpha_out, r_out, g_out, b_out};
-        const int grid = grid_for(in->n);
         if (rgb) {
             k_bin_scatter<true><<<grid, 256, 0, s>>>(g, in->n, a, stage, cursor);
             k_bin_unpack<true><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);

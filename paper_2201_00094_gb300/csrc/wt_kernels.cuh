@@ -12,8 +12,8 @@ namespace wt {
 template <int J> struct MinBlocks { static constexpr int value = J >= 5 ? 3 : 4; };
 
 // §2.1 step 2: build the tile's coefficients and store them once.
-template <int J, typename CT>
-__global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params p) {
+template <int J, typename CT, int MB = MinBlocks<J>::value>
+__global__ void __launch_bounds__(kThreads, MB) k_build(Params p) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
@@ -63,8 +63,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_build(Params 
 }
 
 // §2.1 step 3 (+ step 4 when COMPOSITE): resolve against stored coefficients.
-template <int J, typename CT, bool COMPOSITE>
-__global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Params p) {
+// DEF and MB as for k_fused: DEF when the reading flags (accumulation aside)
+// are the default, MB the blocks per SM the registers are budgeted for.
+template <int J, typename CT, bool COMPOSITE, bool DEF = false, int MB = MinBlocks<J>::value>
+__global__ void __launch_bounds__(kThreads, MB) k_resolve(Params p) {
     constexpr int C = Shape<J>::C, LDV = Shape<J>::LDV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
@@ -89,13 +91,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value) k_resolve(Param
         if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v);
         else load_row<CT, C>(coeff + gp * C, v);
         coeffs_to_bins<J>(v, kLog2e);
-        put_bins<J>(vals + lp * LDV, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000), p.flags);
+        put_bins<J>(vals + lp * LDV, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000),
+                    DEF ? kDefaultFlags : p.flags);
     }
     if (Staged<CT, C>::ok) __syncthreads();  // staged rows consumed
     fill_zero(accw, (int)(Layout<J>::accw(npx) + Layout<J>::words(npx)));
     __syncthreads();
     unsigned bad = 0;
-    phase_resolve<J, true>(p, T, vals, accw, sS, bad);
+    phase_resolve<J, true, DEF>(p, T, vals, accw, sS, bad);
     flush_bad(bad, p.err);
     __syncthreads();
     if (gp < 0) return;
@@ -189,7 +192,7 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
 template <int J, typename CT, bool DEF, int MB>
 __global__ void __launch_bounds__(kThreads, MB) k_fused(Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    fused_tile<J, CT, DEF>(p, blockIdx.x, smem);
+    fused_tile<J, CT, DEF>(p, p.tile0 + (int)blockIdx.x, smem);
 }
 
 // Serving: one persistent launch works through the tile tasks of several
@@ -505,24 +508,48 @@ __global__ void __launch_bounds__(kThreads)
 
 // ---------------------------------------------------------------- launchers
 
-template <int J, typename CT> cudaError_t launch_build_t(const Params &p, int ntiles, cudaStream_t s) {
+template <int J, typename CT, int MB> cudaError_t launch_build_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::build(npx);
-    cudaError_t e = cudaFuncSetAttribute(k_build<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_build<J, CT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_build<J, CT><<<ntiles, kThreads, bytes, s>>>(p);
+    k_build<J, CT, MB><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
 }
+template <int J, typename CT> cudaError_t launch_build_t(const Params &p, int ntiles, cudaStream_t s) {
+    if constexpr (MinBlocks<J>::value < 4) {
+        if (p.g.tile_w * p.g.tile_h <= 192) return launch_build_k<J, CT, 4>(p, ntiles, s);
+    }
+    return launch_build_k<J, CT, MinBlocks<J>::value>(p, ntiles, s);
+}
 
-template <int J, typename CT, bool COMPOSITE>
-cudaError_t launch_resolve_t(const Params &p, int ntiles, cudaStream_t s) {
+template <int J, typename CT, bool COMPOSITE, bool DEF, int MB>
+cudaError_t launch_resolve_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::resolve(npx);
-    cudaError_t e = cudaFuncSetAttribute(k_resolve<J, CT, COMPOSITE>,
+    cudaError_t e = cudaFuncSetAttribute(k_resolve<J, CT, COMPOSITE, DEF, MB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_resolve<J, CT, COMPOSITE><<<ntiles, kThreads, bytes, s>>>(p);
+    k_resolve<J, CT, COMPOSITE, DEF, MB><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
+}
+// The accumulating resolve keeps one generic build; the compositing resolve
+// (the second pass of the two-pass method) gets the default-flags and
+// four-blocks builds of k_fused.
+template <int J, typename CT, bool COMPOSITE>
+cudaError_t launch_resolve_t(const Params &p, int ntiles, cudaStream_t s) {
+    if constexpr (COMPOSITE) {
+        const bool def = (p.flags & ~kAccumulate) == kDefaultFlags;
+        if constexpr (MinBlocks<J>::value < 4) {
+            if (p.g.tile_w * p.g.tile_h <= 192)
+                return def ? launch_resolve_k<J, CT, true, true, 4>(p, ntiles, s)
+                           : launch_resolve_k<J, CT, true, false, 4>(p, ntiles, s);
+        }
+        return def ? launch_resolve_k<J, CT, true, true, MinBlocks<J>::value>(p, ntiles, s)
+                   : launch_resolve_k<J, CT, true, false, MinBlocks<J>::value>(p, ntiles, s);
+    } else {
+        return launch_resolve_k<J, CT, false, false, MinBlocks<J>::value>(p, ntiles, s);
+    }
 }
 
 template <int J, typename CT, bool DEF, int MB>

@@ -63,6 +63,7 @@ struct Geom {
 // Everything a kernel reads or writes; passed by value.
 struct Params {
     Geom g;
+    int32_t tile0;  // first tile of a fused launch (block b works on tile tile0 + b)
     uint32_t flags;
     uint32_t wmagic32;  // ceil(2^32 / width) when that divides every in-tile offset exactly, else 0
     uint64_t wmagic;    // ceil(2^64 / width) (0 when width == 1)

@@ -49,6 +49,24 @@ def test_bin_groups_an_unordered_stream(tile):
         np.testing.assert_array_equal(_records(got, np.arange(s, e)), _records(h, order[s:e]))
 
 
+def test_bin_with_more_tiles_than_shared_counters():
+    """60,000 one-pixel tiles: too many tile counters for shared memory, so the
+    slots come from global atomics."""
+    fr = synth.uniform_frame(300, 200, 1.5, 8, J=2, seed=77, tile_w=1, tile_h=1)
+    h = _shuffled(fr, 5)
+    d = desc_of(fr)
+    g = _to_dev(h)
+    out = wt.wt_bin(d, g["pixel"], g["z"], g["alpha"], g["r"], g["g"], g["b"])
+    assert wt.wt_get_error() == 0
+    order, off = oracle.bin_by_tile(h["pixel"], fr.width, fr.height, 1, 1)
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    np.testing.assert_array_equal(got["tile_offsets"], off)
+    # one tile per pixel: every kept fragment sits in its own pixel's range
+    t = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    np.testing.assert_array_equal(got["pixel"][: off[-1]], t)
+    np.testing.assert_array_equal(_records(got, np.arange(off[-1])), _records(h, order))
+
+
 def test_binned_stream_composites_like_the_oracle():
     fr = synth.uniform_frame(611, 23, 6.0, 40, J=5, seed=611, tile_w=256, tile_h=1)
     h = _shuffled(fr, 2)

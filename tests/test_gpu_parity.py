@@ -294,3 +294,28 @@ def test_alpha_and_depth_clamps():
     g = gpu_run(fr)
     np.testing.assert_allclose(g["out"], r["out"], atol=1e-4)
     assert (np.abs(g["coeff"] - r["coeff"]) <= coeff_tol(fr) * 4).all()
+
+
+def test_tile_ranges_equal_the_whole_frame():
+    """wt_build_resolve_tiles over consecutive tile ranges writes exactly what
+    one wt_build_resolve call writes (tiles are independent)."""
+    fr = synth.uniform_frame(611, 23, 6.0, 40, J=5, seed=612, tile_w=192, tile_h=1)
+    dev = torch.device("cuda")
+    g = fr.to(dev)
+    d = desc_of(fr)
+    f = frags_of(g)
+    C = 1 << d.J
+    out_a, out_b = torch.empty(fr.P, 4, device=dev), torch.full((fr.P, 4), float("nan"), device=dev)
+    c_a, c_b = torch.empty(fr.P, C, device=dev), torch.full((fr.P, C), float("nan"), device=dev)
+    wt.wt_build_resolve(d, f, out_a, c_a, bg=fr.bg)
+    nt = wt.wt_num_tiles(d)
+    cuts = [0, 5, nt // 2, nt]
+    for t0, t1 in zip(cuts[:-1], cuts[1:]):
+        wt.wt_build_resolve_tiles(d, f, t0, t1 - t0, out_b, c_b, bg=fr.bg)
+    wt.wt_build_resolve_tiles(d, f, nt, 0, out_b, c_b, bg=fr.bg)  # empty range: nothing
+    assert wt.wt_get_error() == 0
+    assert torch.equal(out_a, out_b) and torch.equal(c_a, c_b)
+    with pytest.raises(wt.WtError):
+        wt.wt_build_resolve_tiles(d, f, nt - 1, 2, out_b, c_b, bg=fr.bg)
+    with pytest.raises(wt.WtError):
+        wt.wt_build_resolve_tiles(d, f, -1, 1, out_b, c_b, bg=fr.bg)
