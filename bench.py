@@ -289,9 +289,17 @@ def run_wt(args):
             def fused(dsc=dsc, c2=c2, o2=o2):
                 wt.wt_build_resolve(dsc, frags, o2, c2, None, bg=fr.bg, stream=stream)
 
+            # the single pass of §4 on an unchanged scene: frame t-1's
+            # coefficients are this frame's (from the fused call above)
+            c3 = torch.empty_like(c2)
+
+            def single_pass(dsc=dsc, c2=c2, c3=c3, o2=o2):
+                wt.wt_build_resolve_single_pass(dsc, frags, c2, o2, c3, bg=fr.bg, stream=stream)
+
             res = {}
             for label, fn, byts in (("fused", fused, n * 24 + P * C * DTYPE_BYTES[d2] + 16 * P),
-                                    ("two_pass", two_pass, accum_bytes)):
+                                    ("two_pass", two_pass, accum_bytes),
+                                    ("single_pass", single_pass, n * 24 + 2 * P * C * DTYPE_BYTES[d2] + 16 * P)):
                 for _ in range(3):
                     fn()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -305,7 +313,7 @@ def run_wt(args):
                 res[label] = {"ms": round(ms, 4), "fragments_per_s": n / (ms / 1e3),
                               "alg_bytes": byts, "alg_GBps": round(byts / (ms / 1e3) / 1e9, 1)}
             variants[name] = res
-            del c2, o2
+            del c2, c3, o2
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None

@@ -201,6 +201,32 @@ wt_status wt_build_resolve_tiles(const wt_desc *desc, const wt_frags *frags, int
                                  const float bg[3], float *out, wt_stream stream);
 
 /*
+ * wt_build_resolve_single_pass -- the single-pass variant the paper proposes
+ * as future work (§4): frame t's fragments are resolved against frame t-1's
+ * coefficients, which are complete before the pass starts, while the same
+ * pass builds frame t's coefficients for the next frame -- one pass over the
+ * fragments instead of two.  With an unchanged scene the composite equals
+ * wt_build_resolve's; under motion the visibility is the previous frame's
+ * (the paper's approximation; nothing is reprojected).
+ *   coeff_prev [P * C] frame t-1's coefficients in coeff_dtype (the coeff
+ *              output of the previous call, of wt_build or wt_build_resolve).
+ *   zmin_prev  [P] nullable: frame t-1's near bound (the weight offset of
+ *              the resolve comes from it; NULL = no offset).
+ *   coeff      [P * C] nullable, written: frame t's coefficients; must not
+ *              overlap coeff_prev (WT_ERR_ARG).
+ *   zmin       [P] nullable, written: frame t's near bound.
+ *   out        [P * 4] frame t's composite.
+ * Weight exponents are clamped to [0, 120] (log2 units), so a fragment
+ * nearer than anything in frame t-1, or hidden behind more than 120 log2
+ * units of frame t-1's absorbance, keeps a finite, non-zero weight.
+ * WT_ACCUMULATE is not supported here (WT_ERR_UNSUPPORTED).
+ */
+wt_status wt_build_resolve_single_pass(const wt_desc *desc, const wt_frags *frags, const void *coeff_prev,
+                                       const float *zmin_prev, void *coeff, float *zmin,
+                                       const float *bg_img, const float bg[3], float *out,
+                                       wt_stream stream);
+
+/*
  * wt_build_resolve_batch_static -- wt_build_resolve for a batch of frames in
  * one launch, allocating nothing.  The paper has no counterpart: it exists for
  * callers that cannot allocate device memory when they submit work, such as a

@@ -25,7 +25,7 @@ __all__ = [
     "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
     "WtServeInfo", "wt_build_resolve_batch_static", "wt_bin_workspace_bytes", "wt_bin",
-    "wt_depth_bounds", "wt_normalize_depth", "wt_build_resolve_tiles",
+    "wt_depth_bounds", "wt_normalize_depth", "wt_build_resolve_tiles", "wt_build_resolve_single_pass",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_tiles": ([D, Fr, i64, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build_resolve_single_pass": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
@@ -257,6 +258,20 @@ def wt_build_resolve_tiles(desc: WtDesc, frags: WtFrags, first_tile: int, num_ti
                            bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
     _call("wt_build_resolve_tiles", ctypes.byref(desc), ctypes.byref(frags), int(first_tile),
           int(num_tiles), _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
+          _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
+          _stream(stream))
+
+
+def wt_build_resolve_single_pass(desc: WtDesc, frags: WtFrags, coeff_prev: torch.Tensor,
+                                 out: torch.Tensor, coeff: Optional[torch.Tensor] = None,
+                                 zmin_prev: Optional[torch.Tensor] = None,
+                                 zmin: Optional[torch.Tensor] = None, bg: Sequence[float] = (0.5, 0.5, 0.5),
+                                 bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Resolves this frame against the previous frame's coefficients and
+    builds this frame's coefficients in one pass (wt_build_resolve_single_pass)."""
+    _call("wt_build_resolve_single_pass", ctypes.byref(desc), ctypes.byref(frags),
+          _dev(coeff_prev, "coeff_prev", _COEFF_DT), _dev(zmin_prev, "zmin_prev", (torch.float32,)),
+          _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
           _stream(stream))
 

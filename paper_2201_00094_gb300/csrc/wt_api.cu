@@ -248,6 +248,31 @@ wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t fi
     return finish(t[d->J - 1](p, (int)num_tiles, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+wt_status wt_build_resolve_single_pass(const wt_desc *d, const wt_frags *f, const void *coeff_prev,
+                                       const float *zmin_prev, void *coeff, float *zmin, const float *bg_img,
+                                       const float bg[3], float *out, wt_stream stream) {
+    wt_status st = check_desc(d);
+    if (st != WT_OK) return st;
+    if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
+    if ((st = check_frags(f, true)) != WT_OK) return st;
+    if (!coeff_prev || !aligned(coeff_prev, 16) || (coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16) ||
+        (zmin && !aligned(zmin, 4)) || (zmin_prev && !aligned(zmin_prev, 4)))
+        return WT_ERR_ARG;
+    // frame t's outputs must not overlap frame t-1's inputs
+    const size_t cb = (size_t)d->width * d->height * ((size_t)1 << d->J) * dtype_size(d->coeff_dtype);
+    const char *cp = static_cast<const char *>(coeff_prev), *cn = static_cast<const char *>(coeff);
+    if (coeff && cn < cp + cb && cp < cn + cb) return WT_ERR_ARG;
+    if (zmin && zmin_prev && zmin == zmin_prev) return WT_ERR_ARG;
+    Params p = make_params(d, f);
+    p.coeff = coeff;
+    p.zmin = zmin;
+    p.out = out;
+    if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
+    if (!(p.err = err_word())) return WT_ERR_CUDA;
+    const TemporalLaunch *t = d->coeff_dtype == WT_F32 ? kTemporal0 : (d->coeff_dtype == WT_BF16 ? kTemporal1 : kTemporal2);
+    return finish(t[d->J - 1](p, (int)ntiles_of(d), coeff_prev, zmin_prev, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin,
                            const float *bg_img, const float bg[3], float *out, wt_stream stream) {
     wt_status st = check_desc(d);

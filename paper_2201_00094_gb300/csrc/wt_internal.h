@@ -22,6 +22,8 @@ typedef cudaError_t (*ServeLaunch)(const Params *slots, const ServeTask *tasks, 
                                    int64_t total, unsigned long long *counter, int npx, int grid,
                                    cudaStream_t);
 typedef int (*ServeOccupancy)(int npx);
+typedef cudaError_t (*TemporalLaunch)(const Params &, int ntiles, const void *coeff_prev, const float *zmin_prev,
+                                      cudaStream_t);
 typedef cudaError_t (*QueryLaunch)(const Params &, int64_t q, const uint32_t *qpx, const float *qz,
                                    const float *qal, float *outA, cudaStream_t);
 
@@ -34,5 +36,6 @@ extern const TileLaunch kBackward0[5], kBackward1[5], kBackward2[5];
 extern const ServeLaunch kServe0[5], kServe1[5], kServe2[5];
 extern const ServeOccupancy kServeOcc0[5], kServeOcc1[5], kServeOcc2[5];
 extern const QueryLaunch kAbsorbance0[5], kAbsorbance1[5], kAbsorbance2[5];
+extern const TemporalLaunch kTemporal0[5], kTemporal1[5], kTemporal2[5];
 
 }  // namespace wt

@@ -195,6 +195,147 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused(Params p) {
     fused_tile<J, CT, DEF>(p, p.tile0 + (int)blockIdx.x, smem);
 }
 
+// Single pass over a frame's fragments with the previous frame's
+// coefficients (the paper's proposed variant, §4): every fragment of frame t
+// is resolved against frame t-1's coefficients -- already complete, so the
+// resolve needs no second pass -- while the same pass builds frame t's
+// coefficients for the next frame.  With a static scene the result equals the
+// two-pass method's; with motion it is the paper's approximation (visibility
+// from the previous frame).  The weight offset comes from frame t-1's near
+// bound; exponents are clamped to [0, 120] so that fragments nearer or much
+// farther than anything in frame t-1 keep finite, non-zero weights.
+template <int J> struct TemporalLayout {
+    static constexpr size_t vals(int npx) { return 0; }
+    static constexpr size_t F(int npx) { return Layout<J>::vplane(npx); }
+    static constexpr size_t G(int npx) { return F(npx) + Layout<J>::plane(npx); }
+    static constexpr size_t accw(int npx) { return G(npx) + Layout<J>::plane(npx); }
+    static constexpr size_t zw(int npx) { return accw(npx) + Layout<J>::accw(npx); }
+    static constexpr size_t total(int npx) { return zw(npx) + Layout<J>::words(npx); }
+};
+
+template <int J, typename CT, bool DEF, int MB>
+__global__ void __launch_bounds__(kThreads, MB) k_temporal(Params p, const void *coeff_prev, const float *zmin_prev) {
+    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
+    constexpr float kFineStep = 1048576.f;  // 2^20: a step of 2^-7 under the fixed scale
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int npx = p.g.tile_w * p.g.tile_h;
+    float *vals = reinterpret_cast<float *>(smem + TemporalLayout<J>::vals(npx));
+    unsigned *sF = reinterpret_cast<unsigned *>(smem + TemporalLayout<J>::F(npx));
+    unsigned *sG = reinterpret_cast<unsigned *>(smem + TemporalLayout<J>::G(npx));
+    float4 *accw = reinterpret_cast<float4 *>(smem + TemporalLayout<J>::accw(npx));
+    unsigned *sZ = reinterpret_cast<unsigned *>(smem + TemporalLayout<J>::zw(npx));
+    uint4 *st = reinterpret_cast<uint4 *>(accw);  // staging of coefficient rows
+    const uint32_t flags = DEF ? kDefaultFlags : p.flags;
+    const Tile T = tile_of(p, p.tile0 + (int)blockIdx.x, true);
+    prefetch_tile<kWithZ | kWithRGB>(p, T);
+    const int lp = threadIdx.x;
+    int64_t gp = -1;
+    if (lp < npx) gp = global_pixel(p, T, lp);
+    // frame t-1's coefficients -> bin values (log2 units, weight offset folded in)
+    const CT *prev = static_cast<const CT *>(coeff_prev);
+    if (Staged<CT, C>::ok) load_staged<CT, C>(p, T, st, prev);
+    fill_zero(sF, (int)(2 * Layout<J>::plane(npx)));
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
+    __syncthreads();
+    if (gp >= 0) {
+        float v[C];
+        if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v);
+        else load_row<CT, C>(prev + gp * C, v);
+        coeffs_to_bins<J>(v, kLog2e);
+        put_bins<J>(vals + lp * LDV, v, zmin_prev ? zmin_prev[gp] : __int_as_float(0x7f800000), flags);
+    }
+    __syncthreads();  // staged rows consumed
+    fill_zero(accw, (int)Layout<J>::accw(npx));
+    __syncthreads();
+    // the single pass: build frame t's bins and resolve against frame t-1
+    float4 *mine = accw + (threadIdx.x >> 5) * npx;
+    unsigned bad = 0;
+    bool retry = false;
+    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            int lpk = -1;
+            if (G.v) {
+                if (G.z[k] == G.z[k] && G.al[k] == G.al[k]) lpk = local_pixel(G.px[k], p, T);
+                if (lpk < 0) ++bad;
+            }
+            const int l = lpk >= 0 ? lpk : 0;
+            const float ac = clamp_alpha(G.al[k]);
+            const float a = step_of(ac);
+            const float zc = clamp_depth(G.z[k]);
+            if (lpk >= 0) {
+                const float s = zc * (float)C;
+                const Floor m = floor_small(s);
+                const float f = s - m.f;
+                const float as = a * kBinScale;
+                const unsigned vF = __float2uint_rn(as * f), vG = __float2uint_rn(as * (1.f - f));
+                const unsigned oF = atomicAdd(&sF[lpk * LD + m.i], vF);
+                const unsigned oG = atomicAdd(&sG[lpk * LD + m.i], vG);
+                retry |= (oF + vF < oF) | (oG + vG < oG) | (as < kFineStep && a > 0.f);
+                if (a > 0.f) atomicMin(&sZ[lpk], __float_as_uint(zc));
+            }
+            const float Ah = fminf(absorbance_at<J>(vals + l * LDV, zc, a * kLog2e, flags), 120.f);
+            const float w = ac * ex2(-Ah);
+            warp_accumulate(mine, lpk, make_float4(G.r[k] * w, G.g[k] * w, G.b[k] * w, w));
+        }
+    });
+    flush_bad(bad, p.err);
+    const bool scaled = __syncthreads_or(retry);
+    if (scaled) {  // rebuild frame t's bins with per-pixel scales
+        fill_zero(sF, (int)(2 * Layout<J>::plane(npx)));
+        __syncthreads();
+        count_pass<J>(p, T, sF);
+        bins_pass<J, true, false>(p, T, sF, sG, sZ, bad);
+        __syncthreads();
+    }
+    // per pixel: frame t's coefficients and total absorbance, the composite
+    float c[C], S = 0.f;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gp >= 0) {
+        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
+        acc = sum_warps(accw, npx, lp);
+    }
+    __syncthreads();  // accumulators read: their space stages the new coefficients
+    CT *next = static_cast<CT *>(p.coeff);
+    const bool stage = Staged<CT, C>::ok && next != nullptr;
+    if (gp >= 0) {
+        composite_pixel(p, gp, acc.x, acc.y, acc.z, acc.w, S);
+        if (p.zmin) p.zmin[gp] = __uint_as_float(sZ[lp]);
+        if (next) {
+            if (stage) stage_row<CT, C>(st, lp, c);
+            else store_row<CT, C>(next + gp * C, c);
+        }
+    }
+    if (stage) {
+        __syncthreads();
+        copy_staged<CT, C>(p, T, st, npx * Staged<CT, C>::K * 16, next);
+    }
+}
+
+template <int J, typename CT, bool DEF, int MB>
+cudaError_t launch_temporal_k(const Params &p, int ntiles, const void *coeff_prev, const float *zmin_prev,
+                              cudaStream_t s) {
+    const int npx = p.g.tile_w * p.g.tile_h;
+    const size_t bytes = TemporalLayout<J>::total(npx);
+    cudaError_t e = cudaFuncSetAttribute(k_temporal<J, CT, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_temporal<J, CT, DEF, MB><<<ntiles, kThreads, bytes, s>>>(p, coeff_prev, zmin_prev);
+    return cudaGetLastError();
+}
+template <int J, typename CT>
+cudaError_t launch_temporal_t(const Params &p, int ntiles, const void *coeff_prev, const float *zmin_prev,
+                              cudaStream_t s) {
+    // registers budgeted for the blocks per SM that the shared memory allows
+    // (228 KB per SM, 1 KB of it reserved per block)
+    const int npx = p.g.tile_w * p.g.tile_h;
+    const bool three = 3 * (TemporalLayout<J>::total(npx) + 1024) <= 233472;
+    if (p.flags != kDefaultFlags) return launch_temporal_k<J, CT, false, 2>(p, ntiles, coeff_prev, zmin_prev, s);
+    return three ? launch_temporal_k<J, CT, true, 3>(p, ntiles, coeff_prev, zmin_prev, s)
+                 : launch_temporal_k<J, CT, true, 2>(p, ntiles, coeff_prev, zmin_prev, s);
+}
+
 // Serving: one persistent launch works through the tile tasks of several
 // frames (continuous batching).  The step's task table lists, per admitted
 // frame, a slot and a range of its tiles; tasks are numbered by the running
@@ -609,6 +750,9 @@ cudaError_t launch_absorbance_t(const Params &p, int64_t q, const uint32_t *qpx,
     const ServeOccupancy kServeOcc##IDX[5] = {serve_blocks_per_sm<1, CT>, serve_blocks_per_sm<2, CT>, \
                                               serve_blocks_per_sm<3, CT>, serve_blocks_per_sm<4, CT>, \
                                               serve_blocks_per_sm<5, CT>};                        \
+    const TemporalLaunch kTemporal##IDX[5] = {launch_temporal_t<1, CT>, launch_temporal_t<2, CT>,   \
+                                              launch_temporal_t<3, CT>, launch_temporal_t<4, CT>,   \
+                                              launch_temporal_t<5, CT>};                            \
     const QueryLaunch kAbsorbance##IDX[5] = {                                                      \
         launch_absorbance_t<1, CT>, launch_absorbance_t<2, CT>, launch_absorbance_t<3, CT>,       \
         launch_absorbance_t<4, CT>, launch_absorbance_t<5, CT>};                                   \

@@ -1,0 +1,92 @@
+"""The single-pass variant of §4: frame t resolved against frame t-1's
+coefficients while frame t's are built in the same pass, through the C ABI,
+against the oracle's resolve with the previous frame's FP64 coefficients."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2201_00094_gb300 as wt
+import synth
+from wtcheck import coeff_tol, desc_of, frags_of
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda")
+
+
+def _frame(seed, J, tile, lam=8.0):
+    return synth.uniform_frame(96, 40, lam, 40, J=J, seed=seed, tile_w=tile[0], tile_h=tile[1])
+
+
+@pytest.mark.parametrize("J,tile", [(5, (192, 1)), (4, (16, 16)), (3, (7, 3))])
+def test_static_scene_equals_the_two_pass_method(J, tile):
+    """With frame t-1 = frame t the single pass reproduces the fused call, and
+    the coefficients it builds are the build's, bit for bit."""
+    fr = _frame(31 + J, J, tile)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    f = frags_of(g)
+    C = 1 << J
+    prev = torch.empty(fr.P, C, device=DEV)
+    zprev = torch.empty(fr.P, device=DEV)
+    wt.wt_build(d, f, prev, zprev)
+    ref = torch.empty(fr.P, 4, device=DEV)
+    wt.wt_build_resolve(d, f, ref, bg=fr.bg)
+    out = torch.empty(fr.P, 4, device=DEV)
+    nxt = torch.full((fr.P, C), float("nan"), device=DEV)
+    znext = torch.full((fr.P,), float("nan"), device=DEV)
+    wt.wt_build_resolve_single_pass(d, f, prev, out, nxt, zprev, znext, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    torch.testing.assert_close(out, ref, atol=2e-6, rtol=0)
+    assert torch.equal(nxt, prev) and torch.equal(znext, zprev)
+
+
+@pytest.mark.parametrize("dtype", [wt.F32, wt.BF16])
+def test_moving_scene_matches_the_oracle(dtype):
+    """Two different frames: the composite of frame t uses frame t-1's
+    visibility exactly as the oracle's resolve with frame t-1's coefficients;
+    frame t's coefficients match the oracle's build of frame t."""
+    a, b = _frame(41, 4, (192, 1)), _frame(42, 4, (192, 1))
+    d = desc_of(b, dtype=dtype)
+    ga, gb = a.to(DEV), b.to(DEV)
+    C = 16
+    prev = torch.empty(a.P, C, device=DEV, dtype=wt.coeff_torch_dtype(dtype))
+    zprev = torch.empty(a.P, device=DEV)
+    wt.wt_build(d, frags_of(ga), prev, zprev)
+    out = torch.empty(b.P, 4, device=DEV)
+    nxt = torch.empty(b.P, C, device=DEV, dtype=wt.coeff_torch_dtype(dtype))
+    wt.wt_build_resolve_single_pass(d, frags_of(gb), prev, out, nxt, zprev, bg=b.bg)
+    assert wt.wt_get_error() == 0
+    ha, hb = a.numpy(), b.numpy()
+    ca = oracle.build_coeffs(ha["pixel"], ha["z"], ha["alpha"], a.P, 4)
+    if dtype == wt.F32:
+        ref = oracle.resolve(hb["pixel"], hb["z"], hb["alpha"], (hb["r"], hb["g"], hb["b"]), b.P, 4, ca,
+                             bg=b.bg)[0]
+        np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+        cb = oracle.build_coeffs(hb["pixel"], hb["z"], hb["alpha"], b.P, 4)
+        assert (np.abs(nxt.cpu().numpy().astype(np.float64) - cb) <= coeff_tol(b)).all()
+    else:
+        # the oracle resolves against the stored 16-bit coefficients themselves
+        ref = oracle.resolve(hb["pixel"], hb["z"], hb["alpha"], (hb["r"], hb["g"], hb["b"]), b.P, 4,
+                             prev.float().cpu().numpy().astype(np.float64), bg=b.bg)[0]
+        np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+
+
+def test_single_pass_arguments():
+    fr = _frame(50, 4, (192, 1))
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    f = frags_of(g)
+    buf = torch.zeros(fr.P, 16, device=DEV)
+    out = torch.empty(fr.P, 4, device=DEV)
+    with pytest.raises(wt.WtError):  # frame t's coefficients over frame t-1's
+        wt.wt_build_resolve_single_pass(d, f, buf, out, buf, bg=fr.bg)
+    with pytest.raises(wt.WtError):
+        wt.wt_build_resolve_single_pass(d, f, buf, out, buf[1:], bg=fr.bg)
+    # previous coefficients of an empty scene: every fragment fully visible
+    wt.wt_build_resolve_single_pass(d, f, buf, out, None, bg=fr.bg)
+    h = fr.numpy()
+    ref = oracle.resolve(h["pixel"], h["z"], h["alpha"], (h["r"], h["g"], h["b"]), fr.P, 4,
+                         np.zeros((fr.P, 16)), flags=wt.INTERP_LINEAR | wt.RESOLVE_NORMALIZED, bg=fr.bg)[0]
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
