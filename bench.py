@@ -52,10 +52,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# the sources the fused kernel is compiled from (its FP32 instantiation)
+FUSED_SOURCES = ("wt_internal.h", "wt_tile.cuh", "wt_kernels.cuh", "wt_kernels_f32.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2201_00094_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in FUSED_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -332,6 +336,9 @@ def run_wt(args):
     preprocess = None
     if rank == 0 and world == 1 and not args.no_preprocess:
         preprocess = run_preprocess(wt, fr, desc, stream)
+    particles = None
+    if rank == 0 and world == 1 and not args.no_particles:
+        particles = run_particles(wt, args, stream)
     backward = None
     if rank == 0 and world == 1 and not args.no_backward:
         del coeff, out
@@ -380,6 +387,7 @@ def run_wt(args):
             "clocks": clk.summary(),
             "variants": variants,
             "preprocess": preprocess,
+            "particles": particles,
             "backward": backward,
             "serving": serving,
         }
@@ -440,6 +448,52 @@ def run_preprocess(wt, fr, desc, stream):
     return res
 
 
+def run_particles(wt, args, stream):
+    """The whole device chain from particles to the composite on a 4K frame:
+    1.1M smoke particles (centres uniform over the screen, radius U[2,12]
+    pixels, depth from five Gaussian slabs, alpha U[.01,.4], colour U[0,1],
+    seeded) rasterised into an unordered stream (wt_raster_count/_emit,
+    ~200M fragments), grouped by tile (wt_bin) and built + resolved
+    (wt_build_resolve), each step timed on its own."""
+    dev = torch.device("cuda")
+    W, H, N = 3840, 2160, 1_100_000
+    tw, th = tile_of(args)
+    g = torch.Generator(device=dev)
+    g.manual_seed(args.seed + 99)
+    u = lambda lo, hi: lo + (hi - lo) * torch.rand(N, generator=g, device=dev)
+    slab = torch.randint(0, 5, (N,), generator=g, device=dev).float()
+    pt = {"cx": u(0, W), "cy": u(0, H), "radius": u(2, 12),
+          "z": (0.1 + 0.2 * slab + 0.03 * torch.randn(N, generator=g, device=dev)).clamp(0, 1),
+          "alpha": u(0.01, 0.4), "r": u(0, 1), "g": u(0, 1), "b": u(0, 1)}
+    desc = wt.make_desc(W, H, 5, wt.F32, tile_w=tw, tile_h=th)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    times = {"raster": [], "bin": [], "build_resolve": []}
+    out = torch.empty(W * H, 4, device=dev)
+    for rep in range(3):
+        ev[0].record(stream)
+        fr = wt.wt_raster(desc, **pt, stream=stream)
+        ev[1].record(stream)
+        b = wt.wt_bin(desc, fr["pixel"], fr["z"], fr["alpha"], fr["r"], fr["g"], fr["b"], stream=stream)
+        ev[2].record(stream)
+        frags = wt.make_frags(b["pixel"], b["z"], b["alpha"], b["tile_offsets"], b["r"], b["g"], b["b"])
+        wt.wt_build_resolve(desc, frags, out, bg=(0.5, 0.5, 0.5), stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if rep:  # the first repetition warms up
+            times["raster"].append(ev[0].elapsed_time(ev[1]))
+            times["bin"].append(ev[1].elapsed_time(ev[2]))
+            times["build_resolve"].append(ev[2].elapsed_time(ev[3]))
+        n = int(fr["total"])
+        del fr, b, frags
+    assert wt.wt_get_error(stream) == 0
+    res = {k: round(float(np.mean(v)), 4) for k, v in times.items()}
+    tot = sum(res.values())
+    return {"workload": "3840x2160, 1.1M particles, radius U[2,12] px, 5 depth slabs, alpha U[.01,.4], J=5",
+            "fragments": n, "ms": res, "total_ms": round(tot, 4),
+            "fragments_per_s_whole_chain": n / (tot / 1e3),
+            "note": "raster includes one read-back of the fragment total to size the arrays"}
+
+
 def run_backward(wt, args):
     """Adjoint of build + resolve + composite (wt_backward) on the
     differentiation workload: 16 frames of 512x512 stacked as 512x8192 (pixels
@@ -487,9 +541,9 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all, nchunks=8
     """Same metric through the C ABI with the fragment stream copied from
     pinned host memory and the composite copied back, every step.  The frame
     goes up in `nchunks` ranges of whole tile rows: chunk c's arrays are copied
-    on an upload stream while wt_build_resolve_tiles works on chunk c-1, and
-    each chunk's rows of the composite go back on a download stream as soon as
-    they are done.  The host link's own rate (the same bytes copied with
+    on an upload stream while wt_build_resolve_tiles works on chunk c-1; the
+    composite comes back in one copy at the end (concurrent downloads slowed
+    the uploads).  The host link's own rate (the same bytes copied with
     nothing else running) is reported beside it."""
     dev = out.device
     P = fr.P
@@ -509,25 +563,21 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all, nchunks=8
     for r0, r1 in zip(rows[:-1], rows[1:]):
         if r1 > r0:
             t0, t1 = r0 * ntx, r1 * ntx
-            chunks.append((int(t0), int(t1), int(off[t0]), int(off[t1]),
-                           int(r0 * fr.tile_h * fr.width), int(min(r1 * fr.tile_h, fr.height) * fr.width)))
-    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+            chunks.append((int(t0), int(t1), int(off[t0]), int(off[t1])))
+    up = torch.cuda.Stream(device=dev)
     arrays = ("pixel", "z", "alpha", "r", "g", "b")
 
     def step_e2e():
         up.wait_stream(stream)  # the previous step's kernels are done with the buffers
         with torch.cuda.stream(up):
             dev_bufs["tile_offsets"].copy_(host["tile_offsets"], non_blocking=True)
-        for (t0, t1, f0, f1, p0, p1) in chunks:
+        for (t0, t1, f0, f1) in chunks:
             with torch.cuda.stream(up):
                 for k in arrays:
                     dev_bufs[k][f0:f1].copy_(host[k][f0:f1], non_blocking=True)
             stream.wait_stream(up)
             wt.wt_build_resolve_tiles(desc, frags_e2e, t0, t1 - t0, out, coeff, stream=stream)
-            down.wait_stream(stream)
-            with torch.cuda.stream(down):
-                out_host[p0:p1].copy_(out[p0:p1], non_blocking=True)
-        stream.wait_stream(down)
+        out_host.copy_(out, non_blocking=True)  # after the last range, not against the uploads
 
     def copies_only():
         with torch.cuda.stream(up):
@@ -699,6 +749,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-preprocess", action="store_true")
+    ap.add_argument("--no-particles", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--path", default="fused", choices=["fused", "two_pass"],
                     help="fused kernel (default) or wt_build + wt_resolve_composite")

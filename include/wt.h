@@ -27,8 +27,11 @@
  *   coeff[p * C + j], in heap order: j = 0 holds chi_00, j = 2^n + k holds
  *   X_{n,k} for level n = 0..J-1 and shift k = 0..2^n-1 (§2.3).
  * - Depth is normalised to [0, 1) (the per-pixel bounds of §2.1 step 1 are
- *   applied by the caller); z is clamped to [0, 1 - 2^-24] and alpha to
+ *   applied before the build, e.g. with wt_depth_bounds and
+ *   wt_normalize_depth); z is clamped to [0, 1 - 2^-24] and alpha to
  *   [0, 1 - 2^-20] before use.
+ * - The build, resolve and composite calls take a stream grouped by screen
+ *   tile (wt_frags.tile_offsets); wt_bin groups an unordered stream.
  * - Float pointers must be 16-byte aligned.
  */
 #ifndef WT_H
@@ -340,6 +343,52 @@ wt_status wt_depth_bounds(const wt_desc *desc, const wt_frags *frags, float *zlo
  */
 wt_status wt_normalize_depth(const wt_desc *desc, const wt_frags *frags, const float *zlo,
                              const float *zhi, float *z_out, wt_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Below the paper's passes: rasterising transparent particles (the smoke and
+ * fire billboards of the paper's scenes, §3 and Fig. 2-3) into the fragment
+ * stream that the calls above consume.
+ */
+
+/* Particles, structure of arrays, device memory.  Particle i is a
+ * screen-space disc of centre (cx, cy) in pixel units (pixel (x, y) covers
+ * [x, x+1) x [y, y+1)), radius `radius` pixels, normalised depth z, peak
+ * opacity alpha and colour (r, g, b; all three may be NULL). */
+typedef struct wt_particles {
+    int64_t n;
+    const float *cx, *cy, *radius, *z, *alpha;
+    const float *r, *g, *b;
+} wt_particles;
+
+/* Bytes of device workspace of wt_raster_count / wt_raster_emit for n
+ * particles: n + 1 int64 offsets. */
+size_t wt_raster_workspace_bytes(int64_t n_particles);
+
+/*
+ * wt_raster_count -- first pass of the particle rasteriser.  A particle puts a
+ * fragment on every pixel of the image whose centre (x + 1/2, y + 1/2) is at
+ * squared distance d2 < radius^2 from (cx, cy), with opacity
+ * alpha * (1 - d2 / radius^2) (every operation rounded separately in FP32, the
+ * reciprocal of radius^2 taken once).  Writes into workspace (8-byte aligned)
+ * the exclusive offsets of each particle's fragments and, at [n], the total:
+ * read it back to size the fragment arrays of wt_raster_emit.  Particles with
+ * a non-positive or NaN radius, or a NaN centre, give no fragments.
+ */
+wt_status wt_raster_count(const wt_desc *desc, const wt_particles *particles, void *workspace,
+                          wt_stream stream);
+
+/*
+ * wt_raster_emit -- second pass: writes the fragments, each particle's
+ * contiguous at its offset, in particle order and row-major inside a particle
+ * (the order a rasteriser submitting one particle after another produces),
+ * into caller-allocated [capacity] arrays: pixel id y*width + x, the
+ * particle's z and colour, the opacity above.  Fragments beyond capacity are
+ * not written and are counted in the error word.  The stream is not grouped
+ * by tile: wt_bin groups it.  Only the descriptor's width and height are used.
+ */
+wt_status wt_raster_emit(const wt_desc *desc, const wt_particles *particles, const void *workspace,
+                         int64_t capacity, uint32_t *pixel, float *z, float *alpha, float *r,
+                         float *g, float *b, wt_stream stream);
 
 /*
  * wt_get_error -- synchronises `stream`, then returns in *bad_count the

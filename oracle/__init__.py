@@ -246,3 +246,52 @@ def bin_by_tile(pixel, width: int, height: int, tile_w: int, tile_h: int):
     counts = np.bincount(t[keep], minlength=ntiles)
     offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     return order, offsets
+
+
+def raster_particles(width: int, height: int, cx, cy, radius, z, alpha, r=None, g=None, b=None):
+    """Fragments of screen-space disc particles, in particle order and
+    row-major inside a particle: a fragment on every pixel whose centre
+    (x + 1/2, y + 1/2) is at squared distance d2 < radius^2 from the centre,
+    opacity alpha * (1 - d2 * (1 / radius^2)).  Every operation is one FP32
+    operation rounded to nearest (the coverage decision is taken in FP32, the
+    precision of the definition).  Plain loops over particles and rows."""
+    f = np.float32
+    cx, cy, radius, z, alpha = (np.asarray(v, dtype=f) for v in (cx, cy, radius, z, alpha))
+    cols = {"pixel": [], "z": [], "alpha": []}
+    rgb = r is not None
+    if rgb:
+        r, g, b = (np.asarray(v, dtype=f) for v in (r, g, b))
+        cols.update(r=[], g=[], b=[])
+    for i in range(len(cx)):
+        rho = radius[i]
+        if not (rho > 0) or np.isnan(cx[i]) or np.isnan(cy[i]) or not (rho < 1e6) \
+                or not (abs(cx[i]) < 1e9) or not (abs(cy[i]) < 1e9):
+            continue
+        rho2 = f(rho * rho)
+        inv = f(f(1) / rho2)
+        x0 = max(0, int(np.floor(float(cx[i]) - float(rho))) - 2)
+        x1 = min(width - 1, int(np.ceil(float(cx[i]) + float(rho))) + 2)
+        y0 = max(0, int(np.floor(float(cy[i]) - float(rho))) - 2)
+        y1 = min(height - 1, int(np.ceil(float(cy[i]) + float(rho))) + 2)
+        if x1 < x0 or y1 < y0:
+            continue
+        xs = np.arange(x0, x1 + 1)
+        dx = (xs.astype(f) + f(0.5)) - cx[i]
+        dx2 = dx * dx
+        for y in range(y0, y1 + 1):
+            dy = f(f(y) + f(0.5)) - cy[i]
+            d2 = dx2 + f(dy * dy)
+            hit = d2 < rho2
+            if not hit.any():
+                continue
+            cols["pixel"].append((y * width + xs[hit]).astype(np.int64))
+            cols["alpha"].append(alpha[i] * (f(1) - d2[hit] * inv))
+            cols["z"].append(np.full(hit.sum(), z[i], dtype=f))
+            if rgb:
+                for k, v in (("r", r), ("g", g), ("b", b)):
+                    cols[k].append(np.full(hit.sum(), v[i], dtype=f))
+    out = {}
+    for k, v in cols.items():
+        dt = np.int64 if k == "pixel" else f
+        out[k] = np.concatenate(v).astype(dt) if v else np.zeros(0, dtype=dt)
+    return out

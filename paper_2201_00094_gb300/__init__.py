@@ -26,6 +26,7 @@ __all__ = [
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
     "WtServeInfo", "wt_build_resolve_batch_static", "wt_bin_workspace_bytes", "wt_bin",
     "wt_depth_bounds", "wt_normalize_depth", "wt_build_resolve_tiles", "wt_build_resolve_single_pass",
+    "WtParticles", "wt_raster",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -64,6 +65,12 @@ class WtFrags(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("pixel", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("alpha", ctypes.c_void_p), ("r", ctypes.c_void_p), ("g", ctypes.c_void_p),
                 ("b", ctypes.c_void_p), ("tile_offsets", ctypes.c_void_p)]
+
+
+class WtParticles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("cx", ctypes.c_void_p), ("cy", ctypes.c_void_p),
+                ("radius", ctypes.c_void_p), ("z", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
+                ("r", ctypes.c_void_p), ("g", ctypes.c_void_p), ("b", ctypes.c_void_p)]
 
 
 class WtServeConfig(ctypes.Structure):
@@ -113,6 +120,10 @@ def lib() -> ctypes.CDLL:
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "wt_raster_workspace_bytes": ([i64], ctypes.c_size_t),
+        "wt_raster_count": ([D, ctypes.POINTER(WtParticles), vp, vp], ctypes.c_int),
+        "wt_raster_emit": ([D, ctypes.POINTER(WtParticles), vp, i64, vp, vp, vp, vp, vp, vp, vp],
+                           ctypes.c_int),
         "wt_bin_workspace_bytes": ([D, i64], ctypes.c_size_t),
         "wt_bin": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
         "wt_depth_bounds": ([D, Fr, vp, vp, vp], ctypes.c_int),
@@ -334,6 +345,37 @@ def wt_bin(desc: WtDesc, pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tens
           _dev(out.get("b"), "b_out", (torch.float32,)),
           _dev(out["tile_offsets"], "tile_offsets_out", (torch.int64,)),
           _dev(workspace, "workspace", (torch.uint8,)), int(workspace.numel()), _stream(stream))
+    return out
+
+
+def wt_raster(desc: WtDesc, cx: torch.Tensor, cy: torch.Tensor, radius: torch.Tensor, z: torch.Tensor,
+              alpha: torch.Tensor, r: Optional[torch.Tensor] = None, g: Optional[torch.Tensor] = None,
+              b: Optional[torch.Tensor] = None, capacity: Optional[int] = None, stream=None) -> dict:
+    """Rasterises particles into an unordered fragment stream (wt_raster_count,
+    then wt_raster_emit).  Reads the fragment total back to size the output
+    (so it synchronises the stream), unless ``capacity`` is given.  Returns a
+    dict of the fragment arrays (pixel, z, alpha[, r, g, b]) and "total"."""
+    n = int(cx.numel())
+    dev = cx.device
+    f32 = (torch.float32,)
+    pt = WtParticles(n, _dev(cx, "cx", f32), _dev(cy, "cy", f32), _dev(radius, "radius", f32),
+                     _dev(z, "z", f32), _dev(alpha, "alpha", f32), _dev(r, "r", f32), _dev(g, "g", f32),
+                     _dev(b, "b", f32))
+    ws = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    _call("wt_raster_count", ctypes.byref(desc), ctypes.byref(pt), _dev(ws, "workspace", (torch.int64,)),
+          _stream(stream))
+    total = int(ws[n].item()) if capacity is None else None
+    cap = total if capacity is None else int(capacity)
+    out = {"pixel": torch.empty(cap, dtype=torch.int32, device=dev), "z": torch.empty(cap, device=dev),
+           "alpha": torch.empty(cap, device=dev)}
+    if r is not None:
+        for k in ("r", "g", "b"):
+            out[k] = torch.empty(cap, device=dev)
+    _call("wt_raster_emit", ctypes.byref(desc), ctypes.byref(pt), _dev(ws, "workspace", (torch.int64,)), cap,
+          _dev(out["pixel"], "pixel", (torch.int32, torch.uint32)), _dev(out["z"], "z", f32),
+          _dev(out["alpha"], "alpha", f32), _dev(out.get("r"), "r", f32), _dev(out.get("g"), "g", f32),
+          _dev(out.get("b"), "b", f32), _stream(stream))
+    out["total"] = ws[n]
     return out
 
 

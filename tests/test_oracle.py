@@ -451,3 +451,37 @@ def test_bin_by_tile_groups_and_keeps_order():
         assert np.all(np.diff(idx) > 0)  # stable: input order inside a tile
         x, y = pixel[idx] % W, pixel[idx] // W
         assert np.all(x // tw == t % ntx) and np.all(y // th == t // ntx)
+
+
+# ---------------------------------------------------------------- particle rasterisation
+
+def test_raster_single_pixel_and_plus_shape():
+    """A particle centred on pixel (2, 2): radius 1 covers only that pixel
+    (its neighbours' centres are at distance exactly 1, not inside); radius
+    1.2 adds the four edge neighbours (d2 = 1 < 1.44) but not the diagonals
+    (d2 = 2), in row-major order, with opacity alpha (1 - d2 / r^2)."""
+    one = o.raster_particles(5, 5, [2.5], [2.5], [1.0], [0.3], [0.8])
+    assert list(one["pixel"]) == [2 * 5 + 2]
+    assert one["alpha"][0] == np.float32(0.8) and one["z"][0] == np.float32(0.3)
+    plus = o.raster_particles(5, 5, [2.5], [2.5], [1.2], [0.3], [0.8], [0.1], [0.2], [0.3])
+    assert list(plus["pixel"]) == [1 * 5 + 2, 2 * 5 + 1, 2 * 5 + 2, 2 * 5 + 3, 3 * 5 + 2]
+    edge = 0.8 * (1 - 1 / 1.44)
+    np.testing.assert_allclose(plus["alpha"], [edge, edge, 0.8, edge, edge], rtol=1e-6)
+    assert np.all(plus["r"] == np.float32(0.1)) and np.all(plus["b"] == np.float32(0.3))
+
+
+def test_raster_clips_at_the_image_and_skips_empty_particles():
+    out = o.raster_particles(4, 3, [0.2, 3.9, 2.0, 2.0, np.nan, 50.0], [0.2, 2.9, 1.5, 1.5, 1.0, 1.0],
+                             [1.0, 0.6, 0.0, -1.0, 2.0, 3.0], [0.5] * 6, [0.5] * 6)
+    # particle 0 at the top-left corner: pixels (0,0) d2=.18, (1,0) d2=1.78? no; (0,1) no
+    # particle 1 at the bottom-right corner: pixel (3,2) d2=.32 < .36
+    assert list(out["pixel"]) == [0, 2 * 4 + 3]
+    np.testing.assert_allclose(out["alpha"], [0.5 * (1 - 0.18), 0.5 * (1 - 0.32 / 0.36)], rtol=1e-5)
+
+
+def test_raster_covers_the_disc_area():
+    """Pixel count of a large disc approaches pi r^2 (Gauss circle problem:
+    the error is O(r))."""
+    for rho in (20.0, 35.5):
+        out = o.raster_particles(200, 200, [100.3], [99.8], [rho], [0.5], [0.5])
+        assert abs(len(out["pixel"]) - np.pi * rho * rho) < 4 * rho
