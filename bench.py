@@ -319,6 +319,34 @@ def run_wt(args):
             variants[name] = res
             del c2, c3, o2
 
+    # ---- coloured absorbance on the same frame (per-channel opacity alpha x (1, .8, .6)),
+    # FP32 and E5B9G9R9 coefficient storage; method bytes per fragment: pixel, z and
+    # three opacities in the build (20), the same plus r, g, b in the resolve (32)
+    if not args.no_variants:
+        ac = [fr.alpha, (fr.alpha * 0.8).contiguous(), (fr.alpha * 0.6).contiguous()]
+        o3 = torch.empty(P, 4, device=dev)
+        col = {}
+        for label, fmt, cbuf in (("f32", wt.RGB_F32, torch.empty(P, 3, C, device=dev)),
+                                 ("e5b9g9r9", wt.RGB_E5B9G9R9, torch.empty(P, C, device=dev, dtype=torch.int32))):
+            def rgb_step(fmt=fmt, cbuf=cbuf):
+                wt.wt_build_resolve_rgb(desc, frags, *ac, o3, cbuf, fmt, bg=fr.bg, stream=stream)
+            for _ in range(3):
+                rgb_step()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(10):
+                rgb_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 10
+            cbytes = cbuf.numel() * cbuf.element_size()
+            col[label] = {"ms": round(ms, 4), "fragments_per_s": n / (ms / 1e3),
+                          "coeff_bytes": cbytes, "alg_bytes": n * 52 + cbytes + 16 * P}
+            del cbuf
+        assert wt.wt_get_error(stream) == 0
+        variants["coloured"] = col
+        del ac, o3
+
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:

@@ -229,6 +229,39 @@ wt_status wt_build_resolve_single_pass(const wt_desc *desc, const wt_frags *frag
                                        const float *bg_img, const float bg[3], float *out,
                                        wt_stream stream);
 
+/* Storage of the coloured coefficients. */
+enum {
+    WT_RGB_F32 = 0,       /* float [P][3][C]: channel r, g, b rows of each pixel */
+    WT_RGB_E5B9G9R9 = 1   /* uint32 [P][C]: the three channels' magnitudes of each
+                             coefficient index in one word, 9-bit mantissas and a
+                             shared 5-bit exponent (bias 15); chi_00 is stored as
+                             is, the X_{n,k} (all <= 0, §2.3.1) as -X */
+};
+
+/*
+ * wt_build_resolve_rgb -- coloured absorbance: the three-channel form of the
+ * method (§1.2, §2.1: the paper's coefficients carry r, g, b, packed
+ * E5B9G9R9).  Fragment i has one depth z[i] and one opacity per channel,
+ * alpha_r/g/b[i]; each channel is built and resolved as the mono method with
+ * its own opacity and its own colour component,
+ *   out_c = (R_c / W_c)(1 - T_c) + bg_c T_c  (WT_RESOLVE_NORMALIZED), with
+ *   R_c = sum col_c alpha_c v_c(z), W_c = sum alpha_c v_c(z), T_c = exp(-sum a_c),
+ * and out[p*4 + 3] = 1 - (T_r + T_g + T_b)/3.  Fused per tile like
+ * wt_build_resolve; the resolve uses the coefficients rounded to coeff_format.
+ *   frags        pixel, z, r, g, b and tile_offsets as usual (frags->alpha is
+ *                not read).
+ *   alpha_r/g/b  [n] per-channel opacity.
+ *   coeff        nullable: written in coeff_format (WT_RGB_*).
+ * The tile's six bins planes must fit one block's shared memory (every tile of
+ * up to 256 pixels does, at 217 KB for J = 5; fewer blocks fit on an SM than
+ * for the mono kernels), else WT_ERR_UNSUPPORTED.  WT_ACCUMULATE is not
+ * supported.
+ */
+wt_status wt_build_resolve_rgb(const wt_desc *desc, const wt_frags *frags, const float *alpha_r,
+                               const float *alpha_g, const float *alpha_b, void *coeff,
+                               int32_t coeff_format, const float *bg_img, const float bg[3],
+                               float *out, wt_stream stream);
+
 /*
  * wt_build_resolve_batch_static -- wt_build_resolve for a batch of frames in
  * one launch, allocating nothing.  The paper has no counterpart: it exists for

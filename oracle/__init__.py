@@ -295,3 +295,47 @@ def raster_particles(width: int, height: int, cx, cy, radius, z, alpha, r=None, 
         dt = np.int64 if k == "pixel" else f
         out[k] = np.concatenate(v).astype(dt) if v else np.zeros(0, dtype=dt)
     return out
+
+
+def composite_rgb(pixel, z, alpha_c, rgb, P: int, J: int, flags=DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5),
+                  coeffs=None) -> np.ndarray:
+    """Coloured absorbance: channel c is the mono method with its own opacity
+    alpha_c[c] and its own colour component rgb[c] (§1.2, §2.1); out[:, c] is
+    its composite and out[:, 3] the mean of the three coverages 1 - T_c.
+    `coeffs` (three [P, C] arrays) replaces the channels' own coefficients."""
+    out = np.zeros((P, 4))
+    for c in range(3):
+        co = build_coeffs(pixel, z, alpha_c[c], P, J) if coeffs is None else coeffs[c]
+        o = resolve(pixel, z, alpha_c[c], (rgb[c], rgb[c], rgb[c]), P, J, co, flags, (bg[c],) * 3)[0]
+        out[:, c] = o[:, 0]
+        out[:, 3] += o[:, 3] / 3.0
+    return out
+
+
+def e5_encode(r, g, b) -> np.ndarray:
+    """E5B9G9R9 words of three non-negative arrays: the published shared-
+    exponent format (9-bit mantissas, 5-bit exponent, bias 15).  Values are
+    clamped to [0, 511/512 * 2^16]; the exponent comes from the largest channel,
+    floor(log2(max)) + 16 (at least 0), raised by one if that channel's rounded
+    mantissa reaches 512; mantissas are floor(v / 2^(e - 24) + 1/2).  Every
+    step is one FP32 operation, as in the definition's integer decisions."""
+    f = np.float32
+    r, g, b = (np.clip(np.nan_to_num(np.asarray(v, dtype=f), nan=0.0), f(0), f(65408.0)).astype(f)
+               for v in (r, g, b))
+    mx = np.maximum(r, np.maximum(g, b))
+    expo = ((mx.view(np.uint32) >> 23) & 0xFF).astype(np.int64) - 127
+    fl = np.where(mx > 0, np.maximum(expo, -16), -16)
+    e = fl + 16
+    scale = np.ldexp(np.ones_like(mx), 24 - e).astype(f)
+    bump = np.floor(mx * scale + f(0.5)) >= 512
+    e = np.where(bump, e + 1, e)
+    scale = np.where(bump, scale * f(0.5), scale).astype(f)
+    q = [np.floor(v * scale + f(0.5)).astype(np.uint64) for v in (r, g, b)]
+    return (q[0] | (q[1] << 9) | (q[2] << 18) | (e.astype(np.uint64) << 27)).astype(np.uint32)
+
+
+def e5_decode(w):
+    """The three values of E5B9G9R9 words: mantissa * 2^(e - 24)."""
+    w = np.asarray(w, dtype=np.uint32).astype(np.uint64)
+    scale = np.ldexp(1.0, (w >> 27).astype(np.int64) - 24)
+    return tuple((((w >> s) & 511).astype(np.float64) * scale) for s in (0, 9, 18))

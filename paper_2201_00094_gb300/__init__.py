@@ -26,7 +26,7 @@ __all__ = [
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
     "WtServeInfo", "wt_build_resolve_batch_static", "wt_bin_workspace_bytes", "wt_bin",
     "wt_depth_bounds", "wt_normalize_depth", "wt_build_resolve_tiles", "wt_build_resolve_single_pass",
-    "WtParticles", "wt_raster",
+    "WtParticles", "wt_raster", "RGB_F32", "RGB_E5B9G9R9", "wt_build_resolve_rgb",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_tiles": ([D, Fr, i64, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_single_pass": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build_resolve_rgb": ([D, Fr, vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp, vp], ctypes.c_int),
         "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
@@ -285,6 +286,23 @@ def wt_build_resolve_single_pass(desc: WtDesc, frags: WtFrags, coeff_prev: torch
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
           _stream(stream))
+
+
+RGB_F32, RGB_E5B9G9R9 = 0, 1
+
+
+def wt_build_resolve_rgb(desc: WtDesc, frags: WtFrags, alpha_r: torch.Tensor, alpha_g: torch.Tensor,
+                         alpha_b: torch.Tensor, out: torch.Tensor, coeff: Optional[torch.Tensor] = None,
+                         coeff_format: int = RGB_F32, bg: Sequence[float] = (0.5, 0.5, 0.5),
+                         bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Coloured absorbance (wt_build_resolve_rgb): per-channel opacity, one
+    depth; coeff is float32 [P, 3, C] (RGB_F32) or int32/uint32 [P, C] words
+    (RGB_E5B9G9R9)."""
+    f32 = (torch.float32,)
+    cdt = f32 if coeff_format == RGB_F32 else (torch.int32, torch.uint32)
+    _call("wt_build_resolve_rgb", ctypes.byref(desc), ctypes.byref(frags), _dev(alpha_r, "alpha_r", f32),
+          _dev(alpha_g, "alpha_g", f32), _dev(alpha_b, "alpha_b", f32), _dev(coeff, "coeff", cdt),
+          int(coeff_format), _dev(bg_img, "bg_img", f32), _bg(bg), _dev(out, "out", f32), _stream(stream))
 
 
 def wt_build_resolve_batch_static(descs: Sequence[WtDesc], frags: Sequence[WtFrags],

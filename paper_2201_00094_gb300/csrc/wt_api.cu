@@ -273,6 +273,30 @@ wt_status wt_build_resolve_single_pass(const wt_desc *d, const wt_frags *f, cons
     return finish(t[d->J - 1](p, (int)ntiles_of(d), coeff_prev, zmin_prev, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float *alpha_r, const float *alpha_g,
+                               const float *alpha_b, void *coeff, int32_t coeff_format, const float *bg_img,
+                               const float bg[3], float *out, wt_stream stream) {
+    wt_status st = check_desc(d);
+    if (st != WT_OK) return st;
+    if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
+    if (coeff_format != WT_RGB_F32 && coeff_format != WT_RGB_E5B9G9R9) return WT_ERR_ARG;
+    if (!f || f->n < 0 || !f->tile_offsets || !aligned(f->tile_offsets, 8)) return WT_ERR_ARG;
+    const void *req[8] = {f->pixel, f->z, f->r, f->g, f->b, alpha_r, alpha_g, alpha_b};
+    for (const void *q : req)
+        if (f->n > 0 && !q) return WT_ERR_ARG;
+    if ((coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16)) return WT_ERR_ARG;
+    const int npx = d->tile_w * d->tile_h;
+    if (rgb_smem_bytes(d->J, npx) > 227 * 1024) return WT_ERR_UNSUPPORTED;  // a smaller tile is needed
+    Params p = make_params(d, f);
+    p.coeff = coeff;
+    p.out = out;
+    if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
+    if (!(p.err = err_word())) return WT_ERR_CUDA;
+    const float *const ac[3] = {alpha_r, alpha_g, alpha_b};
+    return finish(launch_fused_rgb(p, d->J, ac, coeff_format == WT_RGB_E5B9G9R9, (int)ntiles_of(d),
+                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
 wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin,
                            const float *bg_img, const float bg[3], float *out, wt_stream stream) {
     wt_status st = check_desc(d);

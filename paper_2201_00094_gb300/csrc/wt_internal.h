@@ -38,4 +38,9 @@ extern const ServeOccupancy kServeOcc0[5], kServeOcc1[5], kServeOcc2[5];
 extern const QueryLaunch kAbsorbance0[5], kAbsorbance1[5], kAbsorbance2[5];
 extern const TemporalLaunch kTemporal0[5], kTemporal1[5], kTemporal2[5];
 
+// Coloured absorbance (wt_rgb.cu): shared memory of a tile, and the launch.
+size_t rgb_smem_bytes(int J, int npx);
+cudaError_t launch_fused_rgb(const Params &p, int J, const float *const alpha_c[3], bool e5, int ntiles,
+                             cudaStream_t s);
+
 }  // namespace wt

@@ -131,6 +131,39 @@ template <> struct Cvt<__half> {
     static __device__ __forceinline__ float from(__half x) { return __half2float(x); }
 };
 
+// E5B9G9R9: three non-negative values with one shared 5-bit exponent (bias
+// 15) and 9-bit mantissas, the 32-bit coefficient format of the paper's
+// coloured storage (its coefficients have fixed signs, §2.3.1, so magnitudes
+// suffice).  Encoding follows the published shared-exponent format: clamp to
+// the largest representable value, take the exponent from the largest channel
+// (one more if its rounded mantissa reaches 2^9), round every mantissa to
+// nearest.
+constexpr float kE5Max = 65408.f;  // (511/512) * 2^16
+__device__ __forceinline__ uint32_t e5_encode(float r, float g, float b) {
+    r = fminf(fmaxf(r, 0.f), kE5Max);  // NaN -> 0
+    g = fminf(fmaxf(g, 0.f), kE5Max);
+    b = fminf(fmaxf(b, 0.f), kE5Max);
+    const float mx = fmaxf(r, fmaxf(g, b));
+    // floor(log2(mx)) for mx > 0, from the exponent bits (subnormal FP32 values
+    // are far below the format's smallest exponent and take the floor -16)
+    const int fl = mx > 0.f ? max(((int)(__float_as_uint(mx) >> 23) & 0xff) - 127, -16) : -16;
+    int e = fl + 1 + 15;  // in [0, 32)
+    float scale = ldexpf(1.f, 24 - e);  // 1 / 2^(e - 15 - 9)
+    if (floorf(fmaf(mx, scale, 0.5f)) >= 512.f) {
+        ++e;
+        scale *= 0.5f;
+    }
+    const uint32_t rs = (uint32_t)floorf(fmaf(r, scale, 0.5f)), gs = (uint32_t)floorf(fmaf(g, scale, 0.5f)),
+                   bs = (uint32_t)floorf(fmaf(b, scale, 0.5f));
+    return rs | (gs << 9) | (bs << 18) | ((uint32_t)e << 27);
+}
+__device__ __forceinline__ void e5_decode(uint32_t w, float &r, float &g, float &b) {
+    const float scale = ldexpf(1.f, (int)(w >> 27) - 24);
+    r = (float)(w & 511u) * scale;
+    g = (float)((w >> 9) & 511u) * scale;
+    b = (float)((w >> 18) & 511u) * scale;
+}
+
 // One pixel's C coefficients to / from global memory, 16-byte vectors when
 // the row is a multiple of 16 bytes (it is 16-byte aligned then).
 template <typename CT, int C>
@@ -584,12 +617,20 @@ template <int J> __device__ __forceinline__ void get_row(const float *row, float
 }
 
 template <int J>
+__device__ __forceinline__ void bins_to_coeffs_inv(const unsigned *Frow, const unsigned *Grow, float inv,
+                                                   float (&c)[1 << J], float &S);
+template <int J>
 __device__ __forceinline__ void bins_to_coeffs(const unsigned *Frow, const unsigned *Grow,
                                                float (&c)[1 << J], float &S, bool scaled) {
+    // 1 / s_p (a power of two) when the tile took per-pixel scales, else 2^-27
+    bins_to_coeffs_inv<J>(Frow, Grow, scaled ? __uint_as_float(Frow[Shape<J>::INV]) : kBinInv, c, S);
+}
+// The same with the fixed-point scale's reciprocal given.
+template <int J>
+__device__ __forceinline__ void bins_to_coeffs_inv(const unsigned *Frow, const unsigned *Grow, float inv,
+                                                   float (&c)[1 << J], float &S) {
     constexpr int C = 1 << J;
     float F[C], G[C];
-    // 1 / s_p (a power of two) when the tile took per-pixel scales, else 2^-27
-    const float inv = scaled ? __uint_as_float(Frow[Shape<J>::INV]) : kBinInv;
     get_row<J>(reinterpret_cast<const float *>(Frow), F);
     get_row<J>(reinterpret_cast<const float *>(Grow), G);
     // the tree runs on the integer sums (exact as floats up to 2^24, rounded

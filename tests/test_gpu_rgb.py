@@ -1,0 +1,106 @@
+"""Coloured absorbance (per-channel opacity, one depth) through the C ABI
+against the oracle's definition (each channel is the mono method with its own
+opacity and colour component), in FP32 and in the paper's E5B9G9R9 storage."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2201_00094_gb300 as wt
+import synth
+from wtcheck import coeff_tol, desc_of, frags_of
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda")
+
+
+def _coloured(fr: synth.Frame, seed: int):
+    """Per-channel opacities: the frame's alpha times a seeded factor per channel."""
+    rng = np.random.default_rng(seed)
+    a = fr.numpy()["alpha"]
+    return [np.clip(a * rng.uniform(0.3, 1.2, fr.n), 0, 0.95).astype(np.float32) for _ in range(3)]
+
+
+@pytest.mark.parametrize("J,tile", [(4, (128, 1)), (5, (64, 1)), (3, (7, 3))])
+def test_coloured_fp32_matches_the_oracle(J, tile):
+    fr = synth.uniform_frame(96, 40, 8.0, 40, J=J, seed=70 + J, tile_w=tile[0], tile_h=tile[1])
+    ac = _coloured(fr, J)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    C = 1 << J
+    out = torch.empty(fr.P, 4, device=DEV)
+    coeff = torch.empty(fr.P, 3, C, device=DEV)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, wt.RGB_F32, bg=(0.2, 0.5, 0.8))
+    assert wt.wt_get_error() == 0
+    h = fr.numpy()
+    rgb = (h["r"], h["g"], h["b"])
+    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, rgb, fr.P, J, bg=(0.2, 0.5, 0.8))
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+    got = coeff.cpu().numpy().astype(np.float64)
+    for c in range(3):
+        ref_c = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, J)
+        fc = dataclasses.replace(fr, alpha=torch.from_numpy(ac[c]))
+        assert (np.abs(got[:, c, :] - ref_c) <= coeff_tol(fc)).all()
+
+
+def test_grey_opacity_equals_the_mono_method():
+    """With the same opacity in every channel the coloured call gives the mono
+    call's colour, and each channel's coefficients are the mono build's."""
+    fr = synth.uniform_frame(96, 40, 8.0, 40, J=4, seed=80, tile_w=128, tile_h=1)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    out = torch.empty(fr.P, 4, device=DEV)
+    coeff = torch.empty(fr.P, 3, 16, device=DEV)
+    wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, g.alpha, g.alpha, out, coeff, wt.RGB_F32, bg=fr.bg)
+    mono = torch.empty(fr.P, 4, device=DEV)
+    mcoeff = torch.empty(fr.P, 16, device=DEV)
+    wt.wt_build_resolve(d, frags_of(g), mono, mcoeff, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    torch.testing.assert_close(out, mono, atol=2e-6, rtol=0)
+    for c in range(3):
+        assert torch.equal(coeff[:, c, :], mcoeff)
+
+
+def test_coloured_e5b9g9r9_storage():
+    """E5B9G9R9 storage: the stored words decode to the oracle's coefficients
+    within the format's precision (half a mantissa step of the shared
+    exponent, plus FP32 build rounding), and the composite equals the oracle's
+    resolve against the decoded coefficients."""
+    fr = synth.uniform_frame(96, 40, 8.0, 40, J=4, seed=90, tile_w=128, tile_h=1)
+    ac = _coloured(fr, 3)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    out = torch.empty(fr.P, 4, device=DEV)
+    words = torch.empty(fr.P, 16, device=DEV, dtype=torch.int32)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, words, wt.RGB_E5B9G9R9, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    h = fr.numpy()
+    w = words.cpu().numpy().view(np.uint32)
+    dec = oracle.e5_decode(w)
+    sign = np.where(np.arange(16) == 0, 1.0, -1.0)
+    step = np.ldexp(1.0, (w >> 27).astype(np.int64) - 24)
+    coeffs = []
+    for c in range(3):
+        ref_c = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, 4)
+        got_c = sign * dec[c]
+        assert np.all(np.abs(got_c - ref_c) <= step / 2 + 1e-6 * np.abs(ref_c) + 1e-9)
+        coeffs.append(got_c)
+    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, 4, bg=fr.bg,
+                               coeffs=coeffs)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+
+
+def test_coloured_arguments():
+    fr = synth.uniform_frame(32, 8, 2.0, 8, J=4, seed=91, tile_w=32, tile_h=1)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    out = torch.empty(fr.P, 4, device=DEV)
+    with pytest.raises(wt.WtError):
+        wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, g.alpha, g.alpha, out, None, 7, bg=fr.bg)
+    with pytest.raises(wt.WtError):
+        wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, None, g.alpha, out, None, wt.RGB_F32, bg=fr.bg)

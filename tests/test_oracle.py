@@ -485,3 +485,51 @@ def test_raster_covers_the_disc_area():
     for rho in (20.0, 35.5):
         out = o.raster_particles(200, 200, [100.3], [99.8], [rho], [0.5], [0.5])
         assert abs(len(out["pixel"]) - np.pi * rho * rho) < 4 * rho
+
+
+# ---------------------------------------------------------------- coloured absorbance, E5B9G9R9
+
+def test_e5b9g9r9_hand_encodings():
+    """Shared exponent e = floor(log2(max)) + 16, mantissas v / 2^(e - 24)
+    rounded half up; the bump when the largest mantissa rounds to 512."""
+    w = o.e5_encode([1.0, 1.0, 0.9995, 65408.0, 1e6, 0.0], [0.0, 0.5, 0.0, 0.0, 0.0, 0.0],
+                    [0.0, 0.25, 0.0, 0.0, 0.0, 0.0])
+    assert w[0] == 256 | (16 << 27)
+    assert w[1] == 256 | (128 << 9) | (64 << 18) | (16 << 27)
+    assert w[2] == 256 | (16 << 27)            # 0.9995 * 2^9 = 511.74 rounds to 512: exponent + 1
+    assert w[3] == 511 | (31 << 27)            # the largest value: 511 * 2^7
+    assert w[4] == w[3]                        # clamped
+    assert w[5] == 0
+    r, g, b = o.e5_decode(w[:2])
+    np.testing.assert_array_equal(r, [1.0, 1.0])
+    np.testing.assert_array_equal(g, [0.0, 0.5])
+    np.testing.assert_array_equal(b, [0.0, 0.25])
+
+
+def test_e5b9g9r9_round_trip_error_bound():
+    """Every channel comes back within half a mantissa step of the shared
+    exponent, 2^(e - 25); the largest channel within 2^-10 relative."""
+    rng = np.random.default_rng(8)
+    v = [rng.lognormal(0, 3, 5000) for _ in range(3)]
+    w = o.e5_encode(*v)
+    back = o.e5_decode(w)
+    step = np.ldexp(1.0, (w >> 27).astype(np.int64) - 24)
+    for c in range(3):
+        ok = v[c] <= 65408
+        assert np.all(np.abs(back[c] - v[c].astype(np.float32))[ok] <= step[ok] / 2)
+    mx = np.maximum(v[0], np.maximum(v[1], v[2]))
+    bmx = np.maximum(back[0], np.maximum(back[1], back[2]))
+    ok = mx <= 65408
+    assert np.all(np.abs(bmx - mx)[ok] <= mx[ok] * 2.0 ** -9)
+
+
+def test_coloured_composite_reduces_to_mono_for_grey_opacity():
+    """Equal opacities in the three channels give the mono method's composite."""
+    rng = np.random.default_rng(9)
+    P, n = 30, 400
+    pixel = rng.integers(0, P, n).astype(np.uint32)
+    z, al = rng.random(n).astype(np.float32), rng.uniform(0.05, 0.6, n).astype(np.float32)
+    rgb = tuple(rng.random(n).astype(np.float32) for _ in range(3))
+    mono = o.composite(pixel, z, al, rgb, P, 4)
+    col = o.composite_rgb(pixel, z, (al, al, al), rgb, P, 4)
+    np.testing.assert_allclose(col, mono, atol=1e-12)
