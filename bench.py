@@ -280,7 +280,7 @@ def run_wt(args):
 
     # ---- variants (not part of `value`): two-pass path and 16-bit storage
     variants = {}
-    if not args.no_variants:
+    if not args.no_variants and not args.no_mono_variants:
         for name, d2 in (("f32", wt.F32), ("bf16", wt.BF16), ("f16", wt.F16)):
             dsc = wt.make_desc(fr.width, fr.height, J, d2, tile_w=fr.tile_w, tile_h=fr.tile_h)
             c2, o2 = buffers(d2)
@@ -320,13 +320,14 @@ def run_wt(args):
             del c2, c3, o2
 
     # ---- coloured absorbance on the same frame (per-channel opacity alpha x (1, .8, .6)),
-    # FP32 and E5B9G9R9 coefficient storage; method bytes per fragment: pixel, z and
-    # three opacities in the build (20), the same plus r, g, b in the resolve (32)
+    # FP32 and E5B9G9R9 coefficient storage; the method's bytes as for the mono path:
+    # per fragment pixel, z and three opacities in the build (20), the same plus r, g,
+    # b in the resolve (32); the coefficients written and read once; the output
     if not args.no_variants:
         ac = [fr.alpha, (fr.alpha * 0.8).contiguous(), (fr.alpha * 0.6).contiguous()]
         o3 = torch.empty(P, 4, device=dev)
         col = {}
-        for label, fmt, cbuf in (("f32", wt.RGB_F32, torch.empty(P, 3, C, device=dev)),
+        for label, fmt, cbuf in (("f32", wt.RGB_F32, torch.empty(3, P, C, device=dev)),
                                  ("e5b9g9r9", wt.RGB_E5B9G9R9, torch.empty(P, C, device=dev, dtype=torch.int32))):
             def rgb_step(fmt=fmt, cbuf=cbuf):
                 wt.wt_build_resolve_rgb(desc, frags, *ac, o3, cbuf, fmt, bg=fr.bg, stream=stream)
@@ -341,7 +342,8 @@ def run_wt(args):
             ms = a.elapsed_time(b) / 10
             cbytes = cbuf.numel() * cbuf.element_size()
             col[label] = {"ms": round(ms, 4), "fragments_per_s": n / (ms / 1e3),
-                          "coeff_bytes": cbytes, "alg_bytes": n * 52 + cbytes + 16 * P}
+                          "coeff_bytes": cbytes, "method_bytes": n * 52 + 2 * cbytes + 16 * P,
+                          "frac_method_bytes": round((n * 52 + 2 * cbytes + 16 * P) / (ms / 1e3) / 1e9 / hbm, 4)}
             del cbuf
         assert wt.wt_get_error(stream) == 0
         variants["coloured"] = col
@@ -773,6 +775,8 @@ def main():
     ap.add_argument("--ref-tiles", type=int, default=0, help="tiles per step (0: sized by time)")
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-mono-variants", action="store_true",
+                    help="time only the coloured variants (FP32 and E5B9G9R9 storage)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-backward", action="store_true")

@@ -231,7 +231,8 @@ wt_status wt_build_resolve_single_pass(const wt_desc *desc, const wt_frags *frag
 
 /* Storage of the coloured coefficients. */
 enum {
-    WT_RGB_F32 = 0,       /* float [P][3][C]: channel r, g, b rows of each pixel */
+    WT_RGB_F32 = 0,       /* float [3][P][C]: one plane per channel (r, g, b), each
+                             laid out as the mono coefficient array */
     WT_RGB_E5B9G9R9 = 1   /* uint32 [P][C]: the three channels' magnitudes of each
                              coefficient index in one word, 9-bit mantissas and a
                              shared 5-bit exponent (bias 15); chi_00 is stored as
@@ -252,10 +253,12 @@ enum {
  *                not read).
  *   alpha_r/g/b  [n] per-channel opacity.
  *   coeff        nullable: written in coeff_format (WT_RGB_*).
- * The tile's six bins planes must fit one block's shared memory (every tile of
- * up to 256 pixels does, at 217 KB for J = 5; fewer blocks fit on an SM than
- * for the mono kernels), else WT_ERR_UNSUPPORTED.  WT_ACCUMULATE is not
- * supported.
+ * The channels are built and resolved one after the other in each tile's CTA,
+ * in the mono kernel's shared memory (E5B9G9R9 keeps two more FP32 rows per
+ * pixel until the words are formed); every tile of up to 256 pixels fits.
+ * Invalid fragments (pixel outside their tile, NaN depth or a NaN opacity) are
+ * left out of the channels they are invalid for and counted in the error word
+ * once per channel.  WT_ACCUMULATE is not supported (WT_ERR_UNSUPPORTED).
  */
 wt_status wt_build_resolve_rgb(const wt_desc *desc, const wt_frags *frags, const float *alpha_r,
                                const float *alpha_g, const float *alpha_b, void *coeff,

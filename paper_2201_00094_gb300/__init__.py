@@ -296,8 +296,8 @@ def wt_build_resolve_rgb(desc: WtDesc, frags: WtFrags, alpha_r: torch.Tensor, al
                          coeff_format: int = RGB_F32, bg: Sequence[float] = (0.5, 0.5, 0.5),
                          bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
     """Coloured absorbance (wt_build_resolve_rgb): per-channel opacity, one
-    depth; coeff is float32 [P, 3, C] (RGB_F32) or int32/uint32 [P, C] words
-    (RGB_E5B9G9R9)."""
+    depth; coeff is float32 [3, P, C] (RGB_F32, one plane per channel) or
+    int32/uint32 [P, C] words (RGB_E5B9G9R9)."""
     f32 = (torch.float32,)
     cdt = f32 if coeff_format == RGB_F32 else (torch.int32, torch.uint32)
     _call("wt_build_resolve_rgb", ctypes.byref(desc), ctypes.byref(frags), _dev(alpha_r, "alpha_r", f32),

@@ -286,7 +286,7 @@ wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float 
         if (f->n > 0 && !q) return WT_ERR_ARG;
     if ((coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16)) return WT_ERR_ARG;
     const int npx = d->tile_w * d->tile_h;
-    if (rgb_smem_bytes(d->J, npx) > 227 * 1024) return WT_ERR_UNSUPPORTED;  // a smaller tile is needed
+    if (rgb_smem_bytes(d->J, npx, coeff_format == WT_RGB_E5B9G9R9) > 227 * 1024) return WT_ERR_UNSUPPORTED;
     Params p = make_params(d, f);
     p.coeff = coeff;
     p.out = out;

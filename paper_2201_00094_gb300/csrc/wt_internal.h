@@ -39,7 +39,7 @@ extern const QueryLaunch kAbsorbance0[5], kAbsorbance1[5], kAbsorbance2[5];
 extern const TemporalLaunch kTemporal0[5], kTemporal1[5], kTemporal2[5];
 
 // Coloured absorbance (wt_rgb.cu): shared memory of a tile, and the launch.
-size_t rgb_smem_bytes(int J, int npx);
+size_t rgb_smem_bytes(int J, int npx, bool e5);
 cudaError_t launch_fused_rgb(const Params &p, int J, const float *const alpha_c[3], bool e5, int ntiles,
                              cudaStream_t s);
 

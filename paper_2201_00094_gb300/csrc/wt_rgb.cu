@@ -8,19 +8,22 @@
 //     W_c = sum alpha_c v_c,  T_c = exp(-sum a_c),
 // so each channel is the mono method on (z, alpha_c, col_c).
 //
-// One fused tile kernel builds the three channels' bins in one pass over the
-// fragments (six fixed-point planes), turns them into coefficients, rounds
-// them through the storage format (FP32, or the E5B9G9R9 triple of each
-// coefficient index), synthesises three rows of bin values and resolves the
-// three channels in a second pass, the coefficients never leaving the SM.
+// One CTA per tile works through the channels one after the other with the
+// mono kernel's phases and shared memory: the channel's bins (fixed-point
+// shared atomics, with the counting fallback), its coefficients and their
+// storage, its bin values, and a resolve pass that accumulates (col_c w, w)
+// per pixel.  The pixel's thread keeps each channel's composite in registers
+// and writes the RGBA once.  The tile's fragments are read from HBM once and
+// re-read from L2 by the later passes.  With E5B9G9R9 storage a word holds one
+// coefficient index of all three channels, so channels r and g are built
+// first and their FP32 rows kept in shared memory; after channel b's build the
+// words are formed and stored, and the three resolves run on the decoded
+// values, so that the composite matches the stored words.
 #include "wt.h"
 #include "wt_internal.h"
 #include "wt_tile.cuh"
 
 namespace wt {
-
-unsigned long long *error_word();  // wt_api.cu
-
 namespace {
 
 constexpr int kCh = 3;
@@ -28,284 +31,323 @@ constexpr int kCh = 3;
 struct RgbParams {
     Params p;  // geometry, fragments (pixel, z, r, g, b), coeff (nullable), out, bg, err
     const float *__restrict__ alpha_c[kCh];
-    int e5;  // storage: 1 = E5B9G9R9 [P][C] words, 0 = FP32 [P][3][C]
+    int64_t plane;  // P * C: stride of the FP32 channel planes
 };
 
-template <int J> struct RgbLayout {
-    static constexpr size_t plane(int npx) { return Layout<J>::plane(npx); }
-    static constexpr size_t vplane(int npx) { return Layout<J>::vplane(npx); }
-    static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 32; }  // 2 float4 per pixel
-    static constexpr size_t words(int npx) { return Layout<J>::words(npx); }
-    static constexpr size_t build(int npx) { return 2 * kCh * plane(npx); }
-    static constexpr size_t resolve(int npx) { return kCh * vplane(npx) + accw(npx) + kCh * words(npx); }
-    static constexpr size_t region(int npx) { return build(npx) > resolve(npx) ? build(npx) : resolve(npx); }
-    static constexpr size_t total(int npx) { return region(npx) + words(npx); }  // + nearest-depth words
+// Shared memory (bytes).  The region holds a channel's F and G bins, then its
+// bin values followed by the staged coefficient rows, which are cleared and
+// reused as the warps' (R, W) accumulators.  E5B9G9R9 adds the FP32 rows of
+// channels r and g and one nearest-depth array per channel.
+template <int J, bool E5> struct RgbLayout {
+    static constexpr size_t rows(int npx) { return align16((size_t)npx * Shape<J>::C * 4); }
+    static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 8; }
+    static constexpr size_t after(int npx) { return rows(npx) > accw(npx) ? rows(npx) : accw(npx); }
+    static constexpr size_t region(int npx) {
+        return 2 * Layout<J>::plane(npx) > Layout<J>::vplane(npx) + after(npx) ? 2 * Layout<J>::plane(npx)
+                                                                                : Layout<J>::vplane(npx) + after(npx);
+    }
+    static constexpr size_t stash(int npx) { return E5 ? 2 * rows(npx) : 0; }
+    static constexpr size_t zw(int npx) { return region(npx) + stash(npx); }
+    static constexpr size_t total(int npx) { return zw(npx) + (E5 ? kCh : 1) * Layout<J>::words(npx); }
 };
 
-// Warp-segmented reduction of eight floats per pixel (the rank rounds of
-// warp_accumulate, on two float4 halves).
-__device__ __forceinline__ void accumulate8(float4 *mine, int lp, float4 v0, float4 v1) {
-    float4 o0 = mine[2 * lp], o1 = mine[2 * lp + 1];
-    o0.x += v0.x, o0.y += v0.y, o0.z += v0.z, o0.w += v0.w;
-    o1.x += v1.x, o1.y += v1.y, o1.z += v1.z, o1.w += v1.w;
-    mine[2 * lp] = o0;
-    mine[2 * lp + 1] = o1;
-}
-__device__ __forceinline__ void warp_accumulate8(float4 *mine, int lp, float4 v0, float4 v1) {
+// warp_accumulate on (R, W) pairs: the lanes holding the same pixel are
+// ranked and add into the warp's private copy in rank order.
+__device__ __forceinline__ void warp_accumulate2(float2 *mine, int lp, float2 v) {
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     const unsigned rank = __popc(__match_any_sync(0xffffffffu, lp) & lt);
-    if (lp >= 0 && rank == 0) accumulate8(mine, lp, v0, v1);
+    auto add = [&]() {
+        float2 o = mine[lp];
+        o.x += v.x;
+        o.y += v.y;
+        mine[lp] = o;
+    };
+    if (lp >= 0 && rank == 0) add();
     __syncwarp();
     for (unsigned r = 1; __any_sync(0xffffffffu, lp >= 0 && rank >= r); ++r) {
-        if (lp >= 0 && rank == r) accumulate8(mine, lp, v0, v1);
+        if (lp >= 0 && rank == r) add();
         __syncwarp();
     }
 }
 
-// Counting pass of the fallback for three channels: per pixel the fragment
-// count and the largest clamped opacity over the channels, then one scale s_p
-// for all three channels' bins.
+// Step 3 for one channel: pc.alpha is the channel's opacity and pc.r its
+// colour component; per pixel (R, W) += (col w, w), w = alpha 2^-A'.
+template <int J, bool DEF>
+__device__ __forceinline__ void resolve_channel(const Params &pc, const Tile &T, const float *A2, float2 *accw) {
+    constexpr int LDV = Shape<J>::LDV;
+    const uint32_t flags = DEF ? kDefaultFlags : pc.flags;
+    const int npx = pc.g.tile_w * pc.g.tile_h;
+    float2 *mine = accw + (threadIdx.x >> 5) * npx;
+    for_each_group<kWithZ | kWithR>(T.s, T.e, pc, [&](auto &G) {
+        constexpr int N = std::remove_reference_t<decltype(G)>::size;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int lp = G.v && G.z[k] == G.z[k] && G.al[k] == G.al[k] ? local_pixel(G.px[k], pc, T) : -1;
+            const int l = lp >= 0 ? lp : 0;  // an invalid lane evaluates pixel 0 and adds nothing
+            const float ac = clamp_alpha(G.al[k]);
+            const float Ah = absorbance_at<J>(A2 + l * LDV, clamp_depth(G.z[k]), -lg2(1.f - ac), flags);
+            const float w = ac * ex2(-Ah);
+            warp_accumulate2(mine, lp, make_float2(G.r[k] * w, w));
+        }
+    });
+}
+
+// E5B9G9R9 of one coefficient index k (the stored magnitudes are chi and -X);
+// the channels' values are replaced by the decoded ones.
+__device__ __forceinline__ uint32_t pack_index(int k, float &r, float &g, float &b) {
+    const float sg = k == 0 ? 1.f : -1.f;
+    const uint32_t w = e5_encode(sg * r, sg * g, sg * b);
+    e5_decode(w, r, g, b);
+    r *= sg;
+    g *= sg;
+    b *= sg;
+    return w;
+}
+
+// Step 2 for one channel (opacity alpha): its coefficients into v and its
+// total step into S for the pixel of thread lp, its nearest depths into z.
+// Ends with every bin row read.
 template <int J>
-__device__ __forceinline__ void count_pass_rgb(const RgbParams &q, const Tile &T, unsigned *sF0) {
+__device__ __forceinline__ void build_channel(const Params &p, const float *alpha, const Tile &T,
+                                              unsigned char *smem, unsigned *z, int64_t gp,
+                                              float (&v)[1 << J], float &S, unsigned &bad) {
     constexpr int LD = Shape<J>::LD;
-    constexpr int CNT = Shape<J>::CNT, AMAX = Shape<J>::AMAX, INV = Shape<J>::INV;
-    const Params &p = q.p;
-    for (int64_t i = T.s + threadIdx.x; i < T.e; i += blockDim.x) {
-        const float z = p.z[i];
-        float am = 0.f;
-        bool nan = !(z == z);
-#pragma unroll
-        for (int c = 0; c < kCh; ++c) {
-            const float al = q.alpha_c[c][i];
-            nan |= !(al == al);
-            am = fmaxf(am, clamp_alpha(al));
-        }
-        const int lp = nan ? -1 : local_pixel(p.pixel[i], p, T);
-        if (lp >= 0) {
-            atomicAdd(&sF0[lp * LD + CNT], 1u);
-            atomicMax(&sF0[lp * LD + AMAX], __float_as_uint(am));
-        }
-    }
+    const int npx = p.g.tile_w * p.g.tile_h, lp = threadIdx.x;
+    unsigned *sF = reinterpret_cast<unsigned *>(smem);
+    unsigned *sG = reinterpret_cast<unsigned *>(smem + Layout<J>::plane(npx));
+    Params pc = p;
+    pc.alpha = alpha;
+    fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) z[i] = 0x7f800000u;
     __syncthreads();
-    for (int lp = threadIdx.x; lp < p.g.tile_w * p.g.tile_h; lp += blockDim.x) {
-        unsigned *row = sF0 + lp * LD;
-        const float bound = (float)row[CNT] * step_of(__uint_as_float(row[AMAX]));
-        const int e = bound > 0.f ? max(ilogbf(bound), -30) : 0;
-        row[INV] = __float_as_uint(ldexpf(1.f, e - 30));
-        row[AMAX] = __float_as_uint(ldexpf(1.f, 30 - e));
-    }
+    const bool scaled = phase_bins<J>(pc, T, sF, sG, z, bad);
+    if (gp >= 0) bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S, scaled);
     __syncthreads();
 }
 
-// Bins of the three channels: fixed scale 2^27 (SCALED = false, reports a
-// wrapped word or a step below 2^-7) or the per-pixel scale of channel 0's row
-// (SCALED = true).  Plane 2c is channel c's F, plane 2c+1 its G.
-template <int J, bool SCALED, bool COUNT>
-__device__ __forceinline__ bool bins_pass_rgb(const RgbParams &q, const Tile &T, unsigned *planes, size_t pl,
-                                              unsigned *sZ, unsigned &bad) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, AMAX = Shape<J>::AMAX;
-    constexpr float kFineStep = 1048576.f;  // 2^20: a step of 2^-7 under the fixed scale
-    const Params &p = q.p;
-    bool retry = false;
-    for (int64_t i = T.s + threadIdx.x; i < T.e; i += blockDim.x) {
-        const float z = p.z[i];
-        float al[kCh];
-        bool nan = !(z == z);
-#pragma unroll
-        for (int c = 0; c < kCh; ++c) {
-            al[c] = q.alpha_c[c][i];
-            nan |= !(al[c] == al[c]);
-        }
-        const int lp = nan ? -1 : local_pixel(p.pixel[i], p, T);
-        if (lp < 0) {
-            if (COUNT) ++bad;
-            continue;
-        }
-        const float zc = clamp_depth(z);
-        const float s = zc * (float)C;
-        const Floor m = floor_small(s);
-        const float f = s - m.f;
-        const float sp = SCALED ? __uint_as_float(planes[lp * LD + AMAX]) : kBinScale;
-        bool any = false;
-#pragma unroll
-        for (int c = 0; c < kCh; ++c) {
-            const float a = step_of(clamp_alpha(al[c]));
-            const float as = a * sp;
-            const unsigned vF = __float2uint_rn(as * f), vG = __float2uint_rn(as * (1.f - f));
-            unsigned *F = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(planes) + (2 * c) * pl);
-            unsigned *G = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(planes) + (2 * c + 1) * pl);
-            const unsigned oF = atomicAdd(&F[lp * LD + m.i], vF);
-            const unsigned oG = atomicAdd(&G[lp * LD + m.i], vG);
-            if (!SCALED) retry |= (oF + vF < oF) | (oG + vG < oG) | (as < kFineStep && a > 0.f);
-            any |= a > 0.f;
-        }
-        if (any) atomicMin(&sZ[lp], __float_as_uint(zc));
+// Steps 3 and 4 for one channel from its coefficients in v (the accumulators
+// cleared by the caller): bin values, the resolve pass, and the channel's
+// composite out of its sums, its total step S and its background bg.
+template <int J, bool DEF>
+__device__ __forceinline__ void resolve_channel_px(const Params &p, const float *alpha, const float *col,
+                                                   const Tile &T, unsigned char *smem, const unsigned *z,
+                                                   int64_t gp, float (&v)[1 << J], float S, float bg, float &o,
+                                                   float &cover_sum) {
+    constexpr int LDV = Shape<J>::LDV;
+    const uint32_t flags = DEF ? kDefaultFlags : p.flags;
+    const int npx = p.g.tile_w * p.g.tile_h, lp = threadIdx.x;
+    float *vals = reinterpret_cast<float *>(smem);
+    float2 *accw = reinterpret_cast<float2 *>(smem + Layout<J>::vplane(npx));
+    if (gp >= 0) {
+        coeffs_to_bins<J>(v, kLog2e);
+        put_bins<J>(vals + lp * LDV, v, __uint_as_float(z[lp]), flags);
     }
-    return retry;
+    __syncthreads();
+    Params pc = p;
+    pc.alpha = alpha;
+    pc.r = col;
+    resolve_channel<J, DEF>(pc, T, vals, accw);
+    __syncthreads();
+    if (gp >= 0) {
+        float2 a = accw[lp];
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) {
+            const float2 u = accw[w * npx + lp];
+            a.x += u.x;
+            a.y += u.y;
+        }
+        const float Tc = ex2(-S * kLog2e);
+        // 1 - T; for small S the series S (1 - S/2)
+        const float cover = S < 0.0009765625f ? S * fmaf(-0.5f, S, 1.f) : 1.f - Tc;
+        if (flags & kNormalized) {
+            if (a.y > 0.f) {
+                const float k = a.y >= 1.17549435e-38f ? cover * rcp(a.y) : cover / a.y;  // (subnormal W)
+                o = fmaf(a.x, k, bg * Tc);
+            } else {
+                o = bg;
+            }
+        } else {
+            o = fmaf(bg, Tc, a.x);
+        }
+        cover_sum += cover;
+    }
+    __syncthreads();  // accumulators read
 }
 
-template <int J>
-__global__ void __launch_bounds__(kThreads, 2) k_fused_rgb(RgbParams q) {
-    constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
+template <int J, bool E5, bool DEF, int MB>
+__global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
+    constexpr int C = Shape<J>::C;
+    using L = RgbLayout<J, E5>;
+    using St = Staged<float, C>;
     extern __shared__ __align__(16) unsigned char smem[];
     const Params &p = q.p;
     const int npx = p.g.tile_w * p.g.tile_h;
-    const size_t pl = RgbLayout<J>::plane(npx), vpl = RgbLayout<J>::vplane(npx), wd = RgbLayout<J>::words(npx);
-    unsigned *planes = reinterpret_cast<unsigned *>(smem);  // 6 bins planes, later 3 value planes
-    float *vals = reinterpret_cast<float *>(smem);
-    float4 *accw = reinterpret_cast<float4 *>(smem + kCh * vpl);
-    float *sS = reinterpret_cast<float *>(smem + kCh * vpl + RgbLayout<J>::accw(npx));  // 3 word planes
-    unsigned *sZ = reinterpret_cast<unsigned *>(smem + RgbLayout<J>::region(npx));
+    uint4 *stage = reinterpret_cast<uint4 *>(smem + Layout<J>::vplane(npx));  // rows out, then (R, W)
+    const int after = (int)L::after(npx);
     const Tile T = tile_of(p, p.tile0 + (int)blockIdx.x, true);
-    fill_zero(smem, (int)(2 * kCh * pl));
-    for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
-    __syncthreads();
-    unsigned bad = 0;
-    const bool retry = bins_pass_rgb<J, false, true>(q, T, planes, pl, sZ, bad);
-    flush_bad(bad, p.err);
-    const bool scaled = __syncthreads_or(retry);
-    if (scaled) {
-        fill_zero(smem, (int)(2 * kCh * pl));
-        __syncthreads();
-        count_pass_rgb<J>(q, T, planes);
-        bins_pass_rgb<J, true, false>(q, T, planes, pl, sZ, bad);
-        __syncthreads();
+    // L2 prefetch of what the first build reads; each channel's pass fetches
+    // the next channel's arrays (FP32) or all of them (E5B9G9R9)
+    if (threadIdx.x == 0) {
+        l2_prefetch_range(p.pixel, T.s, T.e);
+        l2_prefetch_range(p.z, T.s, T.e);
+        l2_prefetch_range(q.alpha_c[0], T.s, T.e);
+        if (E5) {
+            l2_prefetch_range(q.alpha_c[1], T.s, T.e);
+            l2_prefetch_range(q.alpha_c[2], T.s, T.e);
+            l2_prefetch_range(p.r, T.s, T.e);
+            l2_prefetch_range(p.gc, T.s, T.e);
+            l2_prefetch_range(p.b, T.s, T.e);
+        }
     }
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
-    // coefficients of the three channels, rounded through the storage format
-    float co[kCh][C], S[kCh] = {0.f, 0.f, 0.f};
-    if (gp >= 0) {
-        // one scale for all three channels: 2^-27, or channel 0's row's 1 / s_p
-        const float inv = scaled ? __uint_as_float(planes[lp * LD + Shape<J>::INV]) : kBinInv;
-#pragma unroll
+    float v[C], o[kCh] = {0.f, 0.f, 0.f}, cover_sum = 0.f;
+    unsigned bad = 0;
+    auto bg_of = [&](int c) {
+        return p.bg_img && gp >= 0 ? p.bg_img[3 * gp + c] : (c == 0 ? p.bg0 : c == 1 ? p.bg1 : p.bg2);
+    };
+
+    if constexpr (!E5) {
+        // one channel at a time (not unrolled: the channels share the mono
+        // kernel's register budget)
+        unsigned *sZ = reinterpret_cast<unsigned *>(smem + L::zw(npx));
+        float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+#pragma unroll 1
         for (int c = 0; c < kCh; ++c) {
-            const unsigned *F = reinterpret_cast<const unsigned *>(smem + 2 * c * pl);
-            const unsigned *G = reinterpret_cast<const unsigned *>(smem + (2 * c + 1) * pl);
-            bins_to_coeffs_inv<J>(F + lp * LD, G + lp * LD, inv, co[c], S[c]);
-        }
-        if (q.e5) {
-            // E5B9G9R9 of each coefficient index (magnitudes: chi >= 0, X <= 0)
-#pragma unroll
-            for (int k = 0; k < C; ++k) {
-                const float sg = k == 0 ? 1.f : -1.f;
-                const uint32_t w = e5_encode(sg * co[0][k], sg * co[1][k], sg * co[2][k]);
-                if (p.coeff) static_cast<uint32_t *>(p.coeff)[gp * C + k] = w;
-                float r, g, b;
-                e5_decode(w, r, g, b);
-                co[0][k] = sg * r;
-                co[1][k] = sg * g;
-                co[2][k] = sg * b;
+            const float *alpha = c == 0 ? q.alpha_c[0] : c == 1 ? q.alpha_c[1] : q.alpha_c[2];
+            const float *col = c == 0 ? p.r : c == 1 ? p.gc : p.b;
+            float S = 0.f;
+            if (threadIdx.x == 0) {
+                l2_prefetch_range(col, T.s, T.e);
+                if (c < kCh - 1) l2_prefetch_range(c == 0 ? q.alpha_c[1] : q.alpha_c[2], T.s, T.e);
             }
-        } else if (p.coeff) {
-            float *dst = static_cast<float *>(p.coeff) + gp * kCh * C;
-#pragma unroll
-            for (int c = 0; c < kCh; ++c) store_row<float, C>(dst + c * C, co[c]);
-        }
-    }
-    __syncthreads();  // every bin row has been read
-    if (gp >= 0) {
-#pragma unroll
-        for (int c = 0; c < kCh; ++c) {
-            coeffs_to_bins<J>(co[c], kLog2e);
-            put_bins<J>(reinterpret_cast<float *>(reinterpret_cast<char *>(vals) + c * vpl) + lp * LDV, co[c],
-                        __uint_as_float(sZ[lp]), p.flags);
-            sS[c * (wd / 4) + lp] = S[c];
-        }
-    }
-    fill_zero(accw, (int)RgbLayout<J>::accw(npx));
-    __syncthreads();
-    // resolve the three channels
-    const uint32_t flags = p.flags;
-    float4 *mine = accw + (threadIdx.x >> 5) * 2 * npx;
-    const int nt = blockDim.x;
-    const int64_t rounds = (T.e - T.s + nt - 1) / nt;  // equal trip counts: warp collectives below
-    for (int64_t it = 0; it < rounds; ++it) {
-        const int64_t i = T.s + it * nt + threadIdx.x;
-        const bool v = i < T.e;
-        int l = -1;
-        float w[kCh] = {0.f, 0.f, 0.f}, col[kCh] = {0.f, 0.f, 0.f};
-        if (v) {
-            const float z = p.z[i];
-            float al[kCh];
-            bool nan = !(z == z);
-#pragma unroll
-            for (int c = 0; c < kCh; ++c) {
-                al[c] = q.alpha_c[c][i];
-                nan |= !(al[c] == al[c]);
+            build_channel<J>(p, alpha, T, smem, sZ, gp, v, S, bad);
+            float *dst = p.coeff ? static_cast<float *>(p.coeff) + c * q.plane : nullptr;
+            if (dst && St::ok) {
+                if (gp >= 0) stage_row<float, C>(stage, lp, v);
+                __syncthreads();
+                copy_staged<float, C>(p, T, stage, after, dst);  // clears the accumulators
+            } else {
+                if (dst && gp >= 0) store_row<float, C>(dst + gp * C, v);
+                fill_zero(stage, after);
             }
-            l = nan ? -1 : local_pixel(p.pixel[i], p, T);
-            if (l >= 0) {
-                col[0] = p.r[i];
-                col[1] = p.gc[i];
-                col[2] = p.b[i];
-                const float zc = clamp_depth(z);
+            float oc = 0.f;
+            resolve_channel_px<J, DEF>(p, alpha, col, T, smem, sZ, gp, v, S, bg_of(c), oc, cover_sum);
+            o0 = c == 0 ? oc : o0;
+            o1 = c == 1 ? oc : o1;
+            o2 = c == 2 ? oc : o2;
+        }
+        o[0] = o0;
+        o[1] = o1;
+        o[2] = o2;
+    } else {
+        uint4 *stash0 = reinterpret_cast<uint4 *>(smem + L::region(npx));
+        uint4 *stash1 = reinterpret_cast<uint4 *>(smem + L::region(npx) + L::rows(npx));
+        const int zs = (int)(Layout<J>::words(npx) / 4);
+        unsigned *sZ = reinterpret_cast<unsigned *>(smem + L::zw(npx));
+        uint32_t *words = static_cast<uint32_t *>(p.coeff);
+        float S[kCh] = {0.f, 0.f, 0.f};
+        build_channel<J>(p, q.alpha_c[0], T, smem, sZ, gp, v, S[0], bad);
+        if (gp >= 0) {
+            if constexpr (St::ok) stage_row<float, C>(stash0, lp, v);
+            else for (int k = 0; k < C; ++k) reinterpret_cast<float *>(stash0)[lp * C + k] = v[k];
+        }
+        build_channel<J>(p, q.alpha_c[1], T, smem, sZ + zs, gp, v, S[1], bad);
+        if (gp >= 0) {
+            if constexpr (St::ok) stage_row<float, C>(stash1, lp, v);
+            else for (int k = 0; k < C; ++k) reinterpret_cast<float *>(stash1)[lp * C + k] = v[k];
+        }
+        build_channel<J>(p, q.alpha_c[2], T, smem, sZ + 2 * zs, gp, v, S[2], bad);
+        // the words, index by index; the decoded values replace the FP32 ones
+        if (gp >= 0) {
+            if constexpr (St::ok) {
+                const int sw = St::sw(lp);
 #pragma unroll
-                for (int c = 0; c < kCh; ++c) {
-                    const float ac = clamp_alpha(al[c]);
-                    const float *row =
-                        reinterpret_cast<const float *>(reinterpret_cast<const char *>(vals) + c * vpl) + l * LDV;
-                    const float Ah = absorbance_at<J>(row, zc, -lg2(1.f - ac), flags);
-                    w[c] = ac * ex2(-Ah);
+                for (int ch = 0; ch < St::K; ++ch) {
+                    const int at = lp * St::K + (ch ^ sw);
+                    float4 r = reinterpret_cast<const float4 *>(stash0)[at];
+                    float4 g = reinterpret_cast<const float4 *>(stash1)[at];
+                    uint4 w;
+                    w.x = pack_index(4 * ch, r.x, g.x, v[4 * ch]);
+                    w.y = pack_index(4 * ch + 1, r.y, g.y, v[4 * ch + 1]);
+                    w.z = pack_index(4 * ch + 2, r.z, g.z, v[4 * ch + 2]);
+                    w.w = pack_index(4 * ch + 3, r.w, g.w, v[4 * ch + 3]);
+                    reinterpret_cast<float4 *>(stash0)[at] = r;
+                    reinterpret_cast<float4 *>(stash1)[at] = g;
+                    if (words) stage[at] = w;
+                }
+            } else {
+                float *r = reinterpret_cast<float *>(stash0) + lp * C;
+                float *g = reinterpret_cast<float *>(stash1) + lp * C;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const uint32_t w = pack_index(k, r[k], g[k], v[k]);
+                    if (words) words[gp * C + k] = w;
                 }
             }
         }
-        warp_accumulate8(mine, l, make_float4(col[0] * w[0], col[1] * w[1], col[2] * w[2], w[0]),
-                         make_float4(w[1], w[2], 0.f, 0.f));
-    }
-    __syncthreads();
-    if (gp >= 0) {
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-        for (int wp = 0; wp < kWarps; ++wp) {
-            const float4 u0 = accw[wp * 2 * npx + 2 * lp], u1 = accw[wp * 2 * npx + 2 * lp + 1];
-            a0.x += u0.x, a0.y += u0.y, a0.z += u0.z, a0.w += u0.w;
-            a1.x += u1.x, a1.y += u1.y;
+        if (words && St::ok) {
+            __syncthreads();
+            copy_staged<float, C>(p, T, stage, after, reinterpret_cast<float *>(words));
+        } else {
+            fill_zero(stage, after);
         }
-        const float R[kCh] = {a0.x, a0.y, a0.z}, W[kCh] = {a0.w, a1.x, a1.y};
-        const float bg[kCh] = {p.bg_img ? p.bg_img[3 * gp] : p.bg0, p.bg_img ? p.bg_img[3 * gp + 1] : p.bg1,
-                               p.bg_img ? p.bg_img[3 * gp + 2] : p.bg2};
-        float o[kCh], cover_sum = 0.f;
+        resolve_channel_px<J, DEF>(p, q.alpha_c[2], p.b, T, smem, sZ + 2 * zs, gp, v, S[2], bg_of(2), o[2],
+                                   cover_sum);
 #pragma unroll
-        for (int c = 0; c < kCh; ++c) {
-            const float Sc = sS[c * (wd / 4) + lp];
-            const float Tc = ex2(-Sc * kLog2e);
-            const float cover = Sc < 0.0009765625f ? Sc * fmaf(-0.5f, Sc, 1.f) : 1.f - Tc;
-            cover_sum += cover;
-            if (flags & kNormalized) {
-                o[c] = W[c] > 0.f ? fmaf(R[c], cover / W[c], bg[c] * Tc) : bg[c];
-            } else {
-                o[c] = fmaf(bg[c], Tc, R[c]);
+        for (int c = 1; c >= 0; --c) {
+            if (gp >= 0) {
+                const uint4 *src = c == 0 ? stash0 : stash1;
+                if constexpr (St::ok) unstage_row<float, C>(src, lp, v);
+                else for (int k = 0; k < C; ++k) v[k] = reinterpret_cast<const float *>(src)[lp * C + k];
             }
+            fill_zero(stage, after);
+            resolve_channel_px<J, DEF>(p, q.alpha_c[c], c == 0 ? p.r : p.gc, T, smem, sZ + c * zs, gp, v, S[c],
+                                       bg_of(c), o[c], cover_sum);
         }
-        reinterpret_cast<float4 *>(p.out)[gp] = make_float4(o[0], o[1], o[2], cover_sum * (1.f / 3.f));
     }
+    flush_bad(bad, p.err);
+    if (gp >= 0) reinterpret_cast<float4 *>(p.out)[gp] = make_float4(o[0], o[1], o[2], cover_sum * (1.f / 3.f));
 }
 
-template <int J> cudaError_t launch_rgb(const RgbParams &q, int ntiles, cudaStream_t s) {
+// FP32 storage uses the mono kernel's shared memory and register budget (four
+// blocks per SM at J = 5 with 192-pixel tiles); E5B9G9R9 keeps two more
+// coefficient rows per pixel and takes fewer blocks.
+template <int J, bool E5, bool DEF> cudaError_t launch_rgb(const RgbParams &q, int ntiles, cudaStream_t s) {
+    constexpr int MB = E5 ? (J == 5 ? 2 : 3) : 4;
     const int npx = q.p.g.tile_w * q.p.g.tile_h;
-    const size_t bytes = RgbLayout<J>::total(npx);
+    const size_t bytes = RgbLayout<J, E5>::total(npx);
     if (bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_fused_rgb<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fused_rgb<J, E5, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_fused_rgb<J><<<ntiles, kThreads, bytes, s>>>(q);
+    k_fused_rgb<J, E5, DEF, MB><<<ntiles, kThreads, bytes, s>>>(q);
     return cudaGetLastError();
 }
 
 typedef cudaError_t (*RgbLaunch)(const RgbParams &, int, cudaStream_t);
-const RgbLaunch kRgb[5] = {launch_rgb<1>, launch_rgb<2>, launch_rgb<3>, launch_rgb<4>, launch_rgb<5>};
+#define WT_RGB_ROW(E5, DEF) \
+    { launch_rgb<1, E5, DEF>, launch_rgb<2, E5, DEF>, launch_rgb<3, E5, DEF>, launch_rgb<4, E5, DEF>, launch_rgb<5, E5, DEF> }
+const RgbLaunch kRgb[2][2][5] = {{WT_RGB_ROW(false, false), WT_RGB_ROW(false, true)},
+                                 {WT_RGB_ROW(true, false), WT_RGB_ROW(true, true)}};
+#undef WT_RGB_ROW
+
+template <int J> size_t rgb_bytes(int npx, bool e5) {
+    return e5 ? RgbLayout<J, true>::total(npx) : RgbLayout<J, false>::total(npx);
+}
 
 }  // namespace
 
 // Shared memory the coloured kernel needs for a tile of npx pixels at J.
-size_t rgb_smem_bytes(int J, int npx) {
+size_t rgb_smem_bytes(int J, int npx, bool e5) {
     switch (J) {
-    case 1: return RgbLayout<1>::total(npx);
-    case 2: return RgbLayout<2>::total(npx);
-    case 3: return RgbLayout<3>::total(npx);
-    case 4: return RgbLayout<4>::total(npx);
-    default: return RgbLayout<5>::total(npx);
+    case 1: return rgb_bytes<1>(npx, e5);
+    case 2: return rgb_bytes<2>(npx, e5);
+    case 3: return rgb_bytes<3>(npx, e5);
+    case 4: return rgb_bytes<4>(npx, e5);
+    default: return rgb_bytes<5>(npx, e5);
     }
 }
 
@@ -314,8 +356,8 @@ cudaError_t launch_fused_rgb(const Params &p, int J, const float *const alpha_c[
     RgbParams q;
     q.p = p;
     for (int c = 0; c < kCh; ++c) q.alpha_c[c] = alpha_c[c];
-    q.e5 = e5 ? 1 : 0;
-    return kRgb[J - 1](q, ntiles, s);
+    q.plane = (int64_t)p.g.width * p.g.height * (int64_t(1) << J);
+    return kRgb[e5 ? 1 : 0][p.flags == kDefaultFlags ? 1 : 0][J - 1](q, ntiles, s);
 }
 
 }  // namespace wt

@@ -412,8 +412,9 @@ __device__ __forceinline__ float step_of(float x) {
 // ---------------------------------------------------------------- streaming
 
 // Up to four consecutive fragments held by one thread.  Only the arrays a
-// phase asks for are loaded (the others stay unset and are optimised away).
-enum : int { kWithZ = 1, kWithRGB = 2 };
+// phase asks for are loaded (the others stay unset and are optimised away);
+// kWithR loads the r array alone (one colour component).
+enum : int { kWithZ = 1, kWithRGB = 2, kWithR = 4 };
 template <int N> struct Group {
     static constexpr int size = N;
     bool v;      // inside the range (all N fragments or none)
@@ -434,6 +435,7 @@ __device__ __forceinline__ void load_one(Group<1> &G, bool v, int64_t i, const P
         G.g[0] = v ? p.gc[i] : 0.f;
         G.b[0] = v ? p.b[i] : 0.f;
     }
+    if (LOAD & kWithR) G.r[0] = v ? p.r[i] : 0.f;
 }
 
 template <int LOAD>
@@ -449,6 +451,7 @@ __device__ __forceinline__ void load_four(Group<4> &G, bool v, int64_t q, const 
             gv = reinterpret_cast<const float4 *>(p.gc)[q];
             bv = reinterpret_cast<const float4 *>(p.b)[q];
         }
+        if (LOAD & kWithR) rv = reinterpret_cast<const float4 *>(p.r)[q];
     }
     G.v = v;
     G.i0 = 4 * q;

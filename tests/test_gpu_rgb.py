@@ -33,7 +33,7 @@ def test_coloured_fp32_matches_the_oracle(J, tile):
     a = [torch.from_numpy(x).to(DEV) for x in ac]
     C = 1 << J
     out = torch.empty(fr.P, 4, device=DEV)
-    coeff = torch.empty(fr.P, 3, C, device=DEV)
+    coeff = torch.empty(3, fr.P, C, device=DEV)
     wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, wt.RGB_F32, bg=(0.2, 0.5, 0.8))
     assert wt.wt_get_error() == 0
     h = fr.numpy()
@@ -44,7 +44,7 @@ def test_coloured_fp32_matches_the_oracle(J, tile):
     for c in range(3):
         ref_c = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, J)
         fc = dataclasses.replace(fr, alpha=torch.from_numpy(ac[c]))
-        assert (np.abs(got[:, c, :] - ref_c) <= coeff_tol(fc)).all()
+        assert (np.abs(got[c] - ref_c) <= coeff_tol(fc)).all()
 
 
 def test_grey_opacity_equals_the_mono_method():
@@ -54,7 +54,7 @@ def test_grey_opacity_equals_the_mono_method():
     g = fr.to(DEV)
     d = desc_of(fr)
     out = torch.empty(fr.P, 4, device=DEV)
-    coeff = torch.empty(fr.P, 3, 16, device=DEV)
+    coeff = torch.empty(3, fr.P, 16, device=DEV)
     wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, g.alpha, g.alpha, out, coeff, wt.RGB_F32, bg=fr.bg)
     mono = torch.empty(fr.P, 4, device=DEV)
     mcoeff = torch.empty(fr.P, 16, device=DEV)
@@ -62,7 +62,7 @@ def test_grey_opacity_equals_the_mono_method():
     assert wt.wt_get_error() == 0
     torch.testing.assert_close(out, mono, atol=2e-6, rtol=0)
     for c in range(3):
-        assert torch.equal(coeff[:, c, :], mcoeff)
+        assert torch.equal(coeff[c], mcoeff)
 
 
 def test_coloured_e5b9g9r9_storage():
@@ -104,3 +104,63 @@ def test_coloured_arguments():
         wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, g.alpha, g.alpha, out, None, 7, bg=fr.bg)
     with pytest.raises(wt.WtError):
         wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, None, g.alpha, out, None, wt.RGB_F32, bg=fr.bg)
+
+
+def test_coloured_nan_opacity_leaves_the_fragment_out_of_that_channel_only():
+    """A NaN opacity in one channel drops the fragment from that channel's
+    build and resolve alone, and is counted once in the error word."""
+    fr = synth.uniform_frame(96, 40, 8.0, 40, J=4, seed=95, tile_w=128, tile_h=1)
+    ac = _coloured(fr, 5)
+    idx = np.random.default_rng(6).choice(fr.n, 25, replace=False)
+    ac[1][idx] = np.nan
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    out = torch.empty(fr.P, 4, device=DEV)
+    coeff = torch.empty(3, fr.P, 16, device=DEV)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, wt.RGB_F32, bg=fr.bg)
+    assert wt.wt_get_error() == 25
+    h = fr.numpy()
+    col = (h["r"], h["g"], h["b"])
+    ref = np.zeros((fr.P, 4))
+    for c in range(3):
+        keep = ~np.isnan(ac[c])
+        px, z, al = h["pixel"][keep], h["z"][keep], ac[c][keep]
+        co = oracle.build_coeffs(px, z, al, fr.P, 4)
+        o = oracle.resolve(px, z, al, (col[c][keep],) * 3, fr.P, 4, co, bg=(fr.bg[c],) * 3)[0]
+        ref[:, c] = o[:, 0]
+        ref[:, 3] += o[:, 3] / 3.0
+        fc = dataclasses.replace(fr, alpha=torch.from_numpy(np.nan_to_num(ac[c])))
+        assert (np.abs(coeff[c].cpu().numpy().astype(np.float64) - co) <= coeff_tol(fc)).all()
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_coloured_bg_image_and_256_pixel_tiles(fmt):
+    """A background image and the largest tile (256 pixels, 16 x 16) at J = 5."""
+    fr = synth.uniform_frame(48, 40, 6.0, 30, J=5, seed=97 + fmt, tile_w=16, tile_h=16)
+    ac = _coloured(fr, 7)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    bg_img = np.random.default_rng(8).random((fr.P, 3)).astype(np.float32)
+    out = torch.empty(fr.P, 4, device=DEV)
+    coeff = (torch.empty(3, fr.P, 32, device=DEV) if fmt == wt.RGB_F32
+             else torch.empty(fr.P, 32, device=DEV, dtype=torch.int32))
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg_img=torch.from_numpy(bg_img).to(DEV))
+    assert wt.wt_get_error() == 0
+    h = fr.numpy()
+    coeffs = None
+    if fmt == wt.RGB_E5B9G9R9:
+        dec = oracle.e5_decode(coeff.cpu().numpy().view(np.uint32))
+        sign = np.where(np.arange(32) == 0, 1.0, -1.0)
+        coeffs = [sign * dec[c] for c in range(3)]
+    ref = np.zeros((fr.P, 4))
+    for c in range(3):
+        co = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, 5) if coeffs is None else coeffs[c]
+        col = (h["r"], h["g"], h["b"])[c]
+        bgc = np.repeat(bg_img[:, c:c + 1], 3, axis=1)
+        o = oracle.resolve(h["pixel"], h["z"], ac[c], (col,) * 3, fr.P, 5, co, bg_img=bgc)[0]
+        ref[:, c] = o[:, 0]
+        ref[:, 3] += o[:, 3] / 3.0
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
