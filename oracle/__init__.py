@@ -339,3 +339,92 @@ def e5_decode(w):
     w = np.asarray(w, dtype=np.uint32).astype(np.uint64)
     scale = np.ldexp(1.0, (w >> 27).astype(np.int64) - 24)
     return tuple((((w >> s) & 511).astype(np.float64) * scale) for s in (0, 9, 18))
+
+
+# ---------------------------------------------------------------- chromatic aberration (§3)
+
+def _smoothstep(e0: float, e1: float, x):
+    """GLSL smoothstep written out: u = clamp((x - e0) / (e1 - e0), 0, 1),
+    u^2 (3 - 2u).  The formula is applied as written also when e0 > e1, as the
+    §3 listing does (the result then falls from 1 to 0)."""
+    u = np.clip((np.asarray(x, dtype=np.float64) - e0) / (e1 - e0), 0.0, 1.0)
+    return u * u * (3.0 - 2.0 * u)
+
+
+def spectral_weights(taps: int) -> np.ndarray:
+    """[taps, 3] colour weights of the chromatic-aberration gather (§3).  Tap i
+    sits at t_i = i / (taps - 1) along the segment (the listing's printed
+    t = 1/2 + 2i/(k-1) leaves [0, 1] after the first tap, so the taps are read as
+    spread evenly over [0, 1]); w_r = smoothstep(1/2, 1/3, t),
+    w_b = smoothstep(1/2, 2/3, t), w_g = 1 - w_r - w_b.  One tap: weight 1."""
+    if taps == 1:
+        return np.ones((1, 3))
+    t = np.arange(taps) / (taps - 1)
+    wr = _smoothstep(0.5, 1.0 / 3.0, t)
+    wb = _smoothstep(0.5, 2.0 / 3.0, t)
+    return np.stack([wr, 1.0 - wr - wb, wb], axis=1)
+
+
+def tap_scales(taps: int, dispersion: float) -> np.ndarray:
+    """Positions of the taps along the refraction offset d, as multiples of d:
+    a segment centred on the refracted sample point p + d, of length
+    dispersion * |d| (proportional to the refraction, §3): s_i = 1 +
+    dispersion (t_i - 1/2)."""
+    if taps == 1:
+        return np.ones(1)
+    t = np.arange(taps) / (taps - 1)
+    return 1.0 + dispersion * (t - 0.5)
+
+
+def bilinear(img, width: int, height: int, x, y) -> np.ndarray:
+    """Bilinear sample of an RGB image [P, 3] at continuous pixel positions
+    (x, y) (texel (i, j) centred at (i + 1/2, j + 1/2)), clamped to the edge."""
+    img = np.asarray(img, dtype=np.float64).reshape(height * width, 3)
+    fx, fy = np.asarray(x, dtype=np.float64) - 0.5, np.asarray(y, dtype=np.float64) - 0.5
+    x0, y0 = np.floor(fx), np.floor(fy)
+    ax, ay = (fx - x0)[..., None], (fy - y0)[..., None]
+    i0 = np.clip(x0, 0, width - 1).astype(np.int64)
+    i1 = np.clip(x0 + 1, 0, width - 1).astype(np.int64)
+    j0 = np.clip(y0, 0, height - 1).astype(np.int64)
+    j1 = np.clip(y0 + 1, 0, height - 1).astype(np.int64)
+    s = lambda i, j: img[j * width + i]
+    return ((1 - ax) * (1 - ay) * s(i0, j0) + ax * (1 - ay) * s(i1, j0)
+            + (1 - ax) * ay * s(i0, j1) + ax * ay * s(i1, j1))
+
+
+def ca_background(bg_img, offset, width: int, height: int, dispersion: float, taps: int) -> np.ndarray:
+    """The background seen through the transparent layers with chromatic
+    aberration (§3): instead of one bilinear sample at the refracted point
+    p + d, `taps` samples along the segment of tap_scales, each channel the
+    weighted mean of the samples under its spectral weight.  A pixel whose
+    offset is not finite takes the unshifted background."""
+    P = width * height
+    d = np.asarray(offset, dtype=np.float64).reshape(P, 2).copy()
+    bad = ~np.isfinite(d).all(axis=1)
+    d[bad] = 0.0
+    px = np.arange(P)
+    x, y = px % width + 0.5, px // width + 0.5
+    w = spectral_weights(taps)
+    acc = np.zeros((P, 3))
+    for i, s in enumerate(tap_scales(taps, dispersion)):
+        acc += w[i] * bilinear(bg_img, width, height, x + s * d[:, 0], y + s * d[:, 1])
+    return acc / w.sum(axis=0)
+
+
+def composite_ca(accum, bg_img, offset, width: int, height: int, dispersion: float = 0.5, taps: int = 5,
+                 flags=DEFAULT_FLAGS) -> np.ndarray:
+    """§2.1 step 4 with the chromatic-aberration background of §3: the
+    composite of `resolve`'s accumulators (accum [P, 6] = R', G', B', W', S, Amin)
+    over ca_background instead of the background pixel."""
+    a = np.asarray(accum, dtype=np.float64)
+    bgc = ca_background(bg_img, offset, width, height, dispersion, taps)
+    R, W, S, Amin = a[:, :3], a[:, 3:4], a[:, 4:5], a[:, 5:6]
+    T = np.exp(-S)
+    out = np.zeros((a.shape[0], 4))
+    if flags & RESOLVE_NORMALIZED:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out[:, :3] = np.where(W > 0, R / np.where(W > 0, W, 1.0) * (1.0 - T) + bgc * T, bgc)
+    else:
+        out[:, :3] = R * np.exp(-Amin) + bgc * T
+    out[:, 3] = 1.0 - T[:, 0]
+    return out

@@ -533,3 +533,94 @@ def test_coloured_composite_reduces_to_mono_for_grey_opacity():
     mono = o.composite(pixel, z, al, rgb, P, 4)
     col = o.composite_rgb(pixel, z, (al, al, al), rgb, P, 4)
     np.testing.assert_allclose(col, mono, atol=1e-12)
+
+
+# ---------------------------------------------------------------- chromatic aberration (§3)
+
+def test_spectral_weights_hand_values():
+    """Worked by hand from the smoothstep formula with t_i = i/(k-1): at k = 5
+    the taps fall on t = 0, 1/4, 1/2, 3/4, 1, where every smoothstep is at an
+    end (red on the first two taps, green in the middle, blue on the last two);
+    at k = 9, t = 3/8 gives u = (3/8 - 1/2)/(1/3 - 1/2) = 3/4 and
+    u^2 (3 - 2u) = 27/32 of red, the rest green."""
+    np.testing.assert_array_equal(o.spectral_weights(5), [[1, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 1]])
+    w9 = o.spectral_weights(9)
+    np.testing.assert_allclose(w9[3], [27 / 32, 5 / 32, 0], atol=1e-15)
+    np.testing.assert_allclose(w9[5], [0, 5 / 32, 27 / 32], atol=1e-15)
+    np.testing.assert_array_equal(w9[4], [0, 1, 0])
+    for k in (3, 5, 7, 9, 15):
+        w = o.spectral_weights(k)
+        np.testing.assert_allclose(w.sum(axis=1), 1.0, atol=1e-15)
+        assert (w >= 0).all() and (w.sum(axis=0) > 0).all()
+        np.testing.assert_allclose(w[::-1, 0], w[:, 2], atol=1e-15)  # red and blue mirror
+    np.testing.assert_allclose(o.tap_scales(5, 0.5), [0.75, 0.875, 1.0, 1.125, 1.25])
+
+
+def test_bilinear_hand_example():
+    """A 2 x 2 image: a texel centre returns the texel, the shared corner the
+    mean of the four, a quarter step the 3:1 mix, and points outside the image
+    the clamped edge."""
+    img = np.array([[0.0, 1.0, 2.0], [4.0, 5.0, 6.0], [8.0, 9.0, 10.0], [12.0, 13.0, 14.0]])
+    b = lambda x, y: o.bilinear(img, 2, 2, np.array([x]), np.array([y]))[0]
+    np.testing.assert_allclose(b(0.5, 0.5), img[0])
+    np.testing.assert_allclose(b(1.5, 1.5), img[3])
+    np.testing.assert_allclose(b(1.0, 1.0), img.mean(axis=0))
+    np.testing.assert_allclose(b(0.75, 0.5), 0.75 * img[0] + 0.25 * img[1])
+    np.testing.assert_allclose(b(-7.0, 0.5), img[0])
+    np.testing.assert_allclose(b(1.5, 99.0), img[3])
+
+
+def _ca_frame(seed, W=12, H=9, n=500):
+    rng = np.random.default_rng(seed)
+    P = W * H
+    pix, z, al, rgb = _rand_frags(rng, n, P)
+    bg = rng.random((P, 3))
+    co = o.build_coeffs(pix, z, al, P, 4)
+    out, acc = o.resolve(pix, z, al, rgb, P, 4, co, bg_img=bg)
+    return rng, P, bg, out, acc
+
+
+def test_ca_zero_offset_is_the_plain_composite():
+    """With no refraction every tap samples the pixel's own texel, so the
+    gather returns the background pixel and the composite is step 4's."""
+    for taps in (1, 5, 9):
+        rng, P, bg, out, acc = _ca_frame(11)
+        got = o.composite_ca(acc, bg, np.zeros((P, 2)), 12, 9, 0.5, taps)
+        np.testing.assert_allclose(got, out, atol=1e-12)
+
+
+def test_ca_constant_background_ignores_the_offset():
+    rng, P, _, _, acc = _ca_frame(12)
+    bg = np.tile([0.2, 0.4, 0.9], (P, 1))
+    d = rng.normal(0, 30, (P, 2))
+    flat = o.composite_ca(acc, bg, np.zeros((P, 2)), 12, 9)
+    np.testing.assert_allclose(o.composite_ca(acc, bg, d, 12, 9), flat, atol=1e-12)
+
+
+def test_ca_linear_ramp_closed_form():
+    """Bilinear interpolation of a linear image is exact, so each channel is
+    the ramp at its weighted mean tap position: red (taps 0, 1 at s = 1 - sigma/2
+    and 1 - sigma/4) at p + d (1 - 3 sigma/8), green at p + d, blue at
+    p + d (1 + 3 sigma/8)."""
+    W, H, sigma = 40, 30, 0.6
+    P = W * H
+    px = np.arange(P)
+    x, y = px % W + 0.5, px // W + 0.5
+    ramp = lambda c, xx, yy: [0.01, 0.03, -0.02][c] * xx + [0.02, -0.01, 0.015][c] * yy + 0.5
+    bg = np.stack([ramp(c, x, y) for c in range(3)], axis=1)
+    rng = np.random.default_rng(13)
+    d = rng.uniform(-3, 3, (P, 2))
+    inner = (x > 8) & (x < W - 8) & (y > 8) & (y < H - 8)  # every tap stays inside
+    got = o.ca_background(bg, d, W, H, sigma, 5)
+    for c, s in enumerate((1 - 3 * sigma / 8, 1.0, 1 + 3 * sigma / 8)):
+        want = ramp(c, x + s * d[:, 0], y + s * d[:, 1])
+        np.testing.assert_allclose(got[inner, c], want[inner], atol=1e-12)
+
+
+def test_ca_nonfinite_offset_takes_the_pixel_background():
+    rng, P, bg, out, acc = _ca_frame(14)
+    d = rng.normal(0, 2, (P, 2))
+    d[3] = [np.nan, 0.0]
+    d[7] = [np.inf, 1.0]
+    got = o.ca_background(bg, d, 12, 9, 0.5, 5)
+    np.testing.assert_allclose(got[[3, 7]], bg[[3, 7]], atol=1e-15)
