@@ -349,6 +349,41 @@ def run_wt(args):
         variants["coloured"] = col
         del ac, o3
 
+    # ---- the chromatic-aberration composite (§3) over this frame's accumulators:
+    # a background image and a smooth refraction-offset field of up to 8 pixels;
+    # bytes per pixel: accumulators 20, offset 8, background 12 (read once), out 16
+    if not args.no_variants:
+        zm = torch.empty(P, device=dev)
+        acc = torch.empty(P, 5, device=dev)
+        wt.wt_build(desc, frags, coeff, zm, stream=stream)
+        wt.wt_resolve(desc, frags, coeff, zm, acc, stream=stream)
+        g = torch.Generator(device=dev)
+        g.manual_seed(args.seed + 7)
+        bg_img = torch.rand(P, 3, device=dev, generator=g)
+        yy = torch.arange(fr.height, device=dev, dtype=torch.float32)[:, None].expand(fr.height, fr.width)
+        xx = torch.arange(fr.width, device=dev, dtype=torch.float32)[None, :].expand(fr.height, fr.width)
+        offset = torch.stack([8.0 * torch.sin(yy / 57.0), 8.0 * torch.cos(xx / 43.0)], dim=-1).reshape(P, 2)
+        offset = offset.contiguous()
+        o_ca = torch.empty(P, 4, device=dev)
+        ca = {}
+        for taps in (1, 5):
+            def ca_step(taps=taps):
+                wt.wt_composite_ca(desc, acc, bg_img, o_ca, offset, 0.5, taps, stream=stream)
+            for _ in range(3):
+                ca_step()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(20):
+                ca_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 20
+            ca[f"taps{taps}"] = {"ms": round(ms, 4), "pixels_per_s": P / (ms / 1e3), "alg_bytes": 56 * P,
+                                 "frac_hbm": round(56 * P / (ms / 1e3) / 1e9 / hbm, 4)}
+        assert wt.wt_get_error(stream) == 0
+        variants["chromatic_aberration"] = ca
+        del zm, acc, bg_img, offset, o_ca, xx, yy
+
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:

@@ -170,6 +170,34 @@ wt_status wt_resolve(const wt_desc *desc, const wt_frags *frags, const void *coe
 wt_status wt_composite(const wt_desc *desc, const float *accum, const float *bg_img,
                        const float bg[3], float *out, wt_stream stream);
 
+/*
+ * wt_composite_ca -- step 4 (§2.1) with the chromatic-aberration approximation
+ * of §3.  The background term samples bg_img not once at the refracted point
+ * p + d (d = offset[p], the pixel's screen-space refraction offset in pixels,
+ * accumulated by the caller during shading) but at `taps` points along a
+ * segment aligned with d and proportional to it:
+ *   x_i = p + s_i d,  s_i = 1 + dispersion (t_i - 1/2),  t_i = i / (taps - 1),
+ * bilinear samples (texel centres at integer + 1/2, clamped to the edge),
+ * and each channel is the mean of the samples under its spectral weight,
+ *   w_r = smoothstep(1/2, 1/3, t), w_b = smoothstep(1/2, 2/3, t),
+ *   w_g = 1 - w_r - w_b
+ * (§3's listing with the taps spread over t in [0, 1]; the smoothstep formula
+ * is applied as written for the falling edge).  Then rgb and alpha as in
+ * wt_composite with that background.
+ *   accum      [P * 5] from wt_resolve.
+ *   bg_img     [P * 3] float background image (required).
+ *   offset     [P * 2] float (dx, dy), 8-byte aligned, nullable (no offset).
+ *              A non-finite offset is replaced by 0 and counted in the error
+ *              word.
+ *   dispersion >= 0: the segment's length as a fraction of |d|.
+ *   taps       1 (the single refracted sample) or odd, 3..15 (the paper: 5).
+ *   out        [P * 4] float RGBA.
+ * Only width, height and WT_RESOLVE_NORMALIZED of desc are used.
+ */
+wt_status wt_composite_ca(const wt_desc *desc, const float *accum, const float *bg_img,
+                          const float *offset, float dispersion, int32_t taps, float *out,
+                          wt_stream stream);
+
 /* wt_resolve followed by wt_composite in one kernel (no accum buffer). */
 wt_status wt_resolve_composite(const wt_desc *desc, const wt_frags *frags, const void *coeff,
                                const float *zmin, const float *bg_img, const float bg[3],

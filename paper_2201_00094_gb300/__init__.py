@@ -26,7 +26,7 @@ __all__ = [
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
     "WtServeInfo", "wt_build_resolve_batch_static", "wt_bin_workspace_bytes", "wt_bin",
     "wt_depth_bounds", "wt_normalize_depth", "wt_build_resolve_tiles", "wt_build_resolve_single_pass",
-    "WtParticles", "wt_raster", "RGB_F32", "RGB_E5B9G9R9", "wt_build_resolve_rgb",
+    "WtParticles", "wt_raster", "RGB_F32", "RGB_E5B9G9R9", "wt_build_resolve_rgb", "wt_composite_ca",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
         "wt_build": ([D, Fr, vp, vp, vp], ctypes.c_int),
         "wt_resolve": ([D, Fr, vp, vp, vp, vp], ctypes.c_int),
         "wt_composite": ([D, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_composite_ca": ([D, vp, vp, vp, ctypes.c_float, ctypes.c_int32, vp, vp], ctypes.c_int),
         "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_tiles": ([D, Fr, i64, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -303,6 +304,18 @@ def wt_build_resolve_rgb(desc: WtDesc, frags: WtFrags, alpha_r: torch.Tensor, al
     _call("wt_build_resolve_rgb", ctypes.byref(desc), ctypes.byref(frags), _dev(alpha_r, "alpha_r", f32),
           _dev(alpha_g, "alpha_g", f32), _dev(alpha_b, "alpha_b", f32), _dev(coeff, "coeff", cdt),
           int(coeff_format), _dev(bg_img, "bg_img", f32), _bg(bg), _dev(out, "out", f32), _stream(stream))
+
+
+def wt_composite_ca(desc: WtDesc, accum: torch.Tensor, bg_img: torch.Tensor, out: torch.Tensor,
+                    offset: Optional[torch.Tensor] = None, dispersion: float = 0.5, taps: int = 5,
+                    stream=None) -> None:
+    """Composite with the chromatic-aberration background gather (wt_composite_ca):
+    accum [P, 5] from wt_resolve, bg_img [P, 3], offset [P, 2] refraction offsets
+    in pixels (None: no offset)."""
+    f32 = (torch.float32,)
+    _call("wt_composite_ca", ctypes.byref(desc), _dev(accum, "accum", f32), _dev(bg_img, "bg_img", f32),
+          _dev(offset, "offset", f32), ctypes.c_float(dispersion), int(taps), _dev(out, "out", f32),
+          _stream(stream))
 
 
 def wt_build_resolve_batch_static(descs: Sequence[WtDesc], frags: Sequence[WtFrags],

@@ -213,7 +213,6 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
         // one channel at a time (not unrolled: the channels share the mono
         // kernel's register budget)
         unsigned *sZ = reinterpret_cast<unsigned *>(smem + L::zw(npx));
-        float o0 = 0.f, o1 = 0.f, o2 = 0.f;
 #pragma unroll 1
         for (int c = 0; c < kCh; ++c) {
             const float *alpha = c == 0 ? q.alpha_c[0] : c == 1 ? q.alpha_c[1] : q.alpha_c[2];
@@ -233,15 +232,17 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
                 if (dst && gp >= 0) store_row<float, C>(dst + gp * C, v);
                 fill_zero(stage, after);
             }
-            float oc = 0.f;
-            resolve_channel_px<J, DEF>(p, alpha, col, T, smem, sZ, gp, v, S, bg_of(c), oc, cover_sum);
-            o0 = c == 0 ? oc : o0;
-            o1 = c == 1 ? oc : o1;
-            o2 = c == 2 ? oc : o2;
+            // the channel's result goes to its component of out at once, and the
+            // coverage sum to out.w (read back by the same thread), so that
+            // nothing stays live from one channel to the next
+            float oc = 0.f, cs = 0.f;
+            resolve_channel_px<J, DEF>(p, alpha, col, T, smem, sZ, gp, v, S, bg_of(c), oc, cs);
+            if (gp >= 0) {
+                float *px = p.out + 4 * gp;
+                px[c] = oc;
+                px[3] = c == 0 ? cs : (c == 1 ? px[3] + cs : (px[3] + cs) * (1.f / 3.f));
+            }
         }
-        o[0] = o0;
-        o[1] = o1;
-        o[2] = o2;
     } else {
         uint4 *stash0 = reinterpret_cast<uint4 *>(smem + L::region(npx));
         uint4 *stash1 = reinterpret_cast<uint4 *>(smem + L::region(npx) + L::rows(npx));
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
         }
     }
     flush_bad(bad, p.err);
-    if (gp >= 0) reinterpret_cast<float4 *>(p.out)[gp] = make_float4(o[0], o[1], o[2], cover_sum * (1.f / 3.f));
+    if (E5 && gp >= 0) reinterpret_cast<float4 *>(p.out)[gp] = make_float4(o[0], o[1], o[2], cover_sum * (1.f / 3.f));
 }
 
 // FP32 storage uses the mono kernel's shared memory and register budget (four
