@@ -297,6 +297,83 @@ def raster_particles(width: int, height: int, cx, cy, radius, z, alpha, r=None, 
     return out
 
 
+def raster_triangles(width: int, height: int, x, y, z, alpha, r=None, g=None, b=None):
+    """Fragments of screen-space triangles (glass panes: two per quad), in
+    triangle order and row-major inside a triangle.  Vertex k of triangle i is
+    (x, y, z)[3i + k]; opacity and colour are per triangle.
+
+    Coverage is decided exactly: the vertices are snapped to 1/256 pixel,
+    X = rint(256 x), and pixel (px, py) is covered when its centre
+    C = (256 px + 128, 256 py + 128) is inside, with the edge functions in
+    integers, E(A->B) = (Bx - Ax)(Cy - Ay) - (By - Ay)(Cx - Ax), on the
+    triangle wound so that its area E(v0->v1)(v2) is positive: every E > 0, or
+    E = 0 on an edge with dy < 0, or dy = 0 and dx > 0 (the edge the centre
+    would enter when moved right and infinitesimally down, so that a centre on
+    an edge or vertex shared by triangles that tile the plane belongs to
+    exactly one of them).  Zero-area triangles, non-finite vertices and vertices
+    at |x| or |y| >= 2^22 give no fragments.  Depth at the centre from the
+    barycentric weights e_k = float32(E_k) opposite vertex k:
+    z = ((e0 z0 + e1 z1) + e2 z2) / float32(area), each operation one FP32
+    rounding."""
+    f = np.float32
+    x, y, z, alpha = (np.asarray(v, dtype=f) for v in (x, y, z, alpha))
+    cols = {"pixel": [], "z": [], "alpha": []}
+    rgb = r is not None
+    if rgb:
+        r, g, b = (np.asarray(v, dtype=f) for v in (r, g, b))
+        cols.update(r=[], g=[], b=[])
+    lim = f(4194304.0)  # 2^22
+    for i in range(len(alpha)):
+        vx, vy, vz = x[3 * i:3 * i + 3], y[3 * i:3 * i + 3], z[3 * i:3 * i + 3].copy()
+        if not (np.all(np.abs(vx) < lim) and np.all(np.abs(vy) < lim)):
+            continue  # also rejects NaN
+        X = [int(np.rint(v * f(256))) for v in vx]
+        Y = [int(np.rint(v * f(256))) for v in vy]
+        area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0])
+        if area == 0:
+            continue
+        if area < 0:
+            X[1], X[2] = X[2], X[1]
+            Y[1], Y[2] = Y[2], Y[1]
+            vz[1], vz[2] = vz[2], vz[1]
+            area = -area
+        x0 = max(0, (min(X) - 128) // 256)
+        x1 = min(width - 1, (max(X) - 128) // 256 + 1)
+        y0 = max(0, (min(Y) - 128) // 256)
+        y1 = min(height - 1, (max(Y) - 128) // 256 + 1)
+        if x1 < x0 or y1 < y0:
+            continue
+        edges = [(1, 2), (2, 0), (0, 1)]  # edge k is opposite vertex k
+        for py in range(y0, y1 + 1):
+            cy = 256 * py + 128
+            for px in range(x0, x1 + 1):
+                cx = 256 * px + 128
+                E = []
+                inside = True
+                for a_, b_ in edges:
+                    dx, dy = X[b_] - X[a_], Y[b_] - Y[a_]
+                    e = dx * (cy - Y[a_]) - dy * (cx - X[a_])
+                    if e < 0 or (e == 0 and not (dy < 0 or (dy == 0 and dx > 0))):
+                        inside = False
+                        break
+                    E.append(e)
+                if not inside:
+                    continue
+                e0, e1, e2 = (f(v) for v in E)
+                zz = f(f(f(e0 * vz[0]) + f(e1 * vz[1])) + f(e2 * vz[2])) / f(area)
+                cols["pixel"].append(np.array([py * width + px], dtype=np.int64))
+                cols["z"].append(np.array([zz], dtype=f))
+                cols["alpha"].append(np.array([alpha[i]], dtype=f))
+                if rgb:
+                    for k, v in (("r", r), ("g", g), ("b", b)):
+                        cols[k].append(np.array([v[i]], dtype=f))
+    out = {}
+    for k, v in cols.items():
+        dt = np.int64 if k == "pixel" else f
+        out[k] = np.concatenate(v).astype(dt) if v else np.zeros(0, dtype=dt)
+    return out
+
+
 def composite_rgb(pixel, z, alpha_c, rgb, P: int, J: int, flags=DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5),
                   coeffs=None) -> np.ndarray:
     """Coloured absorbance: channel c is the mono method with its own opacity

@@ -624,3 +624,81 @@ def test_ca_nonfinite_offset_takes_the_pixel_background():
     d[7] = [np.inf, 1.0]
     got = o.ca_background(bg, d, 12, 9, 0.5, 5)
     np.testing.assert_allclose(got[[3, 7]], bg[[3, 7]], atol=1e-15)
+
+
+# ---------------------------------------------------------------- triangle rasteriser
+
+def test_raster_tri_quad_is_its_half_open_rectangle():
+    """A rectangle [x0, x1) x [y0, y1) cut into two triangles (either diagonal,
+    either winding) covers exactly the pixel centres c with x0 <= cx < x1 and
+    y0 <= cy < y1, each once: centres on the left and top sides are entered by
+    a move right and down, those on the right and bottom sides are left."""
+    rng = np.random.default_rng(40)
+    W, H = 24, 20
+    for it in range(40):
+        xa, xb = sorted(rng.choice(np.arange(0, W * 2 + 1) / 2.0, 2, replace=False))
+        ya, yb = sorted(rng.choice(np.arange(0, H * 2 + 1) / 2.0, 2, replace=False))
+        if it % 2:
+            x = [xa, xb, xb, xa, xb, xa]
+            y = [ya, ya, yb, ya, yb, yb]
+        else:
+            x = [xa, xb, xa, xb, xb, xa]
+            y = [ya, ya, yb, ya, yb, yb]
+        if it % 3 == 0:  # reverse the winding of the first triangle
+            x[1], x[2], y[1], y[2] = x[2], x[1], y[2], y[1]
+        out = o.raster_triangles(W, H, x, y, [0.3] * 6, [0.5, 0.5])
+        px = np.sort(out["pixel"])
+        cx = np.arange(W) + 0.5
+        cy = np.arange(H) + 0.5
+        want = [yy * W + xx for yy in range(H) for xx in range(W)
+                if xa <= cx[xx] < xb and ya <= cy[yy] < yb]
+        np.testing.assert_array_equal(px, np.sort(want))
+
+
+def test_raster_tri_fan_is_watertight():
+    """Triangles fanned around a vertex on a pixel centre tile a polygon: no
+    centre is covered twice, the shared vertex exactly once, and every centre
+    well inside the polygon once."""
+    W, H = 40, 40
+    cx, cy = 20.5, 19.5
+    N = 7
+    ang = np.sort(np.random.default_rng(41).uniform(0, 2 * np.pi, N))
+    rad = np.random.default_rng(42).uniform(9, 16, N)
+    px_, py_ = cx + rad * np.cos(ang), cy + rad * np.sin(ang)
+    x, y = [], []
+    for k in range(N):
+        j = (k + 1) % N
+        x += [cx, px_[k], px_[j]]
+        y += [cy, py_[k], py_[j]]
+    out = o.raster_triangles(W, H, x, y, [0.1] * (3 * N), [0.4] * N)
+    cnt = np.bincount(out["pixel"], minlength=W * H)
+    assert cnt.max() == 1
+    assert cnt[int(cy) * W + int(cx)] == 1
+    # centres within 8 pixels of the centre vertex are inside the polygon (every vertex is >= 9 away
+    # and the gaps between consecutive rays are below pi)
+    if np.max(np.diff(np.concatenate([ang, [ang[0] + 2 * np.pi]]))) < 2.0:
+        yy, xx = np.divmod(np.arange(W * H), W)
+        near = (xx + 0.5 - cx) ** 2 + (yy + 0.5 - cy) ** 2 < 9.0
+        assert (cnt[near] == 1).all()
+
+
+def test_raster_tri_depth_is_the_plane():
+    """Depth interpolated at the centres of a triangle lying in the plane
+    z = 0.1 + 0.01 x + 0.02 y equals the plane to FP32 rounding."""
+    x = [2.25, 30.5, 9.75]
+    y = [1.5, 8.25, 27.0]
+    zf = lambda a, b: 0.1 + 0.01 * a + 0.02 * b
+    z = [zf(np.rint(256 * a) / 256, np.rint(256 * b) / 256) for a, b in zip(x, y)]  # at the snapped vertices
+    out = o.raster_triangles(32, 32, x, y, z, [0.5])
+    py, px = np.divmod(out["pixel"], 32)
+    np.testing.assert_allclose(out["z"], zf(px + 0.5, py + 0.5), atol=4e-7)
+    assert len(out["pixel"]) > 150
+
+
+def test_raster_tri_skips_degenerate_and_invalid():
+    out = o.raster_triangles(16, 16, [1, 5, 9, 1, np.nan, 3, 1, 5e6, 3], [1, 5, 9, 1, 1, 8, 1, 1, 8],
+                             [0.5] * 9, [0.5] * 3)
+    assert len(out["pixel"]) == 0
+    # a sliver thinner than the snapping grid has zero area
+    out = o.raster_triangles(16, 16, [1, 9, 5], [1, 1, 1.001], [0.5] * 3, [0.5])
+    assert len(out["pixel"]) == 0
