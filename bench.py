@@ -553,10 +553,50 @@ def run_particles(wt, args, stream):
     assert wt.wt_get_error(stream) == 0
     res = {k: round(float(np.mean(v)), 4) for k, v in times.items()}
     tot = sum(res.values())
+    del pt
+    # glass panes: 100k quads (two triangles each) with sides U[8,40] px in random
+    # orientations, a depth plane per pane, through the same chain
+    Q = 100_000
+    uq = lambda lo, hi: lo + (hi - lo) * torch.rand(Q, generator=g, device=dev)
+    c = torch.stack([uq(0, W), uq(0, H)], 1)
+    ang = uq(0, 6.2831853)
+    su, sv = uq(8, 40), uq(8, 40)
+    e1 = torch.stack([torch.cos(ang), torch.sin(ang)], 1) * su[:, None]
+    e2 = torch.stack([-torch.sin(ang), torch.cos(ang)], 1) * sv[:, None]
+    p0 = c - (e1 + e2) / 2
+    corners = torch.stack([p0, p0 + e1, p0 + e1 + e2, p0 + e2], 1)  # [Q, 4, 2]
+    zc = torch.rand(Q, 4, generator=g, device=dev)
+    idx = torch.tensor([0, 1, 2, 0, 2, 3], device=dev)
+    tv = corners[:, idx, :].reshape(-1, 2)
+    tri = {"x": tv[:, 0].contiguous(), "y": tv[:, 1].contiguous(), "z": zc[:, idx].reshape(-1).contiguous(),
+           "alpha": uq(0.05, 0.6).repeat_interleave(2), "r": torch.rand(2 * Q, generator=g, device=dev),
+           "g": torch.rand(2 * Q, generator=g, device=dev), "b": torch.rand(2 * Q, generator=g, device=dev)}
+    ptimes = {"raster_tri": [], "bin": [], "build_resolve": []}
+    for rep in range(3):
+        ev[0].record(stream)
+        fr = wt.wt_raster_tri(desc, **tri, stream=stream)
+        ev[1].record(stream)
+        b = wt.wt_bin(desc, fr["pixel"], fr["z"], fr["alpha"], fr["r"], fr["g"], fr["b"], stream=stream)
+        ev[2].record(stream)
+        frags = wt.make_frags(b["pixel"], b["z"], b["alpha"], b["tile_offsets"], b["r"], b["g"], b["b"])
+        wt.wt_build_resolve(desc, frags, out, bg=(0.5, 0.5, 0.5), stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            ptimes["raster_tri"].append(ev[0].elapsed_time(ev[1]))
+            ptimes["bin"].append(ev[1].elapsed_time(ev[2]))
+            ptimes["build_resolve"].append(ev[2].elapsed_time(ev[3]))
+        npanes = int(fr["total"])
+        del fr, b, frags
+    assert wt.wt_get_error(stream) == 0
+    pres = {k: round(float(np.mean(v)), 4) for k, v in ptimes.items()}
     return {"workload": "3840x2160, 1.1M particles, radius U[2,12] px, 5 depth slabs, alpha U[.01,.4], J=5",
             "fragments": n, "ms": res, "total_ms": round(tot, 4),
             "fragments_per_s_whole_chain": n / (tot / 1e3),
-            "note": "raster includes one read-back of the fragment total to size the arrays"}
+            "note": "raster includes one read-back of the fragment total to size the arrays",
+            "panes": {"workload": "100k glass quads (200k triangles), sides U[8,40] px, random orientation, "
+                                  "depth plane per pane, alpha U[.05,.6]",
+                      "fragments": npanes, "ms": pres, "total_ms": round(sum(pres.values()), 4)}}
 
 
 def run_backward(wt, args):

@@ -454,6 +454,42 @@ wt_status wt_raster_emit(const wt_desc *desc, const wt_particles *particles, con
                          int64_t capacity, uint32_t *pixel, float *z, float *alpha, float *r,
                          float *g, float *b, wt_stream stream);
 
+/* Screen-space triangles (glass panes: two per quad), device arrays.  Vertex
+ * k of triangle i is (x, y, z)[3i + k] in pixel units and normalised depth;
+ * opacity and colour are per triangle ([n]); r, g, b nullable together. */
+typedef struct wt_triangles {
+    int64_t n;
+    const float *x, *y, *z;
+    const float *alpha;
+    const float *r, *g, *b;
+} wt_triangles;
+
+/*
+ * wt_raster_tri_count -- first pass of the triangle rasteriser, the
+ * counterpart of wt_raster_count (workspace of wt_raster_workspace_bytes(n)).
+ * Coverage is exact: vertices are snapped to 1/256 pixel (X = rint(256 x),
+ * ties to even) and the pixel centre C = (256 x + 128, 256 y + 128) is inside
+ * when every integer edge function E(A->B) = (Bx-Ax)(Cy-Ay) - (By-Ay)(Cx-Ax)
+ * of the triangle, wound to positive area, is > 0, or = 0 on an edge with
+ * dy < 0, or dy = 0 and dx > 0 (a centre on an edge or vertex shared by
+ * triangles that tile the plane belongs to exactly one of them).  Zero-area
+ * triangles, non-finite vertices and |x| or |y| >= 2^22 give no fragments.
+ * Images of width or height >= 2^21 are WT_ERR_UNSUPPORTED.
+ */
+wt_status wt_raster_tri_count(const wt_desc *desc, const wt_triangles *triangles, void *workspace,
+                              wt_stream stream);
+
+/*
+ * wt_raster_tri_emit -- second pass, as wt_raster_emit: fragments in triangle
+ * order, row-major inside a triangle, with the triangle's opacity and colour
+ * and the depth z = ((e0 z0 + e1 z1) + e2 z2) / area, where e_k is the edge
+ * function opposite vertex k and area the doubled area, each converted to
+ * FP32 and every operation rounded separately in FP32.
+ */
+wt_status wt_raster_tri_emit(const wt_desc *desc, const wt_triangles *triangles, const void *workspace,
+                             int64_t capacity, uint32_t *pixel, float *z, float *alpha, float *r,
+                             float *g, float *b, wt_stream stream);
+
 /*
  * wt_get_error -- synchronises `stream`, then returns in *bad_count the
  * number of fragments (or queries, or tile ranges) rejected by any call on the

@@ -26,7 +26,7 @@ __all__ = [
     "wt_get_error", "wt_backward", "WaveletOIT", "Server", "Planner", "WtServeConfig",
     "WtServeInfo", "wt_build_resolve_batch_static", "wt_bin_workspace_bytes", "wt_bin",
     "wt_depth_bounds", "wt_normalize_depth", "wt_build_resolve_tiles", "wt_build_resolve_single_pass",
-    "WtParticles", "wt_raster", "RGB_F32", "RGB_E5B9G9R9", "wt_build_resolve_rgb", "wt_composite_ca",
+    "WtParticles", "wt_raster", "RGB_F32", "RGB_E5B9G9R9", "wt_build_resolve_rgb", "wt_composite_ca", "WtTriangles", "wt_raster_tri",
 ]
 
 F32, BF16, F16 = 0, 1, 2
@@ -71,6 +71,12 @@ class WtParticles(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("cx", ctypes.c_void_p), ("cy", ctypes.c_void_p),
                 ("radius", ctypes.c_void_p), ("z", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
                 ("r", ctypes.c_void_p), ("g", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
+class WtTriangles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p), ("r", ctypes.c_void_p), ("g", ctypes.c_void_p),
+                ("b", ctypes.c_void_p)]
 
 
 class WtServeConfig(ctypes.Structure):
@@ -126,6 +132,9 @@ def lib() -> ctypes.CDLL:
         "wt_raster_count": ([D, ctypes.POINTER(WtParticles), vp, vp], ctypes.c_int),
         "wt_raster_emit": ([D, ctypes.POINTER(WtParticles), vp, i64, vp, vp, vp, vp, vp, vp, vp],
                            ctypes.c_int),
+        "wt_raster_tri_count": ([D, ctypes.POINTER(WtTriangles), vp, vp], ctypes.c_int),
+        "wt_raster_tri_emit": ([D, ctypes.POINTER(WtTriangles), vp, i64, vp, vp, vp, vp, vp, vp, vp],
+                               ctypes.c_int),
         "wt_bin_workspace_bytes": ([D, i64], ctypes.c_size_t),
         "wt_bin": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
         "wt_depth_bounds": ([D, Fr, vp, vp, vp], ctypes.c_int),
@@ -403,6 +412,37 @@ def wt_raster(desc: WtDesc, cx: torch.Tensor, cy: torch.Tensor, radius: torch.Te
         for k in ("r", "g", "b"):
             out[k] = torch.empty(cap, device=dev)
     _call("wt_raster_emit", ctypes.byref(desc), ctypes.byref(pt), _dev(ws, "workspace", (torch.int64,)), cap,
+          _dev(out["pixel"], "pixel", (torch.int32, torch.uint32)), _dev(out["z"], "z", f32),
+          _dev(out["alpha"], "alpha", f32), _dev(out.get("r"), "r", f32), _dev(out.get("g"), "g", f32),
+          _dev(out.get("b"), "b", f32), _stream(stream))
+    out["total"] = ws[n]
+    return out
+
+
+def wt_raster_tri(desc: WtDesc, x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, alpha: torch.Tensor,
+                  r: Optional[torch.Tensor] = None, g: Optional[torch.Tensor] = None,
+                  b: Optional[torch.Tensor] = None, capacity: Optional[int] = None, stream=None) -> dict:
+    """Rasterises triangles (vertex arrays x, y, z of 3n, per-triangle alpha
+    and colour) into an unordered fragment stream (wt_raster_tri_count, then
+    wt_raster_tri_emit); otherwise as wt_raster."""
+    n = int(alpha.numel())
+    dev = alpha.device
+    f32 = (torch.float32,)
+    if x.numel() != 3 * n or y.numel() != 3 * n or z.numel() != 3 * n:
+        raise ValueError("x, y and z hold three vertices per triangle")
+    tr = WtTriangles(n, _dev(x, "x", f32), _dev(y, "y", f32), _dev(z, "z", f32), _dev(alpha, "alpha", f32),
+                     _dev(r, "r", f32), _dev(g, "g", f32), _dev(b, "b", f32))
+    ws = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    _call("wt_raster_tri_count", ctypes.byref(desc), ctypes.byref(tr), _dev(ws, "workspace", (torch.int64,)),
+          _stream(stream))
+    total = int(ws[n].item()) if capacity is None else None
+    cap = total if capacity is None else int(capacity)
+    out = {"pixel": torch.empty(cap, dtype=torch.int32, device=dev), "z": torch.empty(cap, device=dev),
+           "alpha": torch.empty(cap, device=dev)}
+    if r is not None:
+        for k in ("r", "g", "b"):
+            out[k] = torch.empty(cap, device=dev)
+    _call("wt_raster_tri_emit", ctypes.byref(desc), ctypes.byref(tr), _dev(ws, "workspace", (torch.int64,)), cap,
           _dev(out["pixel"], "pixel", (torch.int32, torch.uint32)), _dev(out["z"], "z", f32),
           _dev(out["alpha"], "alpha", f32), _dev(out.get("r"), "r", f32), _dev(out.get("g"), "g", f32),
           _dev(out.get("b"), "b", f32), _stream(stream))

@@ -1,18 +1,26 @@
-// The layer below the paper's passes: rasterising transparent particle
-// billboards into the fragment stream that the build and resolve consume.
+// The layer below the paper's passes: rasterising transparent primitives into
+// the fragment stream that the build and resolve consume.  Two primitives:
 //
-// A particle is a screen-space disc: centre (cx, cy) in pixel units, radius
-// rho, one depth z, a peak opacity alpha0 and a colour.  It puts a fragment on
-// every pixel whose centre (x + 1/2, y + 1/2) lies strictly inside the disc,
-// with the opacity falling off to zero at the rim:
-//     d2 = dx*dx + dy*dy,  covered iff d2 < rho*rho,
-//     alpha = alpha0 * (1 - d2 * (1 / (rho*rho))),
-// every operation rounded separately in FP32 (no contraction), so that the
-// same decisions and values come out of any FP32 implementation.
+// * Particles (smoke billboards): a screen-space disc, centre (cx, cy) in
+//   pixel units, radius rho, one depth z, a peak opacity alpha0 and a colour.
+//   It puts a fragment on every pixel whose centre (x + 1/2, y + 1/2) lies
+//   strictly inside the disc, with the opacity falling off to zero at the rim:
+//       d2 = dx*dx + dy*dy,  covered iff d2 < rho*rho,
+//       alpha = alpha0 * (1 - d2 * (1 / (rho*rho))),
+//   every operation rounded separately in FP32 (no contraction), so that the
+//   same decisions and values come out of any FP32 implementation.
 //
-// One warp per particle walks the particle's clipped bounding box in
+// * Triangles (glass panes, two per quad), with per-vertex depth and a flat
+//   opacity and colour.  Coverage is exact: the vertices are snapped to 1/256
+//   pixel and the edge functions of the pixel centre are integers.  A centre
+//   on an edge belongs to the triangle it enters when moved right and
+//   infinitesimally down, so triangles that share edges or vertices cover
+//   every centre once.  Depth comes from the barycentric weights in a fixed
+//   sequence of FP32 operations.
+//
+// One warp per primitive walks the primitive's clipped bounding box in
 // row-major order, 32 pixels at a time: a counting pass, a scan of the
-// counts, and an emitting pass that writes each particle's fragments
+// counts, and an emitting pass that writes each primitive's fragments
 // contiguously, in that order.
 #include "wt.h"
 #include "wt_internal.h"
@@ -28,6 +36,14 @@ struct RasterGeom {
     int width, height;
 };
 
+struct RasterOut {
+    uint32_t *pixel;
+    float *z, *alpha, *r, *g, *b;
+    int64_t capacity;
+};
+
+// ---------------------------------------------------------------- particles
+
 struct Particles {
     int64_t n;
     const float *cx, *cy, *radius, *z, *alpha, *r, *g, *b;
@@ -36,50 +52,150 @@ struct Particles {
 // A particle's clipped bounding box and its disc parameters.
 struct Disc {
     int x0, y0, w, h;  // box origin and extent (w or h 0: nothing)
-    float cx, cy, rho2, inv;
+    float cx, cy, rho2, inv, z, a0;
+
+    // Whether pixel (x, y) is covered, and the fragment's depth and opacity.
+    __device__ __forceinline__ bool cover(int x, int y, float &zf, float &af) const {
+        const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), cx);
+        const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), cy);
+        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        zf = z;
+        af = __fmul_rn(a0, __fsub_rn(1.f, __fmul_rn(d2, inv)));
+        return d2 < rho2;
+    }
 };
 
-__device__ __forceinline__ Disc disc_of(const Particles &pt, int64_t i, const RasterGeom &g) {
-    Disc d{};
-    const float cx = pt.cx[i], cy = pt.cy[i], rho = pt.radius[i];
-    if (!(rho > 0.f) || !(cx == cx) || !(cy == cy) || !(rho < 1e6f) || !(fabsf(cx) < 1e9f) || !(fabsf(cy) < 1e9f))
-        return d;  // no area, or coordinates outside any sensible screen
-    // pixel centres inside the disc satisfy |x + 1/2 - cx| < rho; the box is
-    // widened by a pixel on each side so that rounding here never drops one
-    // (the distance test alone decides coverage)
-    const int x0 = max(0, (int)floorf(cx - rho - 0.5f) - 1), x1 = min(g.width - 1, (int)ceilf(cx + rho - 0.5f) + 1);
-    const int y0 = max(0, (int)floorf(cy - rho - 0.5f) - 1), y1 = min(g.height - 1, (int)ceilf(cy + rho - 0.5f) + 1);
-    if (x1 < x0 || y1 < y0) return d;
-    d.x0 = x0;
-    d.y0 = y0;
-    d.w = x1 - x0 + 1;
-    d.h = y1 - y0 + 1;
-    d.cx = cx;
-    d.cy = cy;
-    d.rho2 = __fmul_rn(rho, rho);
-    d.inv = __fdiv_rn(1.f, d.rho2);
-    return d;
-}
+struct DiscPrim {
+    using Input = Particles;
+    using Shape = Disc;
+    static __device__ __forceinline__ Disc make(const Particles &pt, int64_t i, const RasterGeom &g) {
+        Disc d{};
+        const float cx = pt.cx[i], cy = pt.cy[i], rho = pt.radius[i];
+        if (!(rho > 0.f) || !(cx == cx) || !(cy == cy) || !(rho < 1e6f) || !(fabsf(cx) < 1e9f) ||
+            !(fabsf(cy) < 1e9f))
+            return d;  // no area, or coordinates outside any sensible screen
+        // pixel centres inside the disc satisfy |x + 1/2 - cx| < rho; the box is
+        // widened by a pixel on each side so that rounding here never drops one
+        // (the distance test alone decides coverage)
+        const int x0 = max(0, (int)floorf(cx - rho - 0.5f) - 1), x1 = min(g.width - 1, (int)ceilf(cx + rho - 0.5f) + 1);
+        const int y0 = max(0, (int)floorf(cy - rho - 0.5f) - 1), y1 = min(g.height - 1, (int)ceilf(cy + rho - 0.5f) + 1);
+        if (x1 < x0 || y1 < y0) return d;
+        d.x0 = x0;
+        d.y0 = y0;
+        d.w = x1 - x0 + 1;
+        d.h = y1 - y0 + 1;
+        d.cx = cx;
+        d.cy = cy;
+        d.rho2 = __fmul_rn(rho, rho);
+        d.inv = __fdiv_rn(1.f, d.rho2);
+        d.z = pt.z[i];
+        d.a0 = pt.alpha[i];
+        return d;
+    }
+};
 
-// Squared distance of pixel (x, y)'s centre to the disc centre.
-__device__ __forceinline__ float dist2(const Disc &d, int x, int y) {
-    const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), d.cx);
-    const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), d.cy);
-    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-}
+// ---------------------------------------------------------------- triangles
 
-__global__ void __launch_bounds__(256) k_raster_count(RasterGeom g, Particles pt, int64_t *__restrict__ counts) {
+struct Triangles {
+    int64_t n;
+    const float *x, *y, *z, *alpha, *r, *g, *b;
+};
+
+// A triangle snapped to 1/256 pixel and wound so that its doubled area is
+// positive, with its clipped bounding box.
+struct Tri {
+    int x0, y0, w, h;
+    long long X[3], Y[3];
+    float z[3], area, a0;
+
+    // Edge k is the edge opposite vertex k: (1, 2), (2, 0), (0, 1).  Its
+    // function at the centre is the weight of vertex k times the doubled area.
+    __device__ __forceinline__ bool cover(int x, int y, float &zf, float &af) const {
+        const long long cx = 256ll * x + 128, cy = 256ll * y + 128;
+        long long E[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k == 2 ? 0 : k + 1, b = k == 0 ? 2 : (k == 1 ? 0 : 1);
+            const long long dx = X[b] - X[a], dy = Y[b] - Y[a];
+            E[k] = dx * (cy - Y[a]) - dy * (cx - X[a]);
+        }
+        bool in = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k == 2 ? 0 : k + 1, b = k == 0 ? 2 : (k == 1 ? 0 : 1);
+            const long long dx = X[b] - X[a], dy = Y[b] - Y[a];
+            in &= E[k] > 0 || (E[k] == 0 && (dy < 0 || (dy == 0 && dx > 0)));
+        }
+        const float e0 = __ll2float_rn(E[0]), e1 = __ll2float_rn(E[1]), e2 = __ll2float_rn(E[2]);
+        zf = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(e0, z[0]), __fmul_rn(e1, z[1])), __fmul_rn(e2, z[2])), area);
+        af = a0;
+        return in;
+    }
+};
+
+struct TriPrim {
+    using Input = Triangles;
+    using Shape = Tri;
+    static __device__ __forceinline__ Tri make(const Triangles &t, int64_t i, const RasterGeom &g) {
+        Tri s{};
+        float vx[3], vy[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            vx[k] = t.x[3 * i + k];
+            vy[k] = t.y[3 * i + k];
+            s.z[k] = t.z[3 * i + k];
+            if (!(fabsf(vx[k]) < 4194304.f) || !(fabsf(vy[k]) < 4194304.f)) return s;  // also NaN
+            // x * 256 is exact; rounding to the nearest integer, ties to even
+            s.X[k] = __float2ll_rn(vx[k] * 256.f);
+            s.Y[k] = __float2ll_rn(vy[k] * 256.f);
+        }
+        long long area = (s.X[1] - s.X[0]) * (s.Y[2] - s.Y[0]) - (s.Y[1] - s.Y[0]) * (s.X[2] - s.X[0]);
+        if (area == 0) return s;
+        if (area < 0) {
+            long long tx = s.X[1], ty = s.Y[1];
+            s.X[1] = s.X[2];
+            s.Y[1] = s.Y[2];
+            s.X[2] = tx;
+            s.Y[2] = ty;
+            const float tz = s.z[1];
+            s.z[1] = s.z[2];
+            s.z[2] = tz;
+            area = -area;
+        }
+        const long long mnx = min(s.X[0], min(s.X[1], s.X[2])), mxx = max(s.X[0], max(s.X[1], s.X[2]));
+        const long long mny = min(s.Y[0], min(s.Y[1], s.Y[2])), mxy = max(s.Y[0], max(s.Y[1], s.Y[2]));
+        // candidate centres 256 p + 128 in [min, max]: floor((min - 128) / 256) .. floor((max - 128) / 256) + 1
+        const long long x0 = max(0ll, (mnx - 128) >> 8), x1 = min((long long)g.width - 1, ((mxx - 128) >> 8) + 1);
+        const long long y0 = max(0ll, (mny - 128) >> 8), y1 = min((long long)g.height - 1, ((mxy - 128) >> 8) + 1);
+        if (x1 < x0 || y1 < y0) return s;
+        s.x0 = (int)x0;
+        s.y0 = (int)y0;
+        s.w = (int)(x1 - x0 + 1);
+        s.h = (int)(y1 - y0 + 1);
+        s.area = __ll2float_rn(area);
+        s.a0 = t.alpha[i];
+        return s;
+    }
+};
+
+// ---------------------------------------------------------------- the walk
+
+template <class Prim>
+__global__ void __launch_bounds__(256) k_raster_count(RasterGeom g, typename Prim::Input in, int64_t *__restrict__ counts) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < pt.n; i += nw) {
-        const Disc d = disc_of(pt, i, g);
-        const int64_t area = (int64_t)d.w * d.h;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < in.n; i += nw) {
+        const typename Prim::Shape s = Prim::make(in, i, g);
+        const int64_t area = (int64_t)s.w * s.h;
         int64_t c = 0;
         for (int64_t q0 = 0; q0 < area; q0 += 32) {
             const int64_t q = q0 + lane;
-            bool in = false;
-            if (q < area) in = dist2(d, d.x0 + (int)(q % d.w), d.y0 + (int)(q / d.w)) < d.rho2;
-            c += __popc(__ballot_sync(0xffffffffu, in));
+            bool hit = false;
+            if (q < area) {
+                float zf, af;
+                hit = s.cover(s.x0 + (int)(q % s.w), s.y0 + (int)(q / s.w), zf, af);
+            }
+            c += __popc(__ballot_sync(0xffffffffu, hit));
         }
         if (lane == 0) counts[i] = c;
     }
@@ -110,42 +226,36 @@ __global__ void __launch_bounds__(1024) k_raster_scan(int64_t n, int64_t *__rest
     if (threadIdx.x == blockDim.x - 1) offsets[n] = part[threadIdx.x];
 }
 
-struct RasterOut {
-    uint32_t *pixel;
-    float *z, *alpha, *r, *g, *b;
-    int64_t capacity;
-};
-
-__global__ void __launch_bounds__(256) k_raster_emit(RasterGeom g, Particles pt, const int64_t *__restrict__ offsets,
-                                                     RasterOut o, unsigned long long *err) {
+template <class Prim>
+__global__ void __launch_bounds__(256) k_raster_emit(RasterGeom g, typename Prim::Input in,
+                                                     const int64_t *__restrict__ offsets, RasterOut o,
+                                                     unsigned long long *err) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long dropped = 0;
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < pt.n; i += nw) {
-        const Disc d = disc_of(pt, i, g);
-        const int64_t area = (int64_t)d.w * d.h;
-        const float z = pt.z[i], a0 = pt.alpha[i];
-        const float cr = pt.r ? pt.r[i] : 0.f, cg = pt.g ? pt.g[i] : 0.f, cb = pt.b ? pt.b[i] : 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < in.n; i += nw) {
+        const typename Prim::Shape s = Prim::make(in, i, g);
+        const int64_t area = (int64_t)s.w * s.h;
+        const float cr = in.r ? in.r[i] : 0.f, cg = in.g ? in.g[i] : 0.f, cb = in.b ? in.b[i] : 0.f;
         int64_t at = offsets[i];
         for (int64_t q0 = 0; q0 < area; q0 += 32) {
             const int64_t q = q0 + lane;
-            bool in = false;
-            float d2 = 0.f;
+            bool hit = false;
+            float zf = 0.f, af = 0.f;
             int x = 0, y = 0;
             if (q < area) {
-                x = d.x0 + (int)(q % d.w);
-                y = d.y0 + (int)(q / d.w);
-                d2 = dist2(d, x, y);
-                in = d2 < d.rho2;
+                x = s.x0 + (int)(q % s.w);
+                y = s.y0 + (int)(q / s.w);
+                hit = s.cover(x, y, zf, af);
             }
-            const unsigned m = __ballot_sync(0xffffffffu, in);
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
             const int64_t slot = at + __popc(m & lt);
-            if (in) {
+            if (hit) {
                 if (slot < o.capacity) {
                     o.pixel[slot] = (uint32_t)y * (uint32_t)g.width + (uint32_t)x;
-                    o.z[slot] = z;
-                    o.alpha[slot] = __fmul_rn(a0, __fsub_rn(1.f, __fmul_rn(d2, d.inv)));
+                    o.z[slot] = zf;
+                    o.alpha[slot] = af;
                     if (o.r) {
                         o.r[slot] = cr;
                         o.g[slot] = cg;
@@ -169,9 +279,14 @@ int warps_grid(int64_t n) {
     return (int)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
-wt_status check_particles(const wt_desc *desc, const wt_particles *p) {
+wt_status check_geom(const wt_desc *desc) {
     if (!desc || desc->width < 1 || desc->height < 1) return WT_ERR_ARG;
     if ((int64_t)desc->width * desc->height >= (int64_t(1) << 31)) return WT_ERR_ARG;
+    return WT_OK;
+}
+
+wt_status check_particles(const wt_desc *desc, const wt_particles *p) {
+    if (check_geom(desc) != WT_OK) return WT_ERR_ARG;
     if (!p || p->n < 0) return WT_ERR_ARG;
     if (p->n > 0 && (!p->cx || !p->cy || !p->radius || !p->z || !p->alpha)) return WT_ERR_ARG;
     const bool rgb = p->r != nullptr;
@@ -179,8 +294,49 @@ wt_status check_particles(const wt_desc *desc, const wt_particles *p) {
     return WT_OK;
 }
 
+wt_status check_triangles(const wt_desc *desc, const wt_triangles *t) {
+    if (check_geom(desc) != WT_OK) return WT_ERR_ARG;
+    // pixel centres in 1/256 units stay below 2^30, so every edge function fits 64 bits
+    if (desc->width >= (1 << 21) || desc->height >= (1 << 21)) return WT_ERR_UNSUPPORTED;
+    if (!t || t->n < 0) return WT_ERR_ARG;
+    if (t->n > 0 && (!t->x || !t->y || !t->z || !t->alpha)) return WT_ERR_ARG;
+    const bool rgb = t->r != nullptr;
+    if (rgb != (t->g != nullptr) || rgb != (t->b != nullptr)) return WT_ERR_ARG;
+    return WT_OK;
+}
+
 Particles particles_of(const wt_particles *p) {
     return Particles{p->n, p->cx, p->cy, p->radius, p->z, p->alpha, p->r, p->g, p->b};
+}
+
+Triangles triangles_of(const wt_triangles *t) { return Triangles{t->n, t->x, t->y, t->z, t->alpha, t->r, t->g, t->b}; }
+
+template <class Prim>
+wt_status count_t(const wt_desc *desc, const typename Prim::Input &in, void *workspace, wt_stream stream) {
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7)) return WT_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t *offsets = static_cast<int64_t *>(workspace);
+    const RasterGeom g{desc->width, desc->height};
+    if (in.n > 0) k_raster_count<Prim><<<warps_grid(in.n), 256, 0, s>>>(g, in, offsets);
+    k_raster_scan<<<1, 1024, 0, s>>>(in.n, offsets);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+template <class Prim>
+wt_status emit_t(const wt_desc *desc, const typename Prim::Input &in, const void *workspace, int64_t capacity,
+                 uint32_t *pixel, float *z, float *alpha, float *r, float *g, float *b, wt_stream stream) {
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7) || capacity < 0) return WT_ERR_ARG;
+    if (capacity > 0 && (!pixel || !z || !alpha)) return WT_ERR_ARG;
+    const bool rgb = in.r != nullptr;
+    if (rgb && capacity > 0 && (!r || !g || !b)) return WT_ERR_ARG;
+    unsigned long long *err = error_word();
+    if (!err) return WT_ERR_CUDA;
+    if (in.n == 0) return WT_OK;
+    const RasterGeom geo{desc->width, desc->height};
+    const RasterOut o{pixel, z, alpha, rgb ? r : nullptr, rgb ? g : nullptr, rgb ? b : nullptr, capacity};
+    k_raster_emit<Prim><<<warps_grid(in.n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        geo, in, static_cast<const int64_t *>(workspace), o, err);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
 }  // namespace
@@ -196,14 +352,7 @@ extern "C" wt_status wt_raster_count(const wt_desc *desc, const wt_particles *pa
                                      wt_stream stream) {
     wt_status st = check_particles(desc, particles);
     if (st != WT_OK) return st;
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7)) return WT_ERR_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int64_t *offsets = static_cast<int64_t *>(workspace);
-    const RasterGeom g{desc->width, desc->height};
-    if (particles->n > 0)
-        k_raster_count<<<warps_grid(particles->n), 256, 0, s>>>(g, particles_of(particles), offsets);
-    k_raster_scan<<<1, 1024, 0, s>>>(particles->n, offsets);
-    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+    return count_t<DiscPrim>(desc, particles_of(particles), workspace, stream);
 }
 
 extern "C" wt_status wt_raster_emit(const wt_desc *desc, const wt_particles *particles, const void *workspace,
@@ -211,16 +360,20 @@ extern "C" wt_status wt_raster_emit(const wt_desc *desc, const wt_particles *par
                                     float *b, wt_stream stream) {
     wt_status st = check_particles(desc, particles);
     if (st != WT_OK) return st;
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7) || capacity < 0) return WT_ERR_ARG;
-    if (capacity > 0 && (!pixel || !z || !alpha)) return WT_ERR_ARG;
-    const bool rgb = particles->r != nullptr;
-    if (rgb && capacity > 0 && (!r || !g || !b)) return WT_ERR_ARG;
-    unsigned long long *err = error_word();
-    if (!err) return WT_ERR_CUDA;
-    if (particles->n == 0) return WT_OK;
-    const RasterGeom geo{desc->width, desc->height};
-    const RasterOut o{pixel, z, alpha, rgb ? r : nullptr, rgb ? g : nullptr, rgb ? b : nullptr, capacity};
-    k_raster_emit<<<warps_grid(particles->n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        geo, particles_of(particles), static_cast<const int64_t *>(workspace), o, err);
-    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+    return emit_t<DiscPrim>(desc, particles_of(particles), workspace, capacity, pixel, z, alpha, r, g, b, stream);
+}
+
+extern "C" wt_status wt_raster_tri_count(const wt_desc *desc, const wt_triangles *triangles, void *workspace,
+                                         wt_stream stream) {
+    wt_status st = check_triangles(desc, triangles);
+    if (st != WT_OK) return st;
+    return count_t<TriPrim>(desc, triangles_of(triangles), workspace, stream);
+}
+
+extern "C" wt_status wt_raster_tri_emit(const wt_desc *desc, const wt_triangles *triangles, const void *workspace,
+                                        int64_t capacity, uint32_t *pixel, float *z, float *alpha, float *r,
+                                        float *g, float *b, wt_stream stream) {
+    wt_status st = check_triangles(desc, triangles);
+    if (st != WT_OK) return st;
+    return emit_t<TriPrim>(desc, triangles_of(triangles), workspace, capacity, pixel, z, alpha, r, g, b, stream);
 }

@@ -84,3 +84,80 @@ def test_raster_no_particles():
     e = torch.empty(0, device=DEV)
     out = wt.wt_raster(d, e, e, e, e, e)
     assert int(out["total"]) == 0 and out["pixel"].numel() == 0
+
+
+def _triangles(n, W, H, seed):
+    """Random glass panes: quads (two triangles sharing a diagonal) with a
+    tilted depth plane, some slivers, one degenerate and one off-screen."""
+    rng = np.random.default_rng(seed)
+    x, y, z, al = [], [], [], []
+    for q in range(n // 2):
+        cx, cy = rng.uniform(-10, W + 10), rng.uniform(-10, H + 10)
+        u = rng.normal(0, 12, 2)
+        v = rng.normal(0, 12, 2)
+        p0 = np.array([cx, cy]) - (u + v) / 2
+        pts = [p0, p0 + u, p0 + u + v, p0 + v]
+        zz = rng.uniform(0, 1, 4)
+        for tri in ((0, 1, 2), (0, 2, 3)):
+            for k in tri:
+                x.append(pts[k][0])
+                y.append(pts[k][1])
+                z.append(zz[k])
+        a = rng.uniform(0.05, 0.6)
+        al += [a, a]
+    x, y, z, al = (np.asarray(v, dtype=np.float32) for v in (x, y, z, al))
+    x[:3] = [5.0, 9.0, 13.0]  # collinear: no area
+    y[:3] = [5.0, 9.0, 13.0]
+    x[3:6] += 10 * W  # off screen
+    rgb = rng.random((3, len(al))).astype(np.float32)
+    return {"x": x, "y": y, "z": z, "alpha": al, "r": rgb[0], "g": rgb[1], "b": rgb[2]}
+
+
+def test_raster_tri_matches_the_oracle_bit_for_bit():
+    W, H = 120, 90
+    t = _triangles(600, W, H, 5)
+    d = wt.make_desc(W, H, 4)
+    g = _dev(t)
+    out = wt.wt_raster_tri(d, g["x"], g["y"], g["z"], g["alpha"], g["r"], g["g"], g["b"])
+    assert wt.wt_get_error() == 0
+    ref = oracle.raster_triangles(W, H, t["x"], t["y"], t["z"], t["alpha"], t["r"], t["g"], t["b"])
+    assert int(out["total"]) == len(ref["pixel"]) > 0
+    np.testing.assert_array_equal(out["pixel"].cpu().numpy().astype(np.int64), ref["pixel"])
+    for k in ("z", "alpha", "r", "g", "b"):
+        np.testing.assert_array_equal(out[k].cpu().numpy(), ref[k])
+
+
+def test_raster_tri_panes_to_composite_match_the_oracle():
+    """glass panes -> wt_raster_tri -> wt_bin -> wt_build_resolve equals the
+    oracle's rasterisation and composite."""
+    W, H = 192, 48
+    t = _triangles(300, W, H, 6)
+    d = wt.make_desc(W, H, 5, tile_w=192, tile_h=1)
+    g = _dev(t)
+    fr = wt.wt_raster_tri(d, g["x"], g["y"], g["z"], g["alpha"], g["r"], g["g"], g["b"])
+    binned = wt.wt_bin(d, fr["pixel"], fr["z"], fr["alpha"], fr["r"], fr["g"], fr["b"])
+    frags = wt.make_frags(binned["pixel"], binned["z"], binned["alpha"], binned["tile_offsets"], binned["r"],
+                          binned["g"], binned["b"])
+    out = torch.empty(W * H, 4, device=DEV)
+    wt.wt_build_resolve(d, frags, out, bg=(0.5, 0.5, 0.5))
+    assert wt.wt_get_error() == 0
+    ref = oracle.raster_triangles(W, H, t["x"], t["y"], t["z"], t["alpha"], t["r"], t["g"], t["b"])
+    comp = oracle.composite(ref["pixel"], ref["z"], ref["alpha"], (ref["r"], ref["g"], ref["b"]), W * H, 5)
+    np.testing.assert_allclose(out.cpu().numpy(), comp, atol=1e-4, rtol=0)
+
+
+def test_raster_tri_capacity_and_arguments():
+    W, H = 64, 48
+    t = _triangles(40, W, H, 7)
+    d = wt.make_desc(W, H, 4)
+    g = _dev(t)
+    full = wt.wt_raster_tri(d, g["x"], g["y"], g["z"], g["alpha"])
+    total = int(full["total"])
+    part = wt.wt_raster_tri(d, g["x"], g["y"], g["z"], g["alpha"], capacity=total - 11)
+    assert wt.wt_get_error() == 11
+    assert torch.equal(part["pixel"], full["pixel"][:total - 11])
+    e = torch.empty(0, device=DEV)
+    none = wt.wt_raster_tri(d, e, e, e, e)
+    assert int(none["total"]) == 0
+    with pytest.raises(wt.WtError):
+        wt.wt_raster_tri(wt.make_desc(1 << 21, 1, 4), g["x"], g["y"], g["z"], g["alpha"])
