@@ -192,7 +192,8 @@ wt_status wt_composite(const wt_desc *desc, const float *accum, const float *bg_
  *   dispersion >= 0: the segment's length as a fraction of |d|.
  *   taps       1 (the single refracted sample) or odd, 3..15 (the paper: 5).
  *   out        [P * 4] float RGBA.
- * Only width, height and WT_RESOLVE_NORMALIZED of desc are used.
+ * Only width, height and WT_RESOLVE_NORMALIZED of desc are used; images more
+ * than 1048560 pixels high are WT_ERR_UNSUPPORTED.
  */
 wt_status wt_composite_ca(const wt_desc *desc, const float *accum, const float *bg_img,
                           const float *offset, float dispersion, int32_t taps, float *out,

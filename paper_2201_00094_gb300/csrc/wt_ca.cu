@@ -11,8 +11,8 @@
 // other, green from the middle.  The composite over that background is step
 // 4's.
 //
-// One thread per pixel; the background is read through the read-only path and
-// the neighbouring pixels' taps hit the same lines.
+// A block per 64 x 16 tile of pixels, with the background under the tile and
+// a halo staged in shared memory (taps beyond the halo read global memory).
 #include <math.h>
 
 #include "wt.h"
@@ -39,34 +39,64 @@ struct CaParams {
     float w[kMaxTaps][3];  // spectral weights, each channel's column summing to 1
 };
 
-// Bilinear sample of the RGB background at (x, y) (texel (i, j) centred at
-// (i + 1/2, j + 1/2)), clamped to the edge.  Coordinates far outside the image
-// are clamped before the integer conversion.
-__device__ __forceinline__ float3 bilinear(const CaParams &q, float x, float y) {
-    const float fx = x - 0.5f, fy = y - 0.5f;
-    float x0 = floorf(fx), y0 = floorf(fy);
-    const float ax = fx - x0, ay = fy - y0;
+// The bilinear combination of four texels (t00 at (i0, j0), t10 at (i0 + 1, j0), ...).
+__device__ __forceinline__ float3 blend(float ax, float ay, float3 t00, float3 t10, float3 t01, float3 t11) {
+    const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay, w11 = ax * ay;
+    float3 v;
+    v.x = w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x;
+    v.y = w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y;
+    v.z = w00 * t00.z + w10 * t10.z + w01 * t01.z + w11 * t11.z;
+    return v;
+}
+
+__device__ __forceinline__ float3 texel(const float *bg, int64_t k) {
+    return make_float3(__ldg(bg + 3 * k), __ldg(bg + 3 * k + 1), __ldg(bg + 3 * k + 2));
+}
+
+// Bilinear sample of the RGB background from global memory at the texel
+// corner (x0, y0) = floor of the position minus 1/2, weights (ax, ay), clamped
+// to the edge; corners far outside the image are clamped before the integer
+// conversion.
+__device__ __forceinline__ float3 bilinear_global(const CaParams &q, float x0, float y0, float ax, float ay) {
     x0 = fminf(fmaxf(x0, -1.f), (float)q.width);
     y0 = fminf(fmaxf(y0, -1.f), (float)q.height);
     const int ia = (int)x0, ja = (int)y0;
     const int i0 = min(max(ia, 0), q.width - 1), i1 = min(max(ia + 1, 0), q.width - 1);
-    const int j0 = min(max(ja, 0), q.height - 1), j1 = min(max(ja + 1, 0), q.height - 1);
-    const float *r0 = q.bg + 3 * (int64_t)j0 * q.width, *r1 = q.bg + 3 * (int64_t)j1 * q.width;
-    const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay, w11 = ax * ay;
-    float3 v;
-    v.x = w00 * __ldg(r0 + 3 * i0) + w10 * __ldg(r0 + 3 * i1) + w01 * __ldg(r1 + 3 * i0) + w11 * __ldg(r1 + 3 * i1);
-    v.y = w00 * __ldg(r0 + 3 * i0 + 1) + w10 * __ldg(r0 + 3 * i1 + 1) + w01 * __ldg(r1 + 3 * i0 + 1) +
-          w11 * __ldg(r1 + 3 * i1 + 1);
-    v.z = w00 * __ldg(r0 + 3 * i0 + 2) + w10 * __ldg(r0 + 3 * i1 + 2) + w01 * __ldg(r1 + 3 * i0 + 2) +
-          w11 * __ldg(r1 + 3 * i1 + 2);
-    return v;
+    const int64_t j0 = min(max(ja, 0), q.height - 1), j1 = min(max(ja + 1, 0), q.height - 1);
+    return blend(ax, ay, texel(q.bg, j0 * q.width + i0), texel(q.bg, j0 * q.width + i1),
+                 texel(q.bg, j1 * q.width + i0), texel(q.bg, j1 * q.width + i1));
 }
 
+// A block composites a 64 x 16 tile of pixels (256 threads, four rows each)
+// and first stages the background under the tile and a 12-pixel halo in
+// shared memory, one plane per channel, texels clamped to the image as the
+// global path clamps them.  A tap whose four texels lie in the staged region
+// reads them there (the same values the global path reads); others read
+// global memory.
+constexpr int kCaTW = 64, kCaTH = 16, kCaHalo = 12;
+constexpr int kCaRW = kCaTW + 2 * kCaHalo + 1, kCaRH = kCaTH + 2 * kCaHalo + 1;
+
 template <int TAPS> __global__ void __launch_bounds__(256) k_composite_ca(CaParams q) {
-    const int64_t P = (int64_t)q.width * q.height;
+    __shared__ float sbg[3][kCaRH][kCaRW];
+    const int tx0 = blockIdx.x * kCaTW, ty0 = blockIdx.y * kCaTH;
+    const int rx0 = tx0 - kCaHalo, ry0 = ty0 - kCaHalo;
+    for (int t = threadIdx.x; t < kCaRW * kCaRH; t += blockDim.x) {
+        const int rj = t / kCaRW, ri = t - rj * kCaRW;
+        const int gx = min(max(rx0 + ri, 0), q.width - 1), gy = min(max(ry0 + rj, 0), q.height - 1);
+        const float3 v = texel(q.bg, (int64_t)gy * q.width + gx);
+        sbg[0][rj][ri] = v.x;
+        sbg[1][rj][ri] = v.y;
+        sbg[2][rj][ri] = v.z;
+    }
+    __syncthreads();
+    auto staged = [&](int ri, int rj) { return make_float3(sbg[0][rj][ri], sbg[1][rj][ri], sbg[2][rj][ri]); };
     unsigned bad = 0;
-    for (int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < P; gp += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(gp / q.width), x = (int)(gp - (int64_t)y * q.width);
+    const int lx = threadIdx.x % kCaTW;
+#pragma unroll 1
+    for (int ly = threadIdx.x / kCaTW; ly < kCaTH; ly += blockDim.x / kCaTW) {
+        const int x = tx0 + lx, y = ty0 + ly;
+        if (x >= q.width || y >= q.height) continue;
+        const int64_t gp = (int64_t)y * q.width + x;
         float2 d = q.offset ? q.offset[gp] : make_float2(0.f, 0.f);
         if (!(fabsf(d.x) <= 3.4e38f) || !(fabsf(d.y) <= 3.4e38f)) {  // NaN or infinite: no shift
             d = make_float2(0.f, 0.f);
@@ -76,7 +106,17 @@ template <int TAPS> __global__ void __launch_bounds__(256) k_composite_ca(CaPara
         float3 bgc = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < TAPS; ++i) {
-            const float3 v = bilinear(q, fmaf(q.s[i], d.x, cx), fmaf(q.s[i], d.y, cy));
+            const float fx = fmaf(q.s[i], d.x, cx) - 0.5f, fy = fmaf(q.s[i], d.y, cy) - 0.5f;
+            const float x0 = floorf(fx), y0 = floorf(fy);
+            const float ax = fx - x0, ay = fy - y0;
+            const float rxf = x0 - (float)rx0, ryf = y0 - (float)ry0;
+            float3 v;
+            if (rxf >= 0.f && rxf <= (float)(kCaRW - 2) && ryf >= 0.f && ryf <= (float)(kCaRH - 2)) {
+                const int ri = (int)rxf, rj = (int)ryf;
+                v = blend(ax, ay, staged(ri, rj), staged(ri + 1, rj), staged(ri, rj + 1), staged(ri + 1, rj + 1));
+            } else {
+                v = bilinear_global(q, x0, y0, ax, ay);
+            }
             bgc.x = fmaf(q.w[i][0], v.x, bgc.x);
             bgc.y = fmaf(q.w[i][1], v.y, bgc.y);
             bgc.z = fmaf(q.w[i][2], v.z, bgc.z);
@@ -109,11 +149,9 @@ template <int TAPS> __global__ void __launch_bounds__(256) k_composite_ca(CaPara
 }
 
 template <int TAPS> cudaError_t launch_ca(const CaParams &q, cudaStream_t s) {
-    int dev = 0, sms = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t P = (int64_t)q.width * q.height;
-    const int64_t want = (P + 255) / 256, cap = (int64_t)sms * 8;
-    k_composite_ca<TAPS><<<(int)(want < cap ? want : cap), 256, 0, s>>>(q);
+    const dim3 grid((q.width + kCaTW - 1) / kCaTW, (q.height + kCaTH - 1) / kCaTH);
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    k_composite_ca<TAPS><<<grid, 256, 0, s>>>(q);
     return cudaGetLastError();
 }
 
@@ -140,6 +178,7 @@ extern "C" wt_status wt_composite_ca(const wt_desc *desc, const float *accum, co
         return WT_ERR_ARG;
     if (taps < 1 || taps > kMaxTaps || taps % 2 == 0) return WT_ERR_ARG;
     if (!(dispersion >= 0.f) || !(dispersion <= 3.4e38f)) return WT_ERR_ARG;
+    if ((desc->height + kCaTH - 1) / kCaTH > 65535) return WT_ERR_UNSUPPORTED;  // rows of the launch grid
     CaParams q{};
     q.width = desc->width;
     q.height = desc->height;
