@@ -469,32 +469,35 @@ def bilinear(img, width: int, height: int, x, y) -> np.ndarray:
             + (1 - ax) * ay * s(i0, j1) + ax * ay * s(i1, j1))
 
 
-def ca_background(bg_img, offset, width: int, height: int, dispersion: float, taps: int) -> np.ndarray:
+def ca_background(bg_img, offset, width: int, height: int, dispersion: float, taps: int,
+                  pixels=None) -> np.ndarray:
     """The background seen through the transparent layers with chromatic
     aberration (§3): instead of one bilinear sample at the refracted point
     p + d, `taps` samples along the segment of tap_scales, each channel the
     weighted mean of the samples under its spectral weight.  A pixel whose
-    offset is not finite takes the unshifted background."""
+    offset is not finite takes the unshifted background.  `pixels` (ids)
+    restricts the result to those pixels."""
     P = width * height
-    d = np.asarray(offset, dtype=np.float64).reshape(P, 2).copy()
+    px = np.arange(P) if pixels is None else np.asarray(pixels, dtype=np.int64)
+    d = np.asarray(offset, dtype=np.float64).reshape(P, 2)[px].copy()
     bad = ~np.isfinite(d).all(axis=1)
     d[bad] = 0.0
-    px = np.arange(P)
     x, y = px % width + 0.5, px // width + 0.5
     w = spectral_weights(taps)
-    acc = np.zeros((P, 3))
+    acc = np.zeros((len(px), 3))
     for i, s in enumerate(tap_scales(taps, dispersion)):
         acc += w[i] * bilinear(bg_img, width, height, x + s * d[:, 0], y + s * d[:, 1])
     return acc / w.sum(axis=0)
 
 
 def composite_ca(accum, bg_img, offset, width: int, height: int, dispersion: float = 0.5, taps: int = 5,
-                 flags=DEFAULT_FLAGS) -> np.ndarray:
+                 flags=DEFAULT_FLAGS, pixels=None) -> np.ndarray:
     """§2.1 step 4 with the chromatic-aberration background of §3: the
     composite of `resolve`'s accumulators (accum [P, 6] = R', G', B', W', S, Amin)
-    over ca_background instead of the background pixel."""
+    over ca_background instead of the background pixel.  With `pixels`, accum
+    holds those pixels' rows only."""
     a = np.asarray(accum, dtype=np.float64)
-    bgc = ca_background(bg_img, offset, width, height, dispersion, taps)
+    bgc = ca_background(bg_img, offset, width, height, dispersion, taps, pixels)
     R, W, S, Amin = a[:, :3], a[:, 3:4], a[:, 4:5], a[:, 5:6]
     T = np.exp(-S)
     out = np.zeros((a.shape[0], 4))

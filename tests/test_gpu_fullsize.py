@@ -47,7 +47,7 @@ def test_absorbance_step_accuracy():
 
 def _sample_check(fr, J, dtype, flags, fused, npix, seed):
     dev = fr.pixel.device
-    d = wt.make_desc(fr.width, fr.height, J, DT[dtype], flags)
+    d = wt.make_desc(fr.width, fr.height, J, DT[dtype], flags, fr.tile_w, fr.tile_h)
     f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
     coeff = torch.empty(fr.P, 1 << J, device=dev, dtype=wt.coeff_torch_dtype(DT[dtype]))
     out = torch.empty(fr.P, 4, device=dev)
@@ -68,12 +68,16 @@ def _sample_check(fr, J, dtype, flags, fused, npix, seed):
     got = out[pix].cpu().numpy().astype(np.float64)
     err = np.abs(got - ref).max(axis=1)
     counts = np.bincount(loc.astype(np.int64), minlength=npix)
-    return err, counts
+    ac = np.minimum(h["alpha"].astype(np.float64), 1 - 2.0 ** -20)
+    S = np.bincount(loc.astype(np.int64), weights=-np.log1p(-ac), minlength=npix)
+    return err, counts, S
 
 
 @pytest.fixture(scope="module")
 def heavy4k():
-    fr = synth.heavy4k(seed=0, device="cuda")
+    """The bench's frame in the bench's launch configuration (192 x 1 tiles,
+    the four-blocks-per-SM builds); 16 x 16 tiles are covered at 1080p."""
+    fr = synth.heavy4k(seed=0, device="cuda", tile_w=192, tile_h=1)
     yield fr
     del fr
     torch.cuda.empty_cache()
@@ -83,17 +87,26 @@ def heavy4k():
 def test_heavy4k_fp32_sampled_pixels(heavy4k, fused):
     """3840x2160 heavy smoke, J = 5, FP32 storage: composites within 1e-4 of
     the FP64 oracle on 4096 seeded sampled pixels."""
-    err, counts = _sample_check(heavy4k, 5, "f32", wt.DEFAULT_FLAGS, fused, 4096, seed=4096)
+    err, counts, _ = _sample_check(heavy4k, 5, "f32", wt.DEFAULT_FLAGS, fused, 4096, seed=4096)
     assert err.max() <= 1e-4, (err.max(), counts[err.argmax()])
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_heavy4k_16bit_storage_error_by_depth(heavy4k, dtype, capsys):
     """16-bit coefficient storage, FP32 accumulation: error against FP64 by
-    fragments-per-pixel bucket.  FP16 keeps 2e-3 everywhere in this frame;
-    BF16 (8-bit mantissa) keeps it for pixels of up to 48 fragments, and its
-    tail is reported, not hidden."""
-    err, counts = _sample_check(heavy4k, 5, dtype, wt.DEFAULT_FLAGS, True, 4096, seed=4097)
+    fragments-per-pixel bucket.
+
+    Bound from the arithmetic: a stored coefficient is off by at most u of
+    itself (u = 2^-9 for BF16, 2^-11 for FP16); a bin value is chi_00 plus J
+    detail terms, of size at most S_p and S_p/2 (S_p = the pixel's total step),
+    so |dA| <= u (1 + J/2) S_p; weights off by factors within e^(+-dA) move the
+    normalised colour R/W, a weighted mean of colours in [0, 1], by at most
+    tanh(dA) <= dA.  Every pixel is held to that (plus the FP32 path's 1e-4).
+    FP16 also meets the 2e-3 target everywhere in this frame; BF16's share
+    within 2e-3 is reported, not hidden."""
+    err, counts, S = _sample_check(heavy4k, 5, dtype, wt.DEFAULT_FLAGS, True, 4096, seed=4097)
+    u = 2.0 ** -9 if dtype == "bf16" else 2.0 ** -11
+    assert (err <= u * (1 + 5 / 2) * S + 1e-4).all(), float(np.max(err - u * 3.5 * S))
     edges = [0, 8, 16, 32, 48, 64, 128, 256, 2048]
     rows = []
     for lo, hi in zip(edges[:-1], edges[1:]):
@@ -101,26 +114,25 @@ def test_heavy4k_16bit_storage_error_by_depth(heavy4k, dtype, capsys):
         if m.any():
             rows.append((lo, hi, int(m.sum()), float(err[m].max()), float(np.median(err[m]))))
     with capsys.disabled():
-        print(f"\n{dtype} storage, heavy4k, max|err| by fragments/pixel:")
+        print(f"\n{dtype} storage, heavy4k, max|err| by fragments/pixel "
+              f"({100 * np.mean(err <= 2e-3):.2f}% of pixels within 2e-3):")
         for r in rows:
             print(f"  [{r[0]:4d},{r[1]:4d}) n={r[2]:5d} max={r[3]:.2e} median={r[4]:.2e}")
     if dtype == "f16":
         assert err.max() <= 2e-3
-    else:
-        assert err[counts < 48].max() <= 2e-3
 
 
 def test_smoke1080_sampled_pixels():
     fr = synth.smoke1080(seed=0, device="cuda")
     for fused in (True, False):
-        err, counts = _sample_check(fr, 4, "f32", wt.DEFAULT_FLAGS, fused, 4096, seed=1080)
+        err, counts, _ = _sample_check(fr, 4, "f32", wt.DEFAULT_FLAGS, fused, 4096, seed=1080)
         assert err.max() <= 1e-4, (err.max(), counts[err.argmax()])
 
 
 def test_fused_equals_two_pass_full_frame(heavy4k):
     fr = heavy4k
     dev = fr.pixel.device
-    d = wt.make_desc(fr.width, fr.height, 5)
+    d = wt.make_desc(fr.width, fr.height, 5, tile_w=fr.tile_w, tile_h=fr.tile_h)
     f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
     c1 = torch.empty(fr.P, 32, device=dev)
     c2 = torch.empty(fr.P, 32, device=dev)
@@ -136,3 +148,70 @@ def test_fused_equals_two_pass_full_frame(heavy4k):
     assert torch.equal(c1, c2)
     assert (o1 - o2).abs().max().item() <= 2e-5
     assert math.isfinite(o1.sum().item())
+
+
+def test_heavy4k_coloured_sampled_pixels(heavy4k):
+    """Coloured absorbance on the bench's frame (opacities alpha x (1, .8, .6)),
+    FP32 and E5B9G9R9 storage: 2048 sampled pixels against the oracle (with
+    the decoded coefficients for E5B9G9R9)."""
+    fr = heavy4k
+    dev = fr.pixel.device
+    d = wt.make_desc(fr.width, fr.height, 5, tile_w=fr.tile_w, tile_h=fr.tile_h)
+    f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+    ac = [fr.alpha, (fr.alpha * 0.8).contiguous(), (fr.alpha * 0.6).contiguous()]
+    out = torch.empty(fr.P, 4, device=dev)
+    rng = np.random.default_rng(4100)
+    pix = torch.from_numpy(rng.choice(fr.P, 2048, replace=False)).to(dev)
+    idx, loc = synth.pixel_subset(fr, pix)
+    h = {k: getattr(fr, k)[idx].cpu().numpy() for k in ("z", "r", "g", "b")}
+    al = [a[idx].cpu().numpy() for a in ac]
+    loc = loc.cpu().numpy().astype(np.uint32)
+    words = torch.empty(fr.P, 32, device=dev, dtype=torch.int32)
+    for fmt, coeff in ((wt.RGB_F32, None), (wt.RGB_E5B9G9R9, words)):
+        wt.wt_build_resolve_rgb(d, f, *ac, out, coeff, fmt, bg=fr.bg)
+        assert wt.wt_get_error() == 0
+        coeffs = None
+        if fmt == wt.RGB_E5B9G9R9:
+            dec = oracle.e5_decode(words[pix].cpu().numpy().view(np.uint32))
+            sign = np.where(np.arange(32) == 0, 1.0, -1.0)
+            coeffs = [sign * dec[c] for c in range(3)]
+        ref = oracle.composite_rgb(loc, h["z"], al, (h["r"], h["g"], h["b"]), 2048, 5, bg=fr.bg,
+                                   coeffs=coeffs)
+        err = np.abs(out[pix].cpu().numpy() - ref).max()
+        assert err <= 1e-4, (fmt, err)
+
+
+def test_heavy4k_chromatic_aberration_sampled_pixels(heavy4k):
+    """wt_composite_ca on the bench's accumulators, background and offset
+    field (up to 8 pixels, 5 taps): 4096 sampled pixels against the oracle."""
+    fr = heavy4k
+    dev = fr.pixel.device
+    d = wt.make_desc(fr.width, fr.height, 5, tile_w=fr.tile_w, tile_h=fr.tile_h)
+    f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
+    coeff = torch.empty(fr.P, 32, device=dev)
+    zmin = torch.empty(fr.P, device=dev)
+    acc = torch.empty(fr.P, 5, device=dev)
+    wt.wt_build(d, f, coeff, zmin)
+    wt.wt_resolve(d, f, coeff, zmin, acc)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    bg = torch.rand(fr.P, 3, device=dev, generator=g)
+    yy = torch.arange(fr.height, device=dev, dtype=torch.float32)[:, None].expand(fr.height, fr.width)
+    xx = torch.arange(fr.width, device=dev, dtype=torch.float32)[None, :].expand(fr.height, fr.width)
+    off = torch.stack([8.0 * torch.sin(yy / 57.0), 8.0 * torch.cos(xx / 43.0)], dim=-1).reshape(fr.P, 2)
+    off = off.contiguous()
+    out = torch.empty(fr.P, 4, device=dev)
+    wt.wt_composite_ca(d, acc, bg, out, off, 0.5, 5)
+    assert wt.wt_get_error() == 0
+    rng = np.random.default_rng(4101)
+    pix_np = np.sort(rng.choice(fr.P, 4096, replace=False))
+    pix = torch.from_numpy(pix_np).to(dev)
+    idx, loc = synth.pixel_subset(fr, pix)
+    h = {k: getattr(fr, k)[idx].cpu().numpy() for k in ("z", "alpha", "r", "g", "b")}
+    loc = loc.cpu().numpy().astype(np.uint32)
+    co = oracle.build_coeffs(loc, h["z"], h["alpha"], 4096, 5)
+    _, acc_ref = oracle.resolve(loc, h["z"], h["alpha"], (h["r"], h["g"], h["b"]), 4096, 5, co)
+    ref = oracle.composite_ca(acc_ref, bg.cpu().numpy(), off.cpu().numpy(), fr.width, fr.height, 0.5, 5,
+                              pixels=pix_np)
+    err = np.abs(out[pix].cpu().numpy() - ref).max()
+    assert err <= 1e-4, err
