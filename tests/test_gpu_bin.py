@@ -49,10 +49,11 @@ def test_bin_groups_an_unordered_stream(tile):
         np.testing.assert_array_equal(_records(got, np.arange(s, e)), _records(h, order[s:e]))
 
 
-def test_bin_with_more_tiles_than_shared_counters():
-    """60,000 one-pixel tiles: too many tile counters for shared memory, so the
-    slots come from global atomics."""
-    fr = synth.uniform_frame(300, 200, 1.5, 8, J=2, seed=77, tile_w=1, tile_h=1)
+@pytest.mark.parametrize("W,H", [(300, 200), (1500, 1500)])
+def test_bin_one_pixel_tiles(W, H):
+    """One-pixel tiles, 60,000 and 2.25M of them: too many tile counters for
+    shared memory, so the slots come from global atomics."""
+    fr = synth.uniform_frame(W, H, 1.5, 8, J=2, seed=77, tile_w=1, tile_h=1)
     h = _shuffled(fr, 5)
     d = desc_of(fr)
     g = _to_dev(h)
