@@ -282,9 +282,11 @@ enum {
  *                not read).
  *   alpha_r/g/b  [n] per-channel opacity.
  *   coeff        nullable: written in coeff_format (WT_RGB_*).
- * The channels are built and resolved one after the other in each tile's CTA,
- * in the mono kernel's shared memory (E5B9G9R9 keeps two more FP32 rows per
- * pixel until the words are formed); every tile of up to 256 pixels fits.
+ * With FP32 storage the channels are three launches of a one-channel fused
+ * kernel (out's components are written one by one, out.w summed in channel
+ * order); with E5B9G9R9 one CTA per tile works through the channels, keeping
+ * two more FP32 rows per pixel until the words are formed.  Every tile of up
+ * to 256 pixels fits.
  * Invalid fragments (pixel outside their tile, NaN depth or a NaN opacity) are
  * left out of the channels they are invalid for and counted in the error word
  * once per channel.  WT_ACCUMULATE is not supported (WT_ERR_UNSUPPORTED).

@@ -8,17 +8,18 @@
 //     W_c = sum alpha_c v_c,  T_c = exp(-sum a_c),
 // so each channel is the mono method on (z, alpha_c, col_c).
 //
-// One CTA per tile works through the channels one after the other with the
-// mono kernel's phases and shared memory: the channel's bins (fixed-point
-// shared atomics, with the counting fallback), its coefficients and their
-// storage, its bin values, and a resolve pass that accumulates (col_c w, w)
-// per pixel.  The pixel's thread keeps each channel's composite in registers
-// and writes the RGBA once.  The tile's fragments are read from HBM once and
-// re-read from L2 by the later passes.  With E5B9G9R9 storage a word holds one
-// coefficient index of all three channels, so channels r and g are built
-// first and their FP32 rows kept in shared memory; after channel b's build the
-// words are formed and stored, and the three resolves run on the decoded
-// values, so that the composite matches the stored words.
+// Each channel runs the mono kernel's phases in its shared memory: the
+// channel's bins (fixed-point shared atomics, with the counting fallback), its
+// coefficients and their storage, its bin values, and a resolve pass that
+// accumulates (col_c w, w) per pixel.  With FP32 storage the channels are
+// three launches of a one-channel kernel (mono-shaped: the mono kernel's
+// register budget, four CTAs per SM); each writes its component of out and
+// adds its coverage to out.w in channel order.  With E5B9G9R9 storage a word
+// holds one coefficient index of all three channels, so one CTA per tile
+// builds channels r and g first and keeps their FP32 rows in shared memory;
+// after channel b's build the words are formed and stored, and the three
+// resolves run on the decoded values, so that the composite matches the
+// stored words.
 #include "wt.h"
 #include "wt_internal.h"
 #include "wt_tile.cuh"
@@ -32,6 +33,7 @@ struct RgbParams {
     Params p;  // geometry, fragments (pixel, z, r, g, b), coeff (nullable), out, bg, err
     const float *__restrict__ alpha_c[kCh];
     int64_t plane;  // P * C: stride of the FP32 channel planes
+    int ch;         // FP32 storage: the channel of this launch
 };
 
 // Shared memory (bytes).  The region holds a channel's F and G bins, then its
@@ -185,71 +187,64 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
     const int npx = p.g.tile_w * p.g.tile_h;
     uint4 *stage = reinterpret_cast<uint4 *>(smem + Layout<J>::vplane(npx));  // rows out, then (R, W)
     const int after = (int)L::after(npx);
-    const Tile T = tile_of(p, p.tile0 + (int)blockIdx.x, true);
-    // L2 prefetch of what the first build reads; each channel's pass fetches
-    // the next channel's arrays (FP32) or all of them (E5B9G9R9)
-    if (threadIdx.x == 0) {
-        l2_prefetch_range(p.pixel, T.s, T.e);
-        l2_prefetch_range(p.z, T.s, T.e);
-        l2_prefetch_range(q.alpha_c[0], T.s, T.e);
-        if (E5) {
-            l2_prefetch_range(q.alpha_c[1], T.s, T.e);
-            l2_prefetch_range(q.alpha_c[2], T.s, T.e);
-            l2_prefetch_range(p.r, T.s, T.e);
-            l2_prefetch_range(p.gc, T.s, T.e);
-            l2_prefetch_range(p.b, T.s, T.e);
-        }
-    }
+    const Tile T = tile_of(p, p.tile0 + (int)blockIdx.x, E5 || q.ch == 0);  // a bad range counts once
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
-    float v[C], o[kCh] = {0.f, 0.f, 0.f}, cover_sum = 0.f;
+    float v[C];
     unsigned bad = 0;
     auto bg_of = [&](int c) {
         return p.bg_img && gp >= 0 ? p.bg_img[3 * gp + c] : (c == 0 ? p.bg0 : c == 1 ? p.bg1 : p.bg2);
     };
 
     if constexpr (!E5) {
-        // one channel at a time (not unrolled: the channels share the mono
-        // kernel's register budget)
+        // one channel per launch (the three launches share the mono kernel's
+        // register budget and shared memory); its result goes to its component
+        // of out, and its coverage is added to out.w in channel order
+        const int c = q.ch;
+        const float *alpha = c == 0 ? q.alpha_c[0] : c == 1 ? q.alpha_c[1] : q.alpha_c[2];
+        const float *col = c == 0 ? p.r : c == 1 ? p.gc : p.b;
+        if (threadIdx.x == 0) {
+            l2_prefetch_range(p.pixel, T.s, T.e);
+            l2_prefetch_range(p.z, T.s, T.e);
+            l2_prefetch_range(alpha, T.s, T.e);
+            l2_prefetch_range(col, T.s, T.e);
+        }
         unsigned *sZ = reinterpret_cast<unsigned *>(smem + L::zw(npx));
-#pragma unroll 1
-        for (int c = 0; c < kCh; ++c) {
-            const float *alpha = c == 0 ? q.alpha_c[0] : c == 1 ? q.alpha_c[1] : q.alpha_c[2];
-            const float *col = c == 0 ? p.r : c == 1 ? p.gc : p.b;
-            float S = 0.f;
-            if (threadIdx.x == 0) {
-                l2_prefetch_range(col, T.s, T.e);
-                if (c < kCh - 1) l2_prefetch_range(c == 0 ? q.alpha_c[1] : q.alpha_c[2], T.s, T.e);
-            }
-            build_channel<J>(p, alpha, T, smem, sZ, gp, v, S, bad);
-            float *dst = p.coeff ? static_cast<float *>(p.coeff) + c * q.plane : nullptr;
-            if (dst && St::ok) {
-                if (gp >= 0) stage_row<float, C>(stage, lp, v);
-                __syncthreads();
-                copy_staged<float, C>(p, T, stage, after, dst);  // clears the accumulators
-            } else {
-                if (dst && gp >= 0) store_row<float, C>(dst + gp * C, v);
-                fill_zero(stage, after);
-            }
-            // the channel's result goes to its component of out at once, and the
-            // coverage sum to out.w (read back by the same thread), so that
-            // nothing stays live from one channel to the next
-            float oc = 0.f, cs = 0.f;
-            resolve_channel_px<J, DEF>(p, alpha, col, T, smem, sZ, gp, v, S, bg_of(c), oc, cs);
-            if (gp >= 0) {
-                float *px = p.out + 4 * gp;
-                px[c] = oc;
-                px[3] = c == 0 ? cs : (c == 1 ? px[3] + cs : (px[3] + cs) * (1.f / 3.f));
-            }
+        float S = 0.f;
+        build_channel<J>(p, alpha, T, smem, sZ, gp, v, S, bad);
+        float *dst = p.coeff ? static_cast<float *>(p.coeff) + c * q.plane : nullptr;
+        if (dst && St::ok) {
+            if (gp >= 0) stage_row<float, C>(stage, lp, v);
+            __syncthreads();
+            copy_staged<float, C>(p, T, stage, after, dst);  // clears the accumulators
+        } else {
+            if (dst && gp >= 0) store_row<float, C>(dst + gp * C, v);
+            fill_zero(stage, after);
+        }
+        float oc = 0.f, cs = 0.f;
+        resolve_channel_px<J, DEF>(p, alpha, col, T, smem, sZ, gp, v, S, bg_of(c), oc, cs);
+        if (gp >= 0) {
+            float *px = p.out + 4 * gp;
+            px[c] = oc;
+            px[3] = c == 0 ? cs : (c == 1 ? px[3] + cs : (px[3] + cs) * (1.f / 3.f));
         }
     } else {
+        if (threadIdx.x == 0) {
+            l2_prefetch_range(p.pixel, T.s, T.e);
+            l2_prefetch_range(p.z, T.s, T.e);
+#pragma unroll
+            for (int c = 0; c < kCh; ++c) l2_prefetch_range(q.alpha_c[c], T.s, T.e);
+            l2_prefetch_range(p.r, T.s, T.e);
+            l2_prefetch_range(p.gc, T.s, T.e);
+            l2_prefetch_range(p.b, T.s, T.e);
+        }
         uint4 *stash0 = reinterpret_cast<uint4 *>(smem + L::region(npx));
         uint4 *stash1 = reinterpret_cast<uint4 *>(smem + L::region(npx) + L::rows(npx));
         const int zs = (int)(Layout<J>::words(npx) / 4);
         unsigned *sZ = reinterpret_cast<unsigned *>(smem + L::zw(npx));
         uint32_t *words = static_cast<uint32_t *>(p.coeff);
-        float S[kCh] = {0.f, 0.f, 0.f};
+        float S[kCh] = {0.f, 0.f, 0.f}, o[kCh] = {0.f, 0.f, 0.f}, cover_sum = 0.f;
         build_channel<J>(p, q.alpha_c[0], T, smem, sZ, gp, v, S[0], bad);
         if (gp >= 0) {
             if constexpr (St::ok) stage_row<float, C>(stash0, lp, v);
@@ -308,9 +303,9 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
             resolve_channel_px<J, DEF>(p, q.alpha_c[c], c == 0 ? p.r : p.gc, T, smem, sZ + c * zs, gp, v, S[c],
                                        bg_of(c), o[c], cover_sum);
         }
+        if (gp >= 0) reinterpret_cast<float4 *>(p.out)[gp] = make_float4(o[0], o[1], o[2], cover_sum * (1.f / 3.f));
     }
     flush_bad(bad, p.err);
-    if (E5 && gp >= 0) reinterpret_cast<float4 *>(p.out)[gp] = make_float4(o[0], o[1], o[2], cover_sum * (1.f / 3.f));
 }
 
 // FP32 storage uses the mono kernel's shared memory and register budget (four
@@ -358,7 +353,17 @@ cudaError_t launch_fused_rgb(const Params &p, int J, const float *const alpha_c[
     q.p = p;
     for (int c = 0; c < kCh; ++c) q.alpha_c[c] = alpha_c[c];
     q.plane = (int64_t)p.g.width * p.g.height * (int64_t(1) << J);
-    return kRgb[e5 ? 1 : 0][p.flags == kDefaultFlags ? 1 : 0][J - 1](q, ntiles, s);
+    const RgbLaunch f = kRgb[e5 ? 1 : 0][p.flags == kDefaultFlags ? 1 : 0][J - 1];
+    if (e5) {
+        q.ch = 0;
+        return f(q, ntiles, s);
+    }
+    for (int c = 0; c < kCh; ++c) {
+        q.ch = c;
+        const cudaError_t e = f(q, ntiles, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace wt
