@@ -263,9 +263,11 @@ enum {
     WT_RGB_F32 = 0,       /* float [3][P][C]: one plane per channel (r, g, b), each
                              laid out as the mono coefficient array */
     WT_RGB_E5B9G9R9 = 1   /* uint32 [P][C]: the three channels' magnitudes of each
-                             coefficient index in one word, 9-bit mantissas and a
-                             shared 5-bit exponent (bias 15); chi_00 is stored as
-                             is, the X_{n,k} (all <= 0, §2.3.1) as -X */
+                             coefficient index in one word: r in bits 0-8, g in
+                             9-17, b in 18-26, a shared exponent e in 27-31,
+                             value = mantissa * 2^(e - 24) (bias 15, no hidden
+                             bit); chi_00 is stored as is, the X_{n,k} (all <= 0,
+                             §2.3.1) as -X; 64 bytes per pixel at J = 4 */
 };
 
 /*
