@@ -100,3 +100,22 @@ def test_composite_ca_arguments():
             wt.wt_composite_ca(d, acc, bg, out, None, disp, taps)
     with pytest.raises(wt.WtError):
         wt.wt_composite_ca(d, acc, None, out, None, 0.5, 5)
+
+
+@pytest.mark.parametrize("W,H", [(1, 37), (130, 70)])
+def test_composite_ca_thin_and_ragged_images(W, H):
+    """A one-pixel-wide image (every staged texel clamps to column 0) and an
+    image whose tiles are ragged on both sides, with offsets that leave the
+    staged halo."""
+    fr = synth.uniform_frame(W, H, 3.0, 20, J=3, seed=140 + W, tile_w=1 if W == 1 else 130, tile_h=1)
+    d, acc, h, co = _accum(fr)
+    rng = np.random.default_rng(W)
+    bg = rng.random((fr.P, 3)).astype(np.float32)
+    off = rng.normal(0, 9, (fr.P, 2)).astype(np.float32)
+    out = torch.empty(fr.P, 4, device=DEV)
+    wt.wt_composite_ca(d, acc, torch.from_numpy(bg).to(DEV), out, torch.from_numpy(off).to(DEV), 0.7, 7)
+    assert wt.wt_get_error() == 0
+    _, acc_ref = oracle.resolve(h["pixel"], h["z"], h["alpha"], (h["r"], h["g"], h["b"]), fr.P, fr.J, co,
+                                bg_img=bg)
+    ref = oracle.composite_ca(acc_ref, bg, off, fr.width, fr.height, 0.7, 7)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)

@@ -164,3 +164,24 @@ def test_coloured_bg_image_and_256_pixel_tiles(fmt):
         ref[:, c] = o[:, 0]
         ref[:, 3] += o[:, 3] / 3.0
     np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_coloured_empty_stream(fmt):
+    """No fragments: the background, zero coverage, zero coefficients (the
+    E5B9G9R9 word of three zeros is 0)."""
+    W, H = 50, 7
+    d = wt.make_desc(W, H, 4, tile_w=32, tile_h=1)
+    e = torch.empty(0, device=DEV)
+    pix = torch.empty(0, dtype=torch.int32, device=DEV)
+    nt = int(wt.wt_num_tiles(d))
+    off = torch.zeros(nt + 1, dtype=torch.int64, device=DEV)
+    frags = wt.make_frags(pix, e, e, off, e, e, e)
+    out = torch.full((W * H, 4), 7.0, device=DEV)
+    coeff = (torch.full((3, W * H, 16), 7.0, device=DEV) if fmt == wt.RGB_F32
+             else torch.full((W * H, 16), 7, device=DEV, dtype=torch.int32))
+    wt.wt_build_resolve_rgb(d, frags, e, e, e, out, coeff, fmt, bg=(0.1, 0.2, 0.3))
+    assert wt.wt_get_error() == 0
+    torch.testing.assert_close(out, torch.tensor([0.1, 0.2, 0.3, 0.0], device=DEV).expand(W * H, 4),
+                               atol=0, rtol=0)
+    assert (coeff == 0).all()
