@@ -5,6 +5,7 @@
 
 #include "wt.h"
 #include "wt_internal.h"
+#include "wt_trace.h"
 #include "wt_tile.cuh"
 
 namespace wt {
@@ -164,6 +165,7 @@ size_t wt_coeff_bytes(const wt_desc *d) {
 int64_t wt_num_tiles(const wt_desc *d) { return check_desc(d) == WT_OK ? ntiles_of(d) : 0; }
 
 wt_status wt_build(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if ((st = check_frags(f, false)) != WT_OK) return st;
@@ -178,6 +180,7 @@ wt_status wt_build(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin
 
 wt_status wt_resolve(const wt_desc *d, const wt_frags *f, const void *coeff, const float *zmin,
                      float *accum, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if ((st = check_frags(f, true)) != WT_OK) return st;
@@ -194,6 +197,7 @@ wt_status wt_resolve(const wt_desc *d, const wt_frags *f, const void *coeff, con
 
 wt_status wt_composite(const wt_desc *d, const float *accum, const float *bg_img, const float bg[3],
                        float *out, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (!accum || !aligned(accum, 4) || !out || !aligned(out, 16)) return WT_ERR_ARG;
@@ -210,6 +214,7 @@ wt_status wt_composite(const wt_desc *d, const float *accum, const float *bg_img
 wt_status wt_resolve_composite(const wt_desc *d, const wt_frags *f, const void *coeff,
                                const float *zmin, const float *bg_img, const float bg[3], float *out,
                                wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if ((st = check_frags(f, true)) != WT_OK) return st;
@@ -228,6 +233,7 @@ wt_status wt_resolve_composite(const wt_desc *d, const wt_frags *f, const void *
 wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t first_tile, int64_t num_tiles,
                                  void *coeff, float *zmin, const float *bg_img, const float bg[3], float *out,
                                  wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
@@ -251,6 +257,7 @@ wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t fi
 wt_status wt_build_resolve_single_pass(const wt_desc *d, const wt_frags *f, const void *coeff_prev,
                                        const float *zmin_prev, void *coeff, float *zmin, const float *bg_img,
                                        const float bg[3], float *out, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
@@ -276,6 +283,7 @@ wt_status wt_build_resolve_single_pass(const wt_desc *d, const wt_frags *f, cons
 wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float *alpha_r, const float *alpha_g,
                                const float *alpha_b, void *coeff, int32_t coeff_format, const float *bg_img,
                                const float bg[3], float *out, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
@@ -299,6 +307,7 @@ wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float 
 
 wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin,
                            const float *bg_img, const float bg[3], float *out, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     return wt_build_resolve_tiles(d, f, 0, ntiles_of(d), coeff, zmin, bg_img, bg, out, stream);
@@ -306,6 +315,7 @@ wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, flo
 
 wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, const float bg[3],
                       const float *grad_out, float *grad_alpha, float *grad_rgb, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
@@ -325,6 +335,7 @@ wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, 
 
 wt_status wt_absorbance(const wt_desc *d, const void *coeff, int64_t q, const uint32_t *pixel,
                         const float *z, const float *alpha, float *A_out, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (q < 0 || !coeff || !aligned(coeff, 4)) return WT_ERR_ARG;
@@ -339,6 +350,7 @@ wt_status wt_absorbance(const wt_desc *d, const void *coeff, int64_t q, const ui
 }
 
 wt_status wt_get_error(wt_stream stream, int64_t *bad_count) {
+    WT_TRACE();
     if (!bad_count) return WT_ERR_ARG;
     unsigned long long *w = err_word();
     if (!w) return WT_ERR_CUDA;

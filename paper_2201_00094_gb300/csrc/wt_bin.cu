@@ -20,6 +20,7 @@
 // order correctly.
 #include "wt.h"
 #include "wt_internal.h"
+#include "wt_trace.h"
 #include "wt_tile.cuh"
 
 namespace wt {
@@ -329,6 +330,7 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
                             float *alpha_out, float *r_out, float *g_out, float *b_out,
                             int64_t *tile_offsets_out, void *workspace, size_t workspace_bytes,
                             wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_geom(desc);
     if (st != WT_OK) return st;
     if (!in || in->n < 0 || !tile_offsets_out || !workspace) return WT_ERR_ARG;
@@ -396,6 +398,7 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
 
 extern "C" wt_status wt_depth_bounds(const wt_desc *desc, const wt_frags *frags, float *zlo, float *zhi,
                                      wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_geom(desc);
     if (st != WT_OK) return st;
     if (!frags || frags->n < 0 || !frags->tile_offsets || !zlo || !zhi) return WT_ERR_ARG;
@@ -425,6 +428,7 @@ extern "C" wt_status wt_depth_bounds(const wt_desc *desc, const wt_frags *frags,
 
 extern "C" wt_status wt_normalize_depth(const wt_desc *desc, const wt_frags *frags, const float *zlo,
                                         const float *zhi, float *z_out, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_geom(desc);
     if (st != WT_OK) return st;
     if (!frags || frags->n < 0 || !zlo || !zhi) return WT_ERR_ARG;

@@ -17,6 +17,7 @@
 
 #include "wt.h"
 #include "wt_internal.h"
+#include "wt_trace.h"
 #include "wt_tile.cuh"
 
 namespace wt {
@@ -170,6 +171,7 @@ using namespace wt;
 extern "C" wt_status wt_composite_ca(const wt_desc *desc, const float *accum, const float *bg_img,
                                      const float *offset, float dispersion, int32_t taps, float *out,
                                      wt_stream stream) {
+    WT_TRACE();
     if (!desc || desc->width < 1 || desc->height < 1 || desc->reserved != 0) return WT_ERR_ARG;
     if ((int64_t)desc->width * desc->height >= (int64_t(1) << 31)) return WT_ERR_ARG;
     if (!accum || (reinterpret_cast<uintptr_t>(accum) & 3) || !bg_img || (reinterpret_cast<uintptr_t>(bg_img) & 3))

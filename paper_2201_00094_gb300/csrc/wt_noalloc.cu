@@ -16,6 +16,7 @@
 
 #include "wt.h"
 #include "wt_internal.h"
+#include "wt_trace.h"
 #include "wt_tile.cuh"
 
 namespace wt {
@@ -67,6 +68,7 @@ using namespace wt;
 extern "C" wt_status wt_build_resolve_batch_static(const wt_desc *descs, const wt_frags *frags,
                                                    const float *bgs, float *const *outs,
                                                    int32_t nframes, wt_stream stream) {
+    WT_TRACE();
     if (!descs || !frags || !bgs || !outs) return WT_ERR_ARG;
     if (nframes < 1 || nframes > kStaticBatchFrames) return WT_ERR_ARG;  // beyond the stated maximum
     const wt_desc &d0 = descs[0];

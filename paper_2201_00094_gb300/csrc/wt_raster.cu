@@ -24,6 +24,7 @@
 // contiguously, in that order.
 #include "wt.h"
 #include "wt_internal.h"
+#include "wt_trace.h"
 #include "wt_tile.cuh"
 
 namespace wt {
@@ -350,6 +351,7 @@ extern "C" size_t wt_raster_workspace_bytes(int64_t n_particles) {
 
 extern "C" wt_status wt_raster_count(const wt_desc *desc, const wt_particles *particles, void *workspace,
                                      wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_particles(desc, particles);
     if (st != WT_OK) return st;
     return count_t<DiscPrim>(desc, particles_of(particles), workspace, stream);
@@ -358,6 +360,7 @@ extern "C" wt_status wt_raster_count(const wt_desc *desc, const wt_particles *pa
 extern "C" wt_status wt_raster_emit(const wt_desc *desc, const wt_particles *particles, const void *workspace,
                                     int64_t capacity, uint32_t *pixel, float *z, float *alpha, float *r, float *g,
                                     float *b, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_particles(desc, particles);
     if (st != WT_OK) return st;
     return emit_t<DiscPrim>(desc, particles_of(particles), workspace, capacity, pixel, z, alpha, r, g, b, stream);
@@ -365,6 +368,7 @@ extern "C" wt_status wt_raster_emit(const wt_desc *desc, const wt_particles *par
 
 extern "C" wt_status wt_raster_tri_count(const wt_desc *desc, const wt_triangles *triangles, void *workspace,
                                          wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_triangles(desc, triangles);
     if (st != WT_OK) return st;
     return count_t<TriPrim>(desc, triangles_of(triangles), workspace, stream);
@@ -373,6 +377,7 @@ extern "C" wt_status wt_raster_tri_count(const wt_desc *desc, const wt_triangles
 extern "C" wt_status wt_raster_tri_emit(const wt_desc *desc, const wt_triangles *triangles, const void *workspace,
                                         int64_t capacity, uint32_t *pixel, float *z, float *alpha, float *r,
                                         float *g, float *b, wt_stream stream) {
+    WT_TRACE();
     wt_status st = check_triangles(desc, triangles);
     if (st != WT_OK) return st;
     return emit_t<TriPrim>(desc, triangles_of(triangles), workspace, capacity, pixel, z, alpha, r, g, b, stream);

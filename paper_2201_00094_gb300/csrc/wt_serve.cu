@@ -23,6 +23,7 @@
 
 #include "wt.h"
 #include "wt_internal.h"
+#include "wt_trace.h"
 #include "wt_tile.cuh"
 
 namespace wt {
@@ -381,6 +382,7 @@ struct wt_planner {
 extern "C" {
 
 wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **out) {
+    WT_TRACE();
     if (!cfg || !out) return WT_ERR_ARG;
     if (cfg->J < 1 || cfg->J > 5 || (cfg->coeff_dtype != WT_F32 && cfg->coeff_dtype != WT_BF16 &&
                                      cfg->coeff_dtype != WT_F16))
@@ -428,6 +430,7 @@ wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **out) {
 
 wt_status wt_serve_submit(wt_server *s, const wt_desc *d, const wt_frags *f, const float bg[3],
                           float *out, wt_stream ready_stream, int64_t *request_id) {
+    WT_TRACE();
     if (!s || !d || !f || !bg || !out || !request_id) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     if (d->J != S.cfg.J || d->coeff_dtype != S.cfg.coeff_dtype || d->flags != S.cfg.flags ||
@@ -496,6 +499,7 @@ wt_status wt_serve_submit(wt_server *s, const wt_desc *d, const wt_frags *f, con
 }
 
 wt_status wt_serve_wait(wt_server *s, int64_t id, int64_t timeout_us) {
+    WT_TRACE();
     if (!s || timeout_us < 0) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     std::unique_lock<std::mutex> lk(S.mu);
@@ -510,6 +514,7 @@ wt_status wt_serve_wait(wt_server *s, int64_t id, int64_t timeout_us) {
 }
 
 wt_status wt_serve_query(wt_server *s, int64_t id, wt_serve_info *info) {
+    WT_TRACE();
     if (!s || !info) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     std::lock_guard<std::mutex> g(S.mu);
@@ -525,6 +530,7 @@ wt_status wt_serve_query(wt_server *s, int64_t id, wt_serve_info *info) {
 }
 
 wt_status wt_serve_release(wt_server *s, int64_t id) {
+    WT_TRACE();
     if (!s) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     std::lock_guard<std::mutex> g(S.mu);
@@ -540,6 +546,7 @@ wt_status wt_serve_release(wt_server *s, int64_t id) {
 }
 
 wt_status wt_serve_stats(wt_server *s, int64_t *used_bytes, int64_t *queued, int64_t *active) {
+    WT_TRACE();
     if (!s) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     std::lock_guard<std::mutex> g(S.mu);
@@ -551,6 +558,7 @@ wt_status wt_serve_stats(wt_server *s, int64_t *used_bytes, int64_t *queued, int
 }
 
 wt_status wt_serve_destroy(wt_server *s) {
+    WT_TRACE();
     if (!s) return WT_ERR_ARG;
     ServerImpl &S = s->impl;
     {
