@@ -185,3 +185,62 @@ def test_coloured_empty_stream(fmt):
     torch.testing.assert_close(out, torch.tensor([0.1, 0.2, 0.3, 0.0], device=DEV).expand(W * H, 4),
                                atol=0, rtol=0)
     assert (coeff == 0).all()
+
+
+@pytest.mark.parametrize("J", [1, 2])
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_coloured_short_rows(J, fmt):
+    """J = 1 (rows of 8 bytes: no staged stores, words written directly) and
+    J = 2, in both storage formats, against the oracle."""
+    fr = synth.uniform_frame(70, 30, 6.0, 30, J=J, seed=150 + 2 * J + fmt, tile_w=64, tile_h=1)
+    ac = _coloured(fr, 11 + J)
+    g = fr.to(DEV)
+    d = desc_of(fr)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    C = 1 << J
+    out = torch.empty(fr.P, 4, device=DEV)
+    coeff = (torch.empty(3, fr.P, C, device=DEV) if fmt == wt.RGB_F32
+             else torch.empty(fr.P, C, device=DEV, dtype=torch.int32))
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    h = fr.numpy()
+    coeffs = None
+    if fmt == wt.RGB_E5B9G9R9:
+        dec = oracle.e5_decode(coeff.cpu().numpy().view(np.uint32))
+        sign = np.where(np.arange(C) == 0, 1.0, -1.0)
+        coeffs = [sign * dec[c] for c in range(3)]
+    else:
+        for c in range(3):
+            ref_c = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, J)
+            fc = dataclasses.replace(fr, alpha=torch.from_numpy(ac[c]))
+            assert (np.abs(coeff[c].cpu().numpy().astype(np.float64) - ref_c) <= coeff_tol(fc)).all()
+    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, J, bg=fr.bg,
+                               coeffs=coeffs)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
+
+
+@pytest.mark.parametrize("flags", [wt.SELF_EXCLUDE | wt.INTERP_LINEAR, wt.SELF_EXCLUDE | wt.RESOLVE_NORMALIZED,
+                                   wt.INTERP_LINEAR | wt.RESOLVE_NORMALIZED])
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_coloured_reading_flags(flags, fmt):
+    """The literal resolve, the staircase reconstruction and the fragment's own
+    step kept, in both storage formats (the kernels built for arbitrary flags)."""
+    fr = synth.uniform_frame(96, 24, 6.0, 30, J=4, seed=160 + flags + 10 * fmt, tile_w=128, tile_h=1)
+    ac = _coloured(fr, 17)
+    g = fr.to(DEV)
+    d = desc_of(fr, flags=flags)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    out = torch.empty(fr.P, 4, device=DEV)
+    coeff = (torch.empty(3, fr.P, 16, device=DEV) if fmt == wt.RGB_F32
+             else torch.empty(fr.P, 16, device=DEV, dtype=torch.int32))
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    h = fr.numpy()
+    coeffs = None
+    if fmt == wt.RGB_E5B9G9R9:
+        dec = oracle.e5_decode(coeff.cpu().numpy().view(np.uint32))
+        sign = np.where(np.arange(16) == 0, 1.0, -1.0)
+        coeffs = [sign * dec[c] for c in range(3)]
+    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, 4, flags=flags, bg=fr.bg,
+                               coeffs=coeffs)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
