@@ -702,3 +702,21 @@ def test_raster_tri_skips_degenerate_and_invalid():
     # a sliver thinner than the snapping grid has zero area
     out = o.raster_triangles(16, 16, [1, 9, 5], [1, 1, 1.001], [0.5] * 3, [0.5])
     assert len(out["pixel"]) == 0
+
+
+def test_e5b9g9r9_representable_values_round_trip_exactly():
+    """Triples that the format holds exactly -- m_c * 2^(e - 24) with 9-bit
+    mantissas m_c and the largest one normalised (m >= 256, or e = 0) --
+    decode to themselves and encode to the word built from the definition's
+    bit layout."""
+    rng = np.random.default_rng(21)
+    for _ in range(2000):
+        e = int(rng.integers(0, 32))
+        m = rng.integers(0, 512, 3)
+        if e > 0:
+            m[rng.integers(0, 3)] = rng.integers(256, 512)  # the largest sets the exponent
+        vals = [np.float32(np.ldexp(float(x), e - 24)) for x in m]
+        w = int(o.e5_encode(*[np.array([v]) for v in vals])[0])
+        assert w == int(m[0]) | (int(m[1]) << 9) | (int(m[2]) << 18) | (e << 27), (e, m, hex(w))
+        dec = [float(d[0]) for d in o.e5_decode(np.array([w], dtype=np.uint32))]
+        assert dec == [float(v) for v in vals]
