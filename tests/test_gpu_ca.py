@@ -100,6 +100,13 @@ def test_composite_ca_arguments():
             wt.wt_composite_ca(d, acc, bg, out, None, disp, taps)
     with pytest.raises(wt.WtError):
         wt.wt_composite_ca(d, acc, None, out, None, 0.5, 5)
+    # taller than the launch grid allows (more than 65535 rows of 16-pixel tiles)
+    tall = wt.make_desc(1, 1 << 20, 3)
+    acc_t = torch.zeros(1 << 20, 5, device=DEV)
+    bg_t = torch.zeros(1 << 20, 3, device=DEV)
+    out_t = torch.empty(1 << 20, 4, device=DEV)
+    with pytest.raises(wt.WtError):
+        wt.wt_composite_ca(tall, acc_t, bg_t, out_t, None, 0.5, 5)
 
 
 @pytest.mark.parametrize("W,H", [(1, 37), (130, 70)])

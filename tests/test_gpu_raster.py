@@ -161,3 +161,23 @@ def test_raster_tri_capacity_and_arguments():
     assert int(none["total"]) == 0
     with pytest.raises(wt.WtError):
         wt.wt_raster_tri(wt.make_desc(1 << 21, 1, 4), g["x"], g["y"], g["z"], g["alpha"])
+
+
+def test_raster_tri_full_screen_pane():
+    """One pane over the whole image (two triangles sharing the diagonal):
+    every pixel gets exactly one fragment, bit for bit the oracle's (long walks
+    of the bounding box, and the shared edge)."""
+    W, H = 160, 100
+    x = np.array([0, W, W, 0, W, 0], dtype=np.float32)
+    y = np.array([0, 0, H, 0, H, H], dtype=np.float32)
+    z = np.array([0.1, 0.5, 0.9, 0.1, 0.9, 0.4], dtype=np.float32)
+    al = np.array([0.3, 0.3], dtype=np.float32)
+    d = wt.make_desc(W, H, 4)
+    g = {k: torch.from_numpy(v).to(DEV) for k, v in (("x", x), ("y", y), ("z", z), ("alpha", al))}
+    out = wt.wt_raster_tri(d, g["x"], g["y"], g["z"], g["alpha"])
+    assert wt.wt_get_error() == 0
+    px = out["pixel"].cpu().numpy().astype(np.int64)
+    assert np.array_equal(np.sort(px), np.arange(W * H))
+    ref = oracle.raster_triangles(W, H, x, y, z, al)
+    np.testing.assert_array_equal(px, ref["pixel"])
+    np.testing.assert_array_equal(out["z"].cpu().numpy(), ref["z"])
