@@ -206,10 +206,44 @@ def make_frags(pixel: torch.Tensor, z: torch.Tensor, alpha: torch.Tensor,
                g: Optional[torch.Tensor] = None, b: Optional[torch.Tensor] = None) -> WtFrags:
     """Fragment stream descriptor.  The caller keeps the tensors alive."""
     f32 = (torch.float32,)
-    return WtFrags(int(z.numel()), _dev(pixel, "pixel", (torch.int32, torch.uint32)),
-                   _dev(z, "z", f32), _dev(alpha, "alpha", f32), _dev(r, "r", f32),
-                   _dev(g, "g", f32), _dev(b, "b", f32),
-                   _dev(tile_offsets, "tile_offsets", (torch.int64,)))
+    n = int(z.numel())
+    for t, name in ((pixel, "pixel"), (alpha, "alpha"), (r, "r"), (g, "g"), (b, "b")):
+        _need(t, name, n)
+    f = WtFrags(n, _dev(pixel, "pixel", (torch.int32, torch.uint32)),
+                _dev(z, "z", f32), _dev(alpha, "alpha", f32), _dev(r, "r", f32),
+                _dev(g, "g", f32), _dev(b, "b", f32),
+                _dev(tile_offsets, "tile_offsets", (torch.int64,)))
+    f._tile_offsets = int(tile_offsets.numel())  # checked against a descriptor's tile count
+    return f
+
+
+# Size checks: the C ABI takes bare pointers, so the binding checks that every
+# tensor holds at least what the call reads or writes.
+def _need(t: Optional[torch.Tensor], name: str, count: int) -> None:
+    if t is not None and t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} elements; the call needs {count}")
+
+
+def _pixels(desc: "WtDesc") -> int:
+    return int(desc.width) * int(desc.height)
+
+
+def _check_frags(desc: "WtDesc", frags: "WtFrags") -> None:
+    have = getattr(frags, "_tile_offsets", None)
+    if have is not None:
+        ntiles = (-(-int(desc.width) // int(desc.tile_w))) * (-(-int(desc.height) // int(desc.tile_h)))
+        if have < ntiles + 1:
+            raise ValueError(f"tile_offsets holds {have} entries; the descriptor has {ntiles} tiles")
+
+
+def _check_pixel_buffers(desc: "WtDesc", coeff=None, zmin=None, accum=None, out=None, bg_img=None,
+                         coeff_per_pixel: Optional[int] = None) -> None:
+    P = _pixels(desc)
+    _need(coeff, "coeff", P * (coeff_per_pixel if coeff_per_pixel is not None else 1 << int(desc.J)))
+    _need(zmin, "zmin", P)
+    _need(accum, "accum", 5 * P)
+    _need(out, "out", 4 * P)
+    _need(bg_img, "bg_img", 3 * P)
 
 
 def _bg(bg: Sequence[float]):
@@ -235,12 +269,16 @@ def wt_num_tiles(desc: WtDesc) -> int:
 
 def wt_build(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
              zmin: Optional[torch.Tensor] = None, stream=None) -> None:
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin)
     _call("wt_build", ctypes.byref(desc), ctypes.byref(frags), _dev(coeff, "coeff", _COEFF_DT),
           _dev(zmin, "zmin", (torch.float32,)), _stream(stream))
 
 
 def wt_resolve(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor, zmin: Optional[torch.Tensor],
                accum: torch.Tensor, stream=None) -> None:
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, accum=accum)
     _call("wt_resolve", ctypes.byref(desc), ctypes.byref(frags), _dev(coeff, "coeff", _COEFF_DT),
           _dev(zmin, "zmin", (torch.float32,)), _dev(accum, "accum", (torch.float32,)),
           _stream(stream))
@@ -249,6 +287,7 @@ def wt_resolve(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor, zmin: Optional
 def wt_composite(desc: WtDesc, accum: torch.Tensor, out: torch.Tensor,
                  bg: Sequence[float] = (0.5, 0.5, 0.5), bg_img: Optional[torch.Tensor] = None,
                  stream=None) -> None:
+    _check_pixel_buffers(desc, accum=accum, out=out, bg_img=bg_img)
     _call("wt_composite", ctypes.byref(desc), _dev(accum, "accum", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
           _stream(stream))
@@ -258,6 +297,8 @@ def wt_resolve_composite(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
                          zmin: Optional[torch.Tensor], out: torch.Tensor,
                          bg: Sequence[float] = (0.5, 0.5, 0.5),
                          bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img)
     _call("wt_resolve_composite", ctypes.byref(desc), ctypes.byref(frags),
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
@@ -268,6 +309,8 @@ def wt_build_resolve(desc: WtDesc, frags: WtFrags, out: torch.Tensor,
                      coeff: Optional[torch.Tensor] = None, zmin: Optional[torch.Tensor] = None,
                      bg: Sequence[float] = (0.5, 0.5, 0.5), bg_img: Optional[torch.Tensor] = None,
                      stream=None) -> None:
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img)
     _call("wt_build_resolve", ctypes.byref(desc), ctypes.byref(frags),
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
@@ -278,6 +321,8 @@ def wt_build_resolve_tiles(desc: WtDesc, frags: WtFrags, first_tile: int, num_ti
                            out: torch.Tensor, coeff: Optional[torch.Tensor] = None,
                            zmin: Optional[torch.Tensor] = None, bg: Sequence[float] = (0.5, 0.5, 0.5),
                            bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img)
     _call("wt_build_resolve_tiles", ctypes.byref(desc), ctypes.byref(frags), int(first_tile),
           int(num_tiles), _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
@@ -291,6 +336,9 @@ def wt_build_resolve_single_pass(desc: WtDesc, frags: WtFrags, coeff_prev: torch
                                  bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
     """Resolves this frame against the previous frame's coefficients and
     builds this frame's coefficients in one pass (wt_build_resolve_single_pass)."""
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, coeff=coeff_prev, zmin=zmin_prev, out=out, bg_img=bg_img)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin)
     _call("wt_build_resolve_single_pass", ctypes.byref(desc), ctypes.byref(frags),
           _dev(coeff_prev, "coeff_prev", _COEFF_DT), _dev(zmin_prev, "zmin_prev", (torch.float32,)),
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
@@ -310,6 +358,12 @@ def wt_build_resolve_rgb(desc: WtDesc, frags: WtFrags, alpha_r: torch.Tensor, al
     int32/uint32 [P, C] words (RGB_E5B9G9R9)."""
     f32 = (torch.float32,)
     cdt = f32 if coeff_format == RGB_F32 else (torch.int32, torch.uint32)
+    _check_frags(desc, frags)
+    for t, name in ((alpha_r, "alpha_r"), (alpha_g, "alpha_g"), (alpha_b, "alpha_b")):
+        _need(t, name, int(frags.n))
+    C = 1 << int(desc.J)
+    _check_pixel_buffers(desc, coeff=coeff, out=out, bg_img=bg_img,
+                         coeff_per_pixel=3 * C if coeff_format == RGB_F32 else C)
     _call("wt_build_resolve_rgb", ctypes.byref(desc), ctypes.byref(frags), _dev(alpha_r, "alpha_r", f32),
           _dev(alpha_g, "alpha_g", f32), _dev(alpha_b, "alpha_b", f32), _dev(coeff, "coeff", cdt),
           int(coeff_format), _dev(bg_img, "bg_img", f32), _bg(bg), _dev(out, "out", f32), _stream(stream))
@@ -322,6 +376,8 @@ def wt_composite_ca(desc: WtDesc, accum: torch.Tensor, bg_img: torch.Tensor, out
     accum [P, 5] from wt_resolve, bg_img [P, 3], offset [P, 2] refraction offsets
     in pixels (None: no offset)."""
     f32 = (torch.float32,)
+    _check_pixel_buffers(desc, accum=accum, out=out, bg_img=bg_img)
+    _need(offset, "offset", 2 * _pixels(desc))
     _call("wt_composite_ca", ctypes.byref(desc), _dev(accum, "accum", f32), _dev(bg_img, "bg_img", f32),
           _dev(offset, "offset", f32), ctypes.c_float(dispersion), int(taps), _dev(out, "out", f32),
           _stream(stream))
@@ -452,12 +508,18 @@ def wt_raster_tri(desc: WtDesc, x: torch.Tensor, y: torch.Tensor, z: torch.Tenso
 
 def wt_depth_bounds(desc: WtDesc, frags: WtFrags, zlo: torch.Tensor, zhi: torch.Tensor,
                     stream=None) -> None:
+    _check_frags(desc, frags)
+    _need(zlo, "zlo", _pixels(desc))
+    _need(zhi, "zhi", _pixels(desc))
     _call("wt_depth_bounds", ctypes.byref(desc), ctypes.byref(frags),
           _dev(zlo, "zlo", (torch.float32,)), _dev(zhi, "zhi", (torch.float32,)), _stream(stream))
 
 
 def wt_normalize_depth(desc: WtDesc, frags: WtFrags, zlo: torch.Tensor, zhi: torch.Tensor,
                        z_out: torch.Tensor, stream=None) -> None:
+    _need(zlo, "zlo", _pixels(desc))
+    _need(zhi, "zhi", _pixels(desc))
+    _need(z_out, "z_out", int(frags.n))
     _call("wt_normalize_depth", ctypes.byref(desc), ctypes.byref(frags),
           _dev(zlo, "zlo", (torch.float32,)), _dev(zhi, "zhi", (torch.float32,)),
           _dev(z_out, "z_out", (torch.float32,)), _stream(stream))
@@ -467,6 +529,11 @@ def wt_backward(desc: WtDesc, frags: WtFrags, grad_out: torch.Tensor, grad_alpha
                 grad_rgb: torch.Tensor, bg: Sequence[float] = (0.5, 0.5, 0.5),
                 bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
     """grad_rgb is planar [3, n]."""
+    _check_frags(desc, frags)
+    _check_pixel_buffers(desc, bg_img=bg_img)
+    _need(grad_out, "grad_out", 4 * _pixels(desc))
+    _need(grad_alpha, "grad_alpha", int(frags.n))
+    _need(grad_rgb, "grad_rgb", 3 * int(frags.n))
     _call("wt_backward", ctypes.byref(desc), ctypes.byref(frags),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg),
           _dev(grad_out, "grad_out", (torch.float32,)),

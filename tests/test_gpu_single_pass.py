@@ -82,8 +82,9 @@ def test_single_pass_arguments():
     out = torch.empty(fr.P, 4, device=DEV)
     with pytest.raises(wt.WtError):  # frame t's coefficients over frame t-1's
         wt.wt_build_resolve_single_pass(d, f, buf, out, buf, bg=fr.bg)
+    big = torch.zeros(fr.P + 1, 16, device=DEV)  # overlapping views of full size
     with pytest.raises(wt.WtError):
-        wt.wt_build_resolve_single_pass(d, f, buf, out, buf[1:], bg=fr.bg)
+        wt.wt_build_resolve_single_pass(d, f, big[:-1], out, big[1:], bg=fr.bg)
     # previous coefficients of an empty scene: every fragment fully visible
     wt.wt_build_resolve_single_pass(d, f, buf, out, None, bg=fr.bg)
     h = fr.numpy()
