@@ -720,3 +720,24 @@ def test_e5b9g9r9_representable_values_round_trip_exactly():
         assert w == int(m[0]) | (int(m[1]) << 9) | (int(m[2]) << 18) | (e << 27), (e, m, hex(w))
         dec = [float(d[0]) for d in o.e5_decode(np.array([w], dtype=np.uint32))]
         assert dec == [float(v) for v in vals]
+
+
+def test_coloured_single_fragment_is_over_per_channel():
+    """One fragment per pixel: each channel is the textbook 'over' with its own
+    opacity, c alpha_c + bg (1 - alpha_c), and out.w is the mean opacity; a
+    channel with zero opacity shows its background."""
+    rng = np.random.default_rng(23)
+    P = 50
+    pixel = np.arange(P, dtype=np.uint32)
+    z = rng.random(P).astype(np.float32)
+    al = [rng.uniform(0.05, 0.9, P).astype(np.float32) for _ in range(3)]
+    al[1][:10] = 0.0
+    rgb = tuple(rng.random(P).astype(np.float32) for _ in range(3))
+    bg = (0.2, 0.5, 0.7)
+    out = o.composite_rgb(pixel, z, al, rgb, P, 4, bg=bg)
+    for c in range(3):
+        a = al[c].astype(np.float64)
+        want = rgb[c].astype(np.float64) * a + bg[c] * (1 - a)
+        np.testing.assert_allclose(out[:, c], want, atol=1e-12)
+    np.testing.assert_allclose(out[:10, 1], bg[1], atol=1e-15)
+    np.testing.assert_allclose(out[:, 3], np.mean([a.astype(np.float64) for a in al], axis=0), atol=1e-12)
