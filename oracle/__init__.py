@@ -390,8 +390,10 @@ def composite_rgb(pixel, z, alpha_c, rgb, P: int, J: int, flags=DEFAULT_FLAGS, b
 
 
 def e5_encode(r, g, b) -> np.ndarray:
-    """E5B9G9R9 words of three non-negative arrays: the published shared-
-    exponent format (9-bit mantissas, 5-bit exponent, bias 15).  Values are
+    """E5B9G9R9 words of three non-negative arrays (§2.1: the coefficients of
+    the three channels are packed into 32 bits with a shared exponent; the bit
+    layout is the shared-exponent format the name denotes: 9-bit mantissas,
+    5-bit exponent, bias 15).  Values are
     clamped to [0, 511/512 * 2^16]; the exponent comes from the largest channel,
     floor(log2(max)) + 16 (at least 0), raised by one if that channel's rounded
     mantissa reaches 512; mantissas are floor(v / 2^(e - 24) + 1/2).  Every
