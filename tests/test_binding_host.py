@@ -1,0 +1,40 @@
+"""Host logic of the Python binding that needs no GPU: the size checks it
+applies before every call (the C ABI takes bare pointers)."""
+import pytest
+import torch
+
+import paper_2201_00094_gb300 as wt
+
+
+def test_need_counts_elements():
+    wt._need(None, "x", 10)  # optional buffers
+    wt._need(torch.empty(10), "x", 10)
+    wt._need(torch.empty(2, 5), "x", 10)
+    with pytest.raises(ValueError, match="x holds 9 elements"):
+        wt._need(torch.empty(9), "x", 10)
+
+
+def test_pixel_buffers_follow_the_descriptor():
+    d = wt.make_desc(7, 5, 3)  # P = 35, C = 8
+    P = 35
+    wt._check_pixel_buffers(d, coeff=torch.empty(P, 8), zmin=torch.empty(P), accum=torch.empty(P, 5),
+                            out=torch.empty(P, 4), bg_img=torch.empty(P, 3))
+    for kw in ({"coeff": torch.empty(P, 7)}, {"zmin": torch.empty(P - 1)}, {"accum": torch.empty(P, 4)},
+               {"out": torch.empty(P - 1, 4)}, {"bg_img": torch.empty(P, 2)}):
+        with pytest.raises(ValueError):
+            wt._check_pixel_buffers(d, **kw)
+    # the coloured call's FP32 planes hold three coefficient rows per pixel
+    wt._check_pixel_buffers(d, coeff=torch.empty(3, P, 8), coeff_per_pixel=24)
+    with pytest.raises(ValueError):
+        wt._check_pixel_buffers(d, coeff=torch.empty(P, 8), coeff_per_pixel=24)
+
+
+def test_tile_offsets_must_cover_the_descriptor_tiles():
+    d = wt.make_desc(40, 20, 4, tile_w=16, tile_h=16)  # 3 x 2 tiles
+    f = wt.WtFrags(0, None, None, None, None, None, None, None)
+    wt._check_frags(d, f)  # built without make_frags: nothing recorded, nothing checked
+    f._tile_offsets = 7
+    wt._check_frags(d, f)
+    f._tile_offsets = 6
+    with pytest.raises(ValueError, match="6 tiles"):
+        wt._check_frags(d, f)
