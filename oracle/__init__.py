@@ -420,6 +420,86 @@ def e5_decode(w):
     return tuple((((w >> s) & 511).astype(np.float64) * scale) for s in (0, 9, 18))
 
 
+# ---------------------------------------------------------------- shared-exponent 16-bit storage
+
+SE16_EMIN, SE16_EMAX, SE16_BIAS = -100, 100, 128
+
+
+def se16_level_shift(J: int) -> np.ndarray:
+    """floor(n / 2) for every heap index of a row of 2^J coefficients (0 for
+    chi_00; index 2^n + k is on level n)."""
+    C = 1 << J
+    sh = np.zeros(C, np.int64)
+    for i in range(1, C):
+        sh[i] = (i.bit_length() - 1) // 2
+    return sh
+
+
+def se16_encode(coeff, J: int):
+    """Mono coefficients [P, 2^J] -> (mantissas uint16 [P, 2^J], exponent
+    bytes uint8 [P]), the 16-bit shared-exponent storage.
+
+    The format rests on the sign property of §2.3.1 (chi_00 >= 0, every
+    X_{n,k} <= 0), which lets every coefficient be stored as an unsigned
+    magnitude, as the paper does for its E5B9G9R9 words (§2.1); here the
+    exponent is shared by the 2^J coefficients of one pixel instead of the
+    three channels of one coefficient.  Per pixel:
+      m_0 = chi_00, m_i = -X_{n,k} 2^floor(n/2)  (i = 2^n + k; both clamped
+            at 0, NaN -> 0; the power of two keeps every m_i <= sum of the
+            pixel's steps, since |X_{n,k}| <= 2^(-n/2) S / 2);
+      M = max_i m_i;  e = floor(log2 M) + 1 from M's FP32 exponent, clamped
+            to [-100, 100] (e = -100 when M is 0 or below 2^-126);
+      q_i = rint(m_i 2^(16 - e)) (half to even); if the largest q reaches
+            2^16, e is raised by one and the q_i taken again;
+      exponent byte = e + 128.
+    Every product and rounding is one FP32 operation, so the integer codes
+    are those of the definition applied to the given FP32 values."""
+    f = np.float32
+    c = np.asarray(coeff, dtype=f)
+    P, C = c.shape
+    assert C == 1 << J
+    sh = se16_level_shift(J)
+    neg = np.concatenate([np.ones(1, f), -np.ones(C - 1, f)])
+    m = np.fmax(c * neg, f(0)) * np.ldexp(f(1), sh).astype(f)  # exact scalings
+    M = m.max(axis=1)
+    bits = M.view(np.uint32)
+    ex = ((bits >> 23) & 0xFF).astype(np.int64)
+    e = np.where(ex > 0, ex - 127 + 1, SE16_EMIN)
+    e = np.clip(e, SE16_EMIN, SE16_EMAX)
+
+    def quant(e):
+        scale = np.ldexp(f(1), 16 - e).astype(f)
+        return np.rint(m * scale[:, None]).astype(f)
+
+    q = quant(e)
+    bump = q.max(axis=1) >= 65536
+    e = np.where(bump, e + 1, e)
+    q = np.where(bump[:, None], quant(e), q)
+    q = np.minimum(q, 65535)
+    return q.astype(np.uint16), (e + SE16_BIAS).astype(np.uint8)
+
+
+def se16_decode(mant, expo, J: int) -> np.ndarray:
+    """Coefficients [P, 2^J] (float64) of shared-exponent 16-bit rows:
+    chi_00 = q_0 2^(e - 16), X_{n,k} = -q_i 2^(e - 16 - floor(n/2))."""
+    q = np.asarray(mant, dtype=np.uint16).astype(np.float64)
+    e = np.asarray(expo, dtype=np.uint8).astype(np.int64) - SE16_BIAS
+    sh = se16_level_shift(J)
+    sign = np.concatenate([np.ones(1), -np.ones((1 << J) - 1)])
+    return sign * q * np.ldexp(1.0, e[:, None] - 16 - sh[None, :])
+
+
+def se16_split(buf, P: int, J: int):
+    """(mantissas [P, 2^J], exponent bytes [P]) of a storage buffer in the
+    library's layout: P * 2^J little-endian uint16 mantissas, pixel-major in
+    heap order, followed by P exponent bytes."""
+    raw = np.asarray(buf).view(np.uint8).reshape(-1)
+    C = 1 << J
+    mant = raw[:2 * P * C].view(np.uint16).reshape(P, C)
+    expo = raw[2 * P * C:2 * P * C + P]
+    return mant, expo
+
+
 # ---------------------------------------------------------------- chromatic aberration (§3)
 
 def _smoothstep(e0: float, e1: float, x):

@@ -741,3 +741,104 @@ def test_coloured_single_fragment_is_over_per_channel():
         np.testing.assert_allclose(out[:, c], want, atol=1e-12)
     np.testing.assert_allclose(out[:10, 1], bg[1], atol=1e-15)
     np.testing.assert_allclose(out[:, 3], np.mean([a.astype(np.float64) for a in al], axis=0), atol=1e-12)
+
+
+# ---------------------------------------------------------------- shared-exponent 16-bit storage
+
+def test_se16_hand_encodings():
+    """Hand-worked rows: e = floor(log2 M) + 1 over the magnitudes m_0 = chi_00,
+    m_i = -X_{n,k} 2^floor(n/2); q_i = rint(m_i 2^(16 - e)), ties to even;
+    the exponent byte is e + 128."""
+    # J = 2: chi = 1, X00 = -0.5, X10 = -0.25 (level 1: no shift), X11 = 0
+    q, e = o.se16_encode(np.array([[1.0, -0.5, -0.25, 0.0]]), 2)
+    assert e[0] == 129
+    np.testing.assert_array_equal(q[0], [32768, 16384, 8192, 0])
+    # J = 3: index 4 is level 2, shifted by one: X20 = -0.25 -> m = 0.5
+    q, e = o.se16_encode(np.array([[0.75, 0, 0, 0, -0.25, 0, 0, 0]]), 3)
+    assert e[0] == 128  # M = 0.75: floor(log2) = -1, e = 0
+    np.testing.assert_array_equal(q[0], [49152, 0, 0, 0, 32768, 0, 0, 0])
+    # the largest magnitude rounds up to 2^16: the exponent is raised
+    M = np.float32(1.0 - 2.0 ** -18)  # e = 0 first, M 2^16 = 65535.75
+    q, e = o.se16_encode(np.array([[M, 0.0]], np.float32), 1)
+    assert e[0] == 129 and q[0, 0] == 32768
+    # ties go to even: 2.5 and 3.5 units of 2^(e - 16)
+    unit = 2.0 ** (1 - 16)
+    q, e = o.se16_encode(np.array([[1.0, -2.5 * unit, -3.5 * unit, 0.0]]), 2)
+    assert e[0] == 129
+    np.testing.assert_array_equal(q[0], [32768, 2, 4, 0])
+    # an empty pixel: the smallest exponent, every mantissa 0
+    q, e = o.se16_encode(np.zeros((1, 8)), 3)
+    assert e[0] == 28 and not q.any()
+    # values of the wrong sign (and NaN) store as 0 -- the sign property makes
+    # every stored quantity a magnitude
+    q, e = o.se16_encode(np.array([[1.0, 0.5, np.nan, -1.0]]), 2)
+    np.testing.assert_array_equal(q[0], [32768, 0, 0, 32768])
+
+
+def test_se16_representable_rows_round_trip_exactly():
+    """Rows that the format holds exactly -- q_i 2^(e - 16 - floor(n/2)) with
+    16-bit q_i and the largest q_i at least 2^15 -- encode to those q_i and e
+    and decode to themselves."""
+    rng = np.random.default_rng(31)
+    for J in (1, 3, 5, 6):
+        C = 1 << J
+        sh = o.se16_level_shift(J)
+        for _ in range(200):
+            e = int(rng.integers(-60, 20))
+            q = rng.integers(0, 65536, C)
+            q[rng.integers(0, C)] = rng.integers(32768, 65536)
+            sign = np.where(np.arange(C) == 0, 1.0, -1.0)
+            row = (sign * np.ldexp(q.astype(np.float64), e - 16 - sh)).astype(np.float32)
+            qq, ee = o.se16_encode(row[None, :], J)
+            assert int(ee[0]) == e + 128
+            np.testing.assert_array_equal(qq[0], q)
+            np.testing.assert_array_equal(o.se16_decode(qq, ee, J)[0], row.astype(np.float64))
+
+
+def test_se16_round_trip_error_bound_and_bin_values():
+    """Every coefficient comes back within half a unit of its level,
+    2^(e - 17 - floor(n/2)); so every bin value A_m = chi_00 + sum_n (+-)
+    2^(n/2) X_{n,k} (evaluated by the oracle's own synthesis) moves by at most
+    2^(e - 17) (1 + sqrt(2) J): the error is absolute, set by the pixel's
+    largest magnitude, and does not grow with a coefficient's own size."""
+    rng = np.random.default_rng(32)
+    for J in (2, 4, 5):
+        P = 400
+        pixel = rng.integers(0, P, 30 * P).astype(np.uint32)
+        z = rng.random(30 * P).astype(np.float32)
+        al = rng.uniform(0.01, 0.9, 30 * P).astype(np.float32)
+        co = o.build_coeffs(pixel, z, al, P, J).astype(np.float32).astype(np.float64)
+        q, e = o.se16_encode(co, J)
+        dec = o.se16_decode(q, e, J)
+        ee = e.astype(np.int64) - 128
+        half = np.ldexp(1.0, ee[:, None] - 17 - o.se16_level_shift(J)[None, :])
+        assert np.all(np.abs(dec - co) <= half)
+        bound = np.ldexp(1.0, ee - 17) * (1 + math.sqrt(2) * J)
+        for p in range(0, P, 37):
+            d = np.abs(o.bin_values(dec[p], J) - o.bin_values(co[p], J)).max()
+            assert d <= bound[p] * (1 + 1e-12), (J, p, d, bound[p])
+
+
+def test_se16_composite_within_2e3_on_deep_pixels():
+    """The target of 16-bit storage -- composites within 2e-3 of FP64 -- on
+    deep slab pixels (200 to 1024 fragments, five depth slabs, the heavy-smoke
+    opacities), where BF16 storage (8-bit significand) is shown to miss it."""
+    rng = np.random.default_rng(33)
+    P = 48
+    counts = rng.integers(200, 1025, P)
+    pixel = np.repeat(np.arange(P), counts).astype(np.uint32)
+    n = len(pixel)
+    slab = rng.integers(0, 5, n)
+    z = np.clip(0.1 + 0.2 * slab + 0.03 * rng.standard_normal(n), 0, 0.9999).astype(np.float32)
+    al = rng.uniform(0.01, 0.4, n).astype(np.float32)
+    rgb = tuple(rng.random(n).astype(np.float32) for _ in range(3))
+    J = 5
+    co = o.build_coeffs(pixel, z, al, P, J)
+    ref = o.resolve(pixel, z, al, rgb, P, J, co)[0]
+    q, e = o.se16_encode(co, J)
+    se = o.resolve(pixel, z, al, rgb, P, J, o.se16_decode(q, e, J))[0]
+    assert np.abs(se - ref).max() <= 2e-3
+    bits = co.astype(np.float32).view(np.uint32)
+    bf = ((bits.astype(np.uint64) + 0x7FFF + ((bits >> 16) & 1)) >> 16 << 16).astype(np.uint32)
+    bfc = bf.view(np.float32).astype(np.float64)
+    assert np.abs(o.resolve(pixel, z, al, rgb, P, J, bfc)[0] - ref).max() > 2e-3
