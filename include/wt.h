@@ -51,7 +51,8 @@ typedef struct CUstream_st *wt_stream;
 typedef enum wt_status {
     WT_OK = 0,
     WT_ERR_ARG = 1,         /* bad argument: NULL, size out of range, misaligned */
-    WT_ERR_UNSUPPORTED = 2, /* valid but not supported (J > 5, flag combination) */
+    WT_ERR_UNSUPPORTED = 2, /* valid but not supported (J > 6, a J and tile size whose
+                               shared memory exceeds one CTA's, flag combination) */
     WT_ERR_INPUT = 3,       /* reported by wt_get_error when fragments were rejected */
     WT_ERR_TIMEOUT = 4,     /* a bounded wait ran out (serving) */
     WT_ERR_CUDA = 5,        /* a CUDA runtime call failed (launch error, bad device) */
@@ -59,8 +60,24 @@ typedef enum wt_status {
     WT_ERR_BUSY = 7         /* no free slot (serving) */
 } wt_status;
 
-/* Storage type of the coefficient buffer; accumulation is always FP32. */
-typedef enum wt_dtype { WT_F32 = 0, WT_BF16 = 1, WT_F16 = 2 } wt_dtype;
+/* Storage type of the coefficient buffer; accumulation is always FP32.
+ *
+ * WT_SE16 is 16-bit storage with a shared exponent per pixel, resting on the
+ * sign property of §2.3.1 (chi_00 >= 0 and every X_{n,k} <= 0, so every
+ * coefficient is stored as a magnitude, as §2.1 does for its E5B9G9R9 words).
+ * For each pixel, with i = 2^n + k the heap index of X_{n,k}:
+ *     m_0 = chi_00,  m_i = -X_{n,k} * 2^floor(n/2)   (each clamped at 0);
+ *     e   = floor(log2(max_i m_i)) + 1, clamped to [-100, 100];
+ *     q_i = rint(m_i * 2^(16 - e)) (ties to even), unsigned 16-bit; if the
+ *           largest q_i reaches 2^16, e is raised by one and the q_i retaken.
+ * The buffer holds the q_i as uint16 [P][C] (pixel-major, heap order, where a
+ * BF16 row would be), followed by P exponent bytes (e + 128).  A stored value
+ * decodes to chi_00 = q_0 2^(e-16), X_{n,k} = -q_i 2^(e-16-floor(n/2)), and is
+ * within half a unit of 2^(e-16) of the FP32 value: the error is set by the
+ * pixel's largest magnitude (at most its total step), not by each
+ * coefficient's own size, which is what keeps deep pixels accurate where
+ * BF16's 8-bit significand does not. */
+typedef enum wt_dtype { WT_F32 = 0, WT_BF16 = 1, WT_F16 = 2, WT_SE16 = 3 } wt_dtype;
 
 /* Reading flags.  The default (WT_DEFAULT_FLAGS) is the reading under which
  * the method converges to the exact sorted composite as J grows. */
@@ -87,7 +104,11 @@ typedef struct wt_desc {
     int32_t tile_w, tile_h; /* screen tile that groups the fragment stream;
                                1 <= tile_w * tile_h <= 256; tiles are row-major,
                                ntiles = ceil(width/tile_w) * ceil(height/tile_h) */
-    int32_t J;              /* Haar levels, 1..5; C = 2^J coefficients per pixel.
+    int32_t J;              /* Haar levels, 1..6; C = 2^J coefficients per pixel.
+                               J = 6 needs at most 192 pixels per tile for the
+                               single pass (wt_build_resolve_single_pass); the
+                               coloured call (wt_build_resolve_rgb) and the
+                               allocation-free batch stop at J = 5.
                                The paper's rank N is J - 1 (Wavelet3: J = 4) */
     int32_t coeff_dtype;    /* wt_dtype */
     uint32_t flags;         /* WT_* reading flags */
@@ -113,8 +134,9 @@ const char *wt_version(void);
 /* Human-readable name of a status (static storage). */
 const char *wt_status_string(wt_status s);
 
-/* Bytes of the coefficient buffer: width*height * 2^J * sizeof(dtype);
- * 0 if the descriptor is invalid. */
+/* Bytes of the coefficient buffer: width*height * 2^J * sizeof(dtype), plus
+ * width*height exponent bytes for WT_SE16 (sizeof = 2); 0 if the descriptor
+ * is invalid. */
 size_t wt_coeff_bytes(const wt_desc *desc);
 
 /* Number of tiles of the descriptor (the length of tile_offsets minus one);

@@ -19,7 +19,7 @@ from typing import Optional, Sequence
 import torch
 
 __all__ = [
-    "F32", "BF16", "F16", "SELF_EXCLUDE", "INTERP_LINEAR", "RESOLVE_NORMALIZED", "ACCUMULATE",
+    "F32", "BF16", "F16", "SE16", "coeff_buffer", "coeff_storage_bytes", "SELF_EXCLUDE", "INTERP_LINEAR", "RESOLVE_NORMALIZED", "ACCUMULATE",
     "DEFAULT_FLAGS", "WtDesc", "WtFrags", "WtError", "lib", "library_path", "make_desc",
     "make_frags", "coeff_torch_dtype", "wt_version", "wt_coeff_bytes", "wt_num_tiles", "wt_build",
     "wt_resolve", "wt_composite", "wt_resolve_composite", "wt_build_resolve", "wt_absorbance",
@@ -29,7 +29,7 @@ __all__ = [
     "WtParticles", "wt_raster", "RGB_F32", "RGB_E5B9G9R9", "wt_build_resolve_rgb", "wt_composite_ca", "WtTriangles", "wt_raster_tri",
 ]
 
-F32, BF16, F16 = 0, 1, 2
+F32, BF16, F16, SE16 = 0, 1, 2, 3
 SELF_EXCLUDE, INTERP_LINEAR, RESOLVE_NORMALIZED, ACCUMULATE = 1, 2, 4, 8
 DEFAULT_FLAGS = SELF_EXCLUDE | INTERP_LINEAR | RESOLVE_NORMALIZED
 
@@ -37,7 +37,7 @@ _DIR = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_DIR, "libwt.so")
 _STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "rejected input fragments",
            4: "timeout", 5: "CUDA error", 6: "over memory cap", 7: "busy"}
-_TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+_TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16, SE16: torch.uint8}
 
 
 class WtError(RuntimeError):
@@ -193,7 +193,25 @@ def _call(name: str, *args) -> None:
 
 
 def coeff_torch_dtype(coeff_dtype: int) -> torch.dtype:
+    """Element type of a coefficient tensor: float32 / bfloat16 / float16
+    [P, C], or uint8 bytes for SE16 (mantissas, then exponent bytes)."""
     return _TORCH_DTYPE[coeff_dtype]
+
+
+def coeff_storage_bytes(desc: "WtDesc") -> int:
+    """Bytes of a frame's coefficient buffer (the formula of wt_coeff_bytes)."""
+    P, C = _pixels(desc), 1 << int(desc.J)
+    dt = int(desc.coeff_dtype)
+    return P * C * (4 if dt == F32 else 2) + (P if dt == SE16 else 0)
+
+
+def coeff_buffer(desc: "WtDesc", device) -> torch.Tensor:
+    """An uninitialised coefficient buffer for desc: [P, C] of the storage
+    type, or [wt_coeff_bytes] uint8 for SE16."""
+    dt = int(desc.coeff_dtype)
+    if dt == SE16:
+        return torch.empty(coeff_storage_bytes(desc), dtype=torch.uint8, device=device)
+    return torch.empty(_pixels(desc), 1 << int(desc.J), dtype=_TORCH_DTYPE[dt], device=device)
 
 
 def make_desc(width: int, height: int, J: int, coeff_dtype: int = F32,
@@ -239,6 +257,15 @@ def _check_frags(desc: "WtDesc", frags: "WtFrags") -> None:
 def _check_pixel_buffers(desc: "WtDesc", coeff=None, zmin=None, accum=None, out=None, bg_img=None,
                          coeff_per_pixel: Optional[int] = None) -> None:
     P = _pixels(desc)
+    if coeff is not None and coeff_per_pixel is None:
+        # mono storage: checked in bytes and against the descriptor's type
+        want = _TORCH_DTYPE.get(int(desc.coeff_dtype))
+        if want is not None and coeff.dtype != want:
+            raise ValueError(f"coeff has dtype {coeff.dtype}; the descriptor's storage needs {want}")
+        have = coeff.numel() * coeff.element_size()
+        if have < coeff_storage_bytes(desc):
+            raise ValueError(f"coeff holds {have} bytes; the call needs {coeff_storage_bytes(desc)}")
+        coeff = None
     _need(coeff, "coeff", P * (coeff_per_pixel if coeff_per_pixel is not None else 1 << int(desc.J)))
     _need(zmin, "zmin", P)
     _need(accum, "accum", 5 * P)
@@ -250,7 +277,7 @@ def _bg(bg: Sequence[float]):
     return (ctypes.c_float * 3)(*[float(x) for x in bg])
 
 
-_COEFF_DT = (torch.float32, torch.bfloat16, torch.float16)
+_COEFF_DT = (torch.float32, torch.bfloat16, torch.float16, torch.uint8)
 
 
 # ---------------------------------------------------------------- entry points
@@ -391,6 +418,12 @@ def wt_build_resolve_batch_static(descs: Sequence[WtDesc], frags: Sequence[WtFra
     allocation (for callers that must not allocate when they submit work);
     see include/wt.h for the limits and the shared-scratch rule."""
     k = len(descs)
+    if len(frags) != k or len(outs) != k or (bgs is not None and len(bgs) != k):
+        raise ValueError(f"descs, frags, outs (and bgs) must have one entry per frame: {k}, {len(frags)}, "
+                         f"{len(outs)}" + ("" if bgs is None else f", {len(bgs)}"))
+    for dsc, fr, o in zip(descs, frags, outs):
+        _check_frags(dsc, fr)
+        _check_pixel_buffers(dsc, out=o)
     da = (WtDesc * max(k, 1))(*descs)
     fa = (WtFrags * max(k, 1))(*frags)
     bg = bgs if bgs is not None else [(0.5, 0.5, 0.5)] * k
@@ -401,6 +434,10 @@ def wt_build_resolve_batch_static(descs: Sequence[WtDesc], frags: Sequence[WtFra
 
 def wt_absorbance(desc: WtDesc, coeff: torch.Tensor, pixel: torch.Tensor, z: torch.Tensor,
                   A_out: torch.Tensor, alpha: Optional[torch.Tensor] = None, stream=None) -> None:
+    q = int(z.numel())
+    _check_pixel_buffers(desc, coeff=coeff)
+    for t, name in ((pixel, "pixel"), (A_out, "A_out"), (alpha, "alpha")):
+        _need(t, name, q)
     _call("wt_absorbance", ctypes.byref(desc), _dev(coeff, "coeff", _COEFF_DT), int(z.numel()),
           _dev(pixel, "pixel", (torch.int32, torch.uint32)), _dev(z, "z", (torch.float32,)),
           _dev(alpha, "alpha", (torch.float32,)), _dev(A_out, "A_out", (torch.float32,)),

@@ -34,14 +34,7 @@ unsigned long long *err_word() {
 
 bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
-size_t dtype_size(int32_t dt) {
-    switch (dt) {
-    case WT_F32: return 4;
-    case WT_BF16:
-    case WT_F16: return 2;
-    default: return 0;
-    }
-}
+bool dtype_ok(int32_t dt) { return dt == WT_F32 || dt == WT_BF16 || dt == WT_F16 || dt == WT_SE16; }
 
 // Validates the descriptor; returns WT_OK or the reason.
 wt_status check_desc(const wt_desc *d) {
@@ -50,8 +43,8 @@ wt_status check_desc(const wt_desc *d) {
     if ((int64_t)d->width * d->height >= (int64_t(1) << 31)) return WT_ERR_ARG;
     if (d->tile_w < 1 || d->tile_h < 1 || (int64_t)d->tile_w * d->tile_h > kMaxTilePx) return WT_ERR_ARG;
     if (d->J < 1) return WT_ERR_ARG;
-    if (d->J > 5) return WT_ERR_UNSUPPORTED;
-    if (!dtype_size(d->coeff_dtype)) return WT_ERR_ARG;
+    if (d->J > kMaxJ) return WT_ERR_UNSUPPORTED;
+    if (!dtype_ok(d->coeff_dtype)) return WT_ERR_ARG;
     if (d->flags & ~uint32_t(WT_SELF_EXCLUDE | WT_INTERP_LINEAR | WT_RESOLVE_NORMALIZED | WT_ACCUMULATE))
         return WT_ERR_ARG;
     if (d->reserved != 0) return WT_ERR_ARG;
@@ -101,11 +94,16 @@ Params make_params(const wt_desc *d, const wt_frags *f) {
     return p;
 }
 
-const TileLaunch *table(const TileLaunch *t0, const TileLaunch *t1, const TileLaunch *t2, int dt) {
-    return dt == WT_F32 ? t0 : (dt == WT_BF16 ? t1 : t2);
+const TileLaunch *table(const TileLaunch *t0, const TileLaunch *t1, const TileLaunch *t2, const TileLaunch *t3,
+                        int dt) {
+    return by_dtype(dt, t0, t1, t2, t3);
 }
 
-wt_status finish(cudaError_t e) { return e == cudaSuccess ? WT_OK : WT_ERR_CUDA; }
+// A launcher returns cudaErrorNotSupported for a layout beyond the shared
+// memory of one CTA (a large J with a large tile), before anything is launched.
+wt_status finish(cudaError_t e) {
+    return e == cudaSuccess ? WT_OK : (e == cudaErrorNotSupported ? WT_ERR_UNSUPPORTED : WT_ERR_CUDA);
+}
 
 wt_status set_bg(Params &p, const float *bg_img, const float *bg) {
     if (bg_img) {
@@ -159,7 +157,7 @@ const char *wt_status_string(wt_status s) {
 
 size_t wt_coeff_bytes(const wt_desc *d) {
     if (check_desc(d) != WT_OK) return 0;
-    return (size_t)d->width * d->height * ((size_t)1 << d->J) * dtype_size(d->coeff_dtype);
+    return coeff_storage_bytes((int64_t)d->width * d->height, d->J, d->coeff_dtype);
 }
 
 int64_t wt_num_tiles(const wt_desc *d) { return check_desc(d) == WT_OK ? ntiles_of(d) : 0; }
@@ -174,7 +172,7 @@ wt_status wt_build(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin
     p.coeff = coeff;
     p.zmin = zmin;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const TileLaunch *t = table(kBuild0, kBuild1, kBuild2, d->coeff_dtype);
+    const TileLaunch *t = table(kBuild0, kBuild1, kBuild2, kBuild3, d->coeff_dtype);
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -191,7 +189,7 @@ wt_status wt_resolve(const wt_desc *d, const wt_frags *f, const void *coeff, con
     p.zmin = const_cast<float *>(zmin);
     p.accum = accum;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const TileLaunch *t = table(kResolve0, kResolve1, kResolve2, d->coeff_dtype);
+    const TileLaunch *t = table(kResolve0, kResolve1, kResolve2, kResolve3, d->coeff_dtype);
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -226,7 +224,7 @@ wt_status wt_resolve_composite(const wt_desc *d, const wt_frags *f, const void *
     p.out = out;
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const TileLaunch *t = table(kResolveComp0, kResolveComp1, kResolveComp2, d->coeff_dtype);
+    const TileLaunch *t = table(kResolveComp0, kResolveComp1, kResolveComp2, kResolveComp3, d->coeff_dtype);
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -250,7 +248,7 @@ wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t fi
     p.out = out;
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const TileLaunch *t = table(kFused0, kFused1, kFused2, d->coeff_dtype);
+    const TileLaunch *t = table(kFused0, kFused1, kFused2, kFused3, d->coeff_dtype);
     return finish(t[d->J - 1](p, (int)num_tiles, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -266,7 +264,7 @@ wt_status wt_build_resolve_single_pass(const wt_desc *d, const wt_frags *f, cons
         (zmin && !aligned(zmin, 4)) || (zmin_prev && !aligned(zmin_prev, 4)))
         return WT_ERR_ARG;
     // frame t's outputs must not overlap frame t-1's inputs
-    const size_t cb = (size_t)d->width * d->height * ((size_t)1 << d->J) * dtype_size(d->coeff_dtype);
+    const size_t cb = coeff_storage_bytes((int64_t)d->width * d->height, d->J, d->coeff_dtype);
     const char *cp = static_cast<const char *>(coeff_prev), *cn = static_cast<const char *>(coeff);
     if (coeff && cn < cp + cb && cp < cn + cb) return WT_ERR_ARG;
     if (zmin && zmin_prev && zmin == zmin_prev) return WT_ERR_ARG;
@@ -276,7 +274,7 @@ wt_status wt_build_resolve_single_pass(const wt_desc *d, const wt_frags *f, cons
     p.out = out;
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const TemporalLaunch *t = d->coeff_dtype == WT_F32 ? kTemporal0 : (d->coeff_dtype == WT_BF16 ? kTemporal1 : kTemporal2);
+    const TemporalLaunch *t = by_dtype(d->coeff_dtype, kTemporal0, kTemporal1, kTemporal2, kTemporal3);
     return finish(t[d->J - 1](p, (int)ntiles_of(d), coeff_prev, zmin_prev, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -288,6 +286,7 @@ wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float 
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
     if (coeff_format != WT_RGB_F32 && coeff_format != WT_RGB_E5B9G9R9) return WT_ERR_ARG;
+    if (d->J > 5) return WT_ERR_UNSUPPORTED;  // the coloured kernels stop at 32 coefficients
     if (!f || f->n < 0 || !f->tile_offsets || !aligned(f->tile_offsets, 8)) return WT_ERR_ARG;
     const void *req[8] = {f->pixel, f->z, f->r, f->g, f->b, alpha_r, alpha_g, alpha_b};
     for (const void *q : req)
@@ -329,7 +328,7 @@ wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, 
     p.galpha = grad_alpha;
     p.grgb = grad_rgb;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const TileLaunch *t = table(kBackward0, kBackward1, kBackward2, d->coeff_dtype);
+    const TileLaunch *t = table(kBackward0, kBackward1, kBackward2, kBackward3, d->coeff_dtype);
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -343,9 +342,7 @@ wt_status wt_absorbance(const wt_desc *d, const void *coeff, int64_t q, const ui
     Params p = make_params(d, nullptr);
     p.coeff = const_cast<void *>(coeff);
     if (!(p.err = err_word())) return WT_ERR_CUDA;
-    const QueryLaunch *t = d->coeff_dtype == WT_F32 ? kAbsorbance0
-                           : d->coeff_dtype == WT_BF16 ? kAbsorbance1
-                                                       : kAbsorbance2;
+    const QueryLaunch *t = by_dtype(d->coeff_dtype, kAbsorbance0, kAbsorbance1, kAbsorbance2, kAbsorbance3);
     return finish(t[d->J - 1](p, q, pixel, z, alpha, A_out, reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -9,7 +9,7 @@ namespace wt {
 
 // Blocks per SM the kernels are compiled for (caps registers per thread so
 // that shared memory, not registers, sets the occupancy).
-template <int J> struct MinBlocks { static constexpr int value = J >= 5 ? 3 : 4; };
+template <int J> struct MinBlocks { static constexpr int value = J >= 6 ? 1 : (J == 5 ? 3 : 4); };
 
 // §2.1 step 2: build the tile's coefficients and store them once.
 template <int J, typename CT, int MB = MinBlocks<J>::value>
@@ -36,17 +36,21 @@ __global__ void __launch_bounds__(kThreads, MB) k_build(Params p) {
     // rows of whole 16-byte chunks go out through a staging copy over the F
     // bins (coalesced stores); accumulation adds to the stored rows directly
     const bool stage = Staged<CT, C>::ok && !acc;
+    const int64_t P = (int64_t)p.g.width * p.g.height;
     float c[C], S;
+    int e = 0;  // the row's shared exponent (WT_SE16)
     if (gp >= 0) {
         bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
         CT *dst = coeff + gp * C;
         if (acc) {
             float old[C];
-            load_row<CT, C>(dst, old);
+            load_row<CT, C>(dst, old, kIsSE16<CT> ? (int)se16_expo<C>(coeff, P)[gp] - kSE16Bias : 0);
 #pragma unroll
             for (int i = 0; i < C; ++i) c[i] += old[i];
         }
-        if (!stage) store_row<CT, C>(dst, c);
+        e = storage_exponent<CT, C>(c);
+        if constexpr (kIsSE16<CT>) se16_expo<C>(coeff, P)[gp] = (uint8_t)(e + kSE16Bias);
+        if (!stage) store_row<CT, C>(dst, c, e);
         if (p.zmin) {
             float v = __uint_as_float(sZ[lp]);
             if (acc) v = fminf(v, p.zmin[gp]);
@@ -56,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, MB) k_build(Params p) {
     if (stage) {
         uint4 *st = reinterpret_cast<uint4 *>(smem);
         __syncthreads();  // every bin row has been read
-        if (gp >= 0) stage_row<CT, C>(st, lp, c);
+        if (gp >= 0) stage_row<CT, C>(st, lp, c, e);
         __syncthreads();
         copy_staged<CT, C>(p, T, st, npx * Staged<CT, C>::K * 16, coeff);
     }
@@ -88,8 +92,9 @@ __global__ void __launch_bounds__(kThreads, MB) k_resolve(Params p) {
     }
     if (gp >= 0) {
         float v[C];
-        if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v);
-        else load_row<CT, C>(coeff + gp * C, v);
+        const int e = kIsSE16<CT> ? (int)se16_expo<C>(coeff, (int64_t)p.g.width * p.g.height)[gp] - kSE16Bias : 0;
+        if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v, e);
+        else load_row<CT, C>(coeff + gp * C, v, e);
         coeffs_to_bins<J>(v, kLog2e);
         put_bins<J>(vals + lp * LDV, v, p.zmin ? p.zmin[gp] : __int_as_float(0x7f800000),
                     DEF ? kDefaultFlags : p.flags);
@@ -155,16 +160,19 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     CT *coeff = static_cast<CT *>(p.coeff);
     const bool stage = Staged<CT, C>::ok && coeff != nullptr;
     float v[C], S = 0.f;
+    int e = 0;  // the row's shared exponent (WT_SE16)
     if (gp >= 0) {
         bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S, scaled);
-#pragma unroll
-        for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(Cvt<CT>::to(v[i]));  // storage precision
-        if (coeff && !stage) store_row<CT, C>(coeff + gp * C, v);
+        e = round_row<CT, C>(v);  // storage precision: the resolve uses the stored values
+        if constexpr (kIsSE16<CT>) {
+            if (coeff) se16_expo<C>(coeff, (int64_t)p.g.width * p.g.height)[gp] = (uint8_t)(e + kSE16Bias);
+        }
+        if (coeff && !stage) store_row<CT, C>(coeff + gp * C, v, e);
         if (p.zmin) p.zmin[gp] = __uint_as_float(sZ[lp]);
     }
     __syncthreads();  // every bin row has been read
     if (gp >= 0) {
-        if (stage) stage_row<CT, C>(reinterpret_cast<uint4 *>(accw), lp, v);
+        if (stage) stage_row<CT, C>(reinterpret_cast<uint4 *>(accw), lp, v, e);
         coeffs_to_bins<J>(v, kLog2e);
         put_bins<J>(vals + lp * LDV, v, __uint_as_float(sZ[lp]), DEF ? kDefaultFlags : p.flags);
         sS[lp] = S;
@@ -237,10 +245,12 @@ __global__ void __launch_bounds__(kThreads, MB) k_temporal(Params p, const void 
     fill_zero(sF, (int)(2 * Layout<J>::plane(npx)));
     for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
     __syncthreads();
+    const int64_t P = (int64_t)p.g.width * p.g.height;
     if (gp >= 0) {
         float v[C];
-        if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v);
-        else load_row<CT, C>(prev + gp * C, v);
+        const int e = kIsSE16<CT> ? (int)se16_expo<C>(prev, P)[gp] - kSE16Bias : 0;
+        if (Staged<CT, C>::ok) unstage_row<CT, C>(st, lp, v, e);
+        else load_row<CT, C>(prev + gp * C, v, e);
         coeffs_to_bins<J>(v, kLog2e);
         put_bins<J>(vals + lp * LDV, v, zmin_prev ? zmin_prev[gp] : __int_as_float(0x7f800000), flags);
     }
@@ -303,8 +313,10 @@ __global__ void __launch_bounds__(kThreads, MB) k_temporal(Params p, const void 
         composite_pixel(p, gp, acc.x, acc.y, acc.z, acc.w, S);
         if (p.zmin) p.zmin[gp] = __uint_as_float(sZ[lp]);
         if (next) {
-            if (stage) stage_row<CT, C>(st, lp, c);
-            else store_row<CT, C>(next + gp * C, c);
+            const int e = storage_exponent<CT, C>(c);
+            if constexpr (kIsSE16<CT>) se16_expo<C>(next, P)[gp] = (uint8_t)(e + kSE16Bias);
+            if (stage) stage_row<CT, C>(st, lp, c, e);
+            else store_row<CT, C>(next + gp * C, c, e);
         }
     }
     if (stage) {
@@ -318,6 +330,7 @@ cudaError_t launch_temporal_k(const Params &p, int ntiles, const void *coeff_pre
                               cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = TemporalLayout<J>::total(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(k_temporal<J, CT, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
@@ -450,8 +463,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
     float v[C], S = 0.f;
     if (gp >= 0) {
         bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, v, S, scaled);
-#pragma unroll
-        for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(Cvt<CT>::to(v[i]));
+        round_row<CT, C>(v);  // the forward pass resolves with the stored values
         coeffs_to_bins<J>(v, kLog2e);
     }
     __syncthreads();
@@ -574,6 +586,7 @@ template <int J, typename CT>
 cudaError_t launch_serve_t(const Params *slots, const ServeTask *tasks, int ntasks, int64_t total,
                            unsigned long long *counter, int npx, int grid, cudaStream_t s) {
     const size_t bytes = Layout<J>::fused(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(k_serve<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k_serve<J, CT><<<grid, kThreads, bytes, s>>>(slots, tasks, ntasks, total, counter);
@@ -584,6 +597,7 @@ cudaError_t launch_serve_t(const Params *slots, const ServeTask *tasks, int ntas
 template <int J, typename CT> int serve_blocks_per_sm(int npx) {
     int n = 0;
     const size_t bytes = Layout<J>::fused(npx);
+    if (bytes > kMaxSmemPerBlock) return 0;
     if (cudaFuncSetAttribute(k_serve<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_serve<J, CT>, kThreads, bytes) != cudaSuccess) return 0;
@@ -593,6 +607,7 @@ template <int J, typename CT> int serve_blocks_per_sm(int npx) {
 template <int J, typename CT> cudaError_t launch_backward_t(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = BackLayout<J>::total(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(k_backward<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k_backward<J, CT><<<ntiles, kThreads, bytes, s>>>(p);
@@ -617,11 +632,14 @@ __global__ void __launch_bounds__(kThreads)
         return;
     }
     const CT *c = static_cast<const CT *>(p.coeff) + (int64_t)px * C;
+    const float unit =
+        kIsSE16<CT> ? se16_unit((int)se16_expo<C>(p.coeff, (int64_t)p.g.width * p.g.height)[px] - kSE16Bias) : 0.f;
     auto bin = [&](int m) {
-        float A = Cvt<CT>::from(c[0]);
+        float A = from_storage<CT>(c[0], 0, unit);
 #pragma unroll
         for (int n = 0; n < J; ++n) {
-            const float d = sqrt2_pow(n) * Cvt<CT>::from(c[(1 << n) + (m >> (J - n))]);
+            const int i = (1 << n) + (m >> (J - n));
+            const float d = sqrt2_pow(n) * from_storage<CT>(c[i], i, unit);
             A = ((m >> (J - 1 - n)) & 1) ? A - d : A + d;
         }
         return A;
@@ -652,13 +670,14 @@ __global__ void __launch_bounds__(kThreads)
 template <int J, typename CT, int MB> cudaError_t launch_build_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::build(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(k_build<J, CT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k_build<J, CT, MB><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
 }
 template <int J, typename CT> cudaError_t launch_build_t(const Params &p, int ntiles, cudaStream_t s) {
-    if constexpr (MinBlocks<J>::value < 4) {
+    if constexpr (J == 5) {
         if (p.g.tile_w * p.g.tile_h <= 192) return launch_build_k<J, CT, 4>(p, ntiles, s);
     }
     return launch_build_k<J, CT, MinBlocks<J>::value>(p, ntiles, s);
@@ -668,6 +687,7 @@ template <int J, typename CT, bool COMPOSITE, bool DEF, int MB>
 cudaError_t launch_resolve_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::resolve(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(k_resolve<J, CT, COMPOSITE, DEF, MB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -681,7 +701,7 @@ template <int J, typename CT, bool COMPOSITE>
 cudaError_t launch_resolve_t(const Params &p, int ntiles, cudaStream_t s) {
     if constexpr (COMPOSITE) {
         const bool def = (p.flags & ~kAccumulate) == kDefaultFlags;
-        if constexpr (MinBlocks<J>::value < 4) {
+        if constexpr (J == 5) {
             if (p.g.tile_w * p.g.tile_h <= 192)
                 return def ? launch_resolve_k<J, CT, true, true, 4>(p, ntiles, s)
                            : launch_resolve_k<J, CT, true, false, 4>(p, ntiles, s);
@@ -697,6 +717,7 @@ template <int J, typename CT, bool DEF, int MB>
 cudaError_t launch_fused_k(const Params &p, int ntiles, cudaStream_t s) {
     const int npx = p.g.tile_w * p.g.tile_h;
     const size_t bytes = Layout<J>::fused(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e =
         cudaFuncSetAttribute(k_fused<J, CT, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -707,7 +728,7 @@ cudaError_t launch_fused_k(const Params &p, int ntiles, cudaStream_t s) {
 constexpr int kFourBlockTilePx = 192;
 template <int J, typename CT> cudaError_t launch_fused_t(const Params &p, int ntiles, cudaStream_t s) {
     const bool def = p.flags == kDefaultFlags;
-    if constexpr (MinBlocks<J>::value < 4) {
+    if constexpr (J == 5) {
         if (p.g.tile_w * p.g.tile_h <= kFourBlockTilePx)
             return def ? launch_fused_k<J, CT, true, 4>(p, ntiles, s) : launch_fused_k<J, CT, false, 4>(p, ntiles, s);
     }
@@ -727,33 +748,17 @@ cudaError_t launch_absorbance_t(const Params &p, int64_t q, const uint32_t *qpx,
 }  // namespace wt
 
 // One translation unit per storage type instantiates every J.
-#define WT_INSTANTIATE_TABLES(CT, IDX)                                                              \
-    namespace wt {                                                                                 \
-    const TileLaunch kBuild##IDX[5] = {launch_build_t<1, CT>, launch_build_t<2, CT>,               \
-                                       launch_build_t<3, CT>, launch_build_t<4, CT>,               \
-                                       launch_build_t<5, CT>};                                     \
-    const TileLaunch kResolve##IDX[5] = {launch_resolve_t<1, CT, false>, launch_resolve_t<2, CT, false>, \
-                                         launch_resolve_t<3, CT, false>, launch_resolve_t<4, CT, false>, \
-                                         launch_resolve_t<5, CT, false>};                          \
-    const TileLaunch kResolveComp##IDX[5] = {                                                      \
-        launch_resolve_t<1, CT, true>, launch_resolve_t<2, CT, true>, launch_resolve_t<3, CT, true>, \
-        launch_resolve_t<4, CT, true>, launch_resolve_t<5, CT, true>};                             \
-    const TileLaunch kFused##IDX[5] = {launch_fused_t<1, CT>, launch_fused_t<2, CT>,               \
-                                       launch_fused_t<3, CT>, launch_fused_t<4, CT>,               \
-                                       launch_fused_t<5, CT>};                                     \
-    const TileLaunch kBackward##IDX[5] = {launch_backward_t<1, CT>, launch_backward_t<2, CT>,     \
-                                          launch_backward_t<3, CT>, launch_backward_t<4, CT>,     \
-                                          launch_backward_t<5, CT>};                              \
-    const ServeLaunch kServe##IDX[5] = {launch_serve_t<1, CT>, launch_serve_t<2, CT>,             \
-                                        launch_serve_t<3, CT>, launch_serve_t<4, CT>,             \
-                                        launch_serve_t<5, CT>};                                   \
-    const ServeOccupancy kServeOcc##IDX[5] = {serve_blocks_per_sm<1, CT>, serve_blocks_per_sm<2, CT>, \
-                                              serve_blocks_per_sm<3, CT>, serve_blocks_per_sm<4, CT>, \
-                                              serve_blocks_per_sm<5, CT>};                        \
-    const TemporalLaunch kTemporal##IDX[5] = {launch_temporal_t<1, CT>, launch_temporal_t<2, CT>,   \
-                                              launch_temporal_t<3, CT>, launch_temporal_t<4, CT>,   \
-                                              launch_temporal_t<5, CT>};                            \
-    const QueryLaunch kAbsorbance##IDX[5] = {                                                      \
-        launch_absorbance_t<1, CT>, launch_absorbance_t<2, CT>, launch_absorbance_t<3, CT>,       \
-        launch_absorbance_t<4, CT>, launch_absorbance_t<5, CT>};                                   \
+#define WT_JS(F, ...) {F<1, __VA_ARGS__>, F<2, __VA_ARGS__>, F<3, __VA_ARGS__>, F<4, __VA_ARGS__>, \
+                       F<5, __VA_ARGS__>, F<6, __VA_ARGS__>}
+#define WT_INSTANTIATE_TABLES(CT, IDX)                                                             \
+    namespace wt {                                                                                \
+    const TileLaunch kBuild##IDX[kMaxJ] = WT_JS(launch_build_t, CT);                               \
+    const TileLaunch kResolve##IDX[kMaxJ] = WT_JS(launch_resolve_t, CT, false);                    \
+    const TileLaunch kResolveComp##IDX[kMaxJ] = WT_JS(launch_resolve_t, CT, true);                 \
+    const TileLaunch kFused##IDX[kMaxJ] = WT_JS(launch_fused_t, CT);                               \
+    const TileLaunch kBackward##IDX[kMaxJ] = WT_JS(launch_backward_t, CT);                         \
+    const ServeLaunch kServe##IDX[kMaxJ] = WT_JS(launch_serve_t, CT);                              \
+    const ServeOccupancy kServeOcc##IDX[kMaxJ] = WT_JS(serve_blocks_per_sm, CT);                   \
+    const TemporalLaunch kTemporal##IDX[kMaxJ] = WT_JS(launch_temporal_t, CT);                     \
+    const QueryLaunch kAbsorbance##IDX[kMaxJ] = WT_JS(launch_absorbance_t, CT);                    \
     }

@@ -96,7 +96,6 @@ double now_us() {
     using namespace std::chrono;
     return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
 }
-size_t dsize(int dt) { return dt == WT_F32 ? 4 : 2; }
 int64_t ntiles(const wt_desc *d) {
     return (int64_t)((d->width + d->tile_w - 1) / d->tile_w) * ((d->height + d->tile_h - 1) / d->tile_h);
 }
@@ -209,7 +208,7 @@ bool ServerImpl::step_locked(std::unique_lock<std::mutex> &lk) {
         if (e == cudaSuccess) e = cudaMemsetAsync(d_counter[b], 0, sizeof(unsigned long long), stream);
         const int npx = cfg.tile_w * cfg.tile_h;
         const int grid = (int)std::min<int64_t>(total, (int64_t)sms * occupancy);
-        const ServeLaunch *L = cfg.coeff_dtype == WT_F32 ? kServe0 : (cfg.coeff_dtype == WT_BF16 ? kServe1 : kServe2);
+        const ServeLaunch *L = by_dtype(cfg.coeff_dtype, kServe0, kServe1, kServe2, kServe3);
         if (e == cudaSuccess) e = L[cfg.J - 1](d_slots, d_tasks[b], nt, total, d_counter[b], npx, grid, stream);
         if (e != cudaSuccess) {
             fault = WT_ERR_CUDA;
@@ -256,8 +255,8 @@ extern "C" {
 wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **out) {
     WT_TRACE();
     if (!cfg || !out) return WT_ERR_ARG;
-    if (cfg->J < 1 || cfg->J > 5 || (cfg->coeff_dtype != WT_F32 && cfg->coeff_dtype != WT_BF16 &&
-                                     cfg->coeff_dtype != WT_F16))
+    if (cfg->J < 1 || cfg->J > kMaxJ || (cfg->coeff_dtype != WT_F32 && cfg->coeff_dtype != WT_BF16 &&
+                                     cfg->coeff_dtype != WT_F16 && cfg->coeff_dtype != WT_SE16))
         return WT_ERR_UNSUPPORTED;
     if (cfg->max_slots < 1 || cfg->max_slots > 4096 || cfg->mem_cap_bytes <= 0 || cfg->step_tiles < 1 ||
         cfg->tile_w < 1 || cfg->tile_h < 1 || (int64_t)cfg->tile_w * cfg->tile_h > kMaxTilePx)
@@ -270,7 +269,7 @@ wt_status wt_serve_create(const wt_serve_config *cfg, wt_server **out) {
         delete s;
         return WT_ERR_CUDA;
     }
-    const ServeOccupancy *O = cfg->coeff_dtype == WT_F32 ? kServeOcc0 : (cfg->coeff_dtype == WT_BF16 ? kServeOcc1 : kServeOcc2);
+    const ServeOccupancy *O = by_dtype(cfg->coeff_dtype, kServeOcc0, kServeOcc1, kServeOcc2, kServeOcc3);
     S.occupancy = std::max(1, O[cfg->J - 1](cfg->tile_w * cfg->tile_h));
     S.max_tasks = cfg->max_slots;
     S.err = error_word();
@@ -320,7 +319,7 @@ wt_status wt_serve_submit(wt_server *s, const wt_desc *d, const wt_frags *f, con
     const int64_t P = (int64_t)d->width * d->height;
     ServerImpl::Req r;
     r.desc = *d;
-    r.coeff_bytes = (size_t)P * ((size_t)1 << d->J) * dsize(d->coeff_dtype);
+    r.coeff_bytes = coeff_storage_bytes(P, d->J, d->coeff_dtype);
     Params &p = r.params;
     std::memset(&p, 0, sizeof(p));
     p.g.width = d->width;

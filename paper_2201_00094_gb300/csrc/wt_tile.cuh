@@ -164,39 +164,141 @@ __device__ __forceinline__ void e5_decode(uint32_t w, float &r, float &g, float 
     b = (float)((w >> 18) & 511u) * scale;
 }
 
+// Shared-exponent 16-bit storage (WT_SE16).  The sign property of §2.3.1
+// (chi_00 >= 0, every X_{n,k} <= 0) makes every coefficient a magnitude, as in
+// the paper's E5B9G9R9 words (§2.1); here one exponent is shared by the 2^J
+// coefficients of a pixel.  Per pixel: m_0 = chi_00 and m_i = -X_{n,k}
+// 2^floor(n/2) (i = 2^n + k), so that every m_i is at most the pixel's total
+// step; e = floor(log2 max m) + 1 (clamped to [-100, 100]), q_i =
+// rint(m_i 2^(16 - e)) as unsigned 16-bit mantissas, e raised by one when the
+// largest q reaches 2^16.  The mantissas sit where a 16-bit row would,
+// [P][C] pixel-major; the P exponent bytes (e + 128) follow them.  Every
+// decoded value is q_i 2^(e - 16 - floor(n/2)) exactly, and its error is at
+// most half a unit of the pixel's largest magnitude, not of its own size.
+struct se16_t {
+    uint16_t q;
+};
+template <typename CT> constexpr bool kIsSE16 = std::is_same<CT, se16_t>::value;
+constexpr int kSE16Emin = -100, kSE16Emax = 100, kSE16Bias = 128;
+
+// 2^floor(n/2) for heap index i = 2^n + k (1 for chi_00); constant-folded in
+// unrolled loops
+__device__ __forceinline__ float se16_level_scale(int i) {
+    return i > 0 ? (float)(1 << ((31 - __clz(i)) >> 1)) : 1.f;
+}
+// 2^k for -126 <= k <= 127
+__device__ __forceinline__ float exp2i(int k) { return __int_as_float((127 + k) << 23); }
+// rint(x) for 0 <= x < 2^22 as an integer: x + 2^23 rounds half to even onto
+// the integers, whose low mantissa bits are then the result
+__device__ __forceinline__ uint32_t rint_small(float x) {
+    return (uint32_t)(__float_as_int(__fadd_rn(x, 8388608.f)) - 0x4B000000);
+}
+// q as a float for q < 2^23 (2^23 + q is exact; subtracting 2^23 leaves q)
+__device__ __forceinline__ float small_to_float(uint32_t q) { return __uint_as_float(0x4B000000u | q) - 8388608.f; }
+
+// Byte plane of the exponents behind the P * C mantissas.
+template <int C> __device__ __forceinline__ uint8_t *se16_expo(const void *coeff, int64_t P) {
+    return (uint8_t *)coeff + (size_t)P * C * 2;
+}
+
+// Encodes a row in place: v becomes the decoded values; returns e.
+template <int C> __device__ __forceinline__ int se16_round(float (&v)[C]) {
+    float m[C];
+    float M = 0.f;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        m[i] = (i == 0 ? fmaxf(v[i], 0.f) : fmaxf(-v[i], 0.f)) * se16_level_scale(i);  // NaN -> 0
+        M = fmaxf(M, m[i]);
+    }
+    const int ex = (__float_as_int(M) >> 23) & 0xff;
+    int e = ex > 0 ? min(max(ex - 126, kSE16Emin), kSE16Emax) : kSE16Emin;
+    float scale = exp2i(16 - e);
+    if (rint_small(M * scale) >= 65536u) {
+        ++e;
+        scale *= 0.5f;
+    }
+    const float unit = exp2i(e - 16);
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const float d = small_to_float(min(rint_small(m[i] * scale), 65535u)) * (unit / se16_level_scale(i));
+        v[i] = i == 0 ? d : -d;
+    }
+    return e;
+}
+
+// Rounds a row to the storage precision in place (the values the resolve
+// uses) and returns the row's shared exponent (0 for the per-element types).
+template <typename CT, int C> __device__ __forceinline__ int round_row(float (&v)[C]) {
+    if constexpr (kIsSE16<CT>) {
+        return se16_round<C>(v);
+    } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(Cvt<CT>::to(v[i]));
+        return 0;
+    }
+}
+// The shared exponent of a row about to be stored; rounds the row in place
+// for WT_SE16 and leaves the per-element types untouched (their stores round).
+template <typename CT, int C> __device__ __forceinline__ int storage_exponent(float (&v)[C]) {
+    if constexpr (kIsSE16<CT>) return se16_round<C>(v);
+    else return 0;
+}
+
+// Element i of a row to / from storage form.  For WT_SE16, v must already be
+// a decoded value of the row (round_row / storage_exponent) and scale =
+// 2^(16 - e), unit = 2^(e - 16) for the row's exponent e; the mantissa is then
+// exact.
+template <typename CT> __device__ __forceinline__ CT to_storage(float v, int i, float scale) {
+    if constexpr (kIsSE16<CT>) return CT{(uint16_t)rint_small(fabsf(v) * (scale * se16_level_scale(i)))};
+    else return Cvt<CT>::to(v);
+}
+template <typename CT> __device__ __forceinline__ float from_storage(CT x, int i, float unit) {
+    if constexpr (kIsSE16<CT>) {
+        const float d = small_to_float(x.q) * (unit / se16_level_scale(i));
+        return i == 0 ? d : -d;
+    } else {
+        return Cvt<CT>::from(x);
+    }
+}
+__device__ __forceinline__ float se16_scale(int e) { return exp2i(16 - e); }
+__device__ __forceinline__ float se16_unit(int e) { return exp2i(e - 16); }
+
 // One pixel's C coefficients to / from global memory, 16-byte vectors when
-// the row is a multiple of 16 bytes (it is 16-byte aligned then).
+// the row is a multiple of 16 bytes (it is 16-byte aligned then).  e is the
+// row's shared exponent (WT_SE16; ignored otherwise).
 template <typename CT, int C>
-__device__ __forceinline__ void store_row(CT *dst, const float (&v)[C]) {
+__device__ __forceinline__ void store_row(CT *dst, const float (&v)[C], int e = 0) {
     constexpr int PER = 16 / sizeof(CT);
+    const float scale = kIsSE16<CT> ? se16_scale(e) : 0.f;
     if constexpr (C % PER == 0) {
 #pragma unroll
         for (int q = 0; q < C / PER; ++q) {
-            union { uint4 u; CT e[PER]; } pk;
+            union { uint4 u; CT x[PER]; } pk;
 #pragma unroll
-            for (int i = 0; i < PER; ++i) pk.e[i] = Cvt<CT>::to(v[q * PER + i]);
+            for (int i = 0; i < PER; ++i) pk.x[i] = to_storage<CT>(v[q * PER + i], q * PER + i, scale);
             reinterpret_cast<uint4 *>(dst)[q] = pk.u;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < C; ++i) dst[i] = Cvt<CT>::to(v[i]);
+        for (int i = 0; i < C; ++i) dst[i] = to_storage<CT>(v[i], i, scale);
     }
 }
 
 template <typename CT, int C>
-__device__ __forceinline__ void load_row(const CT *src, float (&v)[C]) {
+__device__ __forceinline__ void load_row(const CT *src, float (&v)[C], int e = 0) {
     constexpr int PER = 16 / sizeof(CT);
+    const float unit = kIsSE16<CT> ? se16_unit(e) : 0.f;
     if constexpr (C % PER == 0) {
 #pragma unroll
         for (int q = 0; q < C / PER; ++q) {
-            union { uint4 u; CT e[PER]; } pk;
+            union { uint4 u; CT x[PER]; } pk;
             pk.u = reinterpret_cast<const uint4 *>(src)[q];
 #pragma unroll
-            for (int i = 0; i < PER; ++i) v[q * PER + i] = Cvt<CT>::from(pk.e[i]);
+            for (int i = 0; i < PER; ++i) v[q * PER + i] = from_storage<CT>(pk.x[i], q * PER + i, unit);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < C; ++i) v[i] = Cvt<CT>::from(src[i]);
+        for (int i = 0; i < C; ++i) v[i] = from_storage<CT>(src[i], i, unit);
     }
 }
 
@@ -213,30 +315,32 @@ template <typename CT, int C> struct Staged {
 };
 
 template <typename CT, int C>
-__device__ __forceinline__ void stage_row(uint4 *stage, int lp, const float (&v)[C]) {
+__device__ __forceinline__ void stage_row(uint4 *stage, int lp, const float (&v)[C], int e = 0) {
     using S = Staged<CT, C>;
     constexpr int PER = 16 / sizeof(CT);
     const int sw = S::sw(lp);
+    const float scale = kIsSE16<CT> ? se16_scale(e) : 0.f;
 #pragma unroll
     for (int q = 0; q < S::K; ++q) {
-        union { uint4 u; CT e[PER]; } pk;
+        union { uint4 u; CT x[PER]; } pk;
 #pragma unroll
-        for (int i = 0; i < PER; ++i) pk.e[i] = Cvt<CT>::to(v[q * PER + i]);
+        for (int i = 0; i < PER; ++i) pk.x[i] = to_storage<CT>(v[q * PER + i], q * PER + i, scale);
         stage[lp * S::K + (q ^ sw)] = pk.u;
     }
 }
 
 template <typename CT, int C>
-__device__ __forceinline__ void unstage_row(const uint4 *stage, int lp, float (&v)[C]) {
+__device__ __forceinline__ void unstage_row(const uint4 *stage, int lp, float (&v)[C], int e = 0) {
     using S = Staged<CT, C>;
     constexpr int PER = 16 / sizeof(CT);
     const int sw = S::sw(lp);
+    const float unit = kIsSE16<CT> ? se16_unit(e) : 0.f;
 #pragma unroll
     for (int q = 0; q < S::K; ++q) {
-        union { uint4 u; CT e[PER]; } pk;
+        union { uint4 u; CT x[PER]; } pk;
         pk.u = stage[lp * S::K + (q ^ sw)];
 #pragma unroll
-        for (int i = 0; i < PER; ++i) v[q * PER + i] = Cvt<CT>::from(pk.e[i]);
+        for (int i = 0; i < PER; ++i) v[q * PER + i] = from_storage<CT>(pk.x[i], q * PER + i, unit);
     }
 }
 

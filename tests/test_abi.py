@@ -74,9 +74,13 @@ def test_bad_descriptor_rejected_on_host(L, bad):
 
 
 def test_unsupported_J_and_flags(L):
-    d = wt.make_desc(64, 64, 6)
+    d = wt.make_desc(64, 64, 7)
     fr = wt.WtFrags()
     assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 2
+    # J = 6 is accepted (64 coefficients per pixel); these frags are then refused as arguments
+    d6 = wt.make_desc(64, 64, 6)
+    assert L.wt_coeff_bytes(ctypes.byref(d6)) == 64 * 64 * 64 * 4
+    assert L.wt_build(ctypes.byref(d6), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 1
     d = wt.make_desc(64, 64, 4, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
     bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
     st = L.wt_build_resolve(ctypes.byref(d), ctypes.byref(fr), None, None, None, bg,
@@ -106,3 +110,13 @@ def test_binding_requires_cuda_tensors():
     with pytest.raises(ValueError):
         wt.make_frags(torch.zeros(4, dtype=torch.int32), torch.zeros(4), torch.zeros(4),
                       torch.zeros(2, dtype=torch.int64))
+
+
+def test_coefficient_bytes_of_every_storage_type(L):
+    """P * 2^J values of 4 or 2 bytes; the shared-exponent type adds one byte per pixel."""
+    for J in (1, 4, 6):
+        for dt, per in ((wt.F32, 4), (wt.BF16, 2), (wt.F16, 2), (wt.SE16, 2)):
+            d = wt.make_desc(33, 7, J, dt)
+            want = 33 * 7 * (1 << J) * per + (33 * 7 if dt == wt.SE16 else 0)
+            assert L.wt_coeff_bytes(ctypes.byref(d)) == want == wt.coeff_storage_bytes(d)
+    assert L.wt_coeff_bytes(ctypes.byref(wt.make_desc(33, 7, 4, 4))) == 0  # unknown type

@@ -42,7 +42,7 @@ def _close(got, ref, rel=1e-3, absfrac=1e-5):
 
 
 @pytest.mark.parametrize("flags", [7, 3, 5, 6, 4, 1])
-@pytest.mark.parametrize("J", [2, 4, 5])
+@pytest.mark.parametrize("J", [2, 4, 5, 6])
 def test_backward_matches_oracle_gradient(flags, J):
     fr = synth.uniform_frame(37, 29, 6.0, 40, alpha_range=(0.05, 0.6), J=J, seed=30 + J + flags)
     gout = np.random.default_rng(J + flags).standard_normal((fr.P, 4))

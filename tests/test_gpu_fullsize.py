@@ -11,10 +11,11 @@ import torch
 import oracle
 import paper_2201_00094_gb300 as wt
 import synth
+from wtcheck import e5_oracle_composite, e5_words_of
 
 pytestmark = pytest.mark.gpu
 
-DT = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}
+DT = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16, "se16": wt.SE16}
 
 
 def test_absorbance_step_accuracy():
@@ -45,11 +46,11 @@ def test_absorbance_step_accuracy():
     assert rel.max() < 6e-7, (rel.max(), al[rel.argmax()])
 
 
-def _sample_check(fr, J, dtype, flags, fused, npix, seed):
+def _sample_check(fr, J, dtype, flags, fused, npix, seed, pixels=None):
     dev = fr.pixel.device
     d = wt.make_desc(fr.width, fr.height, J, DT[dtype], flags, fr.tile_w, fr.tile_h)
     f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
-    coeff = torch.empty(fr.P, 1 << J, device=dev, dtype=wt.coeff_torch_dtype(DT[dtype]))
+    coeff = wt.coeff_buffer(d, dev)
     out = torch.empty(fr.P, 4, device=dev)
     if fused:
         wt.wt_build_resolve(d, f, out, coeff, None, bg=fr.bg)
@@ -58,8 +59,9 @@ def _sample_check(fr, J, dtype, flags, fused, npix, seed):
         wt.wt_build(d, f, coeff, zmin)
         wt.wt_resolve_composite(d, f, coeff, zmin, out, bg=fr.bg)
     assert wt.wt_get_error() == 0
-    rng = np.random.default_rng(seed)
-    pix = torch.from_numpy(rng.choice(fr.P, npix, replace=False)).to(dev)
+    if pixels is None:
+        pixels = np.random.default_rng(seed).choice(fr.P, npix, replace=False)
+    pix = torch.from_numpy(np.asarray(pixels)).to(dev)
     idx, loc = synth.pixel_subset(fr, pix)
     h = {k: getattr(fr, k)[idx].cpu().numpy() for k in ("z", "alpha", "r", "g", "b")}
     loc = loc.cpu().numpy().astype(np.uint32)
@@ -91,42 +93,78 @@ def test_heavy4k_fp32_sampled_pixels(heavy4k, fused):
     assert err.max() <= 1e-4, (err.max(), counts[err.argmax()])
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_heavy4k_16bit_storage_error_by_depth(heavy4k, dtype, capsys):
-    """16-bit coefficient storage, FP32 accumulation: error against FP64 by
-    fragments-per-pixel bucket.
+# Fragments-per-pixel count below which BF16 storage holds 2e-3 on these
+# frames; deeper pixels exceed it (see _check_16bit).
+BF16_HOLDS_BELOW = 32
 
-    Bound from the arithmetic: a stored coefficient is off by at most u of
-    itself (u = 2^-9 for BF16, 2^-11 for FP16); a bin value is chi_00 plus J
-    detail terms, of size at most S_p and S_p/2 (S_p = the pixel's total step),
-    so |dA| <= u (1 + J/2) S_p; weights off by factors within e^(+-dA) move the
-    normalised colour R/W, a weighted mean of colours in [0, 1], by at most
-    tanh(dA) <= dA.  Every pixel is held to that (plus the FP32 path's 1e-4).
-    FP16 also meets the 2e-3 target everywhere in this frame; BF16's share
-    within 2e-3 is reported, not hidden."""
-    err, counts, S = _sample_check(heavy4k, 5, dtype, wt.DEFAULT_FLAGS, True, 4096, seed=4097)
-    u = 2.0 ** -9 if dtype == "bf16" else 2.0 ** -11
-    assert (err <= u * (1 + 5 / 2) * S + 1e-4).all(), float(np.max(err - u * 3.5 * S))
-    edges = [0, 8, 16, 32, 48, 64, 128, 256, 2048]
+
+def _check_16bit(err, counts, S, dtype, J, frame, capsys):
+    """16-bit coefficient storage, FP32 accumulation: error against FP64 by
+    fragments-per-pixel bucket, reported, and asserted against the 2e-3 target
+    wherever the format can hold it.
+
+    * SE16 (shared exponent) and FP16 hold 2e-3 on every sampled pixel.
+    * BF16 cannot on deep pixels, by its arithmetic: a stored coefficient is
+      off by up to u = 2^-8 of itself (8-bit significand); a bin value is
+      chi_00 plus J detail terms, of size at most S_p and S_p/2 (S_p = the
+      pixel's total step), so |dA| <= u (1 + J/2) S_p, and weights off by
+      factors within e^(+-dA) move the normalised colour (a weighted mean of
+      colours in [0, 1]) by at most tanh(dA) <= dA.  That bound passes 2e-3
+      once S_p > 0.15; measured, BF16 stays within 2e-3 below 32 fragments per
+      pixel, which is asserted, and every pixel is held to the bound."""
+    edges = [0, 8, 16, 32, 48, 64, 128, 256, 512, 2048]
     rows = []
     for lo, hi in zip(edges[:-1], edges[1:]):
         m = (counts >= lo) & (counts < hi)
         if m.any():
             rows.append((lo, hi, int(m.sum()), float(err[m].max()), float(np.median(err[m]))))
     with capsys.disabled():
-        print(f"\n{dtype} storage, heavy4k, max|err| by fragments/pixel "
+        print(f"\n{dtype} storage, {frame}, max|err| by fragments/pixel "
               f"({100 * np.mean(err <= 2e-3):.2f}% of pixels within 2e-3):")
         for r in rows:
             print(f"  [{r[0]:4d},{r[1]:4d}) n={r[2]:5d} max={r[3]:.2e} median={r[4]:.2e}")
-    if dtype == "f16":
-        assert err.max() <= 2e-3
+    if dtype in ("se16", "f16"):
+        assert err.max() <= 2e-3, (err.max(), counts[err.argmax()])
+    else:
+        u = 2.0 ** -8
+        assert (err <= u * (1 + J / 2) * S + 1e-4).all(), float(np.max(err - u * (1 + J / 2) * S))
+        shallow = counts < BF16_HOLDS_BELOW
+        assert err[shallow].max() <= 2e-3, (err[shallow].max(), counts[shallow][err[shallow].argmax()])
 
 
-def test_smoke1080_sampled_pixels():
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "se16"])
+def test_heavy4k_16bit_storage_error_by_depth(heavy4k, dtype, capsys):
+    err, counts, S = _sample_check(heavy4k, 5, dtype, wt.DEFAULT_FLAGS, True, 4096, seed=4097)
+    _check_16bit(err, counts, S, dtype, 5, "heavy4k", capsys)
+
+
+@pytest.fixture(scope="module")
+def smoke1080():
     fr = synth.smoke1080(seed=0, device="cuda")
+    yield fr
+    del fr
+    torch.cuda.empty_cache()
+
+
+def test_smoke1080_sampled_pixels(smoke1080):
     for fused in (True, False):
-        err, counts, _ = _sample_check(fr, 4, "f32", wt.DEFAULT_FLAGS, fused, 4096, seed=1080)
+        err, counts, _ = _sample_check(smoke1080, 4, "f32", wt.DEFAULT_FLAGS, fused, 4096, seed=1080)
         assert err.max() <= 1e-4, (err.max(), counts[err.argmax()])
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "se16"])
+def test_smoke1080_16bit_storage_error_by_depth(smoke1080, dtype, capsys):
+    """The 1920x1080 smoke frame (FP32 vs BF16/FP16 storage), 4096 sampled
+    pixels weighted to the smoke: half drawn from pixels with 24 or more
+    fragments."""
+    fr = smoke1080
+    cnt = torch.bincount(fr.pixel.long(), minlength=fr.P).cpu().numpy()
+    rng = np.random.default_rng(1081)
+    deep = np.nonzero(cnt >= 24)[0]
+    pix = np.unique(np.concatenate([rng.choice(fr.P, 2048, replace=False),
+                                    rng.choice(deep, 2048, replace=False)]))
+    err, counts, S = _sample_check(fr, 4, dtype, wt.DEFAULT_FLAGS, True, len(pix), None, pixels=pix)
+    _check_16bit(err, counts, S, dtype, 4, "smoke1080", capsys)
 
 
 def test_fused_equals_two_pass_full_frame(heavy4k):
@@ -152,33 +190,41 @@ def test_fused_equals_two_pass_full_frame(heavy4k):
 
 def test_heavy4k_coloured_sampled_pixels(heavy4k):
     """Coloured absorbance on the bench's frame (opacities alpha x (1, .8, .6)),
-    FP32 and E5B9G9R9 storage: 2048 sampled pixels against the oracle (with
-    the decoded coefficients for E5B9G9R9)."""
+    2048 sampled pixels.  FP32 storage: composites within 1e-4 of the oracle.
+    E5B9G9R9: the stored words equal, bit for bit, the oracle's encoding of
+    the FP32 call's coefficients, and the composite equals the one computed
+    wholly on the oracle side (its own encoding) at 1e-4 wherever the two
+    encodings agree, within the one-step bound elsewhere."""
     fr = heavy4k
     dev = fr.pixel.device
     d = wt.make_desc(fr.width, fr.height, 5, tile_w=fr.tile_w, tile_h=fr.tile_h)
     f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
     ac = [fr.alpha, (fr.alpha * 0.8).contiguous(), (fr.alpha * 0.6).contiguous()]
-    out = torch.empty(fr.P, 4, device=dev)
     rng = np.random.default_rng(4100)
     pix = torch.from_numpy(rng.choice(fr.P, 2048, replace=False)).to(dev)
     idx, loc = synth.pixel_subset(fr, pix)
     h = {k: getattr(fr, k)[idx].cpu().numpy() for k in ("z", "r", "g", "b")}
+    h["pixel"] = loc.cpu().numpy().astype(np.uint32)
     al = [a[idx].cpu().numpy() for a in ac]
-    loc = loc.cpu().numpy().astype(np.uint32)
+    out = torch.empty(fr.P, 4, device=dev)
+    c32 = torch.empty(3, fr.P, 32, device=dev)
+    wt.wt_build_resolve_rgb(d, f, *ac, out, c32, wt.RGB_F32, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    ref = oracle.composite_rgb(h["pixel"], h["z"], al, (h["r"], h["g"], h["b"]), 2048, 5, bg=fr.bg)
+    assert np.abs(out[pix].cpu().numpy() - ref).max() <= 1e-4
+    c32s = [c32[c][pix].cpu().numpy() for c in range(3)]
+    del c32
     words = torch.empty(fr.P, 32, device=dev, dtype=torch.int32)
-    for fmt, coeff in ((wt.RGB_F32, None), (wt.RGB_E5B9G9R9, words)):
-        wt.wt_build_resolve_rgb(d, f, *ac, out, coeff, fmt, bg=fr.bg)
-        assert wt.wt_get_error() == 0
-        coeffs = None
-        if fmt == wt.RGB_E5B9G9R9:
-            dec = oracle.e5_decode(words[pix].cpu().numpy().view(np.uint32))
-            sign = np.where(np.arange(32) == 0, 1.0, -1.0)
-            coeffs = [sign * dec[c] for c in range(3)]
-        ref = oracle.composite_rgb(loc, h["z"], al, (h["r"], h["g"], h["b"]), 2048, 5, bg=fr.bg,
-                                   coeffs=coeffs)
-        err = np.abs(out[pix].cpu().numpy() - ref).max()
-        assert err <= 1e-4, (fmt, err)
+    wt.wt_build_resolve_rgb(d, f, *ac, out, words, wt.RGB_E5B9G9R9, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    w = words[pix].cpu().numpy().view(np.uint32)
+    assert np.array_equal(w, e5_words_of(c32s, 32))
+    got = out[pix].cpu().numpy().astype(np.float64)
+    ref, bound, same = e5_oracle_composite(h, al, 2048, 5, fr.bg, w)
+    err = np.abs(got - ref).max(axis=1)
+    assert same.mean() > 0.99
+    assert err[same].max() <= 1e-4
+    assert (err <= bound).all()
 
 
 def test_heavy4k_chromatic_aberration_sampled_pixels(heavy4k):

@@ -38,14 +38,16 @@ def _direct(fr, dtype=wt.BF16):
     return out
 
 
-# Two runs of the same frame differ only in the order of FP32 shared-memory
-# additions; with 16-bit storage that can move a coefficient by one 16-bit
-# ulp, so those runs are compared at the 16-bit storage tolerance.
-TOL = {wt.F32: 1e-5, wt.BF16: 2e-3, wt.F16: 2e-3}
-
-
-@pytest.mark.parametrize("dtype", [wt.F32, wt.BF16])
+@pytest.mark.parametrize("dtype", [wt.F32, wt.BF16, wt.SE16])
 def test_served_frame_equals_direct_call_and_oracle(dtype):
+    """A served frame is the direct call's result bit for bit (every tile is
+    computed from order-independent integer bins in one CTA, whatever else
+    shares the launch), and matches the FP64 oracle: at 1e-4 with FP32
+    storage; with SE16 at 1e-4 against the oracle's own encoding and within
+    2e-3 of the unquantised composite; with BF16 within BF16's derived bound
+    u (1 + J/2) S_p + 1e-4 (u = 2^-8) on every pixel -- this frame's
+    opacities reach 0.6, and BF16 misses 2e-3 on some pixels of fewer than 32
+    fragments here -- with the share within 2e-3 asserted above 99%."""
     fr = _frame(333, 197, 12.0, seed=1)
     with wt.Server(J=4, coeff_dtype=dtype, max_slots=4, mem_cap_bytes=1 << 30,
                    step_tiles=64) as srv:
@@ -55,16 +57,29 @@ def test_served_frame_equals_direct_call_and_oracle(dtype):
         assert info.state == 2 and info.done_us >= info.admit_us >= info.submit_us >= 0
         assert info.coeff
         srv.release(rid)
-    ref = _direct(fr, dtype)
-    assert (out - ref).abs().max().item() <= TOL[dtype]
+    assert torch.equal(out, _direct(fr, dtype))
+    h = fr.to("cpu").numpy()
+    rgb = (h["r"], h["g"], h["b"])
+    exact = oracle.composite(h["pixel"], h["z"], h["alpha"], rgb, fr.P, 4)
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - exact).max(axis=1)
     if dtype == wt.F32:
-        h = fr.to("cpu").numpy()
-        o = oracle.composite(h["pixel"], h["z"], h["alpha"], (h["r"], h["g"], h["b"]), fr.P, 4)
-        assert np.abs(out.cpu().numpy() - o).max() <= 1e-4
+        assert err.max() <= 1e-4
+    elif dtype == wt.SE16:
+        c32 = oracle.build_coeffs(h["pixel"], h["z"], h["alpha"], fr.P, 4).astype(np.float32)
+        enc = oracle.se16_decode(*oracle.se16_encode(c32, 4), 4)
+        ref = oracle.resolve(h["pixel"], h["z"], h["alpha"], rgb, fr.P, 4, enc)[0]
+        assert np.abs(got - ref).max() <= 1e-4
+        assert err.max() <= 2e-3
+    else:
+        ac = np.minimum(h["alpha"].astype(np.float64), 1 - 2.0 ** -20)
+        S = np.bincount(h["pixel"].astype(np.int64), weights=-np.log1p(-ac), minlength=fr.P)
+        assert (err <= 2.0 ** -8 * 3 * S + 1e-4).all()
+        assert np.mean(err <= 2e-3) >= 0.99
     assert wt.wt_get_error() == 0
 
 
-@pytest.mark.parametrize("dtype", [wt.BF16, wt.F32])
+@pytest.mark.parametrize("dtype", [wt.BF16, wt.F32, wt.SE16])
 def test_same_result_alone_and_in_mix(dtype):
     """A frame served alone and the same frame served among 24 concurrent
     frames of other sizes and depths give the same composite: bit for bit, as
@@ -111,7 +126,7 @@ def test_admission_waits_for_memory_and_times_out():
         assert srv.wait(rb, 20_000_000)
         srv.release(rb)
         assert srv.stats()["used_bytes"] == 0
-    assert (ob - _direct(b)).abs().max().item() <= TOL[wt.BF16]
+    assert torch.equal(ob, _direct(b))
 
 
 def test_refused_requests():
@@ -149,4 +164,4 @@ def test_many_small_requests_complete_in_order_of_work():
         for rid, out, fr in subs:
             assert srv.wait(rid, 30_000_000)
             srv.release(rid)
-            assert (out - _direct(fr, wt.F16)).abs().max().item() <= TOL[wt.F16]
+            assert torch.equal(out, _direct(fr, wt.F16))
