@@ -40,7 +40,7 @@ def test_plain64_other_paths(mode):
         np.testing.assert_allclose(acc[:, 4], ref[:, 4], rtol=1e-5, atol=1e-6)
 
 
-@pytest.mark.parametrize("J", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("J", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("tile", [(16, 16), (8, 4), (7, 3), (1, 1), (16, 1)])
 def test_ragged_tiles_every_J(J, tile):
     fr = synth.uniform_frame(53, 37, 5.0, 40, J=J, seed=J * 7 + tile[0], tile_w=tile[0],
@@ -319,3 +319,29 @@ def test_tile_ranges_equal_the_whole_frame():
         wt.wt_build_resolve_tiles(d, f, nt - 1, 2, out_b, c_b, bg=fr.bg)
     with pytest.raises(wt.WtError):
         wt.wt_build_resolve_tiles(d, f, -1, 1, out_b, c_b, bg=fr.bg)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("tile", [(192, 1), (16, 16)])
+def test_rank_bands_back_to_back_equal_the_whole_frame(world, tile):
+    """The ranks' bands of a frame split by tile rows (paper_2201_00094_gb300.shard),
+    run one after the other on one GPU, give the whole-frame call's output and
+    coefficients bit for bit: every tile is independent of the others."""
+    from paper_2201_00094_gb300 import shard
+
+    fr = synth.uniform_frame(611, 97, 7.0, 64, J=5, seed=97 + world, tile_w=tile[0], tile_h=tile[1])
+    dev = torch.device("cuda")
+    g = fr.to(dev)
+    d = desc_of(fr)
+    f = frags_of(g)
+    ref = torch.empty(fr.P, 4, device=dev)
+    cref = torch.empty(fr.P, 32, device=dev)
+    wt.wt_build_resolve(d, f, ref, cref, bg=fr.bg)
+    ranges = shard.split_tile_rows(fr.tile_offsets.numpy(), d, world)
+    assert sum(n for _, n in ranges) == fr.ntiles
+    out = torch.full((fr.P, 4), float("nan"), device=dev)
+    coeff = torch.full((fr.P, 32), float("nan"), device=dev)
+    for rng in ranges:
+        shard.build_resolve_band(d, f, rng, out, coeff, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    assert torch.equal(out, ref) and torch.equal(coeff, cref)

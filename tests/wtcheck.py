@@ -93,3 +93,34 @@ def coeff_tol(fr: synth.Frame) -> np.ndarray:
 
 def absorbance_tol(A_ref: np.ndarray, S: np.ndarray, J: int) -> np.ndarray:
     return 1e-5 * np.maximum(1.0, A_ref) + 4 * (J + 2) * U32 * S
+
+
+def e5_words_of(coeffs, C):
+    """E5B9G9R9 words of three channels' [P, C] coefficients, encoded by the
+    oracle (the stored magnitudes are chi_00 and -X_{n,k}, §2.3.1)."""
+    sign = np.where(np.arange(C) == 0, 1.0, -1.0).astype(np.float32)
+    return oracle.e5_encode(*[np.asarray(c, np.float32) * sign for c in coeffs])
+
+
+def e5_oracle_composite(h, alphas, P, J, bg, words_gpu):
+    """The E5B9G9R9 composite computed wholly on the oracle side -- FP64
+    coefficients rounded to FP32, encoded and decoded by the oracle -- and the
+    per-pixel bound within which the GPU's must lie.  The GPU's FP32
+    coefficients can round across a mantissa tie differently from FP64's in
+    rare last places; at a pixel whose words differ, each differing index i
+    (level n) moves a bin value by at most 2^(n/2) times the mantissa steps
+    of the two words, and the composite is 1-Lipschitz in the absorbance
+    (the normalised colour moves by at most tanh of it).  Returns (reference,
+    bound per pixel, words equal per pixel)."""
+    C = 1 << J
+    sign = np.where(np.arange(C) == 0, 1.0, -1.0)
+    co = [oracle.build_coeffs(h["pixel"], h["z"], alphas[c], P, J).astype(np.float32) for c in range(3)]
+    w = e5_words_of(co, C)
+    dec = oracle.e5_decode(w)
+    ref = oracle.composite_rgb(h["pixel"], h["z"], alphas, (h["r"], h["g"], h["b"]), P, J, bg=bg,
+                               coeffs=[sign * dec[c] for c in range(3)])
+    lvl = np.array([0] + [int(np.log2(i)) for i in range(1, C)])
+    step = lambda x: np.ldexp(1.0, (x >> 27).astype(np.int64) - 24)
+    diff = w != words_gpu
+    bound = 1e-4 + (diff * np.sqrt(2.0) ** lvl * (step(w) + step(words_gpu))).sum(axis=1)
+    return ref, bound, ~diff.any(axis=1)
