@@ -39,8 +39,14 @@ WORKLOADS = {
                  "70% surface pixels U{0..4}, J=4",
     "plain64": "64x64, Poisson(4) capped at 16, alpha U[.05,.6], J=4",
 }
-DTYPE_NAME = {0: "f32", 1: "bf16", 2: "f16"}
-DTYPE_BYTES = {0: 4, 1: 2, 2: 2}
+DTYPE_NAME = {0: "f32", 1: "bf16", 2: "f16", 3: "se16"}
+DTYPE_BYTES = {0: 4, 1: 2, 2: 2, 3: 2}
+
+
+def coeff_bytes(P: int, C: int, dt: int) -> int:
+    """Bytes of a frame's stored coefficients: P C values, plus one shared
+    exponent byte per pixel for SE16."""
+    return P * C * DTYPE_BYTES[dt] + (P if dt == 3 else 0)
 
 
 def peaks():
@@ -196,15 +202,60 @@ def sample_tiles(fr, ntiles_sample: int, seed: int):
     return tiles, uniq, local.astype(np.uint32), cols
 
 
-def run_oracle_sample(fr, ntiles_sample, seed):
+def _oracle_frame(J, bg, sample):
+    """The oracle's build + resolve + composite of one tile sample (FP64)."""
     import oracle
-    _, uniq, local, c = sample_tiles(fr, ntiles_sample, seed)
+    _, uniq, local, c = sample
+    coeff = oracle.build_coeffs(local, c["z"], c["alpha"], len(uniq), J)
+    return oracle.resolve(local, c["z"], c["alpha"], (c["r"], c["g"], c["b"]), len(uniq), J, coeff, bg=bg)[0]
+
+
+def run_oracle_sample(fr, ntiles_sample, seed):
+    sample = sample_tiles(fr, ntiles_sample, seed)
     t0 = time.perf_counter()
-    coeff = oracle.build_coeffs(local, c["z"], c["alpha"], len(uniq), fr.J)
-    out, _ = oracle.resolve(local, c["z"], c["alpha"], (c["r"], c["g"], c["b"]), len(uniq), fr.J,
-                            coeff, bg=fr.bg)
+    out = _oracle_frame(fr.J, fr.bg, sample)
     dt = time.perf_counter() - t0
-    return dict(n=len(local), pixels=len(uniq), seconds=dt, out=out, pixel_ids=uniq)
+    return dict(n=len(sample[2]), pixels=len(sample[1]), seconds=dt, out=out, pixel_ids=sample[1])
+
+
+def run_oracle_threads(fr, ntiles_sample, threads, seed):
+    """The oracle as it stands on `threads` host cores at once: every thread
+    runs the single-threaded FP64 oracle on its own seeded sample of whole
+    tiles (the oracle's C functions hold no global state, and ctypes releases
+    the interpreter lock for the duration of each C call).  Samples are drawn
+    before the clock starts; the wall time of all threads is timed."""
+    from concurrent.futures import ThreadPoolExecutor
+    samples = [sample_tiles(fr, ntiles_sample, seed + t) for t in range(threads)]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda _: None, range(threads)))  # threads started before the clock
+        t0 = time.perf_counter()
+        list(ex.map(lambda smp: _oracle_frame(fr.J, fr.bg, smp), samples))
+        dt = time.perf_counter() - t0
+    return dict(n=sum(len(smp[2]) for smp in samples), pixels=sum(len(smp[1]) for smp in samples),
+                seconds=dt, threads=threads)
+
+
+def host_cpu() -> dict:
+    """The host's logical core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        import subprocess
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -217,24 +268,38 @@ def run_wt(args):
     dev = torch.device("cuda", local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
-    # weak scaling: every rank renders its own independent frame
-    fr = synth.make(args.workload, seed=rank_seed(args.seed, rank), device=dev, **size_kw(args))
+    # weak scaling (default): every rank renders its own independent frame;
+    # --split rows: every rank holds the same frame and renders its own band of
+    # tile rows of it (strong scaling), then the bands are gathered
+    split = args.split == "rows"
+    seed = args.seed if split else rank_seed(args.seed, rank)
+    fr = synth.make(args.workload, seed=seed, device=dev, **size_kw(args))
     torch.cuda.synchronize()
     n, P, J = fr.n, fr.P, fr.J
-    dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[args.dtype]
+    dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16, "se16": wt.SE16}[args.dtype]
     C = 1 << J
     frags = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
     stream = torch.cuda.current_stream()
 
     def buffers(dtype):
-        return (torch.empty(P, C, device=dev, dtype=wt.coeff_torch_dtype(dtype)),
-                torch.empty(P, 4, device=dev))
+        d = wt.make_desc(fr.width, fr.height, J, dtype, tile_w=fr.tile_w, tile_h=fr.tile_h)
+        return wt.coeff_buffer(d, dev), torch.empty(P, 4, device=dev)
 
     coeff, out = buffers(dt)
     desc = wt.make_desc(fr.width, fr.height, J, dt, tile_w=fr.tile_w, tile_h=fr.tile_h)
 
+    band = None
+    if split:
+        from paper_2201_00094_gb300 import shard
+        ranges = shard.split_tile_rows(fr.tile_offsets.cpu().numpy(), desc, world)
+        band = ranges[rank]
+
     def step_fused(d=desc, c=coeff, o=out):
-        if args.path == "fused":
+        if band is not None:
+            shard.build_resolve_band(d, frags, band, o, c, bg=fr.bg, stream=stream)
+            if world > 1:
+                shard.gather_bands(o, ranges, d, rank)
+        elif args.path == "fused":
             wt.wt_build_resolve(d, frags, o, c, None, bg=fr.bg, stream=stream)
         else:
             wt.wt_build(d, frags, c, None, stream=stream)
@@ -263,28 +328,42 @@ def run_wt(args):
         barrier(world)
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
     launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    frags_all = sum_over_ranks(float(n), world)
+    frags_all = float(n) if split else sum_over_ranks(float(n), world)
     value = frags_all * K / (total_ms / 1e3)
 
-    s = DTYPE_BYTES[dt]
+    # the dominant kernel's share of the frame: all of it, or this rank's band
+    n_k, P_k = n, P
+    if band is not None:
+        offs = fr.tile_offsets.cpu().numpy()
+        n_k = int(offs[band[0] + band[1]] - offs[band[0]])
+        y0, y1 = shard.band_rows(band, desc)
+        P_k = (y1 - y0) * fr.width
+    cb = coeff_bytes(P_k, C, dt)
     # Algorithmic bytes of one frame of the method (two passes over the
     # fragments, coefficients written once and read once, RGBA written once):
     # 36 n + 2 P C s + 16 P.  The fused kernel's own minimum is 24 n + P C s + 16 P
     # (fragments read once, coefficients written once); both are reported.
-    method_bytes = n * 36 + 2 * P * C * s + 16 * P
-    fused_min_bytes = n * 24 + P * C * s + 16 * P
+    # (P C s is the coefficient storage, with SE16's exponent bytes.)
+    method_bytes = n_k * 36 + 2 * cb + 16 * P_k
+    fused_min_bytes = n_k * 24 + cb + 16 * P_k
     alg_bytes = method_bytes
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = profiled_traffic("k_fused", args.workload, args.dtype) if args.path == "fused" else None
 
-    # ---- variants (not part of `value`): two-pass path and 16-bit storage
+    # ---- variants (not part of `value`): two-pass path, single pass and 16-bit
+    # storage.  Every (storage, path) is timed in REPEATS rounds interleaved
+    # across the storage types, so that a drift of the clock or of the memory
+    # system affects all of them alike; the median and the spread are reported.
     variants = {}
     if not args.no_variants and not args.no_mono_variants:
-        for name, d2 in (("f32", wt.F32), ("bf16", wt.BF16), ("f16", wt.F16)):
+        REPEATS = 3
+        runs = {}
+        for name, d2 in (("f32", wt.F32), ("bf16", wt.BF16), ("f16", wt.F16), ("se16", wt.SE16)):
             dsc = wt.make_desc(fr.width, fr.height, J, d2, tile_w=fr.tile_w, tile_h=fr.tile_h)
             c2, o2 = buffers(d2)
-            accum_bytes = n * 36 + 2 * P * C * DTYPE_BYTES[d2] + 16 * P
+            c3 = torch.empty_like(c2)
+            cb2 = coeff_bytes(P, C, d2)
 
             def two_pass(dsc=dsc, c2=c2, o2=o2):
                 wt.wt_build(dsc, frags, c2, None, stream=stream)
@@ -294,30 +373,39 @@ def run_wt(args):
                 wt.wt_build_resolve(dsc, frags, o2, c2, None, bg=fr.bg, stream=stream)
 
             # the single pass of §4 on an unchanged scene: frame t-1's
-            # coefficients are this frame's (from the fused call above)
-            c3 = torch.empty_like(c2)
-
+            # coefficients are this frame's (from the fused call)
             def single_pass(dsc=dsc, c2=c2, c3=c3, o2=o2):
                 wt.wt_build_resolve_single_pass(dsc, frags, c2, o2, c3, bg=fr.bg, stream=stream)
 
+            runs[name] = [(label, fn, byts) for label, fn, byts in (
+                ("fused", fused, n * 24 + cb2 + 16 * P),
+                ("two_pass", two_pass, n * 36 + 2 * cb2 + 16 * P),
+                ("single_pass", single_pass, n * 24 + 2 * cb2 + 16 * P))]
+            fused()
+        times = {(nm, lb): [] for nm in runs for lb, _, _ in runs[nm]}
+        reps = max(3, min(K, 20))
+        for _ in range(REPEATS):
+            for nm, lst in runs.items():
+                for label, fn, byts in lst:
+                    for _ in range(3):
+                        fn()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    for _ in range(reps):
+                        fn()
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    times[(nm, label)].append(a.elapsed_time(b) / reps)
+        for nm, lst in runs.items():
             res = {}
-            for label, fn, byts in (("fused", fused, n * 24 + P * C * DTYPE_BYTES[d2] + 16 * P),
-                                    ("two_pass", two_pass, accum_bytes),
-                                    ("single_pass", single_pass, n * 24 + 2 * P * C * DTYPE_BYTES[d2] + 16 * P)):
-                for _ in range(3):
-                    fn()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                reps = max(3, min(K, 20))
-                a.record(stream)
-                for _ in range(reps):
-                    fn()
-                b.record(stream)
-                torch.cuda.synchronize()
-                ms = a.elapsed_time(b) / reps
-                res[label] = {"ms": round(ms, 4), "fragments_per_s": n / (ms / 1e3),
-                              "alg_bytes": byts, "alg_GBps": round(byts / (ms / 1e3) / 1e9, 1)}
-            variants[name] = res
-            del c2, c3, o2
+            for label, fn, byts in lst:
+                t = sorted(times[(nm, label)])
+                ms = float(np.median(t))
+                res[label] = {"ms": round(ms, 4), "ms_min_max": [round(t[0], 4), round(t[-1], 4)],
+                              "fragments_per_s": n / (ms / 1e3), "alg_bytes": byts,
+                              "alg_GBps": round(byts / (ms / 1e3) / 1e9, 1)}
+            variants[nm] = res
+        del runs
 
     # ---- coloured absorbance on the same frame (per-channel opacity alpha x (1, .8, .6)),
     # FP32 and E5B9G9R9 coefficient storage; the method's bytes as for the mono path:
@@ -393,10 +481,18 @@ def run_wt(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = run_oracle_sample(fr, args.cpu_tiles, seed=1234)
         got = out.cpu().numpy()[res["pixel_ids"]]
-        cpu = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_tiles} seeded random {fr.tile_w}x{fr.tile_h} tiles of the same frame "
-                         f"({res['pixels']} pixels, {res['n']} fragments), build + resolve + "
-                         f"composite, FP64, single thread, {res['seconds']:.1f} s",
+        host = host_cpu()
+        threads = max(1, host["nproc"] or 1)
+        par = run_oracle_threads(fr, args.cpu_tiles, threads, seed=5678)
+        cpu = {"value": par["n"] / par["seconds"], "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{threads} threads, each on its own {args.cpu_tiles} seeded random "
+                         f"{fr.tile_w}x{fr.tile_h} tiles of the same frame ({par['pixels']} pixels, "
+                         f"{par['n']} fragments in all), build + resolve + composite, FP64, "
+                         f"{par['seconds']:.1f} s wall",
+               "host": host,
+               "single_thread": {"value": res["n"] / res["seconds"], "cores": 1,
+                                 "sample": f"{args.cpu_tiles} tiles ({res['pixels']} pixels, {res['n']} "
+                                           f"fragments), {res['seconds']:.1f} s"},
                "max_abs_err_gpu_vs_oracle_on_sample": float(np.abs(got - res["out"]).max())}
     preprocess = None
     if rank == 0 and world == 1 and not args.no_preprocess:
@@ -429,8 +525,11 @@ def run_wt(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                       "split": ("bands of tile rows of one frame, gathered with all_gather"
+                                 if split else "one independent frame per rank"),
                        "fragments_per_gpu": n, "pixels": P, "J": J,
                        "coeff_storage": args.dtype, "path": path_name,
                        "size_override": args.size or None, "tile": args.tile,
@@ -792,15 +891,18 @@ def run_reference(args):
     dev = torch.device("cuda", local) if torch.cuda.is_available() else torch.device("cpu")
     fr = synth.make(args.workload, seed=args.seed, device=dev, **size_kw(args))
     K, W = args.steps, args.warmup
-    # size each step's sample so the whole run stays near --ref-seconds
-    probe = run_oracle_sample(fr, 1, seed=99_999)
-    per_tile = max(probe["seconds"], 1e-3)
+    host = host_cpu()
+    threads = max(1, host["nproc"] or 1)
+    probe = run_oracle_sample(fr, 4, seed=99_999)
+    per_tile = max(probe["seconds"] / 4, 1e-4)
+    # every step runs `threads` samples of `tiles` tiles at once, one per core;
+    # the whole run is sized to stay near --ref-seconds of wall time
     tiles = args.ref_tiles or max(1, int(args.ref_seconds / (K + W) / per_tile))
     for w in range(W):
-        run_oracle_sample(fr, tiles, seed=10_000 + w)
+        run_oracle_threads(fr, tiles, threads, seed=10_000 + 100 * w)
     tot_n, tot_s = 0, 0.0
     for k in range(K):
-        r = run_oracle_sample(fr, tiles, seed=k)
+        r = run_oracle_threads(fr, tiles, threads, seed=100 * k)
         tot_n += r["n"]
         tot_s += r["seconds"]
     value = tot_n / tot_s
@@ -811,9 +913,11 @@ def run_reference(args):
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
                    "fragments_per_gpu": fr.n, "pixels": fr.P, "J": fr.J,
                    "coeff_storage": "f64", "path": "FP64 CPU oracle", "tile": args.tile},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step {tiles} seeded random {fr.tile_w}x{fr.tile_h} tiles of the frame, "
-                                   "build + resolve + composite, FP64, single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "host": host,
+                         "sample": f"per step {threads} threads at once, each on its own {tiles} seeded "
+                                   f"random {fr.tile_w}x{fr.tile_h} tiles of the frame, build + resolve + "
+                                   "composite, FP64 (the single-threaded oracle on every core)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -843,7 +947,9 @@ def main():
     ap.add_argument("--tile", default="192x1",
                     help="screen tile WxH (one CTA each); row spans need no division, and at J = 5 "
                          "tiles of <= 192 pixels fit four CTAs per SM")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16", "se16"])
+    ap.add_argument("--split", default="none", choices=["none", "rows"],
+                    help="rows: one frame split across the ranks by bands of tile rows (strong scaling)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--size", default="", help="override the workload's WxH (profiling runs)")
     ap.add_argument("--cpu-tiles", type=int, default=96)

@@ -38,3 +38,37 @@ def test_tile_offsets_must_cover_the_descriptor_tiles():
     f._tile_offsets = 6
     with pytest.raises(ValueError, match="6 tiles"):
         wt._check_frags(d, f)
+
+
+def test_shared_exponent_buffers_are_checked_in_bytes():
+    """SE16 coefficient buffers are bytes: P * C two-byte mantissas, then P
+    exponent bytes; a buffer of another storage type is refused."""
+    d = wt.make_desc(7, 5, 3, wt.SE16)  # P = 35, C = 8
+    assert wt.coeff_storage_bytes(d) == 35 * 8 * 2 + 35
+    wt._check_pixel_buffers(d, coeff=torch.empty(35 * 17, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="bytes"):
+        wt._check_pixel_buffers(d, coeff=torch.empty(35 * 17 - 1, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="dtype"):
+        wt._check_pixel_buffers(d, coeff=torch.empty(35, 8, dtype=torch.bfloat16))
+    with pytest.raises(ValueError, match="dtype"):
+        wt._check_pixel_buffers(wt.make_desc(7, 5, 3, wt.BF16), coeff=torch.empty(35, 8))
+
+
+def test_static_batch_checks_every_frame_before_the_call():
+    """wt_build_resolve_batch_static takes bare pointers for up to 64 frames:
+    the binding refuses lists of different lengths and an undersized output
+    or tile table of any frame before anything reaches the library."""
+    d = wt.make_desc(8, 4, 4, tile_w=8, tile_h=1)  # P = 32, 4 tiles
+    f = wt.WtFrags(0, None, None, None, None, None, None, None)
+    f._tile_offsets = 5
+    ok = torch.empty(32, 4)
+    with pytest.raises(ValueError, match="one entry per frame"):
+        wt.wt_build_resolve_batch_static([d, d], [f], [ok, ok])
+    with pytest.raises(ValueError, match="one entry per frame"):
+        wt.wt_build_resolve_batch_static([d], [f], [ok], bgs=[(0.5, 0.5, 0.5)] * 2)
+    with pytest.raises(ValueError, match="out holds"):
+        wt.wt_build_resolve_batch_static([d, d], [f, f], [ok, torch.empty(31, 4)])
+    short = wt.WtFrags(0, None, None, None, None, None, None, None)
+    short._tile_offsets = 4
+    with pytest.raises(ValueError, match="4 tiles"):
+        wt.wt_build_resolve_batch_static([d, d], [f, short], [ok, ok])
