@@ -510,13 +510,11 @@ def run_wt(args):
     if rank == 0 and world == 1 and not args.no_serve:
         coeff = out = None
         torch.cuda.empty_cache()
-        serving, pool = {}, None
-        for dname in ("bf16", "f32"):
-            serving[dname], pool = run_serving(args, dname, pool)
-        serving["workload"] = (f"{args.serve_requests} requests, Poisson arrivals mean 2 ms, "
-                               "sizes {360p,720p,1080p,4K}, Poisson(lambda ~ U[2,32]) "
-                               "fragments/pixel, J=4, 40 GB cap, step 8192 tiles")
-        del pool
+        serving = serving_legs(args)
+        serving["workload"] = (f"{args.serve_requests} requests from a pool of {SERVE_POOL} frames (sizes "
+                               "{360p,720p,1080p,4K}, Poisson(lambda ~ U[2,32]) fragments/pixel per frame, "
+                               "alpha U[.02,.6]), J=4, 40 GB cap, step 8192 tiles; open: Poisson arrivals "
+                               "mean 2 ms; closed: 8 requests in flight; 3 interleaved repeats, median [min, max]")
         torch.cuda.empty_cache()
     kernel_name = "k_fused" if args.path == "fused" else "k_build + k_resolve"
     path_name = ("wt_build_resolve (fused kernel)" if args.path == "fused"
@@ -815,71 +813,109 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all, nchunks=8
 
 # ---------------------------------------------------------------- serving
 
-SERVE_LAMBDAS = (6.0, 14.0, 22.0, 30.0)
+SERVE_POOL = 96  # distinct pre-rendered frames, each with its own size and lambda
 
 
-def run_serving(args, dtype_name, pool=None):
-    """Continuous-batching serving run: ``args.serve_requests`` frame requests
-    with exponential inter-arrival times (mean 2 ms), resolutions drawn from
-    {640x360, 1280x720, 1920x1080, 3840x2160} and Poisson(lambda) fragments per
-    pixel, lambda ~ U[2, 32] per request (served from a pool of pre-rendered
-    frames at lambda 6/14/22/30, the nearest to the request's lambda), J = 4,
-    40 GB cap.  Latency = GPU completion of a request's last tile (CUDA event)
-    minus its submission time."""
+def serve_pool(args):
+    """The frames the serving legs draw from: SERVE_POOL frames, each with its
+    own resolution (uniform over the four sizes) and its own lambda ~ U[2, 32]
+    (Poisson fragments per pixel), alpha U[.02, .6], J = 4 -- about 113 GB of
+    fragments on the device.  Request i is served frame i mod SERVE_POOL, so
+    every request's size and lambda are independent draws within a cycle of
+    the pool; distinct frames for all 256 requests would need about 300 GB."""
+    dev = torch.device("cuda")
+    tw, th = tile_of(args)
+    draws = synth.serve_request_params(SERVE_POOL, seed=args.seed + 17)
+    pool = [synth.serve_frame(q["width"], q["height"], q["lam"], seed=q["seed"], device=dev, tile_w=tw, tile_h=th)
+            for q in draws]
+    torch.cuda.synchronize()
+    return pool, [q["lam"] for q in draws]
+
+
+def run_serving(args, dtype_name, pool, mode="open", outstanding=8):
+    """Continuous-batching serving run of ``args.serve_requests`` requests, J = 4,
+    40 GB cap, frames from the pool (serve_pool).
+
+    mode "open": exponential inter-arrival times, mean 2 ms (the configuration's
+    arrival process; the offered load is about a quarter of the service rate,
+    so this leg is bound by the arrivals).  mode "closed": ``outstanding``
+    requests are kept in flight, a new one submitted as soon as one finishes
+    (offered load above the service rate: latency and throughput are those of
+    the service).  Latency = GPU completion of a request's last tile (CUDA
+    event) minus its submission time."""
     import paper_2201_00094_gb300 as wt
     dev = torch.device("cuda")
-    dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16}[dtype_name]
+    dt = {"f32": wt.F32, "bf16": wt.BF16, "f16": wt.F16, "se16": wt.SE16}[dtype_name]
     reqs = synth.serve_request_params(args.serve_requests, seed=args.seed)
     tw, th = tile_of(args)
-    if pool is None:
-        pool = {}
-        for (w, h) in synth.SERVE_SIZES:
-            for k, lam in enumerate(SERVE_LAMBDAS):
-                pool[(w, h, k)] = synth.serve_frame(w, h, lam, seed=1000 + 7 * k + w, device=dev,
-                                                    tile_w=tw, tile_h=th)
-        torch.cuda.synchronize()
     srv = wt.Server(J=4, coeff_dtype=dt, max_slots=64, mem_cap_bytes=40 << 30, step_tiles=8192,
                     tile_w=tw, tile_h=th)
     pending = []
     lat, frags = [], 0
+
+    def retire(block: bool):
+        nonlocal frags
+        while pending and (block or srv.query(pending[0][0]).state == 2):
+            r0, n0 = pending.pop(0)
+            assert srv.wait(r0, 120_000_000), "serving request timed out"
+            info = srv.query(r0)
+            lat.append((info.done_us - info.submit_us) / 1e3)
+            frags += n0
+            srv.release(r0)
+            if block:
+                return
+
     t_start = time.perf_counter()
-    first_submit = None
     try:
-        for rq in reqs:
-            k = int(np.argmin([abs(rq["lam"] - l) for l in SERVE_LAMBDAS]))
-            fr = pool[(rq["width"], rq["height"], k)]
-            while (time.perf_counter() - t_start) * 1e3 < rq["arrival_ms"]:
-                pass
+        for i, rq in enumerate(reqs):
+            fr = pool[i % len(pool)]
+            if mode == "open":
+                while (time.perf_counter() - t_start) * 1e3 < rq["arrival_ms"]:
+                    pass
+            else:
+                while len(pending) >= outstanding:
+                    retire(True)
             d = wt.make_desc(fr.width, fr.height, 4, dt, tile_w=fr.tile_w, tile_h=fr.tile_h)
             f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
             out = torch.empty(fr.P, 4, device=dev)
             rid = srv.submit(d, f, out, keep=fr)
             pending.append((rid, fr.n))
-            first_submit = first_submit if first_submit is not None else rid
-            # retire finished requests so that their memory is released
-            while pending and srv.query(pending[0][0]).state == 2:
-                r0, n0 = pending.pop(0)
-                info = srv.query(r0)
-                lat.append((info.done_us - info.submit_us) / 1e3)
-                frags += n0
-                srv.release(r0)
-        last_done = 0.0
-        for rid, n in pending:
-            assert srv.wait(rid, 120_000_000), "serving request timed out"
-            info = srv.query(rid)
-            lat.append((info.done_us - info.submit_us) / 1e3)
-            last_done = max(last_done, info.done_us)
-            frags += n
-            srv.release(rid)
+            retire(False)  # finished requests release their memory
+        while pending:
+            retire(True)
         makespan_s = time.perf_counter() - t_start
     finally:
         srv.close()
     lat = np.array(lat)
-    return {"requests": len(lat), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "mean_ms": round(float(lat.mean()), 3), "max_ms": round(float(lat.max()), 3),
-            "fragments": int(frags), "fragments_per_s": frags / makespan_s,
-            "makespan_s": round(makespan_s, 3)}, pool
+    return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "max_ms": float(lat.max()), "fragments": int(frags), "fragments_per_s": frags / makespan_s,
+            "makespan_s": makespan_s}
+
+
+def serving_legs(args, dtypes=("bf16", "se16", "f32"), repeats=3):
+    """Both serving legs for each storage type, ``repeats`` runs each,
+    interleaved across the types; per figure the median and the [min, max]."""
+    pool, lams = serve_pool(args)
+    runs = {(m, d): [] for m in ("open", "closed") for d in dtypes}
+    for _ in range(repeats):
+        for m in ("open", "closed"):
+            for d in dtypes:
+                runs[(m, d)].append(run_serving(args, d, pool, m))
+    res = {"pool": {"frames": len(pool), "fragments": int(sum(f.n for f in pool)),
+                    "lambda_min_max": [round(min(lams), 2), round(max(lams), 2)]}}
+    for (m, d), rs in runs.items():
+        leg = res.setdefault(m, {})
+        leg[d] = {}
+        for key in ("p50_ms", "p99_ms", "fragments_per_s"):
+            v = sorted(r[key] for r in rs)
+            leg[d][key] = round(float(np.median(v)), 4) if key != "fragments_per_s" else float(np.median(v))
+            leg[d][key + "_min_max"] = [round(v[0], 4), round(v[-1], 4)] if key != "fragments_per_s" \
+                else [float(v[0]), float(v[-1])]
+        leg[d]["requests"] = rs[0]["requests"]
+        leg[d]["makespan_s"] = round(float(np.median([r["makespan_s"] for r in rs])), 4)
+    del pool
+    return res
 
 
 # ---------------------------------------------------------------- reference arm

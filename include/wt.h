@@ -384,14 +384,18 @@ wt_status wt_backward(const wt_desc *desc, const wt_frags *frags, const float *b
  */
 
 /* Bytes of device workspace wt_bin needs for n fragments with this
- * descriptor: tile counts and cursors (about 12 bytes per tile) and a staging
- * record of 32 bytes per fragment; 0 if the descriptor is invalid or n < 0.
- * Only the descriptor's width, height, tile_w and tile_h are used. */
+ * descriptor: a digit-count matrix (257 x ceil(n / 4096) counters) and, when
+ * the tile ids need two 8-bit sort passes or more (more than 256 tiles), an
+ * intermediate stream of 24 bytes and one digit byte per fragment (twice that
+ * for more than 65536 tiles); 0 if the descriptor is invalid or n < 0.  Only
+ * the descriptor's width, height, tile_w and tile_h are used. */
 size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n);
 
 /*
  * wt_bin -- groups an unordered fragment stream by tile (row-major tiles of
- * desc) into caller-allocated output arrays, a counting sort by tile id:
+ * desc) into caller-allocated output arrays: a stable radix sort by tile id,
+ * 8 bits per pass (one pass for up to 256 tiles, two up to 65536, at most
+ * four), each pass writing coalesced runs of fragments of one digit.
  *   in          n fragments in any order; in->tile_offsets is ignored (may be
  *               NULL); in->r/g/b may all be NULL (then r/g/b_out are unused).
  *   *_out       [n] device arrays (at least in->n elements each), written with
@@ -403,9 +407,8 @@ size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n);
  *               in->n) bytes (else WT_ERR_ARG), 256-byte aligned, owned by the
  *               caller (overwritten).
  * Fragments whose pixel id is >= width*height are dropped and counted in the
- * error word.  The order of the fragments inside a tile is unspecified (it
- * follows the atomics that hand out the slots): the build does not depend on
- * it, the resolve's FP32 sums may change in their last bits between runs.
+ * error word.  The sort is stable: inside a tile the fragments keep their
+ * input order, so the output is the same on every run.
  */
 wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
                  float *alpha_out, float *r_out, float *g_out, float *b_out,

@@ -2,17 +2,26 @@
 // by screen tile, and the per-pixel depth bounds of §2.1 step 1 with the
 // normalisation of depth into them.
 //
-// Binning is a counting sort by tile id (row-major tiles of the descriptor):
-// a histogram pass, one exclusive scan of the tile counts into tile_offsets, a
-// scatter pass in which every fragment takes the next slot of its tile and is
-// staged there as one record, and a pass that unpacks the records in order
-// into the output arrays.  When the tile counters fit in shared memory, each
-// block counts and ranks its own chunk of the stream with shared atomics;
-// otherwise the counts and slots come from global atomics.  Fragments whose pixel id is outside the image are dropped and
-// counted.  The order of the
-// fragments inside a tile is that of the atomics: the build does not depend on
-// it (its sums are integer), the resolve's FP32 sums may differ in the last
-// bits between runs.
+// Binning is a stable least-significant-digit radix sort of the fragments by
+// tile id (row-major tiles of the descriptor), 8 bits per pass: two passes for
+// up to 65536 tiles.  A pass is three kernels:
+//   * a histogram of the pass's digit over each block's 4096 consecutive
+//     fragments (shared-memory counters), stored digit-major [257][blocks];
+//   * an exclusive scan of that matrix along each digit row, and of the row
+//     totals over the digits: fragment (digit d, block b) then starts at
+//     base[d] + M[d][b] in the pass's output;
+//   * a scatter: each block ranks its fragments by digit (match.any within a
+//     warp, per-warp counters in shared memory, in input order, so the sort is
+//     stable), places each field in shared memory in digit order and writes
+//     it out: a block's fragments of one digit are a contiguous run of the
+//     output, so the stores are coalesced however random the input order is.
+// The scatter of a pass that is not the last also writes the next pass's
+// digit as one byte per fragment, so that the next histogram reads one byte.
+// Fragments whose pixel id is outside the image fall into a 257th bucket that
+// is never written, and are counted.  Because every pass is stable, the
+// fragments of a tile come out in their input order: the result is
+// deterministic.  tile_offsets is read off the sorted stream (a tile starts
+// where the tile id changes).
 //
 // Depth bounds run per tile over a tile-grouped stream: shared-memory min/max
 // per pixel, one store per pixel.  Depth is compared through an order-
@@ -29,62 +38,45 @@ unsigned long long *error_word();  // wt_api.cu
 
 namespace {
 
+// floor(x / d) for every 32-bit x by a multiply-high (Granlund & Montgomery
+// 1994, round-up method): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// t = mulhi(x, m), q = (t + ((x - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+    uint32_t m;
+    int s1, s2;
+};
+FastDiv make_fastdiv(uint32_t d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f) {
+    const uint32_t t = __umulhi(x, f.m);
+    return (t + ((x - t) >> f.s1)) >> f.s2;
+}
+
 struct BinGeom {
-    int width, height, tile_w, tile_h, ntx;
+    uint32_t width, tile_w, tile_h, ntx;
     int64_t P;
+    FastDiv dw, dtw, dth;
 };
 
-// Row-major tile index of a pixel id, or -1 outside the image.
-__device__ __forceinline__ int64_t tile_index(uint32_t px, const BinGeom &g) {
-    if ((int64_t)px >= g.P) return -1;
-    const uint32_t y = px / (uint32_t)g.width, x = px - y * (uint32_t)g.width;
-    return (int64_t)(y / (uint32_t)g.tile_h) * g.ntx + x / (uint32_t)g.tile_w;
+// Row-major tile index of a pixel id inside the image.
+__device__ __forceinline__ uint32_t tile_of_pixel(uint32_t px, const BinGeom &g) {
+    const uint32_t y = fdiv(px, g.dw), x = px - y * g.width;
+    return fdiv(y, g.dth) * g.ntx + fdiv(x, g.dtw);
 }
 
-__global__ void __launch_bounds__(256) k_bin_count(BinGeom g, int64_t n, const uint32_t *__restrict__ pixel,
-                                                   unsigned *__restrict__ counts, unsigned long long *err) {
-    unsigned bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = tile_index(pixel[i], g);
-        if (t < 0) ++bad;
-        else atomicAdd(&counts[t], 1u);
-    }
-    bad = __reduce_add_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(err, (unsigned long long)bad);
-}
+constexpr int kRT = 256;             // threads of a sorting block
+constexpr int kRW = kRT / 32;        // its warps
+constexpr int kRI = 16;              // fragments per thread
+constexpr int kRTile = kRT * kRI;    // fragments per block
+constexpr int kRD = 257;             // 256 digits + the bucket of dropped fragments
 
-// One block: exclusive scan of the tile counts into offsets[0 .. ntiles] and
-// the scatter cursors.  Each thread scans a contiguous chunk.
-__global__ void __launch_bounds__(1024) k_bin_scan(const unsigned *__restrict__ counts, int64_t ntiles,
-                                                   int64_t *__restrict__ offsets,
-                                                   unsigned long long *__restrict__ cursor) {
-    __shared__ unsigned long long part[1024];
-    const int64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-    const int64_t b = threadIdx.x * per, e = min(ntiles, b + per);
-    unsigned long long sum = 0;
-    for (int64_t t = b; t < e; ++t) sum += counts[t];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int d = 1; d < (int)blockDim.x; d <<= 1) {  // inclusive Hillis-Steele scan of the chunk sums
-        const unsigned long long v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0ull;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned long long run = part[threadIdx.x] - sum;  // exclusive start of this chunk
-    for (int64_t t = b; t < e; ++t) {
-        offsets[t] = (int64_t)run;
-        cursor[t] = run;
-        run += counts[t];
-    }
-    if (threadIdx.x == blockDim.x - 1) offsets[ntiles] = (int64_t)part[threadIdx.x];
-}
-
-// The scatter writes each kept fragment as one record into its tile's next
-// slot of a staging array -- 32 bytes (pixel, z, alpha, r, g, b) or 16 bytes
-// (pixel, z, alpha) -- so that every slot is one whole-sector store, however
-// scattered the slots are; a second pass copies the records out to the
-// structure-of-arrays output in order, with coalesced loads and stores.
 struct BinIn {
     const uint32_t *pixel;
     const float *z, *alpha, *r, *g, *b;
@@ -94,112 +86,212 @@ struct BinOut {
     float *z, *alpha, *r, *g, *b;
 };
 
-template <bool RGB>
-__global__ void __launch_bounds__(256) k_bin_scatter(BinGeom g, int64_t n, BinIn a, uint4 *__restrict__ stage,
-                                                     unsigned long long *__restrict__ cursor) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t px = a.pixel[i];
-        const int64_t t = tile_index(px, g);
-        if (t < 0) continue;
-        const int64_t slot = (int64_t)atomicAdd(&cursor[t], 1ull);
-        const uint4 r0 = make_uint4(px, __float_as_uint(a.z[i]), __float_as_uint(a.alpha[i]),
-                                    RGB ? __float_as_uint(a.r[i]) : 0u);
-        if (RGB) {
-            stage[2 * slot] = r0;
-            stage[2 * slot + 1] = make_uint4(__float_as_uint(a.g[i]), __float_as_uint(a.b[i]), 0u, 0u);
-        } else {
-            stage[slot] = r0;
-        }
-    }
+// Digit of pass `pass` of a fragment: (tile >> 8 pass) & 255 for a pixel in
+// the image, 256 otherwise.
+__device__ __forceinline__ int first_digit(uint32_t px, const BinGeom &g, int pass) {
+    if ((int64_t)px >= g.P) return 256;
+    return (int)((tile_of_pixel(px, g) >> (8 * pass)) & 255u);
 }
 
-template <bool RGB>
-__global__ void __launch_bounds__(256) k_bin_unpack(int64_t n, const int64_t *__restrict__ kept_at,
-                                                    const uint4 *__restrict__ stage, BinOut o) {
-    const int64_t kept = *kept_at;  // tile_offsets[ntiles]
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kept && i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint4 r0 = stage[RGB ? 2 * i : i];
-        o.pixel[i] = r0.x;
-        o.z[i] = __uint_as_float(r0.y);
-        o.alpha[i] = __uint_as_float(r0.z);
-        if (RGB) {
-            const uint4 r1 = stage[2 * i + 1];
-            o.r[i] = __uint_as_float(r0.w);
-            o.g[i] = __uint_as_float(r1.x);
-            o.b[i] = __uint_as_float(r1.y);
-        }
-    }
-}
-
-// Binning with per-block shared-memory counters, for descriptors whose tile
-// count fits in shared memory: one block per SM owns a contiguous chunk of the
-// stream.  Pass 1 counts the chunk's fragments per tile with shared atomics
-// and stores the block's counts; a pass over the tiles turns them into each
-// block's starting rank inside every tile (blocks in order) and the tile
-// totals; pass 2 hands out ranks with shared atomics again, so no global
-// atomic is issued per fragment.
-constexpr int kBinThreads = 1024;
-
-__global__ void __launch_bounds__(kBinThreads) k_bin_count_local(BinGeom g, int64_t n, int64_t chunk,
-                                                                 int64_t ntiles, const uint32_t *__restrict__ pixel,
-                                                                 unsigned *__restrict__ H, unsigned long long *err) {
-    extern __shared__ unsigned hist[];
-    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0u;
+// Histogram of the pass's digit over each block's fragments, stored
+// digit-major: M[d * nb + block].  FIRST: the digit comes from the pixel id
+// (dropped fragments counted into err); otherwise from the byte array written
+// by the previous pass, over the kept fragments.
+template <bool FIRST>
+__global__ void __launch_bounds__(kRT) k_bin_hist(BinGeom g, int64_t n, const unsigned long long *kept,
+                                                  int pass, int nb, const uint32_t *__restrict__ pixel,
+                                                  const uint8_t *__restrict__ dig, unsigned *__restrict__ M,
+                                                  unsigned long long *err) {
+    __shared__ unsigned h[kRD];
+    for (int d = threadIdx.x; d < kRD; d += kRT) h[d] = 0u;
     __syncthreads();
-    const int64_t s = (int64_t)blockIdx.x * chunk, e = min(n, s + chunk);
+    const int64_t ne = FIRST ? n : (int64_t)*kept;
+    const int64_t b0 = (int64_t)blockIdx.x * kRTile;
     unsigned bad = 0;
-    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const int64_t t = tile_index(pixel[i], g);
-        if (t < 0) ++bad;
-        else atomicAdd(&hist[t], 1u);
+    for (int j = threadIdx.x; j < kRTile; j += kRT) {
+        const int64_t i = b0 + j;
+        if (i >= ne) break;
+        const int d = FIRST ? first_digit(pixel[i], g, pass) : (int)dig[i];
+        if (FIRST && d == 256) ++bad;
+        atomicAdd(&h[d], 1u);
     }
-    bad = __reduce_add_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(err, (unsigned long long)bad);
+    if (FIRST) flush_bad(bad, err);
     __syncthreads();
-    unsigned *row = H + (int64_t)blockIdx.x * ntiles;
-    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = hist[t];
+    for (int d = threadIdx.x; d < kRD; d += kRT) M[(int64_t)d * nb + blockIdx.x] = h[d];
 }
 
-// Per tile: each block's count becomes the number of the tile's fragments in
-// earlier blocks; the tile's total goes to counts[t].
-__global__ void __launch_bounds__(256) k_bin_block_ranks(int nblocks, int64_t ntiles, unsigned *__restrict__ H,
-                                                         unsigned *__restrict__ counts) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntiles) return;
-    unsigned run = 0;
-    for (int b = 0; b < nblocks; ++b) {
-        const unsigned h = H[(int64_t)b * ntiles + t];
-        H[(int64_t)b * ntiles + t] = run;
-        run += h;
-    }
-    counts[t] = run;
-}
-
-template <bool RGB>
-__global__ void __launch_bounds__(kBinThreads) k_bin_scatter_local(BinGeom g, int64_t n, int64_t chunk,
-                                                                   int64_t ntiles, BinIn a,
-                                                                   const unsigned *__restrict__ H,
-                                                                   const int64_t *__restrict__ offsets,
-                                                                   uint4 *__restrict__ stage) {
-    extern __shared__ unsigned cur[];
-    const unsigned *row = H + (int64_t)blockIdx.x * ntiles;
-    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) cur[t] = row[t];
-    __syncthreads();
-    const int64_t s = (int64_t)blockIdx.x * chunk, e = min(n, s + chunk);
-    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const uint32_t px = a.pixel[i];
-        const int64_t t = tile_index(px, g);
-        if (t < 0) continue;
-        const int64_t slot = offsets[t] + atomicAdd(&cur[t], 1u);
-        const uint4 r0 = make_uint4(px, __float_as_uint(a.z[i]), __float_as_uint(a.alpha[i]),
-                                    RGB ? __float_as_uint(a.r[i]) : 0u);
-        if (RGB) {
-            stage[2 * slot] = r0;
-            stage[2 * slot + 1] = make_uint4(__float_as_uint(a.g[i]), __float_as_uint(a.b[i]), 0u, 0u);
-        } else {
-            stage[slot] = r0;
+// Exclusive scan of one digit row of M in place (one block per digit), in
+// rounds of 1024 consecutive entries; the row's total goes to rowsum[d].
+__global__ void __launch_bounds__(1024) k_bin_rows(unsigned *__restrict__ M, int nb,
+                                                   unsigned long long *__restrict__ rowsum) {
+    __shared__ unsigned warp_sum[32];
+    unsigned *row = M + (int64_t)blockIdx.x * nb;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long carry = 0;
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const unsigned v = i < nb ? row[i] : 0u;
+        unsigned x = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
+        if (lane == 31) warp_sum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            unsigned s = warp_sum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sum[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned before = (w ? warp_sum[w - 1] : 0u) + x - v;
+        if (i < nb) row[i] = (unsigned)(carry + before);
+        carry += warp_sum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) rowsum[blockIdx.x] = carry;
+}
+
+// Exclusive scan of the 256 row totals into base[d]; kept = their sum (the
+// fragments that pass through the sort).
+__global__ void __launch_bounds__(256) k_bin_bases(const unsigned long long *__restrict__ rowsum,
+                                                   unsigned long long *__restrict__ base,
+                                                   unsigned long long *__restrict__ kept) {
+    __shared__ unsigned long long s[256];
+    const int t = threadIdx.x;
+    s[t] = rowsum[t];
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const unsigned long long y = t >= o ? s[t - o] : 0ull;
+        __syncthreads();
+        s[t] += y;
+        __syncthreads();
+    }
+    base[t] = s[t] - rowsum[t];
+    if (t == 255) *kept = s[255];
+}
+
+// One pass of the sort: ranks the block's fragments by digit (stable), then
+// moves every field through shared memory into digit order and out to its
+// run.  FIRST: digits from the pixel ids; LAST: no next digit to write.
+template <bool FIRST, bool LAST, bool RGB>
+__global__ void __launch_bounds__(kRT) k_bin_scatter(BinGeom g, int64_t n, const unsigned long long *kept,
+                                                     int pass, int nb, BinIn in, const uint8_t *__restrict__ dig_in,
+                                                     BinOut out, uint8_t *__restrict__ dig_out,
+                                                     const unsigned *__restrict__ M,
+                                                     const unsigned long long *__restrict__ base) {
+    __shared__ unsigned wcnt[kRW][kRD];     // per-warp digit counts, then exclusive offsets over warps
+    __shared__ unsigned lstart[kRD];        // block-local start of each digit's run
+    __shared__ unsigned long long gdst[256];  // where this block's run of each digit starts in the output
+    __shared__ uint32_t stage[kRTile];
+    __shared__ uint8_t sdig[kRTile];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kRW * kRD; i += kRT) (&wcnt[0][0])[i] = 0u;
+    __syncthreads();
+    const int64_t ne = FIRST ? n : (int64_t)*kept;
+    const int64_t b0 = (int64_t)blockIdx.x * kRTile + w * (32 * kRI) + lane;  // fragment k at b0 + 32 k
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    unsigned pos[kRI];
+    int dg[kRI];
+    // rank within the warp's fragments of the same digit, in input order
+#pragma unroll
+    for (int k = 0; k < kRI; ++k) {
+        const int64_t i = b0 + 32 * k;
+        int d = 256;
+        if (i < ne) d = FIRST ? first_digit(in.pixel[i], g, pass) : (int)dig_in[i];
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        unsigned old = 0;
+        if (lane == leader) {
+            old = wcnt[w][d];
+            wcnt[w][d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        pos[k] = old + __popc(peers & lt);
+        dg[k] = d;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRD; d += kRT) {
+        unsigned run = 0;
+        for (int ww = 0; ww < kRW; ++ww) {
+            const unsigned c = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += c;
+        }
+        lstart[d] = run;  // the digit's block total, scanned below
+    }
+    __syncthreads();
+    if (w == 0) {  // exclusive scan of the 257 totals: lane l owns digits 9 l .. 9 l + 8
+        unsigned v[9], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int d = 9 * lane + j;
+            v[j] = d < kRD ? lstart[d] : 0u;
+            sum += v[j];
+        }
+        unsigned x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        unsigned run = x - sum;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int d = 9 * lane + j;
+            if (d < kRD) lstart[d] = run;
+            run += v[j];
+        }
+    }
+    for (int d = threadIdx.x; d < 256; d += kRT) gdst[d] = base[d] + M[(int64_t)d * nb + blockIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRI; ++k) {
+        pos[k] += lstart[dg[k]] + wcnt[w][dg[k]];
+        if (dg[k] < 256) sdig[pos[k]] = (uint8_t)dg[k];
+    }
+    const unsigned nvalid = lstart[256];  // the block's fragments that are written
+    __syncthreads();
+    // one field at a time: into shared memory in digit order, then out in runs
+    auto move = [&](const uint32_t *src, uint32_t *dst, bool next_digit) {
+#pragma unroll
+        for (int k = 0; k < kRI; ++k)
+            if (dg[k] < 256) stage[pos[k]] = src[b0 + 32 * k];
+        __syncthreads();
+        for (unsigned q = threadIdx.x; q < nvalid; q += kRT) {
+            const int d = sdig[q];
+            const uint32_t v = stage[q];
+            const unsigned long long o = gdst[d] + (q - lstart[d]);
+            dst[o] = v;
+            if (!LAST && next_digit) dig_out[o] = (uint8_t)((tile_of_pixel(v, g) >> (8 * pass + 8)) & 255u);
+        }
+        __syncthreads();
+    };
+    move(in.pixel, out.pixel, true);
+    move(reinterpret_cast<const uint32_t *>(in.z), reinterpret_cast<uint32_t *>(out.z), false);
+    move(reinterpret_cast<const uint32_t *>(in.alpha), reinterpret_cast<uint32_t *>(out.alpha), false);
+    if (RGB) {
+        move(reinterpret_cast<const uint32_t *>(in.r), reinterpret_cast<uint32_t *>(out.r), false);
+        move(reinterpret_cast<const uint32_t *>(in.g), reinterpret_cast<uint32_t *>(out.g), false);
+        move(reinterpret_cast<const uint32_t *>(in.b), reinterpret_cast<uint32_t *>(out.b), false);
+    }
+}
+
+// tile_offsets from the sorted stream: position i opens the tiles after the
+// previous fragment's tile up to its own; position kept closes the rest.
+__global__ void __launch_bounds__(256) k_bin_offsets(BinGeom g, int64_t ntiles, const uint32_t *__restrict__ pixel,
+                                                     const unsigned long long *kept, int64_t *__restrict__ off) {
+    const int64_t K = (int64_t)*kept;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= K; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i < K ? (int64_t)tile_of_pixel(pixel[i], g) : ntiles;
+        const int64_t tp = i > 0 ? (int64_t)tile_of_pixel(pixel[i - 1], g) : -1;
+        for (int64_t u = tp + 1; u <= t; ++u) off[u] = i;
     }
 }
 
@@ -286,12 +378,14 @@ wt_status check_geom(const wt_desc *d) {
 
 BinGeom bin_geom(const wt_desc *d) {
     BinGeom g;
-    g.width = d->width;
-    g.height = d->height;
-    g.tile_w = d->tile_w;
-    g.tile_h = d->tile_h;
-    g.ntx = (d->width + d->tile_w - 1) / d->tile_w;
+    g.width = (uint32_t)d->width;
+    g.tile_w = (uint32_t)d->tile_w;
+    g.tile_h = (uint32_t)d->tile_h;
+    g.ntx = (uint32_t)((d->width + d->tile_w - 1) / d->tile_w);
     g.P = (int64_t)d->width * d->height;
+    g.dw = make_fastdiv(g.width);
+    g.dtw = make_fastdiv(g.tile_w);
+    g.dth = make_fastdiv(g.tile_h);
     return g;
 }
 
@@ -299,20 +393,78 @@ int64_t tiles_of(const wt_desc *d) {
     return (int64_t)((d->width + d->tile_w - 1) / d->tile_w) * ((d->height + d->tile_h - 1) / d->tile_h);
 }
 
-size_t ws_counts(int64_t ntiles) { return ((size_t)ntiles * 4 + 255) & ~size_t(255); }
-
-int num_sms() {
-    int dev = 0, sms = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
+// Radix passes of 8 bits that the tile ids need (1 to 4).
+int sort_passes(int64_t ntiles) {
+    int bits = 1;
+    while (bits < 32 && (int64_t(1) << bits) < ntiles) ++bits;
+    return (bits + 7) / 8;
 }
 
-// Tile counters that fit one block's shared memory (the per-block path).
-bool local_bins(int64_t ntiles) { return ntiles * 4 <= 200 * 1024; }
+size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Bytes of the per-block count matrix (one row of ntiles per block).
-size_t ws_blocks(int64_t ntiles) {
-    return local_bins(ntiles) ? (((size_t)num_sms() * ntiles * 4 + 255) & ~size_t(255)) : 0;
+// Workspace layout (256-byte aligned regions): the digit matrix [257][nb]
+// (unsigned), the row totals and digit bases (256 each), the kept count, then
+// for two passes or more one intermediate structure-of-arrays stream (six
+// arrays of n) and one byte per fragment for the next digit, and for three or
+// more a second of each (the passes alternate between them).
+struct BinWorkspace {
+    unsigned *M;
+    unsigned long long *rowsum, *base, *kept;
+    char *soa[2];
+    uint8_t *dig[2];
+};
+size_t workspace_layout(int64_t ntiles, int64_t n, char *ws, BinWorkspace *out) {
+    const int64_t nb = (n + kRTile - 1) / kRTile;
+    const int passes = sort_passes(ntiles);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += up256(bytes);
+        return ws ? ws + at : nullptr;
+    };
+    char *M = take((size_t)kRD * (size_t)(nb > 0 ? nb : 1) * 4);
+    char *rowsum = take(256 * 8), *base = take(256 * 8), *kept = take(8);
+    char *soa[2] = {nullptr, nullptr};
+    char *dig[2] = {nullptr, nullptr};
+    for (int k = 0; k < 2; ++k) {
+        if (passes >= 2 + k) {
+            soa[k] = take((size_t)n * 24);
+            dig[k] = take((size_t)n);
+        }
+    }
+    if (out) {
+        out->M = reinterpret_cast<unsigned *>(M);
+        out->rowsum = reinterpret_cast<unsigned long long *>(rowsum);
+        out->base = reinterpret_cast<unsigned long long *>(base);
+        out->kept = reinterpret_cast<unsigned long long *>(kept);
+        for (int k = 0; k < 2; ++k) {
+            out->soa[k] = soa[k];
+            out->dig[k] = reinterpret_cast<uint8_t *>(dig[k]);
+        }
+    }
+    return o;
+}
+
+// The six arrays of an intermediate stream in a workspace region.
+BinOut soa_arrays(char *base, int64_t n) {
+    BinOut o;
+    o.pixel = reinterpret_cast<uint32_t *>(base);
+    o.z = reinterpret_cast<float *>(base + (size_t)n * 4);
+    o.alpha = reinterpret_cast<float *>(base + (size_t)n * 8);
+    o.r = reinterpret_cast<float *>(base + (size_t)n * 12);
+    o.g = reinterpret_cast<float *>(base + (size_t)n * 16);
+    o.b = reinterpret_cast<float *>(base + (size_t)n * 20);
+    return o;
+}
+
+template <bool FIRST, bool LAST>
+void launch_scatter(bool rgb, int nb, cudaStream_t s, const BinGeom &g, int64_t n, const unsigned long long *kept,
+                    int pass, const BinIn &in, const uint8_t *dig_in, const BinOut &out, uint8_t *dig_out,
+                    const unsigned *M, const unsigned long long *base) {
+    if (rgb)
+        k_bin_scatter<FIRST, LAST, true><<<nb, kRT, 0, s>>>(g, n, kept, pass, nb, in, dig_in, out, dig_out, M, base);
+    else
+        k_bin_scatter<FIRST, LAST, false><<<nb, kRT, 0, s>>>(g, n, kept, pass, nb, in, dig_in, out, dig_out, M, base);
 }
 
 }  // namespace
@@ -322,8 +474,7 @@ using namespace wt;
 
 extern "C" size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n) {
     if (check_geom(desc) != WT_OK || n < 0) return 0;
-    const int64_t nt = tiles_of(desc);
-    return ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)) + ws_blocks(nt) + (size_t)n * 32;
+    return workspace_layout(tiles_of(desc), n, nullptr, nullptr);
 }
 
 extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *pixel_out, float *z_out,
@@ -347,52 +498,40 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
     unsigned long long *err = error_word();
     if (!err) return WT_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t nt = tiles_of(desc);
-    char *ws = static_cast<char *>(workspace);
-    unsigned *counts = reinterpret_cast<unsigned *>(ws);
-    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + ws_counts(nt));
-    const size_t blocks_bytes = ws_blocks(nt);
-    unsigned *H = reinterpret_cast<unsigned *>(ws + ws_counts(nt) + (((size_t)nt * 8 + 255) & ~size_t(255)));
-    uint4 *stage = reinterpret_cast<uint4 *>(reinterpret_cast<char *>(H) + blocks_bytes);
+    const int64_t nt = tiles_of(desc), n = in->n;
+    BinWorkspace W;
+    workspace_layout(nt, n, static_cast<char *>(workspace), &W);
     const BinGeom g = bin_geom(desc);
-    const BinIn a{in->pixel, in->z, in->alpha, in->r, in->g, in->b};
-    const BinOut o{pixel_out, z_out, alpha_out, r_out, g_out, b_out};
-    const int grid = grid_for(in->n);
-    if (blocks_bytes && in->n > 0) {
-        // per-block shared-memory counters
-        const int nb = num_sms();
-        const int64_t chunk = (in->n + nb - 1) / nb;
-        const size_t smem = (size_t)nt * 4;
-        cudaError_t e = cudaFuncSetAttribute(k_bin_count_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(rgb ? (const void *)k_bin_scatter_local<true> : (const void *)k_bin_scatter_local<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return WT_ERR_CUDA;
-        k_bin_count_local<<<nb, kBinThreads, smem, s>>>(g, in->n, chunk, nt, in->pixel, H, err);
-        k_bin_block_ranks<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(nb, nt, H, counts);
-        k_bin_scan<<<1, 1024, 0, s>>>(counts, nt, tile_offsets_out, cursor);
-        if (rgb) {
-            k_bin_scatter_local<true><<<nb, kBinThreads, smem, s>>>(g, in->n, chunk, nt, a, H, tile_offsets_out, stage);
-            k_bin_unpack<true><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
-        } else {
-            k_bin_scatter_local<false><<<nb, kBinThreads, smem, s>>>(g, in->n, chunk, nt, a, H, tile_offsets_out, stage);
-            k_bin_unpack<false><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
+    const int passes = sort_passes(nt);
+    const int64_t nb64 = (n + kRTile - 1) / kRTile;
+    if (nb64 >= (int64_t(1) << 31)) return WT_ERR_ARG;
+    const int nb = (int)nb64;
+    if (nb > 0) {
+        const BinIn src{in->pixel, in->z, in->alpha, in->r, in->g, in->b};
+        const BinOut dst{pixel_out, z_out, alpha_out, r_out, g_out, b_out};
+        BinIn cur = src;
+        const uint8_t *dig_in = nullptr;
+        for (int pass = 0; pass < passes; ++pass) {
+            const bool first = pass == 0, last = pass == passes - 1;
+            if (first)
+                k_bin_hist<true><<<nb, kRT, 0, s>>>(g, n, W.kept, pass, nb, in->pixel, nullptr, W.M, err);
+            else
+                k_bin_hist<false><<<nb, kRT, 0, s>>>(g, n, W.kept, pass, nb, nullptr, dig_in, W.M, err);
+            k_bin_rows<<<256, 1024, 0, s>>>(W.M, nb, W.rowsum);
+            k_bin_bases<<<1, 256, 0, s>>>(W.rowsum, W.base, W.kept);
+            const BinOut to = last ? dst : soa_arrays(W.soa[pass & 1], n);
+            uint8_t *dig_out = last ? nullptr : W.dig[pass & 1];
+            if (first && last) launch_scatter<true, true>(rgb, nb, s, g, n, W.kept, pass, cur, dig_in, to, dig_out, W.M, W.base);
+            else if (first) launch_scatter<true, false>(rgb, nb, s, g, n, W.kept, pass, cur, dig_in, to, dig_out, W.M, W.base);
+            else if (last) launch_scatter<false, true>(rgb, nb, s, g, n, W.kept, pass, cur, dig_in, to, dig_out, W.M, W.base);
+            else launch_scatter<false, false>(rgb, nb, s, g, n, W.kept, pass, cur, dig_in, to, dig_out, W.M, W.base);
+            cur = BinIn{to.pixel, to.z, to.alpha, to.r, to.g, to.b};
+            dig_in = dig_out;
         }
-        return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+    } else if (cudaMemsetAsync(W.kept, 0, 8, s) != cudaSuccess) {
+        return WT_ERR_CUDA;
     }
-    // global atomics (tile counts too large for shared memory, or no fragments)
-    if (cudaMemsetAsync(counts, 0, (size_t)nt * 4, s) != cudaSuccess) return WT_ERR_CUDA;
-    if (in->n > 0) k_bin_count<<<grid, 256, 0, s>>>(g, in->n, in->pixel, counts, err);
-    k_bin_scan<<<1, 1024, 0, s>>>(counts, nt, tile_offsets_out, cursor);
-    if (in->n > 0) {
-        if (rgb) {
-            k_bin_scatter<true><<<grid, 256, 0, s>>>(g, in->n, a, stage, cursor);
-            k_bin_unpack<true><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
-        } else {
-            k_bin_scatter<false><<<grid, 256, 0, s>>>(g, in->n, a, stage, cursor);
-            k_bin_unpack<false><<<grid, 256, 0, s>>>(in->n, tile_offsets_out + nt, stage, o);
-        }
-    }
+    k_bin_offsets<<<grid_for(n + 1), 256, 0, s>>>(g, nt, pixel_out, W.kept, tile_offsets_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 

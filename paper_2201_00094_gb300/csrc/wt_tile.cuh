@@ -188,11 +188,6 @@ __device__ __forceinline__ float se16_level_scale(int i) {
 }
 // 2^k for -126 <= k <= 127
 __device__ __forceinline__ float exp2i(int k) { return __int_as_float((127 + k) << 23); }
-// rint(x) for 0 <= x < 2^22 as an integer: x + 2^23 rounds half to even onto
-// the integers, whose low mantissa bits are then the result
-__device__ __forceinline__ uint32_t rint_small(float x) {
-    return (uint32_t)(__float_as_int(__fadd_rn(x, 8388608.f)) - 0x4B000000);
-}
 // q as a float for q < 2^23 (2^23 + q is exact; subtracting 2^23 leaves q)
 __device__ __forceinline__ float small_to_float(uint32_t q) { return __uint_as_float(0x4B000000u | q) - 8388608.f; }
 
@@ -201,27 +196,33 @@ template <int C> __device__ __forceinline__ uint8_t *se16_expo(const void *coeff
     return (uint8_t *)coeff + (size_t)P * C * 2;
 }
 
-// Encodes a row in place: v becomes the decoded values; returns e.
+// Encodes a row in place: v becomes the decoded values; returns e.  The
+// coefficients come from the bins tree (or sums of its rows), which gives
+// chi_00 >= 0 and X_{n,k} <= 0, so |v_i| is the clamped magnitude of the
+// definition.  Rounding: m 2^(16-e) + 2^23 (one FMA, exact product) rounds
+// half to even onto the integers 2^23 + q; decoding subtracts 2^23 and scales
+// (one more FMA), which is exact.
 template <int C> __device__ __forceinline__ int se16_round(float (&v)[C]) {
     float m[C];
     float M = 0.f;
 #pragma unroll
     for (int i = 0; i < C; ++i) {
-        m[i] = (i == 0 ? fmaxf(v[i], 0.f) : fmaxf(-v[i], 0.f)) * se16_level_scale(i);  // NaN -> 0
+        m[i] = fabsf(v[i]) * se16_level_scale(i);
         M = fmaxf(M, m[i]);
     }
     const int ex = (__float_as_int(M) >> 23) & 0xff;
     int e = ex > 0 ? min(max(ex - 126, kSE16Emin), kSE16Emax) : kSE16Emin;
     float scale = exp2i(16 - e);
-    if (rint_small(M * scale) >= 65536u) {
+    if (fmaf(M, scale, 8388608.f) >= 8388608.f + 65536.f) {  // the largest q reached 2^16
         ++e;
         scale *= 0.5f;
     }
     const float unit = exp2i(e - 16);
 #pragma unroll
     for (int i = 0; i < C; ++i) {
-        const float d = small_to_float(min(rint_small(m[i] * scale), 65535u)) * (unit / se16_level_scale(i));
-        v[i] = i == 0 ? d : -d;
+        const float r = fmaf(m[i], scale, 8388608.f);  // 2^23 + q_i
+        const float c = (i == 0 ? unit : -unit) / se16_level_scale(i);
+        v[i] = fmaf(r, c, -8388608.f * c);  // (r - 2^23) c, exact
     }
     return e;
 }
@@ -249,7 +250,8 @@ template <typename CT, int C> __device__ __forceinline__ int storage_exponent(fl
 // 2^(16 - e), unit = 2^(e - 16) for the row's exponent e; the mantissa is then
 // exact.
 template <typename CT> __device__ __forceinline__ CT to_storage(float v, int i, float scale) {
-    if constexpr (kIsSE16<CT>) return CT{(uint16_t)rint_small(fabsf(v) * (scale * se16_level_scale(i)))};
+    if constexpr (kIsSE16<CT>)
+        return CT{(uint16_t)(__float_as_int(fmaf(fabsf(v), scale * se16_level_scale(i), 8388608.f)) - 0x4B000000)};
     else return Cvt<CT>::to(v);
 }
 template <typename CT> __device__ __forceinline__ float from_storage(CT x, int i, float unit) {
@@ -1096,7 +1098,12 @@ template <int J> struct Layout {
     static constexpr size_t plane(int npx) { return align16((size_t)npx * Shape<J>::LD * 4); }
     static constexpr size_t vplane(int npx) { return align16((size_t)npx * Shape<J>::LDV * 4); }
     static constexpr size_t words(int npx) { return align16((size_t)npx * 4); }
-    static constexpr size_t accw(int npx) { return (size_t)kWarps * npx * 16; }
+    // the warps' accumulators; the same region stages a tile's coefficient
+    // rows on their way to or from global memory, so it holds the larger of
+    // the two (an FP32 row is wider than the accumulators from J = 6 on)
+    static constexpr size_t accw(int npx) {
+        return (size_t)npx * (kWarps * 16 > Shape<J>::C * 4 ? kWarps * 16 : Shape<J>::C * 4);
+    }
     // build: F and G bins + nearest-depth words
     static constexpr size_t build(int npx) { return 2 * plane(npx) + words(npx); }
     // fused: F and G bins, replaced after the build by the bin values, the

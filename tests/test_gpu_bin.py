@@ -26,13 +26,6 @@ def _to_dev(h):
     return {k: torch.from_numpy(np.ascontiguousarray(v)).to(DEV) for k, v in h.items()}
 
 
-def _records(cols, idx):
-    """Rows (pixel, z, alpha, r, g, b) of the given fragments, sorted."""
-    rec = np.stack([cols["pixel"][idx].astype(np.float64)] +
-                   [cols[k][idx].astype(np.float64) for k in ("z", "alpha", "r", "g", "b")], axis=1)
-    return rec[np.lexsort(rec.T[::-1])]
-
-
 @pytest.mark.parametrize("tile", [(7, 3), (256, 1), (16, 16)])
 def test_bin_groups_an_unordered_stream(tile):
     fr = synth.uniform_frame(53, 37, 5.0, 40, J=3, seed=40 + tile[0], tile_w=tile[0], tile_h=tile[1])
@@ -44,16 +37,16 @@ def test_bin_groups_an_unordered_stream(tile):
     order, off = oracle.bin_by_tile(h["pixel"], fr.width, fr.height, *tile)
     got = {k: v.cpu().numpy() for k, v in out.items()}
     np.testing.assert_array_equal(got["tile_offsets"], off)
-    for t in range(len(off) - 1):
-        s, e = off[t], off[t + 1]
-        np.testing.assert_array_equal(_records(got, np.arange(s, e)), _records(h, order[s:e]))
+    # the sort is stable: each tile's fragments in their input order, bit for bit
+    for k in ("pixel", "z", "alpha", "r", "g", "b"):
+        np.testing.assert_array_equal(got[k][:off[-1]], h[k][order])
 
 
-@pytest.mark.parametrize("W,H", [(300, 200), (1500, 1500)])
-def test_bin_one_pixel_tiles(W, H):
-    """One-pixel tiles, 60,000 and 2.25M of them: too many tile counters for
-    shared memory, so the slots come from global atomics."""
-    fr = synth.uniform_frame(W, H, 1.5, 8, J=2, seed=77, tile_w=1, tile_h=1)
+@pytest.mark.parametrize("W,H,lam", [(12, 20, 30.0), (300, 200, 1.5), (1500, 1500, 1.5), (4100, 4100, 0.05)])
+def test_bin_one_pixel_tiles(W, H, lam):
+    """One-pixel tiles: 240 tiles (one radix pass of 8 bits), 60,000 (two),
+    2.25M (three) and 16.8M (four passes)."""
+    fr = synth.uniform_frame(W, H, lam, 64, J=2, seed=77, tile_w=1, tile_h=1)
     h = _shuffled(fr, 5)
     d = desc_of(fr)
     g = _to_dev(h)
@@ -65,7 +58,8 @@ def test_bin_one_pixel_tiles(W, H):
     # one tile per pixel: every kept fragment sits in its own pixel's range
     t = np.repeat(np.arange(len(off) - 1), np.diff(off))
     np.testing.assert_array_equal(got["pixel"][: off[-1]], t)
-    np.testing.assert_array_equal(_records(got, np.arange(off[-1])), _records(h, order))
+    for k in ("pixel", "z", "alpha", "r", "g", "b"):
+        np.testing.assert_array_equal(got[k][:off[-1]], h[k][order])
 
 
 def test_binned_stream_composites_like_the_oracle():
@@ -173,3 +167,30 @@ def test_normalised_depth_and_composite_match_the_oracle():
     wt.wt_normalize_depth(d, wt.make_frags(g.pixel, zi, g.alpha, g.tile_offsets), zlo, zhi, zi)
     torch.cuda.synchronize()
     assert torch.equal(zi, zn)
+
+
+def test_bin_full_size_random_order_frame():
+    """The 4K heavy-smoke frame (199M fragments, 192 x 1 tiles) in a seeded
+    random order, the preprocessing input of the benchmark: the binned stream
+    is the stable sort of that order by tile id (torch's stable sort as the
+    reference), the offsets are the frame's own, and two runs agree bit for
+    bit."""
+    fr = synth.heavy4k(seed=0, device=DEV, tile_w=192, tile_h=1)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(11)
+    perm = torch.randperm(fr.n, device=DEV, generator=g)
+    sh = {k: getattr(fr, k)[perm].contiguous() for k in ("pixel", "z", "alpha", "r", "g", "b")}
+    del perm
+    d = desc_of(fr)
+    out = wt.wt_bin(d, sh["pixel"], sh["z"], sh["alpha"], sh["r"], sh["g"], sh["b"])
+    assert wt.wt_get_error() == 0
+    assert torch.equal(out["tile_offsets"], fr.tile_offsets)
+    px = sh["pixel"].long()
+    tile = (px // fr.width) * ((fr.width + 191) // 192) + (px % fr.width) // 192
+    del px
+    order = torch.sort(tile, stable=True).indices
+    del tile
+    for k in ("pixel", "z", "alpha", "r", "g", "b"):
+        assert torch.equal(out[k], sh[k][order]), k
+    again = wt.wt_bin(d, sh["pixel"], sh["z"], sh["alpha"], sh["r"], sh["g"], sh["b"])
+    assert all(torch.equal(out[k], again[k]) for k in out)
