@@ -178,33 +178,40 @@ __global__ void __launch_bounds__(256) k_bin_bases(const unsigned long long *__r
 
 // One pass of the sort: ranks the block's fragments by digit (stable), then
 // moves every field through shared memory into digit order and out to its
-// run.  FIRST: digits from the pixel ids; LAST: no next digit to write.
+// run.  FIRST: digits from the pixel ids; LAST: no next digit to write.  The
+// keys of all the thread's fragments are loaded before the ranking, and the
+// next field's values are loaded while the current one is written out.
 template <bool FIRST, bool LAST, bool RGB>
-__global__ void __launch_bounds__(kRT) k_bin_scatter(BinGeom g, int64_t n, const unsigned long long *kept,
-                                                     int pass, int nb, BinIn in, const uint8_t *__restrict__ dig_in,
-                                                     BinOut out, uint8_t *__restrict__ dig_out,
-                                                     const unsigned *__restrict__ M,
-                                                     const unsigned long long *__restrict__ base) {
-    __shared__ unsigned wcnt[kRW][kRD];     // per-warp digit counts, then exclusive offsets over warps
-    __shared__ unsigned lstart[kRD];        // block-local start of each digit's run
+__global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, const unsigned long long *kept,
+                                                        int pass, int nb, BinIn in, const uint8_t *__restrict__ dig_in,
+                                                        BinOut out, uint8_t *__restrict__ dig_out,
+                                                        const unsigned *__restrict__ M,
+                                                        const unsigned long long *__restrict__ base) {
+    __shared__ unsigned wcnt[kRW][kRD];       // per-warp digit counts, then exclusive offsets over warps
+    __shared__ unsigned lstart[kRD];          // block-local start of each digit's run
     __shared__ unsigned long long gdst[256];  // where this block's run of each digit starts in the output
     __shared__ uint32_t stage[kRTile];
     __shared__ uint8_t sdig[kRTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRW * kRD; i += kRT) (&wcnt[0][0])[i] = 0u;
-    __syncthreads();
     const int64_t ne = FIRST ? n : (int64_t)*kept;
     const int64_t b0 = (int64_t)blockIdx.x * kRTile + w * (32 * kRI) + lane;  // fragment k at b0 + 32 k
-    unsigned lt;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    unsigned pos[kRI];
-    int dg[kRI];
-    // rank within the warp's fragments of the same digit, in input order
+    // the keys (FIRST: the pixel ids, which are also the first field moved)
+    uint32_t val[kRI];
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
         const int64_t i = b0 + 32 * k;
+        val[k] = i < ne ? (FIRST ? in.pixel[i] : (uint32_t)dig_in[i]) : 0xffffffffu;
+    }
+    __syncthreads();
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    unsigned pos[kRI];
+    // rank within the warp's fragments of the same digit, in input order
+#pragma unroll
+    for (int k = 0; k < kRI; ++k) {
         int d = 256;
-        if (i < ne) d = FIRST ? first_digit(in.pixel[i], g, pass) : (int)dig_in[i];
+        if (b0 + 32 * k < ne) d = FIRST ? first_digit(val[k], g, pass) : (int)val[k];
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         unsigned old = 0;
@@ -213,8 +220,7 @@ __global__ void __launch_bounds__(kRT) k_bin_scatter(BinGeom g, int64_t n, const
             wcnt[w][d] = old + __popc(peers);
         }
         old = __shfl_sync(0xffffffffu, old, leader);
-        pos[k] = old + __popc(peers & lt);
-        dg[k] = d;
+        pos[k] = (old + __popc(peers & lt)) | ((unsigned)d << 16);  // rank (< 4096) and digit
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kRD; d += kRT) {
@@ -251,47 +257,65 @@ __global__ void __launch_bounds__(kRT) k_bin_scatter(BinGeom g, int64_t n, const
     }
     for (int d = threadIdx.x; d < 256; d += kRT) gdst[d] = base[d] + M[(int64_t)d * nb + blockIdx.x];
     __syncthreads();
+    // block-local positions; a position below nvalid is a kept fragment
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
-        pos[k] += lstart[dg[k]] + wcnt[w][dg[k]];
-        if (dg[k] < 256) sdig[pos[k]] = (uint8_t)dg[k];
+        const int d = (int)(pos[k] >> 16);
+        pos[k] = (pos[k] & 0xffffu) + lstart[d] + wcnt[w][d];
+        if (d < 256) sdig[pos[k]] = (uint8_t)d;
     }
     const unsigned nvalid = lstart[256];  // the block's fragments that are written
-    __syncthreads();
-    // one field at a time: into shared memory in digit order, then out in runs
-    auto move = [&](const uint32_t *src, uint32_t *dst, bool next_digit) {
+    if (!FIRST) {  // the first field, the pixel ids
 #pragma unroll
         for (int k = 0; k < kRI; ++k)
-            if (dg[k] < 256) stage[pos[k]] = src[b0 + 32 * k];
+            if (pos[k] < nvalid) val[k] = in.pixel[b0 + 32 * k];
+    }
+    __syncthreads();
+    const uint32_t *src[6] = {in.pixel, reinterpret_cast<const uint32_t *>(in.z),
+                              reinterpret_cast<const uint32_t *>(in.alpha), reinterpret_cast<const uint32_t *>(in.r),
+                              reinterpret_cast<const uint32_t *>(in.g), reinterpret_cast<const uint32_t *>(in.b)};
+    uint32_t *dst[6] = {out.pixel, reinterpret_cast<uint32_t *>(out.z), reinterpret_cast<uint32_t *>(out.alpha),
+                        reinterpret_cast<uint32_t *>(out.r), reinterpret_cast<uint32_t *>(out.g),
+                        reinterpret_cast<uint32_t *>(out.b)};
+    constexpr int kFields = RGB ? 6 : 3;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+#pragma unroll
+        for (int k = 0; k < kRI; ++k)
+            if (pos[k] < nvalid) stage[pos[k]] = val[k];
         __syncthreads();
+        if (f + 1 < kFields) {  // the next field's loads, in flight during the write-out
+#pragma unroll
+            for (int k = 0; k < kRI; ++k)
+                if (pos[k] < nvalid) val[k] = src[f + 1][b0 + 32 * k];
+        }
         for (unsigned q = threadIdx.x; q < nvalid; q += kRT) {
             const int d = sdig[q];
             const uint32_t v = stage[q];
             const unsigned long long o = gdst[d] + (q - lstart[d]);
-            dst[o] = v;
-            if (!LAST && next_digit) dig_out[o] = (uint8_t)((tile_of_pixel(v, g) >> (8 * pass + 8)) & 255u);
+            dst[f][o] = v;
+            if (!LAST && f == 0) dig_out[o] = (uint8_t)((tile_of_pixel(v, g) >> (8 * pass + 8)) & 255u);
         }
         __syncthreads();
-    };
-    move(in.pixel, out.pixel, true);
-    move(reinterpret_cast<const uint32_t *>(in.z), reinterpret_cast<uint32_t *>(out.z), false);
-    move(reinterpret_cast<const uint32_t *>(in.alpha), reinterpret_cast<uint32_t *>(out.alpha), false);
-    if (RGB) {
-        move(reinterpret_cast<const uint32_t *>(in.r), reinterpret_cast<uint32_t *>(out.r), false);
-        move(reinterpret_cast<const uint32_t *>(in.g), reinterpret_cast<uint32_t *>(out.g), false);
-        move(reinterpret_cast<const uint32_t *>(in.b), reinterpret_cast<uint32_t *>(out.b), false);
     }
 }
 
 // tile_offsets from the sorted stream: position i opens the tiles after the
-// previous fragment's tile up to its own; position kept closes the rest.
+// previous fragment's tile up to its own; position kept closes the rest.  A
+// warp covers consecutive positions, so the previous tile id comes from the
+// lane below (lane 0 computes its own).
 __global__ void __launch_bounds__(256) k_bin_offsets(BinGeom g, int64_t ntiles, const uint32_t *__restrict__ pixel,
                                                      const unsigned long long *kept, int64_t *__restrict__ off) {
     const int64_t K = (int64_t)*kept;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= K; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b <= K; b += stride) {
+        const int64_t i = b + lane;
         const int64_t t = i < K ? (int64_t)tile_of_pixel(pixel[i], g) : ntiles;
-        const int64_t tp = i > 0 ? (int64_t)tile_of_pixel(pixel[i - 1], g) : -1;
-        for (int64_t u = tp + 1; u <= t; ++u) off[u] = i;
+        int64_t tp = __shfl_up_sync(0xffffffffu, t, 1);
+        if (lane == 0) tp = i > 0 ? (int64_t)tile_of_pixel(pixel[i - 1], g) : -1;
+        if (i <= K)
+            for (int64_t u = tp + 1; u <= t; ++u) off[u] = i;
     }
 }
 

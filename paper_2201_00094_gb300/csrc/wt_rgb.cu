@@ -315,7 +315,7 @@ template <int J, bool E5, bool DEF> cudaError_t launch_rgb(const RgbParams &q, i
     constexpr int MB = E5 ? (J == 5 ? 2 : 3) : 4;
     const int npx = q.p.g.tile_w * q.p.g.tile_h;
     const size_t bytes = RgbLayout<J, E5>::total(npx);
-    if (bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
     cudaError_t e =
         cudaFuncSetAttribute(k_fused_rgb<J, E5, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -139,29 +139,46 @@ template <> struct Cvt<__half> {
 // (one more if its rounded mantissa reaches 2^9), round every mantissa to
 // nearest.
 constexpr float kE5Max = 65408.f;  // (511/512) * 2^16
-__device__ __forceinline__ uint32_t e5_encode(float r, float g, float b) {
-    r = fminf(fmaxf(r, 0.f), kE5Max);  // NaN -> 0
-    g = fminf(fmaxf(g, 0.f), kE5Max);
-    b = fminf(fmaxf(b, 0.f), kE5Max);
-    const float mx = fmaxf(r, fmaxf(g, b));
+// 2^k for -126 <= k <= 127
+__device__ __forceinline__ float exp2i(int k) { return __int_as_float((127 + k) << 23); }
+// The shared exponent of three clamped values whose largest is mx, with
+// scale = 2^(24 - e) (value -> mantissa units) and unit = 2^(e - 24).
+struct E5Scale {
+    int e;
+    float scale, unit;
+};
+__device__ __forceinline__ float e5_clamp(float x) { return fminf(fmaxf(x, 0.f), kE5Max); }  // NaN -> 0
+// floor(x scale + 1/2) for x scale + 1/2 < 2^23: the fma rounds once, and the
+// round-toward-zero add of 2^23 leaves the floor in the low mantissa bits
+__device__ __forceinline__ uint32_t e5_mant(float x, float scale) {
+    return (uint32_t)(__float_as_int(__fadd_rz(fmaf(x, scale, 0.5f), 8388608.f)) - 0x4B000000);
+}
+__device__ __forceinline__ E5Scale e5_scale(float mx) {
     // floor(log2(mx)) for mx > 0, from the exponent bits (subnormal FP32 values
     // are far below the format's smallest exponent and take the floor -16)
     const int fl = mx > 0.f ? max(((int)(__float_as_uint(mx) >> 23) & 0xff) - 127, -16) : -16;
-    int e = fl + 1 + 15;  // in [0, 32)
-    float scale = ldexpf(1.f, 24 - e);  // 1 / 2^(e - 15 - 9)
-    if (floorf(fmaf(mx, scale, 0.5f)) >= 512.f) {
-        ++e;
-        scale *= 0.5f;
+    E5Scale s;
+    s.e = fl + 1 + 15;  // in [0, 32)
+    s.scale = exp2i(24 - s.e);
+    if (e5_mant(mx, s.scale) >= 512u) {
+        ++s.e;
+        s.scale *= 0.5f;
     }
-    const uint32_t rs = (uint32_t)floorf(fmaf(r, scale, 0.5f)), gs = (uint32_t)floorf(fmaf(g, scale, 0.5f)),
-                   bs = (uint32_t)floorf(fmaf(b, scale, 0.5f));
-    return rs | (gs << 9) | (bs << 18) | ((uint32_t)e << 27);
+    s.unit = exp2i(s.e - 24);
+    return s;
+}
+__device__ __forceinline__ uint32_t e5_encode(float r, float g, float b) {
+    r = e5_clamp(r);
+    g = e5_clamp(g);
+    b = e5_clamp(b);
+    const E5Scale s = e5_scale(fmaxf(r, fmaxf(g, b)));
+    return e5_mant(r, s.scale) | (e5_mant(g, s.scale) << 9) | (e5_mant(b, s.scale) << 18) | ((uint32_t)s.e << 27);
 }
 __device__ __forceinline__ void e5_decode(uint32_t w, float &r, float &g, float &b) {
-    const float scale = ldexpf(1.f, (int)(w >> 27) - 24);
-    r = (float)(w & 511u) * scale;
-    g = (float)((w >> 9) & 511u) * scale;
-    b = (float)((w >> 18) & 511u) * scale;
+    const float unit = exp2i((int)(w >> 27) - 24);
+    r = (float)(w & 511u) * unit;
+    g = (float)((w >> 9) & 511u) * unit;
+    b = (float)((w >> 18) & 511u) * unit;
 }
 
 // Shared-exponent 16-bit storage (WT_SE16).  The sign property of §2.3.1
@@ -186,8 +203,6 @@ constexpr int kSE16Emin = -100, kSE16Emax = 100, kSE16Bias = 128;
 __device__ __forceinline__ float se16_level_scale(int i) {
     return i > 0 ? (float)(1 << ((31 - __clz(i)) >> 1)) : 1.f;
 }
-// 2^k for -126 <= k <= 127
-__device__ __forceinline__ float exp2i(int k) { return __int_as_float((127 + k) << 23); }
 // q as a float for q < 2^23 (2^23 + q is exact; subtracting 2^23 leaves q)
 __device__ __forceinline__ float small_to_float(uint32_t q) { return __uint_as_float(0x4B000000u | q) - 8388608.f; }
 
