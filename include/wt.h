@@ -396,8 +396,9 @@ size_t wt_bin_workspace_bytes(const wt_desc *desc, int64_t n);
  * desc) into caller-allocated output arrays: a stable radix sort by tile id,
  * 8 bits per pass (one pass for up to 256 tiles, two up to 65536, at most
  * four), each pass writing coalesced runs of fragments of one digit.
- *   in          n fragments in any order; in->tile_offsets is ignored (may be
- *               NULL); in->r/g/b may all be NULL (then r/g/b_out are unused).
+ *   in          n fragments in any order, n < 2^32 (else WT_ERR_ARG);
+ *               in->tile_offsets is ignored (may be NULL); in->r/g/b may all
+ *               be NULL (then r/g/b_out are unused).
  *   *_out       [n] device arrays (at least in->n elements each), written with
  *               the kept fragments grouped by tile; they must not overlap in.
  *   tile_offsets_out [ntiles + 1] int64, written: tile t owns

@@ -96,7 +96,8 @@ __device__ __forceinline__ int first_digit(uint32_t px, const BinGeom &g, int pa
 // Histogram of the pass's digit over each block's fragments, stored
 // digit-major: M[d * nb + block].  FIRST: the digit comes from the pixel id
 // (dropped fragments counted into err); otherwise from the byte array written
-// by the previous pass, over the kept fragments.
+// by the previous pass, over the kept fragments.  Each thread reads its 16
+// keys as whole 16-byte vectors where the block's range allows.
 template <bool FIRST>
 __global__ void __launch_bounds__(kRT) k_bin_hist(BinGeom g, int64_t n, const unsigned long long *kept,
                                                   int pass, int nb, const uint32_t *__restrict__ pixel,
@@ -106,16 +107,43 @@ __global__ void __launch_bounds__(kRT) k_bin_hist(BinGeom g, int64_t n, const un
     for (int d = threadIdx.x; d < kRD; d += kRT) h[d] = 0u;
     __syncthreads();
     const int64_t ne = FIRST ? n : (int64_t)*kept;
-    const int64_t b0 = (int64_t)blockIdx.x * kRTile;
+    const int64_t i0 = (int64_t)blockIdx.x * kRTile + (int64_t)threadIdx.x * kRI;  // this thread's 16 keys
     unsigned bad = 0;
-    for (int j = threadIdx.x; j < kRTile; j += kRT) {
-        const int64_t i = b0 + j;
-        if (i >= ne) break;
-        const int d = FIRST ? first_digit(pixel[i], g, pass) : (int)dig[i];
-        if (FIRST && d == 256) ++bad;
-        atomicAdd(&h[d], 1u);
+    if constexpr (FIRST) {
+        uint32_t key[kRI];
+        if (i0 + kRI <= ne) {  // i0 is a multiple of 16 elements: 16-byte aligned
+#pragma unroll
+            for (int j = 0; j < kRI; j += 4) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(pixel + i0 + j);
+                key[j] = u.x, key[j + 1] = u.y, key[j + 2] = u.z, key[j + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kRI; ++j) key[j] = i0 + j < ne ? pixel[i0 + j] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kRI; ++j) {
+            if (i0 + j >= ne) break;
+            const int d = first_digit(key[j], g, pass);
+            if (d == 256) ++bad;
+            atomicAdd(&h[d], 1u);
+        }
+        flush_bad(bad, err);
+    } else {
+        uint4 u = make_uint4(0u, 0u, 0u, 0u);
+        if (i0 + kRI <= ne) {
+            u = *reinterpret_cast<const uint4 *>(dig + i0);
+        } else {
+            uint8_t *ub = reinterpret_cast<uint8_t *>(&u);
+            for (int j = 0; j < kRI; ++j) ub[j] = i0 + j < ne ? dig[i0 + j] : 0;
+        }
+        const uint32_t word[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int j = 0; j < kRI; ++j) {
+            if (i0 + j >= ne) break;
+            atomicAdd(&h[(word[j >> 2] >> (8 * (j & 3))) & 255u], 1u);
+        }
     }
-    if (FIRST) flush_bad(bad, err);
     __syncthreads();
     for (int d = threadIdx.x; d < kRD; d += kRT) M[(int64_t)d * nb + blockIdx.x] = h[d];
 }
@@ -191,7 +219,8 @@ __global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, co
     __shared__ unsigned lstart[kRD];          // block-local start of each digit's run
     __shared__ unsigned long long gdst[256];  // where this block's run of each digit starts in the output
     __shared__ uint32_t stage[kRTile];
-    __shared__ uint8_t sdig[kRTile];
+    __shared__ uint32_t sdst[kRTile];  // output index of each block-local position
+    __shared__ uint8_t snext[FIRST && !LAST ? kRTile : 1];  // the next pass's digit (first pass)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRW * kRD; i += kRT) (&wcnt[0][0])[i] = 0u;
     const int64_t ne = FIRST ? n : (int64_t)*kept;
@@ -207,11 +236,24 @@ __global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, co
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     unsigned pos[kRI];
-    // rank within the warp's fragments of the same digit, in input order
+    // rank within the warp's fragments of the same digit, in input order, kept
+    // as rank | digit << 12 | next << 21 (the first pass keeps the next pass's
+    // digit, from the same tile id)
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
         int d = 256;
-        if (b0 + 32 * k < ne) d = FIRST ? first_digit(val[k], g, pass) : (int)val[k];
+        uint32_t nx = 0;
+        if (b0 + 32 * k < ne) {
+            if constexpr (FIRST) {
+                if ((int64_t)val[k] < g.P) {
+                    const uint32_t t = tile_of_pixel(val[k], g);
+                    d = (int)((t >> (8 * pass)) & 255u);
+                    nx = (t >> (8 * pass + 8)) & 255u;
+                }
+            } else {
+                d = (int)val[k];
+            }
+        }
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         unsigned old = 0;
@@ -220,7 +262,7 @@ __global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, co
             wcnt[w][d] = old + __popc(peers);
         }
         old = __shfl_sync(0xffffffffu, old, leader);
-        pos[k] = (old + __popc(peers & lt)) | ((unsigned)d << 16);  // rank (< 4096) and digit
+        pos[k] = (old + __popc(peers & lt)) | ((unsigned)d << 12) | (nx << 21);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kRD; d += kRT) {
@@ -257,12 +299,18 @@ __global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, co
     }
     for (int d = threadIdx.x; d < 256; d += kRT) gdst[d] = base[d] + M[(int64_t)d * nb + blockIdx.x];
     __syncthreads();
-    // block-local positions; a position below nvalid is a kept fragment
+    // block-local positions (a position below nvalid is a kept fragment) and
+    // the output index of each
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
-        const int d = (int)(pos[k] >> 16);
-        pos[k] = (pos[k] & 0xffffu) + lstart[d] + wcnt[w][d];
-        if (d < 256) sdig[pos[k]] = (uint8_t)d;
+        const int d = (int)((pos[k] >> 12) & 511u);
+        const unsigned nx = pos[k] >> 21;
+        const unsigned within = (pos[k] & 4095u) + wcnt[w][d];  // rank in the block's run of digit d
+        pos[k] = within + lstart[d];
+        if (d < 256) {
+            sdst[pos[k]] = (uint32_t)(gdst[d] + within);
+            if constexpr (FIRST && !LAST) snext[pos[k]] = (uint8_t)nx;
+        }
     }
     const unsigned nvalid = lstart[256];  // the block's fragments that are written
     if (!FIRST) {  // the first field, the pixel ids
@@ -290,32 +338,49 @@ __global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, co
                 if (pos[k] < nvalid) val[k] = src[f + 1][b0 + 32 * k];
         }
         for (unsigned q = threadIdx.x; q < nvalid; q += kRT) {
-            const int d = sdig[q];
+            const uint32_t o = sdst[q];
             const uint32_t v = stage[q];
-            const unsigned long long o = gdst[d] + (q - lstart[d]);
             dst[f][o] = v;
-            if (!LAST && f == 0) dig_out[o] = (uint8_t)((tile_of_pixel(v, g) >> (8 * pass + 8)) & 255u);
+            if (!LAST && f == 0)
+                dig_out[o] = FIRST ? snext[q] : (uint8_t)((tile_of_pixel(v, g) >> (8 * pass + 8)) & 255u);
         }
         __syncthreads();
     }
 }
 
 // tile_offsets from the sorted stream: position i opens the tiles after the
-// previous fragment's tile up to its own; position kept closes the rest.  A
-// warp covers consecutive positions, so the previous tile id comes from the
-// lane below (lane 0 computes its own).
+// previous fragment's tile up to its own; position kept closes the rest.
+// Each thread takes 8 consecutive positions (two 16-byte loads); the tile
+// before its first one comes from the lane below (lane 0 reads it).
+constexpr int kOffPer = 8;
 __global__ void __launch_bounds__(256) k_bin_offsets(BinGeom g, int64_t ntiles, const uint32_t *__restrict__ pixel,
                                                      const unsigned long long *kept, int64_t *__restrict__ off) {
     const int64_t K = (int64_t)*kept;
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b <= K; b += stride) {
-        const int64_t i = b + lane;
-        const int64_t t = i < K ? (int64_t)tile_of_pixel(pixel[i], g) : ntiles;
-        int64_t tp = __shfl_up_sync(0xffffffffu, t, 1);
-        if (lane == 0) tp = i > 0 ? (int64_t)tile_of_pixel(pixel[i - 1], g) : -1;
-        if (i <= K)
-            for (int64_t u = tp + 1; u <= t; ++u) off[u] = i;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kOffPer;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kOffPer; b <= K; b += stride) {
+        const int64_t i0 = b + (int64_t)lane * kOffPer;
+        int64_t t[kOffPer];
+        if (i0 + kOffPer <= K) {  // i0 is a multiple of 8 elements: 16-byte aligned
+            const uint4 u0 = *reinterpret_cast<const uint4 *>(pixel + i0);
+            const uint4 u1 = *reinterpret_cast<const uint4 *>(pixel + i0 + 4);
+            const uint32_t px[kOffPer] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+            for (int j = 0; j < kOffPer; ++j) t[j] = (int64_t)tile_of_pixel(px[j], g);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kOffPer; ++j)
+                t[j] = i0 + j < K ? (int64_t)tile_of_pixel(pixel[i0 + j], g) : ntiles;
+        }
+        int64_t tp = __shfl_up_sync(0xffffffffu, t[kOffPer - 1], 1);
+        if (lane == 0) tp = i0 > 0 ? (int64_t)tile_of_pixel(pixel[i0 - 1], g) : -1;
+#pragma unroll
+        for (int j = 0; j < kOffPer; ++j) {
+            const int64_t i = i0 + j;
+            if (i <= K)
+                for (int64_t u = tp + 1; u <= t[j]; ++u) off[u] = i;
+            tp = t[j];
+        }
     }
 }
 
@@ -518,6 +583,7 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
         for (const void *p : need)
             if (!p) return WT_ERR_ARG;
         if (rgb && (!r_out || !g_out || !b_out)) return WT_ERR_ARG;
+        if (!aligned_to(in->pixel, 16) || !aligned_to(pixel_out, 16)) return WT_ERR_ARG;  // vector loads
     }
     unsigned long long *err = error_word();
     if (!err) return WT_ERR_CUDA;
@@ -527,8 +593,8 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
     workspace_layout(nt, n, static_cast<char *>(workspace), &W);
     const BinGeom g = bin_geom(desc);
     const int passes = sort_passes(nt);
+    if (n >= (int64_t(1) << 32)) return WT_ERR_ARG;  // output indices are 32-bit
     const int64_t nb64 = (n + kRTile - 1) / kRTile;
-    if (nb64 >= (int64_t(1) << 31)) return WT_ERR_ARG;
     const int nb = (int)nb64;
     if (nb > 0) {
         const BinIn src{in->pixel, in->z, in->alpha, in->r, in->g, in->b};
@@ -555,7 +621,7 @@ extern "C" wt_status wt_bin(const wt_desc *desc, const wt_frags *in, uint32_t *p
     } else if (cudaMemsetAsync(W.kept, 0, 8, s) != cudaSuccess) {
         return WT_ERR_CUDA;
     }
-    k_bin_offsets<<<grid_for(n + 1), 256, 0, s>>>(g, nt, pixel_out, W.kept, tile_offsets_out);
+    k_bin_offsets<<<grid_for((n + kOffPer) / kOffPer), 256, 0, s>>>(g, nt, pixel_out, W.kept, tile_offsets_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
