@@ -432,8 +432,8 @@ __device__ __forceinline__ FragState<J> frag_state(const Params &p, const Tile &
 // (1 - f_j) Q_{m_j} + f_j Q_{m_j+1}; self-exclusion removes gamma_j g_j.
 // dL/dalpha = beta 2^-A' + (dL/da) / (1 - alpha) inside the clamp, else 0.
 // Coefficients are rebuilt here (never stored between the passes).
-template <int J, typename CT>
-__global__ void __launch_bounds__(kThreads, 2) k_backward(Params p) {
+template <int J, typename CT, int MB>
+__global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
@@ -604,14 +604,22 @@ template <int J, typename CT> int serve_blocks_per_sm(int npx) {
     return n;
 }
 
-template <int J, typename CT> cudaError_t launch_backward_t(const Params &p, int ntiles, cudaStream_t s) {
-    const int npx = p.g.tile_w * p.g.tile_h;
-    const size_t bytes = BackLayout<J>::total(npx);
-    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
-    cudaError_t e = cudaFuncSetAttribute(k_backward<J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+template <int J, typename CT, int MB> cudaError_t launch_backward_k(const Params &p, int ntiles, cudaStream_t s) {
+    const size_t bytes = BackLayout<J>::total(p.g.tile_w * p.g.tile_h);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_backward<J, CT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_backward<J, CT><<<ntiles, kThreads, bytes, s>>>(p);
+    k_backward<J, CT, MB><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
+}
+// Registers budgeted for the CTAs per SM that the shared memory allows (228 KB
+// per SM, 1 KB of it reserved per CTA): three when at least three fit (80
+// registers, no spills), else two.  Four (64 registers) spill and were slower.
+template <int J, typename CT> cudaError_t launch_backward_t(const Params &p, int ntiles, cudaStream_t s) {
+    const size_t bytes = BackLayout<J>::total(p.g.tile_w * p.g.tile_h);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
+    if (3 * (bytes + 1024) <= 233472) return launch_backward_k<J, CT, 3>(p, ntiles, s);
+    return launch_backward_k<J, CT, 2>(p, ntiles, s);
 }
 
 // Evaluation at arbitrary (pixel, depth) queries: J+1 coefficient reads per
