@@ -308,9 +308,12 @@ enum {
  *   coeff        nullable: written in coeff_format (WT_RGB_*).
  * With FP32 storage the channels are three launches of a one-channel fused
  * kernel (out's components are written one by one, out.w summed in channel
- * order); with E5B9G9R9 one CTA per tile works through the channels, keeping
- * two more FP32 rows per pixel until the words are formed.  Every tile of up
- * to 256 pixels fits.
+ * order); with E5B9G9R9 one CTA per tile works through the channels,
+ * keeping r and g until the words are formed: as 16-bit magnitudes in the
+ * pixel's own row of coeff (with its nearest depths and total steps in its out
+ * entry) when coeff is given, as two FP32 rows per pixel in shared memory when
+ * it is NULL.  Both give the same words and the same out bit for bit.  Every
+ * tile of up to 256 pixels fits.
  * Invalid fragments (pixel outside their tile, NaN depth or a NaN opacity) are
  * left out of the channels they are invalid for and counted in the error word
  * once per channel.  WT_ACCUMULATE is not supported (WT_ERR_UNSUPPORTED).

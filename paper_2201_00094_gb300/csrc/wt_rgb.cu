@@ -16,10 +16,12 @@
 // register budget, four CTAs per SM); each writes its component of out and
 // adds its coverage to out.w in channel order.  With E5B9G9R9 storage a word
 // holds one coefficient index of all three channels, so one CTA per tile
-// builds channels r and g first and keeps their FP32 rows in shared memory;
-// after channel b's build the words are formed and stored, and the three
-// resolves run on the decoded values, so that the composite matches the
-// stored words.
+// builds channels r and g first and keeps them until channel b is built; then
+// the words are formed and stored, and the three resolves run on the decoded
+// values, so that the composite matches the stored words.  Channels r and g
+// wait as FP32 rows in shared memory when no word buffer is given
+// (k_fused_rgb), and as 16-bit magnitudes in the word buffer itself when it is
+// (k_fused_e5, half the shared memory).
 #include "wt.h"
 #include "wt_internal.h"
 #include "wt_tile.cuh"
@@ -308,6 +310,198 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused_rgb(RgbParams q) {
     flush_bad(bad, p.err);
 }
 
+// A clamped channel magnitude y in [0, kE5Max] kept in 16 bits for the word
+// formation: 0 for y < 2^-25, else its FP32 exponent E in [-25, 15] (6 bits, as
+// E + 26) and the top 10 bits of its mantissa, i.e. t = (bits(y) - bits(2^-26))
+// >> 13.  The word reads no more of y: its shared exponent comes from the
+// largest value's exponent and its 9-bit mantissa (rounded), which are the
+// top 10 significant bits at most, and every other channel's mantissa
+// floor(y 2^(24 - e) + 1/2) is fixed by the bits of y down to 2^(e - 25),
+// again 10 significant bits at most (e >= floor(log2 y) + 16).  Below 2^-25
+// a value has mantissa 0 in every word and cannot raise the exponent, whose
+// floor is -16.  So the words formed from the 16-bit values are the words of
+// the FP32 values, bit for bit.
+__device__ __forceinline__ uint32_t e5_keep16(float y) {
+    const uint32_t u = __float_as_uint(y);
+    return u < 0x33000000u ? 0u : (u - 0x32800000u) >> 13;  // 2^-25, 2^-26
+}
+__device__ __forceinline__ float e5_from16(uint32_t t) { return t ? __uint_as_float((t << 13) + 0x32800000u) : 0.f; }
+
+// Channel c (0 or 1) of a pixel's coefficient row v, as the magnitudes the
+// words encode (chi_00 and -X), in 16 bits each: half c of the pixel's row of
+// words (C / 2 words), which is free until the words are formed.
+template <int C> __device__ __forceinline__ void stash16(uint32_t *row, int c, const float (&v)[C]) {
+    uint32_t h[C / 2];
+#pragma unroll
+    for (int i = 0; i < C / 2; ++i) {
+        const float a = e5_clamp(i == 0 ? v[0] : -v[2 * i]), b = e5_clamp(-v[2 * i + 1]);
+        h[i] = e5_keep16(a) | (e5_keep16(b) << 16);
+    }
+    uint32_t *dst = row + c * (C / 2);
+    if constexpr (C / 2 % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < C / 2; i += 4)
+            reinterpret_cast<uint4 *>(dst)[i / 4] = make_uint4(h[i], h[i + 1], h[i + 2], h[i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < C / 2; ++i) dst[i] = h[i];
+    }
+}
+template <int C> __device__ __forceinline__ float unstash16(const uint32_t *row, int c, int k) {
+    const uint32_t h = row[c * (C / 2) + k / 2];
+    return e5_from16(k & 1 ? h >> 16 : h & 0xffffu);
+}
+
+// E5B9G9R9 storage with the word buffer given.  The channels run one after
+// another through the one-channel kernel's phases and shared memory (one
+// nearest-depth array: 57 KB at J = 5 with 192-pixel tiles, three blocks per
+// SM as the registers allow, against two for the two-rows kernel above):
+//   * r and g: bins, coefficients; the coefficients go, as 16-bit magnitudes,
+//     into halves of the pixel's own row of words, and the nearest depth and
+//     total step into the pixel's out entry (both read back by the same thread);
+//   * b: bins, coefficients, then the words from the stashed r, g and b, and
+//     the resolve of b on its decoded values;
+//   * g, then r: the channel decoded from the stored words, its nearest depth
+//     and total step from out, and its resolve.
+// Every value reaches the same arithmetic as in the two-rows kernel above, so
+// words and composite are bit for bit the same.
+template <int J, bool DEF, int MB>
+__global__ void __launch_bounds__(kThreads, MB) k_fused_e5(RgbParams q) {
+    constexpr int C = Shape<J>::C;
+    using L = RgbLayout<J, false>;
+    using St = Staged<float, C>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Params &p = q.p;
+    const int npx = p.g.tile_w * p.g.tile_h;
+    uint4 *stage = reinterpret_cast<uint4 *>(smem + Layout<J>::vplane(npx));  // words out, then (R, W)
+    const int after = (int)L::after(npx);
+    const Tile T = tile_of(p, p.tile0 + (int)blockIdx.x, true);
+    const int lp = threadIdx.x;
+    int64_t gp = -1;
+    if (lp < npx) gp = global_pixel(p, T, lp);
+    uint32_t *words = static_cast<uint32_t *>(p.coeff);
+    uint32_t *row = words + (gp >= 0 ? gp : 0) * C;
+    float2 *keep = reinterpret_cast<float2 *>(p.out) + 2 * (gp >= 0 ? gp : 0);  // (zmin, S) of r, then g
+    unsigned *sZ = reinterpret_cast<unsigned *>(smem + L::zw(npx));
+    if (threadIdx.x == 0) {
+        l2_prefetch_range(p.pixel, T.s, T.e);
+        l2_prefetch_range(p.z, T.s, T.e);
+#pragma unroll
+        for (int c = 0; c < kCh; ++c) l2_prefetch_range(q.alpha_c[c], T.s, T.e);
+        l2_prefetch_range(p.r, T.s, T.e);
+        l2_prefetch_range(p.gc, T.s, T.e);
+        l2_prefetch_range(p.b, T.s, T.e);
+    }
+    auto bg_of = [&](int c) {
+        return p.bg_img && gp >= 0 ? p.bg_img[3 * gp + c] : (c == 0 ? p.bg0 : c == 1 ? p.bg1 : p.bg2);
+    };
+    // (each phase has its own coefficient array, which a thread outside the
+    // image leaves unset, so that no array stays live across a bins pass)
+    unsigned bad = 0;
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+        float v[C], S = 0.f;
+        build_channel<J>(p, c == 0 ? q.alpha_c[0] : q.alpha_c[1], T, smem, sZ, gp, v, S, bad);
+        if (gp >= 0) {
+            stash16<C>(row, c, v);
+            keep[c] = make_float2(__uint_as_float(sZ[lp]), S);
+        }
+    }
+    float ob = 0.f, og = 0.f, orr = 0.f, cover_sum = 0.f;
+    {
+    float v[C], S = 0.f;
+    build_channel<J>(p, q.alpha_c[2], T, smem, sZ, gp, v, S, bad);
+    // the words; channel b's decoded values replace its FP32 ones
+    if constexpr (St::ok) {
+        // b's rows staged in the free bins region; then one 4-index chunk of one
+        // pixel per item: the two stashed halves, b, four words (staged for the
+        // coalesced copy), b decoded in place
+        uint4 *bst = reinterpret_cast<uint4 *>(smem);
+        if (gp >= 0) stage_row<float, C>(bst, lp, v);
+        __syncthreads();
+        for (int it = threadIdx.x; it < npx * St::K; it += blockDim.x) {
+            const int l = it / St::K, ch = it % St::K;
+            const int64_t g2 = global_pixel(p, T, l);
+            if (g2 < 0) continue;
+            const uint32_t *r2 = words + g2 * C;
+            const uint2 hr = reinterpret_cast<const uint2 *>(r2)[ch];
+            const uint2 hg = reinterpret_cast<const uint2 *>(r2 + C / 2)[ch];
+            const int at = l * St::K + (ch ^ St::sw(l));
+            float4 b = reinterpret_cast<const float4 *>(bst)[at];
+            auto word = [&](uint32_t r16, uint32_t g16, float &x, float sg) {
+                const uint32_t w = e5_encode(e5_from16(r16), e5_from16(g16), sg * x);
+                float dr, dg, db;
+                e5_decode(w, dr, dg, db);
+                x = sg * db;
+                return w;
+            };
+            uint4 w;
+            w.x = word(hr.x & 0xffffu, hg.x & 0xffffu, b.x, ch == 0 ? 1.f : -1.f);
+            w.y = word(hr.x >> 16, hg.x >> 16, b.y, -1.f);
+            w.z = word(hr.y & 0xffffu, hg.y & 0xffffu, b.z, -1.f);
+            w.w = word(hr.y >> 16, hg.y >> 16, b.w, -1.f);
+            reinterpret_cast<float4 *>(bst)[at] = b;
+            stage[at] = w;
+        }
+        __syncthreads();  // every stash read before any row is overwritten
+        copy_staged<float, C>(p, T, stage, after, reinterpret_cast<float *>(words));
+        if (gp >= 0) unstage_row<float, C>(bst, lp, v);
+        __syncthreads();  // b's rows read before its bin values overwrite them
+    } else {
+        if (gp >= 0) {
+            uint32_t w[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const float sg = k == 0 ? 1.f : -1.f;
+                w[k] = e5_encode(unstash16<C>(row, 0, k), unstash16<C>(row, 1, k), sg * v[k]);
+                float dr, dg, db;
+                e5_decode(w[k], dr, dg, db);
+                v[k] = sg * db;
+            }
+#pragma unroll
+            for (int k = 0; k < C; ++k) row[k] = w[k];  // every stash read before the row is overwritten
+        }
+        fill_zero(stage, after);
+    }
+    resolve_channel_px<J, DEF>(p, q.alpha_c[2], p.b, T, smem, sZ, gp, v, S, bg_of(2), ob, cover_sum);
+    }
+    // (its barriers have made every word of the tile visible to the block)
+#pragma unroll 1
+    for (int c = 1; c >= 0; --c) {
+        float v[C], Sc = 0.f, oc = 0.f;
+        if (gp >= 0) {
+            const float2 zs = keep[c];
+            sZ[lp] = __float_as_uint(zs.x);
+            Sc = zs.y;
+            auto take = [&](int k, uint32_t w) {
+                float r, g, b;
+                e5_decode(w, r, g, b);
+                v[k] = (k == 0 ? 1.f : -1.f) * (c == 0 ? r : g);
+            };
+            if constexpr (C % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < C; k += 4) {
+                    const uint4 w = reinterpret_cast<const uint4 *>(row)[k / 4];
+                    take(k, w.x);
+                    take(k + 1, w.y);
+                    take(k + 2, w.z);
+                    take(k + 3, w.w);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < C; ++k) take(k, row[k]);
+            }
+        }
+        fill_zero(stage, after);
+        resolve_channel_px<J, DEF>(p, c == 0 ? q.alpha_c[0] : q.alpha_c[1], c == 0 ? p.r : p.gc, T, smem, sZ,
+                                   gp, v, Sc, bg_of(c), oc, cover_sum);
+        if (c == 0) orr = oc;
+        else og = oc;
+    }
+    if (gp >= 0) reinterpret_cast<float4 *>(p.out)[gp] = make_float4(orr, og, ob, cover_sum * (1.f / 3.f));
+    flush_bad(bad, p.err);
+}
+
 // FP32 storage uses the mono kernel's shared memory and register budget (four
 // blocks per SM at J = 5 with 192-pixel tiles); E5B9G9R9 keeps two more
 // coefficient rows per pixel and takes fewer blocks.
@@ -323,12 +517,31 @@ template <int J, bool E5, bool DEF> cudaError_t launch_rgb(const RgbParams &q, i
     return cudaGetLastError();
 }
 
+// E5B9G9R9 with the word buffer given: the one-channel kernel's shared memory;
+// registers for three blocks per SM from J = 3 on (at 64 registers the three
+// channels' phases spill: 400 bytes per thread at J = 5, measured 8.96 ms
+// against 8.33 ms at three blocks).
+template <int J, bool DEF> cudaError_t launch_e5(const RgbParams &q, int ntiles, cudaStream_t s) {
+    constexpr int MB = J >= 3 ? 3 : 4;
+    const int npx = q.p.g.tile_w * q.p.g.tile_h;
+    const size_t bytes = RgbLayout<J, false>::total(npx);
+    if (bytes > kMaxSmemPerBlock) return cudaErrorNotSupported;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fused_e5<J, DEF, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_fused_e5<J, DEF, MB><<<ntiles, kThreads, bytes, s>>>(q);
+    return cudaGetLastError();
+}
+
 typedef cudaError_t (*RgbLaunch)(const RgbParams &, int, cudaStream_t);
 #define WT_RGB_ROW(E5, DEF) \
     { launch_rgb<1, E5, DEF>, launch_rgb<2, E5, DEF>, launch_rgb<3, E5, DEF>, launch_rgb<4, E5, DEF>, launch_rgb<5, E5, DEF> }
 const RgbLaunch kRgb[2][2][5] = {{WT_RGB_ROW(false, false), WT_RGB_ROW(false, true)},
                                  {WT_RGB_ROW(true, false), WT_RGB_ROW(true, true)}};
 #undef WT_RGB_ROW
+#define WT_E5_ROW(DEF) { launch_e5<1, DEF>, launch_e5<2, DEF>, launch_e5<3, DEF>, launch_e5<4, DEF>, launch_e5<5, DEF> }
+const RgbLaunch kE5[2][5] = {WT_E5_ROW(false), WT_E5_ROW(true)};
+#undef WT_E5_ROW
 
 template <int J> size_t rgb_bytes(int npx, bool e5) {
     return e5 ? RgbLayout<J, true>::total(npx) : RgbLayout<J, false>::total(npx);
@@ -353,10 +566,11 @@ cudaError_t launch_fused_rgb(const Params &p, int J, const float *const alpha_c[
     q.p = p;
     for (int c = 0; c < kCh; ++c) q.alpha_c[c] = alpha_c[c];
     q.plane = (int64_t)p.g.width * p.g.height * (int64_t(1) << J);
-    const RgbLaunch f = kRgb[e5 ? 1 : 0][p.flags == kDefaultFlags ? 1 : 0][J - 1];
+    const int def = p.flags == kDefaultFlags ? 1 : 0;
+    const RgbLaunch f = kRgb[e5 ? 1 : 0][def][J - 1];
     if (e5) {
         q.ch = 0;
-        return f(q, ntiles, s);
+        return (p.coeff ? kE5[def][J - 1] : f)(q, ntiles, s);
     }
     for (int c = 0; c < kCh; ++c) {
         q.ch = c;

@@ -24,6 +24,26 @@ def _coloured(fr: synth.Frame, seed: int):
     return [np.clip(a * rng.uniform(0.3, 1.2, fr.n), 0, 0.95).astype(np.float32) for _ in range(3)]
 
 
+def _check_e5(d, g, a, words, out, h, ac, J, bg=(0.5, 0.5, 0.5), flags=None, bg_img=None, bg_t=None):
+    """An E5B9G9R9 call's words and composite: the words equal, bit for bit, the
+    oracle's encoding of the coefficients the RGB_F32 call stores; the
+    composite equals the one computed wholly on the oracle side at 1e-4 where
+    the oracle's own words are the GPU's, within the one-step bound elsewhere."""
+    C = 1 << J
+    P = words.shape[0]
+    c32 = torch.empty(3, P, C, device=DEV)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, torch.empty(P, 4, device=DEV), c32, wt.RGB_F32, bg=bg,
+                            bg_img=bg_t)
+    assert wt.wt_get_error() == 0
+    w = words.cpu().numpy().view(np.uint32)
+    assert np.array_equal(w, e5_words_of(list(c32.cpu().numpy()), C))
+    ref, bound, same = e5_oracle_composite(h, ac, P, J, bg, w, flags=flags, bg_img=bg_img)
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref).max(axis=1)
+    assert same.mean() > 0.99
+    assert err[same].max() <= 1e-4
+    assert (err <= bound).all()
+
+
 @pytest.mark.parametrize("J,tile", [(4, (128, 1)), (5, (64, 1)), (3, (7, 3))])
 def test_coloured_fp32_matches_the_oracle(J, tile):
     fr = synth.uniform_frame(96, 40, 8.0, 40, J=J, seed=70 + J, tile_w=tile[0], tile_h=tile[1])
@@ -95,6 +115,29 @@ def test_coloured_e5b9g9r9_storage(J):
     assert (err <= bound).all()
 
 
+@pytest.mark.parametrize("J,tile", [(1, (64, 1)), (3, (7, 3)), (4, (128, 1)), (5, (192, 1)), (5, (16, 16))])
+def test_coloured_e5b9g9r9_composite_does_not_depend_on_storing_the_words(J, tile):
+    """With a word buffer, channels r and g wait in it (16 bits each) and in
+    out until the words are formed; without one, in shared memory.  The
+    composite is the same bit for bit, on a frame whose width and height are
+    not multiples of the tile, with a background image."""
+    fr = synth.uniform_frame(203, 37, 7.0, 35, J=J, seed=300 + 7 * J + tile[1], tile_w=tile[0], tile_h=tile[1])
+    ac = _coloured(fr, 23 + J)
+    g = fr.to(DEV)
+    d = desc_of(fr, J)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    bg_t = torch.from_numpy(np.random.default_rng(J).random((fr.P, 3)).astype(np.float32)).to(DEV)
+    o1 = torch.full((fr.P, 4), float("nan"), device=DEV)
+    o2 = torch.full((fr.P, 4), float("nan"), device=DEV)
+    words = torch.full((fr.P, 1 << J), -1, device=DEV, dtype=torch.int32)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, o1, words, wt.RGB_E5B9G9R9, bg_img=bg_t)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, o2, None, wt.RGB_E5B9G9R9, bg_img=bg_t)
+    assert wt.wt_get_error() == 0
+    assert torch.equal(o1, o2)
+    h = fr.numpy()
+    _check_e5(d, g, a, words, o1, h, ac, J, bg_img=bg_t.cpu().numpy(), bg_t=bg_t)
+
+
 def test_coloured_arguments():
     fr = synth.uniform_frame(32, 8, 2.0, 8, J=4, seed=91, tile_w=32, tile_h=1)
     g = fr.to(DEV)
@@ -147,17 +190,16 @@ def test_coloured_bg_image_and_256_pixel_tiles(fmt):
     out = torch.empty(fr.P, 4, device=DEV)
     coeff = (torch.empty(3, fr.P, 32, device=DEV) if fmt == wt.RGB_F32
              else torch.empty(fr.P, 32, device=DEV, dtype=torch.int32))
-    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg_img=torch.from_numpy(bg_img).to(DEV))
+    bgt = torch.from_numpy(bg_img).to(DEV)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg_img=bgt)
     assert wt.wt_get_error() == 0
     h = fr.numpy()
-    coeffs = None
     if fmt == wt.RGB_E5B9G9R9:
-        dec = oracle.e5_decode(coeff.cpu().numpy().view(np.uint32))
-        sign = np.where(np.arange(32) == 0, 1.0, -1.0)
-        coeffs = [sign * dec[c] for c in range(3)]
+        _check_e5(d, g, a, coeff, out, h, ac, 5, bg_img=bg_img, bg_t=bgt)
+        return
     ref = np.zeros((fr.P, 4))
     for c in range(3):
-        co = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, 5) if coeffs is None else coeffs[c]
+        co = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, 5)
         col = (h["r"], h["g"], h["b"])[c]
         bgc = np.repeat(bg_img[:, c:c + 1], 3, axis=1)
         o = oracle.resolve(h["pixel"], h["z"], ac[c], (col,) * 3, fr.P, 5, co, bg_img=bgc)[0]
@@ -204,18 +246,14 @@ def test_coloured_short_rows(J, fmt):
     wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg=fr.bg)
     assert wt.wt_get_error() == 0
     h = fr.numpy()
-    coeffs = None
     if fmt == wt.RGB_E5B9G9R9:
-        dec = oracle.e5_decode(coeff.cpu().numpy().view(np.uint32))
-        sign = np.where(np.arange(C) == 0, 1.0, -1.0)
-        coeffs = [sign * dec[c] for c in range(3)]
-    else:
-        for c in range(3):
-            ref_c = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, J)
-            fc = dataclasses.replace(fr, alpha=torch.from_numpy(ac[c]))
-            assert (np.abs(coeff[c].cpu().numpy().astype(np.float64) - ref_c) <= coeff_tol(fc)).all()
-    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, J, bg=fr.bg,
-                               coeffs=coeffs)
+        _check_e5(d, g, a, coeff, out, h, ac, J, bg=fr.bg)
+        return
+    for c in range(3):
+        ref_c = oracle.build_coeffs(h["pixel"], h["z"], ac[c], fr.P, J)
+        fc = dataclasses.replace(fr, alpha=torch.from_numpy(ac[c]))
+        assert (np.abs(coeff[c].cpu().numpy().astype(np.float64) - ref_c) <= coeff_tol(fc)).all()
+    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, J, bg=fr.bg)
     np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
 
 
@@ -236,11 +274,8 @@ def test_coloured_reading_flags(flags, fmt):
     wt.wt_build_resolve_rgb(d, frags_of(g), *a, out, coeff, fmt, bg=fr.bg)
     assert wt.wt_get_error() == 0
     h = fr.numpy()
-    coeffs = None
     if fmt == wt.RGB_E5B9G9R9:
-        dec = oracle.e5_decode(coeff.cpu().numpy().view(np.uint32))
-        sign = np.where(np.arange(16) == 0, 1.0, -1.0)
-        coeffs = [sign * dec[c] for c in range(3)]
-    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, 4, flags=flags, bg=fr.bg,
-                               coeffs=coeffs)
+        _check_e5(d, g, a, coeff, out, h, ac, 4, bg=fr.bg, flags=flags)
+        return
+    ref = oracle.composite_rgb(h["pixel"], h["z"], ac, (h["r"], h["g"], h["b"]), fr.P, 4, flags=flags, bg=fr.bg)
     np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)

@@ -102,7 +102,7 @@ def e5_words_of(coeffs, C):
     return oracle.e5_encode(*[np.asarray(c, np.float32) * sign for c in coeffs])
 
 
-def e5_oracle_composite(h, alphas, P, J, bg, words_gpu):
+def e5_oracle_composite(h, alphas, P, J, bg, words_gpu, flags=None, bg_img=None):
     """The E5B9G9R9 composite computed wholly on the oracle side -- FP64
     coefficients rounded to FP32, encoded and decoded by the oracle -- and the
     per-pixel bound within which the GPU's must lie.  The GPU's FP32
@@ -110,15 +110,27 @@ def e5_oracle_composite(h, alphas, P, J, bg, words_gpu):
     rare last places; at a pixel whose words differ, each differing index i
     (level n) moves a bin value by at most 2^(n/2) times the mantissa steps
     of the two words, and the composite is 1-Lipschitz in the absorbance
-    (the normalised colour moves by at most tanh of it).  Returns (reference,
-    bound per pixel, words equal per pixel)."""
+    (the normalised colour moves by at most tanh of it).  `flags` selects the
+    reading (default: the method's), `bg_img` [P, 3] a background image.
+    Returns (reference, bound per pixel, words equal per pixel)."""
     C = 1 << J
     sign = np.where(np.arange(C) == 0, 1.0, -1.0)
     co = [oracle.build_coeffs(h["pixel"], h["z"], alphas[c], P, J).astype(np.float32) for c in range(3)]
     w = e5_words_of(co, C)
     dec = oracle.e5_decode(w)
-    ref = oracle.composite_rgb(h["pixel"], h["z"], alphas, (h["r"], h["g"], h["b"]), P, J, bg=bg,
-                               coeffs=[sign * dec[c] for c in range(3)])
+    flags = oracle.DEFAULT_FLAGS if flags is None else flags
+    if bg_img is None:
+        ref = oracle.composite_rgb(h["pixel"], h["z"], alphas, (h["r"], h["g"], h["b"]), P, J, flags=flags,
+                                   bg=bg, coeffs=[sign * dec[c] for c in range(3)])
+    else:
+        ref = np.zeros((P, 4))
+        for c in range(3):
+            col = (h["r"], h["g"], h["b"])[c]
+            bgc = np.repeat(np.asarray(bg_img)[:, c:c + 1], 3, axis=1)
+            o = oracle.resolve(h["pixel"], h["z"], alphas[c], (col,) * 3, P, J, sign * dec[c], flags,
+                               bg_img=bgc)[0]
+            ref[:, c] = o[:, 0]
+            ref[:, 3] += o[:, 3] / 3.0
     lvl = np.array([0] + [int(np.log2(i)) for i in range(1, C)])
     step = lambda x: np.ldexp(1.0, (x >> 27).astype(np.int64) - 24)
     diff = w != words_gpu
