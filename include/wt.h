@@ -341,7 +341,7 @@ wt_status wt_build_resolve_rgb(const wt_desc *desc, const wt_frags *frags, const
  *   bgs           host array of nframes * 3 background colours.
  *   outs          host array of nframes device pointers, out[k] of [P_k * 4].
  * The first call on a device resolves the scratch's device address with that
- * device current, so make it before any stream capture.  Every call reuses
+ * device current.  Every call reuses
  * the same scratch (each call re-initialises all of it that it uses, the
  * counter included): calls that overlap on the GPU -- on different streams,
  * or from different host threads without ordering -- race on it.
