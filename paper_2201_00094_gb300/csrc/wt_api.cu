@@ -289,8 +289,8 @@ wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float 
     if (d->J > 5) return WT_ERR_UNSUPPORTED;  // the coloured kernels stop at 32 coefficients
     if (!f || f->n < 0 || !f->tile_offsets || !aligned(f->tile_offsets, 8)) return WT_ERR_ARG;
     const void *req[8] = {f->pixel, f->z, f->r, f->g, f->b, alpha_r, alpha_g, alpha_b};
-    for (const void *q : req)
-        if (f->n > 0 && !q) return WT_ERR_ARG;
+    for (const void *q : req)  // 16-byte aligned: the fragment passes read them as vectors
+        if ((f->n > 0 && !q) || !aligned(q, 16)) return WT_ERR_ARG;
     if ((coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16)) return WT_ERR_ARG;
     const int npx = d->tile_w * d->tile_h;
     if (rgb_smem_bytes(d->J, npx, coeff_format == WT_RGB_E5B9G9R9) > 227 * 1024) return WT_ERR_UNSUPPORTED;

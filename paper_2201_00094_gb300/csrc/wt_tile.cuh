@@ -620,17 +620,22 @@ __device__ __forceinline__ void for_each_group(int64_t s, int64_t e, const Param
 }
 
 // L2 prefetch (bulk, asynchronous) of the 16-byte-aligned interior of the
-// 4-byte-element range a[s, e), in pieces of at most 32 KB: the tile's
-// fragment arrays stream into L2 while the block works on them, instead of
-// arriving one register group at a time.  Addresses stay inside [s, e).
-__device__ __forceinline__ void l2_prefetch_range(const void *a, int64_t s, int64_t e) {
-    const int64_t b0 = (s * 4 + 15) & ~int64_t(15), b1 = (e * 4) & ~int64_t(15);
-    for (int64_t b = b0; b < b1; b += 32768) {
-        const unsigned n = (unsigned)(b1 - b < 32768 ? b1 - b : 32768);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char *>(a) + b),
-                     "r"(n)
-                     : "memory");
+// byte range [a + lo, a + hi), in pieces of at most 32 KB: a block's input
+// streams into L2 while the block works on it, instead of arriving one
+// register group at a time.  The bulk copy wants 16-byte aligned addresses
+// and sizes, so the bounds are rounded inwards on the addresses themselves
+// (any base alignment); addresses stay inside the range.
+__device__ __forceinline__ void l2_prefetch_bytes(const void *a, int64_t lo, int64_t hi) {
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a);
+    const uintptr_t p0 = (base + (uintptr_t)lo + 15) & ~uintptr_t(15), p1 = (base + (uintptr_t)hi) & ~uintptr_t(15);
+    for (uintptr_t q = p0; q < p1; q += 32768) {
+        const unsigned n = (unsigned)(p1 - q < 32768 ? p1 - q : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
     }
+}
+// The same for the 4-byte-element range a[s, e).
+__device__ __forceinline__ void l2_prefetch_range(const void *a, int64_t s, int64_t e) {
+    l2_prefetch_bytes(a, s * 4, e * 4);
 }
 template <int LOAD> __device__ __forceinline__ void prefetch_tile(const Params &p, const Tile &T) {
     if (threadIdx.x != 0) return;

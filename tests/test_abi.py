@@ -100,6 +100,24 @@ def test_bad_fragment_pointers_rejected_on_host(L):
     assert L.wt_get_error(None, None) == 1
 
 
+def test_coloured_fragment_pointers_rejected_on_host(L):
+    """The coloured call reads every fragment array and the three opacity
+    arrays as 16-byte vectors: a misaligned one is refused before any launch."""
+    d = wt.make_desc(64, 64, 4)
+    bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
+    v = ctypes.c_void_p(16)
+    for bad in range(8):
+        ptrs = [16] * 8
+        ptrs[bad] = 20
+        fr = wt.WtFrags(n=10, pixel=ptrs[0], z=ptrs[1], alpha=16, r=ptrs[2], g=ptrs[3], b=ptrs[4],
+                        tile_offsets=16)
+        a = [ctypes.c_void_p(x) for x in ptrs[5:]]
+        st = L.wt_build_resolve_rgb(ctypes.byref(d), ctypes.byref(fr), *a, v, 0, None, bg, v, None)
+        assert st == 1, bad
+    fr = wt.WtFrags(n=10, pixel=16, z=16, alpha=16, r=16, g=16, b=16, tile_offsets=16)
+    assert L.wt_build_resolve_rgb(ctypes.byref(d), ctypes.byref(fr), v, v, v, v, 0, None, bg, None, None) == 1
+
+
 def test_status_strings(L):
     for s in range(8):
         assert L.wt_status_string(s)
