@@ -387,7 +387,7 @@ wt_status wt_backward(const wt_desc *desc, const wt_frags *frags, const float *b
  */
 
 /* Bytes of device workspace wt_bin needs for n fragments with this
- * descriptor: a digit-count matrix (257 x ceil(n / 4096) counters) and, when
+ * descriptor: a digit-count matrix (257 x ceil(n / 8192) counters) and, when
  * the tile ids need two 8-bit sort passes or more (more than 256 tiles), an
  * intermediate stream of 24 bytes and one digit byte per fragment (twice that
  * for more than 65536 tiles); 0 if the descriptor is invalid or n < 0.  Only

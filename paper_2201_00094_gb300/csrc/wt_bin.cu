@@ -5,7 +5,7 @@
 // Binning is a stable least-significant-digit radix sort of the fragments by
 // tile id (row-major tiles of the descriptor), 8 bits per pass: two passes for
 // up to 65536 tiles.  A pass is three kernels:
-//   * a histogram of the pass's digit over each block's 4096 consecutive
+//   * a histogram of the pass's digit over each block's 8192 consecutive
 //     fragments (shared-memory counters), stored digit-major [257][blocks];
 //   * an exclusive scan of that matrix along each digit row, and of the row
 //     totals over the digits: fragment (digit d, block b) then starts at
@@ -71,11 +71,25 @@ __device__ __forceinline__ uint32_t tile_of_pixel(uint32_t px, const BinGeom &g)
     return fdiv(y, g.dth) * g.ntx + fdiv(x, g.dtw);
 }
 
-constexpr int kRT = 256;             // threads of a sorting block
+constexpr int kRT = 512;             // threads of a sorting block
 constexpr int kRW = kRT / 32;        // its warps
 constexpr int kRI = 16;              // fragments per thread
 constexpr int kRTile = kRT * kRI;    // fragments per block
 constexpr int kRD = 257;             // 256 digits + the bucket of dropped fragments
+
+// Shared memory of a scatter block (bytes, dynamic): the run starts of the
+// digits in the output, the per-warp digit counts, the digits' block-local
+// starts, the staged field, the output index of each block-local position and
+// (first of several passes) the next pass's digit.
+struct ScatterSmem {
+    static constexpr size_t gdst = 0;
+    static constexpr size_t wcnt = gdst + 256 * 8;
+    static constexpr size_t lstart = wcnt + (size_t)kRW * kRD * 4;
+    static constexpr size_t stage = (lstart + kRD * 4 + 15) & ~size_t(15);
+    static constexpr size_t sdst = stage + (size_t)kRTile * 4;
+    static constexpr size_t snext = sdst + (size_t)kRTile * 4;
+    static constexpr size_t bytes(bool next) { return snext + (next ? (size_t)kRTile : 16); }
+};
 
 struct BinIn {
     const uint32_t *pixel;
@@ -210,17 +224,21 @@ __global__ void __launch_bounds__(256) k_bin_bases(const unsigned long long *__r
 // keys of all the thread's fragments are loaded before the ranking, and the
 // next field's values are loaded while the current one is written out.
 template <bool FIRST, bool LAST, bool RGB>
-__global__ void __launch_bounds__(kRT, 4) k_bin_scatter(BinGeom g, int64_t n, const unsigned long long *kept,
+__global__ void __launch_bounds__(kRT, 2) k_bin_scatter(BinGeom g, int64_t n, const unsigned long long *kept,
                                                         int pass, int nb, BinIn in, const uint8_t *__restrict__ dig_in,
                                                         BinOut out, uint8_t *__restrict__ dig_out,
                                                         const unsigned *__restrict__ M,
                                                         const unsigned long long *__restrict__ base) {
-    __shared__ unsigned wcnt[kRW][kRD];       // per-warp digit counts, then exclusive offsets over warps
-    __shared__ unsigned lstart[kRD];          // block-local start of each digit's run
-    __shared__ unsigned long long gdst[256];  // where this block's run of each digit starts in the output
-    __shared__ uint32_t stage[kRTile];
-    __shared__ uint32_t sdst[kRTile];  // output index of each block-local position
-    __shared__ uint8_t snext[FIRST && !LAST ? kRTile : 1];  // the next pass's digit (first pass)
+    extern __shared__ __align__(16) unsigned char smem[];
+    using L = ScatterSmem;
+    // where this block's run of each digit starts in the output
+    unsigned long long *gdst = reinterpret_cast<unsigned long long *>(smem + L::gdst);
+    // per-warp digit counts, then exclusive offsets over warps: wcnt[w][d] at w * kRD + d
+    unsigned(*wcnt)[kRD] = reinterpret_cast<unsigned(*)[kRD]>(smem + L::wcnt);
+    unsigned *lstart = reinterpret_cast<unsigned *>(smem + L::lstart);  // block-local start of each digit's run
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem + L::stage);
+    uint32_t *sdst = reinterpret_cast<uint32_t *>(smem + L::sdst);  // output index of each block-local position
+    uint8_t *snext = smem + L::snext;  // the next pass's digit (first of several passes)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRW * kRD; i += kRT) (&wcnt[0][0])[i] = 0u;
     const int64_t ne = FIRST ? n : (int64_t)*kept;
@@ -550,10 +568,17 @@ template <bool FIRST, bool LAST>
 void launch_scatter(bool rgb, int nb, cudaStream_t s, const BinGeom &g, int64_t n, const unsigned long long *kept,
                     int pass, const BinIn &in, const uint8_t *dig_in, const BinOut &out, uint8_t *dig_out,
                     const unsigned *M, const unsigned long long *base) {
-    if (rgb)
-        k_bin_scatter<FIRST, LAST, true><<<nb, kRT, 0, s>>>(g, n, kept, pass, nb, in, dig_in, out, dig_out, M, base);
-    else
-        k_bin_scatter<FIRST, LAST, false><<<nb, kRT, 0, s>>>(g, n, kept, pass, nb, in, dig_in, out, dig_out, M, base);
+    const size_t bytes = ScatterSmem::bytes(FIRST && !LAST);
+    if (rgb) {
+        cudaFuncSetAttribute(k_bin_scatter<FIRST, LAST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        k_bin_scatter<FIRST, LAST, true><<<nb, kRT, bytes, s>>>(g, n, kept, pass, nb, in, dig_in, out, dig_out, M,
+                                                                base);
+    } else {
+        cudaFuncSetAttribute(k_bin_scatter<FIRST, LAST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+        k_bin_scatter<FIRST, LAST, false><<<nb, kRT, bytes, s>>>(g, n, kept, pass, nb, in, dig_in, out, dig_out, M,
+                                                                 base);
+    }
 }
 
 }  // namespace
