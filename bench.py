@@ -564,9 +564,9 @@ def run_preprocess(wt, fr, desc, stream):
     per-pixel depth bounds of §2.1 step 1 with the normalisation of depth into
     them (wt_depth_bounds, wt_normalize_depth).  Bytes per fragment: binning
     reads the pixel id twice and the six arrays once and writes them once
-    (52 B; its 32-byte staging records add 64 B of workspace traffic); bounds
-    read pixel, z, alpha (12 B); normalisation reads pixel and z and writes z
-    (12 B)."""
+    (52 B; with two sort passes its intermediate stream adds 50 B of workspace
+    traffic); bounds read pixel, z, alpha (12 B); normalisation reads pixel
+    and z and writes z (12 B)."""
     dev = fr.pixel.device
     n, P = fr.n, fr.P
     g = torch.Generator(device=dev)

@@ -62,6 +62,29 @@ def test_bin_one_pixel_tiles(W, H, lam):
         np.testing.assert_array_equal(got[k][:off[-1]], h[k][order])
 
 
+@pytest.mark.parametrize("n", [1, 31, 8191, 8192, 8193, 3 * 8192 + 5])
+def test_bin_ragged_block_edges(n):
+    """Stream lengths at and around the sorting block (8192 fragments) and one
+    vector (16 keys per thread), over 300 x 7 pixels in 16 x 1 tiles (133
+    tiles, one pass) and 1 x 1 tiles (2100 tiles, two passes): the binned
+    stream equals the oracle's stable grouping bit for bit."""
+    rng = np.random.default_rng(n)
+    W, H = 300, 7
+    h = {"pixel": rng.integers(0, W * H, n).astype(np.uint32)}
+    for k in ("z", "alpha", "r", "g", "b"):
+        h[k] = rng.random(n).astype(np.float32)
+    g = _to_dev(h)
+    for tw, th in ((16, 1), (1, 1)):
+        d = wt.make_desc(W, H, 3, tile_w=tw, tile_h=th)
+        out = wt.wt_bin(d, g["pixel"], g["z"], g["alpha"], g["r"], g["g"], g["b"])
+        assert wt.wt_get_error() == 0
+        order, off = oracle.bin_by_tile(h["pixel"], W, H, tw, th)
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        np.testing.assert_array_equal(got["tile_offsets"], off)
+        for k in ("pixel", "z", "alpha", "r", "g", "b"):
+            np.testing.assert_array_equal(got[k][:off[-1]], h[k][order])
+
+
 def test_binned_stream_composites_like_the_oracle():
     fr = synth.uniform_frame(611, 23, 6.0, 40, J=5, seed=611, tile_w=256, tile_h=1)
     h = _shuffled(fr, 2)
@@ -167,6 +190,20 @@ def test_normalised_depth_and_composite_match_the_oracle():
     wt.wt_normalize_depth(d, wt.make_frags(g.pixel, zi, g.alpha, g.tile_offsets), zlo, zhi, zi)
     torch.cuda.synchronize()
     assert torch.equal(zi, zn)
+    # 16-byte aligned arrays take four fragments per thread, others one: the same
+    # depths bit for bit, whatever the count modulo 4
+    for cut in (0, 1, 2, 3):
+        m = fr.n - cut
+        pm = torch.empty(m + 1, dtype=g.pixel.dtype, device=DEV)[1:]
+        zm = torch.empty(m + 1, device=DEV)[1:]
+        pm.copy_(g.pixel[:m])
+        zm.copy_(g.z[:m])
+        za = torch.empty(m, device=DEV)
+        zb = torch.empty(m + 1, device=DEV)[1:]
+        wt.wt_normalize_depth(d, wt.make_frags(g.pixel[:m], g.z[:m], g.alpha, g.tile_offsets), zlo, zhi, za)
+        wt.wt_normalize_depth(d, wt.make_frags(pm, zm, g.alpha, g.tile_offsets), zlo, zhi, zb)
+        torch.cuda.synchronize()
+        assert torch.equal(za, zn[:m]) and torch.equal(zb, zn[:m])
 
 
 def test_bin_full_size_random_order_frame():
