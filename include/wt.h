@@ -371,7 +371,9 @@ wt_status wt_absorbance(const wt_desc *desc, const void *coeff, int64_t q, const
  * same desc (J, storage rounding, flags) and background as the forward call.
  *   grad_out   [P * 4] float, dL/d(out RGBA).
  *   grad_alpha [n] float, written; 0 where alpha is clamped (<= 0 or
- *              >= 1 - 2^-20) and for rejected fragments.
+ *              >= 1 - 2^-20) and for rejected fragments.  It holds
+ *              intermediate values during the call, so it must not overlap
+ *              any input or grad_rgb (WT_ERR_ARG).
  *   grad_rgb   [3 * n] float, planar: dL/dr at [0, n), dL/dg at [n, 2n),
  *              dL/db at [2n, 3n).
  * The pixel-level sums use FP32; WT_ACCUMULATE is not supported.

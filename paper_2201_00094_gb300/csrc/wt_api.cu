@@ -322,6 +322,20 @@ wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, 
     if (!grad_out || !aligned(grad_out, 16)) return WT_ERR_ARG;
     if (f->n > 0 && (!grad_alpha || !grad_rgb)) return WT_ERR_ARG;
     if (!aligned(grad_alpha, 4) || !aligned(grad_rgb, 4)) return WT_ERR_ARG;
+    // grad_alpha holds intermediate values while the fragments are still
+    // being read, so it must not overlap any input
+    {
+        const size_t nb = (size_t)f->n * 4, pb = (size_t)d->width * d->height;
+        const char *ga = reinterpret_cast<const char *>(grad_alpha);
+        auto overlaps = [&](const void *q, size_t qb) {
+            const char *c = static_cast<const char *>(q);
+            return c && nb && qb && ga < c + qb && c < ga + nb;
+        };
+        if (overlaps(f->pixel, nb) || overlaps(f->z, nb) || overlaps(f->alpha, nb) || overlaps(f->r, nb) ||
+            overlaps(f->g, nb) || overlaps(f->b, nb) || overlaps(f->tile_offsets, (size_t)(ntiles_of(d) + 1) * 8) ||
+            overlaps(grad_out, pb * 16) || overlaps(bg_img, pb * 12) || overlaps(grad_rgb, 3 * nb))
+            return WT_ERR_ARG;
+    }
     Params p = make_params(d, f);
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     p.gout = grad_out;

@@ -396,10 +396,12 @@ template <int J> struct BackLayout {
 
 // Re-derives everything the adjoint needs about one fragment from its inputs
 // and the pixel's bin values (log2 units, shifted by m_p): local pixel (or -1),
-// clamped alpha, step a, position q, and weight w = alpha 2^-A'.
+// clamped alpha, position q, and weight w = alpha 2^-A'.  The own step
+// removed under self-exclusion is -log2(1 - alpha) from the hardware log2, as
+// in the forward sums the adjoint recomputes (phase_resolve without S).
 template <int J> struct FragState {
     int lp;
-    float ac, a, w;
+    float ac, w;
     Pos q;
 };
 template <int J>
@@ -411,10 +413,9 @@ __device__ __forceinline__ FragState<J> frag_state(const Params &p, const Tile &
     st.lp = local_pixel(px, p, T);
     if (st.lp < 0) return st;
     st.ac = clamp_alpha(al);
-    st.a = step_of(st.ac);
     st.q = locate<J>(clamp_depth(z) * (float)(1 << J), p.flags);
     const float full = recon_at<J>(vals + st.lp * Shape<J>::LDV, st.q, p.flags);
-    const float Ah = (p.flags & kSelfExclude) ? fmaxf(full - st.a * kLog2e * st.q.g, 0.f) : full;
+    const float Ah = (p.flags & kSelfExclude) ? fmaxf(fmaf(lg2(1.f - st.ac), st.q.g, full), 0.f) : full;
     st.w = st.ac * ex2(-Ah);
     return st;
 }
@@ -509,13 +510,16 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
     fill_zero(gam, (int)PL);
     __syncthreads();
     const uint32_t flags = p.flags;
-    // pass 3: colour gradients and the scatter of gamma into the bins
+    // pass 3: colour gradients and the scatter of gamma into the bins; each
+    // fragment's gamma waits in its grad_alpha entry for pass 4 (read back by
+    // the thread that wrote it: both passes split the range the same way)
     for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
         constexpr int N = std::remove_reference_t<decltype(G)>::size;
-        float gr[3][N];
+        float gr[3][N], gm[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             gr[0][k] = gr[1][k] = gr[2][k] = 0.f;
+            gm[k] = 0.f;
             if (!G.v) continue;
             const FragState<J> st = frag_state<J>(p, T, vals, G.px[k], G.z[k], G.al[k]);
             if (st.lp < 0) continue;
@@ -528,6 +532,7 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
                 gr[ch][k] = u * st.w;
             }
             const float gamma = -beta * st.w;
+            gm[k] = gamma;
             float *row = gam + st.lp * LD;
             if (flags & kLinear) {
                 atomicAdd(&row[st.q.lo], gamma * (1.f - st.q.t));
@@ -539,6 +544,7 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
         if (G.v) {
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) store_group<N>(p.grgb + ch * p.n, G.i0, gr[ch]);
+            store_group<N>(p.galpha, G.i0, gm);
         }
     });
     __syncthreads();
@@ -552,31 +558,28 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
         }
     }
     __syncthreads();
-    // pass 4: opacity gradients
-    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
+    // pass 4: opacity gradients from each fragment's gamma (pass 3), its
+    // position in its bin and the suffix sums:
+    // dL/dalpha = beta 2^-A' + (dL/da) / (1 - alpha), beta 2^-A' = -gamma / alpha
+    for_each_group<kWithZ>(T.s, T.e, p, [&](auto &G) {
         constexpr int N = std::remove_reference_t<decltype(G)>::size;
-        float ga[N];
+        float gm[N], ga[N];
+        load_group<N>(p.galpha, G.i0, G.v, gm);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             ga[k] = 0.f;
             if (!G.v) continue;
             const float al = G.al[k];
-            const FragState<J> st = frag_state<J>(p, T, vals, G.px[k], G.z[k], al);
-            if (st.lp < 0) continue;
-            const float c[3] = {G.r[k], G.g[k], G.b[k]};
-            float beta = 0.f;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
-                beta = fmaf(sU[ch * wpl + st.lp], c[ch] - sY[ch * wpl + st.lp], beta);
-            const float gamma = -beta * st.w;
-            const float *Q = gam + st.lp * LD;
-            float da = fmaf(st.q.f, Q[st.q.m + 1], (1.f - st.q.f) * Q[st.q.m]);
-            if (flags & kSelfExclude) da -= gamma * st.q.g;
-            da += sK[st.lp];
-            if (al > 0.f && al < kAlphaMax) {
-                const float direct = st.ac > 0.f ? beta * (st.w / st.ac) : 0.f;
-                ga[k] = direct + da / (1.f - al);
-            }
+            if (!(G.z[k] == G.z[k]) || !(al == al)) continue;
+            const int lp = local_pixel(G.px[k], p, T);
+            if (lp < 0) continue;
+            const Pos q = locate<J>(clamp_depth(G.z[k]) * (float)(1 << J), flags);
+            const float gamma = gm[k];
+            const float *Q = gam + lp * LD;
+            float da = fmaf(q.f, Q[q.m + 1], (1.f - q.f) * Q[q.m]);
+            if (flags & kSelfExclude) da -= gamma * q.g;
+            da += sK[lp];
+            if (al > 0.f && al < kAlphaMax) ga[k] = da / (1.f - al) - gamma / al;
         }
         if (G.v) store_group<N>(p.galpha, G.i0, ga);
     });

@@ -662,6 +662,24 @@ template <int N> __device__ __forceinline__ void store_group(float *dst, int64_t
     for (int k = 0; k < N; ++k) dst[i0 + k] = v[k];
 }
 
+// Loads N per-fragment values src[i0 ..] (zeros when v is false), as one
+// 16-byte vector when N = 4 and the address allows it.
+template <int N>
+__device__ __forceinline__ void load_group(const float *src, int64_t i0, bool v, float (&x)[N]) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = 0.f;
+    if (!v) return;
+    if constexpr (N == 4) {
+        if ((reinterpret_cast<uintptr_t>(src + i0) & 15) == 0) {
+            const float4 q = *reinterpret_cast<const float4 *>(src + i0);
+            x[0] = q.x, x[1] = q.y, x[2] = q.z, x[3] = q.w;
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = src[i0 + k];
+}
+
 // ---------------------------------------------------------------- shared-memory updates
 
 __device__ __forceinline__ void fill_zero(void *smem, int bytes) {

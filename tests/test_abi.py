@@ -118,6 +118,20 @@ def test_coloured_fragment_pointers_rejected_on_host(L):
     assert L.wt_build_resolve_rgb(ctypes.byref(d), ctypes.byref(fr), v, v, v, v, 0, None, bg, None, None) == 1
 
 
+def test_backward_refuses_grad_alpha_overlapping_an_input(L):
+    """grad_alpha holds intermediate values while the fragments are still being
+    read: an overlap with any input array or with grad_rgb is refused before any
+    launch."""
+    d = wt.make_desc(64, 64, 4)
+    bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
+    fr = wt.WtFrags(n=10, pixel=0x10000, z=0x20000, alpha=0x30000, r=0x40000, g=0x50000, b=0x60000,
+                    tile_offsets=0x70000)
+    gout, grgb = ctypes.c_void_p(0x80000), ctypes.c_void_p(0x90000)
+    for ga in (0x30000, 0x30000 + 36, 0x10000 - 8, 0x60000, 0x70000 + 8, 0x80000 + 64, 0x90000 + 100):
+        st = L.wt_backward(ctypes.byref(d), ctypes.byref(fr), None, bg, gout, ctypes.c_void_p(ga), grgb, None)
+        assert st == 1, hex(ga)
+
+
 def test_status_strings(L):
     for s in range(8):
         assert L.wt_status_string(s)
