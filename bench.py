@@ -294,6 +294,10 @@ def run_wt(args):
         ranges = shard.split_tile_rows(fr.tile_offsets.cpu().numpy(), desc, world)
         band = ranges[rank]
 
+    # the two-pass method hands the build's near bounds and totals to the resolve
+    zmin2 = torch.empty(P, device=dev) if args.path == "two_pass" else None
+    total2 = torch.empty(P, device=dev) if args.path == "two_pass" else None
+
     def step_fused(d=desc, c=coeff, o=out):
         if band is not None:
             shard.build_resolve_band(d, frags, band, o, c, bg=fr.bg, stream=stream)
@@ -302,8 +306,8 @@ def run_wt(args):
         elif args.path == "fused":
             wt.wt_build_resolve(d, frags, o, c, None, bg=fr.bg, stream=stream)
         else:
-            wt.wt_build(d, frags, c, None, stream=stream)
-            wt.wt_resolve_composite(d, frags, c, None, o, bg=fr.bg, stream=stream)
+            wt.wt_build(d, frags, c, zmin2, stream=stream, total=total2)
+            wt.wt_resolve_composite(d, frags, c, zmin2, o, bg=fr.bg, stream=stream, total=total2)
 
     K, W = args.steps, args.warmup
     for _ in range(W):
@@ -359,15 +363,18 @@ def run_wt(args):
     if not args.no_variants and not args.no_mono_variants:
         REPEATS = 3
         runs = {}
+        zmin_v, total_v = torch.empty(P, device=dev), torch.empty(P, device=dev)
         for name, d2 in (("f32", wt.F32), ("bf16", wt.BF16), ("f16", wt.F16), ("se16", wt.SE16)):
             dsc = wt.make_desc(fr.width, fr.height, J, d2, tile_w=fr.tile_w, tile_h=fr.tile_h)
             c2, o2 = buffers(d2)
             c3 = torch.empty_like(c2)
             cb2 = coeff_bytes(P, C, d2)
 
+            # the three calls of §2.1 steps 2-4, the build's near bounds and
+            # per-pixel totals handed to the resolve
             def two_pass(dsc=dsc, c2=c2, o2=o2):
-                wt.wt_build(dsc, frags, c2, None, stream=stream)
-                wt.wt_resolve_composite(dsc, frags, c2, None, o2, bg=fr.bg, stream=stream)
+                wt.wt_build(dsc, frags, c2, zmin_v, stream=stream, total=total_v)
+                wt.wt_resolve_composite(dsc, frags, c2, zmin_v, o2, bg=fr.bg, stream=stream, total=total_v)
 
             def fused(dsc=dsc, c2=c2, o2=o2):
                 wt.wt_build_resolve(dsc, frags, o2, c2, None, bg=fr.bg, stream=stream)
@@ -379,7 +386,7 @@ def run_wt(args):
 
             runs[name] = [(label, fn, byts) for label, fn, byts in (
                 ("fused", fused, n * 24 + cb2 + 16 * P),
-                ("two_pass", two_pass, n * 36 + 2 * cb2 + 16 * P),
+                ("two_pass", two_pass, n * 36 + 2 * cb2 + 16 * P + 16 * P),
                 ("single_pass", single_pass, n * 24 + 2 * cb2 + 16 * P))]
             fused()
         times = {(nm, lb): [] for nm in runs for lb, _, _ in runs[nm]}

@@ -157,10 +157,16 @@ int64_t wt_num_tiles(const wt_desc *desc);
  *         depth bounds of §2.1 step 1; under WT_ACCUMULATE the minimum with
  *         the stored value.  wt_resolve uses it to keep the normalised
  *         resolve free of FP32 underflow in very deep pixels.
+ *   total [P] float, nullable.  The pixel's total step S = sum a_i (0 if it
+ *         has no fragments), from the same fixed-point bins as the
+ *         coefficients (the sum of the root's two bins, exact up to one FP32
+ *         rounding); under WT_ACCUMULATE added to the stored value.  Given to
+ *         wt_resolve / wt_resolve_composite, it spares them summing the steps
+ *         again fragment by fragment.
  * frags->r, g, b are not read.
  */
 wt_status wt_build(const wt_desc *desc, const wt_frags *frags, void *coeff, float *zmin,
-                   wt_stream stream);
+                   float *total, wt_stream stream);
 
 /*
  * wt_resolve -- §2.1 step 3 with §2.2 and §2.3.2 ("Interpolation").
@@ -174,11 +180,16 @@ wt_status wt_build(const wt_desc *desc, const wt_frags *frags, void *coeff, floa
  *         positive factor exp(m_p) (m_p fixed by coeff and zmin), so only the
  *         ratios R/W, G/W, B/W are meaningful; without zmin m_p = 0.  In the
  *         literal mode m_p = 0 always.
+ *   total [P] from wt_build, nullable.  If given, S is taken from it instead
+ *         of being summed over the fragments (the own step removed under
+ *         WT_SELF_EXCLUDE is then -log2(1 - alpha) from the hardware log2, as
+ *         in wt_build_resolve).  Not accepted under WT_ACCUMULATE
+ *         (WT_ERR_UNSUPPORTED): total covers every batch of the frame.
  *   accum [P * 5] float {R, G, B, W, S} per pixel, written (or added to under
  *         WT_ACCUMULATE: batches of one frame share m_p).
  */
 wt_status wt_resolve(const wt_desc *desc, const wt_frags *frags, const void *coeff,
-                     const float *zmin, float *accum, wt_stream stream);
+                     const float *zmin, const float *total, float *accum, wt_stream stream);
 
 /*
  * wt_composite -- §2.1 step 4 (composite over the opaque background).
@@ -221,10 +232,12 @@ wt_status wt_composite_ca(const wt_desc *desc, const float *accum, const float *
                           const float *offset, float dispersion, int32_t taps, float *out,
                           wt_stream stream);
 
-/* wt_resolve followed by wt_composite in one kernel (no accum buffer). */
+/* wt_resolve followed by wt_composite in one kernel (no accum buffer); zmin
+ * and total as for wt_resolve.  With both from wt_build (same desc), the
+ * result equals wt_build_resolve's bit for bit. */
 wt_status wt_resolve_composite(const wt_desc *desc, const wt_frags *frags, const void *coeff,
-                               const float *zmin, const float *bg_img, const float bg[3],
-                               float *out, wt_stream stream);
+                               const float *zmin, const float *total, const float *bg_img,
+                               const float bg[3], float *out, wt_stream stream);
 
 /*
  * wt_build_resolve -- steps 2, 3 and 4 of §2.1 fused per screen tile: the

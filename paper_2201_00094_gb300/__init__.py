@@ -115,11 +115,11 @@ def lib() -> ctypes.CDLL:
         "wt_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "wt_coeff_bytes": ([D], ctypes.c_size_t),
         "wt_num_tiles": ([D], i64),
-        "wt_build": ([D, Fr, vp, vp, vp], ctypes.c_int),
-        "wt_resolve": ([D, Fr, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build": ([D, Fr, vp, vp, vp, vp], ctypes.c_int),
+        "wt_resolve": ([D, Fr, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_composite": ([D, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_composite_ca": ([D, vp, vp, vp, ctypes.c_float, ctypes.c_int32, vp, vp], ctypes.c_int),
-        "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_tiles": ([D, Fr, i64, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_single_pass": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -295,20 +295,24 @@ def wt_num_tiles(desc: WtDesc) -> int:
 
 
 def wt_build(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
-             zmin: Optional[torch.Tensor] = None, stream=None) -> None:
+             zmin: Optional[torch.Tensor] = None, stream=None,
+             total: Optional[torch.Tensor] = None) -> None:
+    """total [P] float32, optional: each pixel's total step, for wt_resolve."""
     _check_frags(desc, frags)
     _check_pixel_buffers(desc, coeff=coeff, zmin=zmin)
+    _need(total, "total", _pixels(desc))
     _call("wt_build", ctypes.byref(desc), ctypes.byref(frags), _dev(coeff, "coeff", _COEFF_DT),
-          _dev(zmin, "zmin", (torch.float32,)), _stream(stream))
+          _dev(zmin, "zmin", (torch.float32,)), _dev(total, "total", (torch.float32,)), _stream(stream))
 
 
 def wt_resolve(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor, zmin: Optional[torch.Tensor],
-               accum: torch.Tensor, stream=None) -> None:
+               accum: torch.Tensor, stream=None, total: Optional[torch.Tensor] = None) -> None:
     _check_frags(desc, frags)
     _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, accum=accum)
+    _need(total, "total", _pixels(desc))
     _call("wt_resolve", ctypes.byref(desc), ctypes.byref(frags), _dev(coeff, "coeff", _COEFF_DT),
-          _dev(zmin, "zmin", (torch.float32,)), _dev(accum, "accum", (torch.float32,)),
-          _stream(stream))
+          _dev(zmin, "zmin", (torch.float32,)), _dev(total, "total", (torch.float32,)),
+          _dev(accum, "accum", (torch.float32,)), _stream(stream))
 
 
 def wt_composite(desc: WtDesc, accum: torch.Tensor, out: torch.Tensor,
@@ -323,13 +327,15 @@ def wt_composite(desc: WtDesc, accum: torch.Tensor, out: torch.Tensor,
 def wt_resolve_composite(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
                          zmin: Optional[torch.Tensor], out: torch.Tensor,
                          bg: Sequence[float] = (0.5, 0.5, 0.5),
-                         bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+                         bg_img: Optional[torch.Tensor] = None, stream=None,
+                         total: Optional[torch.Tensor] = None) -> None:
     _check_frags(desc, frags)
     _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img)
+    _need(total, "total", _pixels(desc))
     _call("wt_resolve_composite", ctypes.byref(desc), ctypes.byref(frags),
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
-          _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
-          _stream(stream))
+          _dev(total, "total", (torch.float32,)), _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg),
+          _dev(out, "out", (torch.float32,)), _stream(stream))
 
 
 def wt_build_resolve(desc: WtDesc, frags: WtFrags, out: torch.Tensor,

@@ -162,31 +162,37 @@ size_t wt_coeff_bytes(const wt_desc *d) {
 
 int64_t wt_num_tiles(const wt_desc *d) { return check_desc(d) == WT_OK ? ntiles_of(d) : 0; }
 
-wt_status wt_build(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin, wt_stream stream) {
+wt_status wt_build(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin, float *total,
+                   wt_stream stream) {
     WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if ((st = check_frags(f, false)) != WT_OK) return st;
-    if (!coeff || !aligned(coeff, 16) || (zmin && !aligned(zmin, 4))) return WT_ERR_ARG;
+    if (!coeff || !aligned(coeff, 16) || (zmin && !aligned(zmin, 4)) || (total && !aligned(total, 4)))
+        return WT_ERR_ARG;
     Params p = make_params(d, f);
     p.coeff = coeff;
     p.zmin = zmin;
+    p.total = total;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
     const TileLaunch *t = table(kBuild0, kBuild1, kBuild2, kBuild3, d->coeff_dtype);
     return finish(t[d->J - 1](p, (int)ntiles_of(d), reinterpret_cast<cudaStream_t>(stream)));
 }
 
 wt_status wt_resolve(const wt_desc *d, const wt_frags *f, const void *coeff, const float *zmin,
-                     float *accum, wt_stream stream) {
+                     const float *total, float *accum, wt_stream stream) {
     WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if ((st = check_frags(f, true)) != WT_OK) return st;
-    if (!coeff || !aligned(coeff, 16) || !accum || !aligned(accum, 4) || (zmin && !aligned(zmin, 4)))
+    if (!coeff || !aligned(coeff, 16) || !accum || !aligned(accum, 4) || (zmin && !aligned(zmin, 4)) ||
+        (total && !aligned(total, 4)))
         return WT_ERR_ARG;
+    if (total && (d->flags & WT_ACCUMULATE)) return WT_ERR_UNSUPPORTED;  // total covers every batch
     Params p = make_params(d, f);
     p.coeff = const_cast<void *>(coeff);
     p.zmin = const_cast<float *>(zmin);
+    p.total = const_cast<float *>(total);
     p.accum = accum;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
     const TileLaunch *t = table(kResolve0, kResolve1, kResolve2, kResolve3, d->coeff_dtype);
@@ -210,17 +216,20 @@ wt_status wt_composite(const wt_desc *d, const float *accum, const float *bg_img
 }
 
 wt_status wt_resolve_composite(const wt_desc *d, const wt_frags *f, const void *coeff,
-                               const float *zmin, const float *bg_img, const float bg[3], float *out,
-                               wt_stream stream) {
+                               const float *zmin, const float *total, const float *bg_img, const float bg[3],
+                               float *out, wt_stream stream) {
     WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if ((st = check_frags(f, true)) != WT_OK) return st;
-    if (!coeff || !aligned(coeff, 16) || !out || !aligned(out, 16) || (zmin && !aligned(zmin, 4)))
+    if (!coeff || !aligned(coeff, 16) || !out || !aligned(out, 16) || (zmin && !aligned(zmin, 4)) ||
+        (total && !aligned(total, 4)))
         return WT_ERR_ARG;
+    if (total && (d->flags & WT_ACCUMULATE)) return WT_ERR_UNSUPPORTED;
     Params p = make_params(d, f);
     p.coeff = const_cast<void *>(coeff);
     p.zmin = const_cast<float *>(zmin);
+    p.total = const_cast<float *>(total);
     p.out = out;
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     if (!(p.err = err_word())) return WT_ERR_CUDA;

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kThreads, MB) k_build(Params p) {
             if (acc) v = fminf(v, p.zmin[gp]);
             p.zmin[gp] = v;
         }
+        if (p.total) p.total[gp] = acc ? p.total[gp] + S : S;
     }
     if (stage) {
         uint4 *st = reinterpret_cast<uint4 *>(smem);
@@ -103,12 +104,15 @@ __global__ void __launch_bounds__(kThreads, MB) k_resolve(Params p) {
     fill_zero(accw, (int)(Layout<J>::accw(npx) + Layout<J>::words(npx)));
     __syncthreads();
     unsigned bad = 0;
-    phase_resolve<J, true, DEF>(p, T, vals, accw, sS, bad);
+    // with the build's totals the steps need not be summed again (and the own
+    // step of the self-exclusion comes from the hardware log2, as in the
+    // fused kernel)
+    phase_resolve<J, true, DEF>(p, T, vals, accw, p.total ? nullptr : sS, bad);
     flush_bad(bad, p.err);
     __syncthreads();
     if (gp < 0) return;
     const float4 a = sum_warps(accw, npx, lp);
-    const float S = sS[lp];
+    const float S = p.total ? p.total[gp] : sS[lp];
     if (COMPOSITE) {
         composite_pixel(p, gp, a.x, a.y, a.z, a.w, S);
     } else {

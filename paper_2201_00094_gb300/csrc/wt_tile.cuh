@@ -77,6 +77,7 @@ struct Params {
     const int64_t *__restrict__ off;
     void *coeff;
     float *zmin;
+    float *total;  // per-pixel total step S: written by the build, read by the resolve (nullable)
     float *accum;
     float *out;
     const float *__restrict__ bg_img;

@@ -69,18 +69,18 @@ def test_bad_descriptor_rejected_on_host(L, bad):
     d = wt.make_desc(**kw)
     assert L.wt_coeff_bytes(ctypes.byref(d)) == 0
     fr = wt.WtFrags()
-    st = L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None)
+    st = L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None, None)
     assert st == 1
 
 
 def test_unsupported_J_and_flags(L):
     d = wt.make_desc(64, 64, 7)
     fr = wt.WtFrags()
-    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 2
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None, None) == 2
     # J = 6 is accepted (64 coefficients per pixel); these frags are then refused as arguments
     d6 = wt.make_desc(64, 64, 6)
     assert L.wt_coeff_bytes(ctypes.byref(d6)) == 64 * 64 * 64 * 4
-    assert L.wt_build(ctypes.byref(d6), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 1
+    assert L.wt_build(ctypes.byref(d6), ctypes.byref(fr), ctypes.c_void_p(16), None, None, None) == 1
     d = wt.make_desc(64, 64, 4, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
     bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
     st = L.wt_build_resolve(ctypes.byref(d), ctypes.byref(fr), None, None, None, bg,
@@ -91,13 +91,28 @@ def test_unsupported_J_and_flags(L):
 def test_bad_fragment_pointers_rejected_on_host(L):
     d = wt.make_desc(64, 64, 4)
     fr = wt.WtFrags(n=10, pixel=None, z=16, alpha=16, tile_offsets=16)
-    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 1
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None, None) == 1
     fr = wt.WtFrags(n=10, pixel=20, z=16, alpha=16, tile_offsets=16)  # misaligned
-    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None) == 1
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None, None) == 1
     fr = wt.WtFrags(n=10, pixel=16, z=16, alpha=16, tile_offsets=16)  # resolve needs rgb
-    assert L.wt_resolve(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None,
+    assert L.wt_resolve(ctypes.byref(d), ctypes.byref(fr), ctypes.c_void_p(16), None, None,
                         ctypes.c_void_p(16), None) == 1
     assert L.wt_get_error(None, None) == 1
+
+
+def test_resolve_totals_rejected_on_host(L):
+    """The build's per-pixel totals: a misaligned array is refused, and so is
+    using them in an accumulating resolve (they cover every batch of a frame)."""
+    fr = wt.WtFrags(n=10, pixel=16, z=16, alpha=16, r=16, g=16, b=16, tile_offsets=16)
+    v, bad = ctypes.c_void_p(16), ctypes.c_void_p(18)
+    bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
+    d = wt.make_desc(64, 64, 4)
+    assert L.wt_build(ctypes.byref(d), ctypes.byref(fr), v, None, bad, None) == 1
+    assert L.wt_resolve(ctypes.byref(d), ctypes.byref(fr), v, None, bad, v, None) == 1
+    assert L.wt_resolve_composite(ctypes.byref(d), ctypes.byref(fr), v, None, bad, None, bg, v, None) == 1
+    da = wt.make_desc(64, 64, 4, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
+    assert L.wt_resolve(ctypes.byref(da), ctypes.byref(fr), v, None, v, v, None) == 2
+    assert L.wt_resolve_composite(ctypes.byref(da), ctypes.byref(fr), v, None, v, None, bg, v, None) == 2
 
 
 def test_coloured_fragment_pointers_rejected_on_host(L):

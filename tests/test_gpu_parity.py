@@ -52,6 +52,46 @@ def test_ragged_tiles_every_J(J, tile):
     np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0)
     gf = gpu_run(fr, fused=True)
     np.testing.assert_allclose(gf["out"], r["out"], atol=1e-4, rtol=0)
+    gt = gpu_run(fr, totals=True)
+    np.testing.assert_allclose(gt["out"], r["out"], atol=1e-4, rtol=0)
+
+
+def test_build_totals_are_the_pixels_step_sums():
+    """wt_build's optional per-pixel totals: S = sum of the clamped steps,
+    against the FP64 sums; 0 for pixels without fragments; under WT_ACCUMULATE
+    two batches add up to the whole frame's."""
+    fr = synth.uniform_frame(61, 29, 9.0, 120, J=4, seed=77)
+    g = gpu_run(fr, totals=True)
+    S = pixel_step_sums(fr)
+    k = pixel_counts(fr)
+    assert (np.abs(g["total"] - S) <= 8 * 2.0 ** -24 * (k + 1) * S).all()
+    assert (g["total"][k == 0] == 0).all()
+    dev = torch.device("cuda")
+    gd = fr.to(dev)
+    d1, dA = desc_of(fr), desc_of(fr, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
+    coeff = torch.empty(fr.P, 16, device=dev)
+    total = torch.empty(fr.P, device=dev)
+    f = frags_of(gd)
+    wt.wt_build(d1, f, coeff, None, total=total)
+    wt.wt_build(dA, f, coeff, None, total=total)  # the same batch again: twice the totals
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(total.cpu().numpy(), 2 * g["total"], rtol=2e-7, atol=0)
+
+
+@pytest.mark.parametrize("dtype", [wt.F32, wt.BF16, wt.F16, wt.SE16])
+@pytest.mark.parametrize("J,tile,flags", [(4, (16, 16), wt.DEFAULT_FLAGS), (5, (192, 1), wt.DEFAULT_FLAGS),
+                                          (3, (7, 3), 3), (6, (16, 16), wt.DEFAULT_FLAGS), (5, (256, 1), 4)])
+def test_two_pass_with_totals_equals_fused_bit_for_bit(dtype, J, tile, flags):
+    """wt_build + wt_resolve_composite with the build's zmin and totals runs
+    the fused kernel's arithmetic in two launches: the same composite, bit for
+    bit."""
+    fr = synth.uniform_frame(203, 41, 14.0, 200, J=J, seed=J * 31 + tile[0] + flags, tile_w=tile[0],
+                             tile_h=tile[1])
+    gt = gpu_run(fr, dtype=dtype, flags=flags, totals=True)
+    gf = gpu_run(fr, dtype=dtype, flags=flags, fused=True)
+    assert gt["bad"] == 0 and gf["bad"] == 0
+    np.testing.assert_array_equal(gt["out"], gf["out"])
+    np.testing.assert_array_equal(gt["coeff"], gf["coeff"])
 
 
 def test_row_span_tiles():
@@ -81,7 +121,8 @@ def test_wide_image_general_row_division():
 def test_every_reading_flag(flags):
     fr = synth.uniform_frame(40, 24, 8.0, 64, J=4, seed=100 + flags)
     r = oracle_run(fr, flags=flags)
-    for kw in (dict(), dict(fused=True), dict(two_step=True)):
+    for kw in (dict(), dict(fused=True), dict(two_step=True), dict(totals=True),
+               dict(two_step=True, totals=True)):
         g = gpu_run(fr, flags=flags, **kw)
         np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0, err_msg=str(kw))
 

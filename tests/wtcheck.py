@@ -34,14 +34,18 @@ def desc_of(fr: synth.Frame, J=None, dtype=wt.F32, flags=wt.DEFAULT_FLAGS):
 
 
 def gpu_run(fr: synth.Frame, J=None, dtype=wt.F32, flags=wt.DEFAULT_FLAGS, bg=(0.5, 0.5, 0.5),
-            bg_img=None, fused=False, two_step=False):
-    """Returns dict with coeff (float64 numpy), zmin, out [P,4] (and accum)."""
+            bg_img=None, fused=False, two_step=False, totals=False):
+    """Returns dict with coeff (float64 numpy), zmin, out [P,4] (and accum,
+    and total when the build's per-pixel totals go to the resolve)."""
     dev = torch.device("cuda")
     g = fr.to(dev)
     d = desc_of(fr, J, dtype, flags)
     f = frags_of(g)
     C = 1 << d.J
-    coeff = torch.full((fr.P, C), float("nan"), device=dev, dtype=wt.coeff_torch_dtype(dtype))
+    if dtype == wt.SE16:  # raw bytes: mantissas, then exponents
+        coeff = wt.coeff_buffer(d, dev).fill_(0xAB)
+    else:
+        coeff = torch.full((fr.P, C), float("nan"), device=dev, dtype=wt.coeff_torch_dtype(dtype))
     zmin = torch.full((fr.P,), float("nan"), device=dev)
     out = torch.full((fr.P, 4), float("nan"), device=dev)
     bgt = None if bg_img is None else torch.as_tensor(bg_img, dtype=torch.float32, device=dev)
@@ -49,14 +53,17 @@ def gpu_run(fr: synth.Frame, J=None, dtype=wt.F32, flags=wt.DEFAULT_FLAGS, bg=(0
     if fused:
         wt.wt_build_resolve(d, f, out, coeff, zmin, bg=bg, bg_img=bgt)
     else:
-        wt.wt_build(d, f, coeff, zmin)
+        total = torch.full((fr.P,), float("nan"), device=dev) if totals else None
+        wt.wt_build(d, f, coeff, zmin, total=total)
         if two_step:
             accum = torch.full((fr.P, 5), float("nan"), device=dev)
-            wt.wt_resolve(d, f, coeff, zmin, accum)
+            wt.wt_resolve(d, f, coeff, zmin, accum, total=total)
             wt.wt_composite(d, accum, out, bg=bg, bg_img=bgt)
             res["accum"] = accum.cpu().numpy().astype(np.float64)
         else:
-            wt.wt_resolve_composite(d, f, coeff, zmin, out, bg=bg, bg_img=bgt)
+            wt.wt_resolve_composite(d, f, coeff, zmin, out, bg=bg, bg_img=bgt, total=total)
+        if totals:
+            res["total"] = total.cpu().numpy().astype(np.float64)
     res["bad"] = wt.wt_get_error()
     torch.cuda.synchronize()
     res["coeff"] = coeff.float().cpu().numpy().astype(np.float64)
