@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<J>::value)
 // ---------------------------------------------------------------- adjoint
 
 // Shared-memory layout of the adjoint: F, G bins; later the bin values, the
-// warps' accumulators and then the scattered adjoint bins Gamma; then nine
-// per-pixel words (depth, S, u[3], ybar[3], const).
+// warps' accumulators and then the scattered adjoint bins Gamma; then ten
+// per-pixel words (depth, S, u[3], ybar[3], const, Gamma's fixed-point scale).
 template <int J> struct BackLayout {
     static constexpr size_t P(int npx) { return Layout<J>::plane(npx); }
     static constexpr size_t V(int npx) { return Layout<J>::vplane(npx); }
@@ -395,7 +395,7 @@ template <int J> struct BackLayout {
     static constexpr size_t region(int npx) {
         return 2 * P(npx) > V(npx) + second(npx) ? 2 * P(npx) : V(npx) + second(npx);
     }
-    static constexpr size_t total(int npx) { return region(npx) + 9 * W(npx); }
+    static constexpr size_t total(int npx) { return region(npx) + 10 * W(npx); }
 };
 
 // Re-derives everything the adjoint needs about one fragment from its inputs
@@ -454,6 +454,8 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
     float *sU = reinterpret_cast<float *>(wbase + 2 * WD);  // 3 planes
     float *sY = reinterpret_cast<float *>(wbase + 5 * WD);  // 3 planes
     float *sK = reinterpret_cast<float *>(wbase + 8 * WD);
+    float *sX = reinterpret_cast<float *>(wbase + 9 * WD);  // Gamma's scale 2^(30 - e) per pixel
+    int *gi = reinterpret_cast<int *>(gam);                  // Gamma in fixed point
     const int wpl = (int)(WD / 4);  // floats per word plane
     const Tile T = tile_of(p, blockIdx.x, true);
     fill_zero(smem, (int)(2 * PL));
@@ -510,55 +512,97 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
             sY[ch * wpl + lp] = y;
         }
         sK[lp] = -Tt * tau;
+        // sum |gamma| over the pixel <= (|u_r| + |u_g| + |u_b|) W when colours
+        // lie in [0, 1]: the scale 2^(30 - e), B < 2^e, keeps that sum below
+        // 2^30 (B is W up to FP32 rounding, and 2^e > B leaves a factor of up
+        // to two).  A non-finite B comes with non-finite gammas, which pass 3
+        // sends down the FP32 path.
+        const float B = (fabsf(sU[lp]) + fabsf(sU[wpl + lp]) + fabsf(sU[2 * wpl + lp])) * acc.w;
+        const int e = B > 0.f && B < 3.0e38f ? min(max(ilogbf(B) + 1, -90), 97) : 0;
+        sX[lp] = exp2i(30 - e);
     }
     fill_zero(gam, (int)PL);
     __syncthreads();
     const uint32_t flags = p.flags;
     // pass 3: colour gradients and the scatter of gamma into the bins; each
     // fragment's gamma waits in its grad_alpha entry for pass 4 (read back by
-    // the thread that wrote it: both passes split the range the same way)
-    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
-        constexpr int N = std::remove_reference_t<decltype(G)>::size;
-        float gr[3][N], gm[N];
+    // the thread that wrote it: both passes split the range the same way).
+    // The scatter adds rint(gamma s_p) with 32-bit integer atomics (order-free,
+    // so the gradients are the same on every run).  The scale keeps a pixel's
+    // sum of |gamma| s_p below 2^30 whenever its colours lie in [0, 1] (their
+    // weighted mean then does too, and |beta| <= |u_r| + |u_g| + |u_b|), so no
+    // word can wrap; a fragment with a colour outside [0, 1] (or NaN) sends
+    // the tile through the pass again with FP32 atomics.
+    auto pass3 = [&](auto fixed_tag) {
+        constexpr bool FIXED = decltype(fixed_tag)::value;
+        bool ovf = false;
+        for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
+            constexpr int N = std::remove_reference_t<decltype(G)>::size;
+            float gr[3][N], gm[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            gr[0][k] = gr[1][k] = gr[2][k] = 0.f;
-            gm[k] = 0.f;
-            if (!G.v) continue;
-            const FragState<J> st = frag_state<J>(p, T, vals, G.px[k], G.z[k], G.al[k]);
-            if (st.lp < 0) continue;
-            const float c[3] = {G.r[k], G.g[k], G.b[k]};
-            float beta = 0.f;
+            for (int k = 0; k < N; ++k) {
+                gr[0][k] = gr[1][k] = gr[2][k] = 0.f;
+                gm[k] = 0.f;
+                if (!G.v) continue;
+                const FragState<J> st = frag_state<J>(p, T, vals, G.px[k], G.z[k], G.al[k]);
+                if (st.lp < 0) continue;
+                const float c[3] = {G.r[k], G.g[k], G.b[k]};
+                float beta = 0.f;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const float u = sU[ch * wpl + st.lp];
-                beta = fmaf(u, c[ch] - sY[ch * wpl + st.lp], beta);
-                gr[ch][k] = u * st.w;
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float u = sU[ch * wpl + st.lp];
+                    beta = fmaf(u, c[ch] - sY[ch * wpl + st.lp], beta);
+                    gr[ch][k] = u * st.w;
+                }
+                const float gamma = -beta * st.w;
+                gm[k] = gamma;
+                if constexpr (FIXED)
+                    ovf |= !(fminf(fminf(c[0], c[1]), c[2]) >= 0.f && fmaxf(fmaxf(c[0], c[1]), c[2]) <= 1.f &&
+                             fabsf(gamma) <= 3.0e38f);
+                const float sc = FIXED ? sX[st.lp] : 1.f;
+                auto add = [&](int m, float x) {
+                    if constexpr (FIXED) atomicAdd(&gi[st.lp * LD + m], __float2int_rn(x * sc));
+                    else atomicAdd(&gam[st.lp * LD + m], x);
+                };
+                if (flags & kLinear) {
+                    add(st.q.lo, gamma * (1.f - st.q.t));
+                    add(st.q.lo + 1, gamma * st.q.t);
+                } else {
+                    add(st.q.m, gamma);
+                }
             }
-            const float gamma = -beta * st.w;
-            gm[k] = gamma;
-            float *row = gam + st.lp * LD;
-            if (flags & kLinear) {
-                atomicAdd(&row[st.q.lo], gamma * (1.f - st.q.t));
-                atomicAdd(&row[st.q.lo + 1], gamma * st.q.t);
-            } else {
-                atomicAdd(&row[st.q.m], gamma);
-            }
-        }
-        if (G.v) {
+            if (G.v) {
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) store_group<N>(p.grgb + ch * p.n, G.i0, gr[ch]);
-            store_group<N>(p.galpha, G.i0, gm);
-        }
-    });
+                for (int ch = 0; ch < 3; ++ch) store_group<N>(p.grgb + ch * p.n, G.i0, gr[ch]);
+                store_group<N>(p.galpha, G.i0, gm);
+            }
+        });
+        return ovf;
+    };
+    const bool fp32 = __syncthreads_or(pass3(std::true_type{}));
+    if (fp32) {  // rare: the tile again, in FP32 (its outputs are rewritten with the same values)
+        fill_zero(gam, (int)PL);
+        __syncthreads();
+        pass3(std::false_type{});
+    }
     __syncthreads();
     if (gp >= 0) {  // inclusive suffix sums Q_m, with Q_C = 0
         float *row = gam + lp * LD;
-        float acc_s = 0.f;
         row[C] = 0.f;
-        for (int m = C - 1; m >= 0; --m) {
-            acc_s += row[m];
-            row[m] = acc_s;
+        if (!fp32) {  // exact integer sums, one rounding each
+            const int *qi = gi + lp * LD;
+            const float inv = 1.f / sX[lp];  // a power of two
+            long long acc_q = 0;
+            for (int m = C - 1; m >= 0; --m) {
+                acc_q += qi[m];
+                row[m] = (float)acc_q * inv;
+            }
+        } else {
+            float acc_s = 0.f;
+            for (int m = C - 1; m >= 0; --m) {
+                acc_s += row[m];
+                row[m] = acc_s;
+            }
         }
     }
     __syncthreads();

@@ -65,6 +65,37 @@ def test_backward_background_image_and_clamped_alpha():
     assert (ga[::17] == 0).all() and (ga[5::23] == 0).all()
 
 
+def test_backward_is_the_same_on_every_run():
+    """The scatter of gamma into the bins is integer fixed point, so two runs
+    on the same inputs give the same gradients bit for bit."""
+    fr = synth.uniform_frame(64, 48, 30.0, 200, alpha_range=(0.02, 0.6), J=5, seed=91, tile_w=192,
+                             tile_h=1)
+    gout = np.random.default_rng(91).standard_normal((fr.P, 4))
+    a1, c1 = _gpu_grad(fr, gout)
+    a2, c2 = _gpu_grad(fr, gout)
+    np.testing.assert_array_equal(a1, a2)
+    np.testing.assert_array_equal(c1, c2)
+    ra, rc = _ref_grad(fr, gout)
+    _close(a1, ra)
+    _close(c1, rc)
+
+
+@pytest.mark.parametrize("flags", [7, 3])
+def test_backward_with_colours_beyond_one(flags):
+    """Colours far outside [0, 1] break the bound the fixed-point scale of the
+    gamma scatter assumes; the tiles where a term or a sum would not fit take
+    the FP32 scatter, and the gradients still match the oracle."""
+    fr = synth.uniform_frame(40, 30, 12.0, 80, alpha_range=(0.05, 0.6), J=4, seed=55 + flags)
+    rng = np.random.default_rng(5)
+    for ch in ("r", "g", "b"):
+        setattr(fr, ch, torch.from_numpy((rng.random(fr.n) * 4000.0 - 2000.0).astype(np.float32)))
+    gout = rng.standard_normal((fr.P, 4))
+    ga, gc = _gpu_grad(fr, gout, flags=flags)
+    ra, rc = _ref_grad(fr, gout, flags=flags)
+    _close(ga, ra)
+    _close(gc, rc)
+
+
 def test_autograd_function_matches_direct_call():
     fr = synth.uniform_frame(48, 32, 10.0, 40, alpha_range=(0.05, 0.5), J=4, seed=8)
     dev = torch.device("cuda")
