@@ -735,12 +735,19 @@ def run_backward(wt, args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    fwd_ms = timed(lambda: wt.wt_build_resolve(desc, frags, out, None, None, bg=fr.bg, stream=stream))
+    # the forward as the autograd function runs it (it keeps the pixel sums,
+    # 20 B per pixel, for the backward), and the backward with and without them
+    accum = torch.empty(P, 5, device=dev)
+    fwd_ms = timed(lambda: wt.wt_build_resolve(desc, frags, out, None, None, bg=fr.bg, stream=stream,
+                                               accum=accum))
     bwd_ms = timed(lambda: wt.wt_backward(desc, frags, grad_out, grad_alpha, grad_rgb, bg=fr.bg,
-                                          stream=stream))
+                                          stream=stream, accum=accum))
+    bwd_re_ms = timed(lambda: wt.wt_backward(desc, frags, grad_out, grad_alpha, grad_rgb, bg=fr.bg,
+                                             stream=stream))
     assert wt.wt_get_error(stream) == 0
     return {"workload": "16 x 512x512 stacked as 512x8192, Poisson(32) cap 256, alpha U[.05,.5], J=4, FP32",
             "fragments": n, "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "backward_ms_forward_sums_recomputed": round(bwd_re_ms, 4),
             "backward_fragments_per_s": n / (bwd_ms / 1e3),
             "backward_bytes_per_fragment": 24 + 16,
             "backward_GBps_of_fragment_io": round(n * 40 / (bwd_ms / 1e3) / 1e9, 1)}

@@ -248,16 +248,21 @@ wt_status wt_resolve_composite(const wt_desc *desc, const wt_frags *frags, const
  *   coeff [P * C] nullable: if given, the coefficients are also stored.
  *   zmin  [P] nullable: if given, the depth bound is also stored.
  *   out   [P * 4] float RGBA.
+ *   accum [P * 5] float nullable: if given, the pixel sums {R, G, B, W, S}
+ *         of the resolve are also stored (as wt_resolve's, with the weight
+ *         offset m_p of the tile's near bound); wt_backward takes them to
+ *         skip recomputing the forward sums.
  * WT_ACCUMULATE is not supported here (WT_ERR_UNSUPPORTED).
  */
 wt_status wt_build_resolve(const wt_desc *desc, const wt_frags *frags, void *coeff, float *zmin,
-                           const float *bg_img, const float bg[3], float *out, wt_stream stream);
+                           const float *bg_img, const float bg[3], float *out, float *accum,
+                           wt_stream stream);
 
 /*
  * wt_build_resolve_tiles -- wt_build_resolve for the tiles
  * [first_tile, first_tile + num_tiles) only (tiles are independent, §2.1: the
  * method keeps constant state per pixel).  Only those tiles' fragment ranges
- * are read and only their pixels of coeff, zmin and out are written, so a
+ * are read and only their pixels of coeff, zmin, out and accum are written, so a
  * caller can stream a frame in pieces, for example overlapping the upload of
  * the next range of tiles with the work on this one.  frags->tile_offsets
  * must still cover every tile.  A range outside [0, ntiles] is WT_ERR_ARG;
@@ -265,7 +270,7 @@ wt_status wt_build_resolve(const wt_desc *desc, const wt_frags *frags, void *coe
  */
 wt_status wt_build_resolve_tiles(const wt_desc *desc, const wt_frags *frags, int64_t first_tile,
                                  int64_t num_tiles, void *coeff, float *zmin, const float *bg_img,
-                                 const float bg[3], float *out, wt_stream stream);
+                                 const float bg[3], float *out, float *accum, wt_stream stream);
 
 /*
  * wt_build_resolve_single_pass -- the single-pass variant the paper proposes
@@ -354,7 +359,8 @@ wt_status wt_build_resolve_rgb(const wt_desc *desc, const wt_frags *frags, const
  *   bgs           host array of nframes * 3 background colours.
  *   outs          host array of nframes device pointers, out[k] of [P_k * 4].
  * The first call on a device resolves the scratch's device address with that
- * device current.  Every call reuses
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture begins.  Every call reuses
  * the same scratch (each call re-initialises all of it that it uses, the
  * counter included): calls that overlap on the GPU -- on different streams,
  * or from different host threads without ordering -- race on it.
@@ -383,6 +389,11 @@ wt_status wt_absorbance(const wt_desc *desc, const void *coeff, int64_t q, const
  * call from the fragments (nothing from the forward pass is stored), with the
  * same desc (J, storage rounding, flags) and background as the forward call.
  *   grad_out   [P * 4] float, dL/d(out RGBA).
+ *   accum      [P * 5] float, nullable: the forward call's pixel sums, as
+ *              stored by wt_build_resolve's accum with this desc, these
+ *              fragments and this background; if given, the forward sums are
+ *              not recomputed (one pass over the fragments fewer) and the
+ *              result is the same.  Not checked against the fragments.
  *   grad_alpha [n] float, written; 0 where alpha is clamped (<= 0 or
  *              >= 1 - 2^-20) and for rejected fragments.  It holds
  *              intermediate values during the call, so it must not overlap
@@ -392,7 +403,7 @@ wt_status wt_absorbance(const wt_desc *desc, const void *coeff, int64_t q, const
  * The pixel-level sums use FP32; WT_ACCUMULATE is not supported.
  */
 wt_status wt_backward(const wt_desc *desc, const wt_frags *frags, const float *bg_img,
-                      const float bg[3], const float *grad_out, float *grad_alpha,
+                      const float bg[3], const float *grad_out, const float *accum, float *grad_alpha,
                       float *grad_rgb, wt_stream stream);
 
 /* ------------------------------------------------------------------------

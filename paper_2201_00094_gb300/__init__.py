@@ -120,12 +120,12 @@ def lib() -> ctypes.CDLL:
         "wt_composite": ([D, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_composite_ca": ([D, vp, vp, vp, ctypes.c_float, ctypes.c_int32, vp, vp], ctypes.c_int),
         "wt_resolve_composite": ([D, Fr, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
-        "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
-        "wt_build_resolve_tiles": ([D, Fr, i64, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build_resolve": ([D, Fr, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_build_resolve_tiles": ([D, Fr, i64, i64, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_single_pass": ([D, Fr, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_rgb": ([D, Fr, vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp, vp], ctypes.c_int),
         "wt_absorbance": ([D, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
-        "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "wt_backward": ([D, Fr, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "wt_build_resolve_batch_static": ([D, Fr, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "wt_get_error": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "wt_raster_workspace_bytes": ([i64], ctypes.c_size_t),
@@ -341,25 +341,27 @@ def wt_resolve_composite(desc: WtDesc, frags: WtFrags, coeff: torch.Tensor,
 def wt_build_resolve(desc: WtDesc, frags: WtFrags, out: torch.Tensor,
                      coeff: Optional[torch.Tensor] = None, zmin: Optional[torch.Tensor] = None,
                      bg: Sequence[float] = (0.5, 0.5, 0.5), bg_img: Optional[torch.Tensor] = None,
-                     stream=None) -> None:
+                     stream=None, accum: Optional[torch.Tensor] = None) -> None:
+    """accum [P, 5] float32, optional: the pixel sums, for wt_backward."""
     _check_frags(desc, frags)
-    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img, accum=accum)
     _call("wt_build_resolve", ctypes.byref(desc), ctypes.byref(frags),
           _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
-          _stream(stream))
+          _dev(accum, "accum", (torch.float32,)), _stream(stream))
 
 
 def wt_build_resolve_tiles(desc: WtDesc, frags: WtFrags, first_tile: int, num_tiles: int,
                            out: torch.Tensor, coeff: Optional[torch.Tensor] = None,
                            zmin: Optional[torch.Tensor] = None, bg: Sequence[float] = (0.5, 0.5, 0.5),
-                           bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
+                           bg_img: Optional[torch.Tensor] = None, stream=None,
+                           accum: Optional[torch.Tensor] = None) -> None:
     _check_frags(desc, frags)
-    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img)
+    _check_pixel_buffers(desc, coeff=coeff, zmin=zmin, out=out, bg_img=bg_img, accum=accum)
     _call("wt_build_resolve_tiles", ctypes.byref(desc), ctypes.byref(frags), int(first_tile),
           int(num_tiles), _dev(coeff, "coeff", _COEFF_DT), _dev(zmin, "zmin", (torch.float32,)),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg), _dev(out, "out", (torch.float32,)),
-          _stream(stream))
+          _dev(accum, "accum", (torch.float32,)), _stream(stream))
 
 
 def wt_build_resolve_single_pass(desc: WtDesc, frags: WtFrags, coeff_prev: torch.Tensor,
@@ -570,16 +572,18 @@ def wt_normalize_depth(desc: WtDesc, frags: WtFrags, zlo: torch.Tensor, zhi: tor
 
 def wt_backward(desc: WtDesc, frags: WtFrags, grad_out: torch.Tensor, grad_alpha: torch.Tensor,
                 grad_rgb: torch.Tensor, bg: Sequence[float] = (0.5, 0.5, 0.5),
-                bg_img: Optional[torch.Tensor] = None, stream=None) -> None:
-    """grad_rgb is planar [3, n]."""
+                bg_img: Optional[torch.Tensor] = None, stream=None,
+                accum: Optional[torch.Tensor] = None) -> None:
+    """grad_rgb is planar [3, n]; accum [P, 5], optional: the forward call's
+    pixel sums from wt_build_resolve (the forward sums are then not recomputed)."""
     _check_frags(desc, frags)
-    _check_pixel_buffers(desc, bg_img=bg_img)
+    _check_pixel_buffers(desc, bg_img=bg_img, accum=accum)
     _need(grad_out, "grad_out", 4 * _pixels(desc))
     _need(grad_alpha, "grad_alpha", int(frags.n))
     _need(grad_rgb, "grad_rgb", 3 * int(frags.n))
     _call("wt_backward", ctypes.byref(desc), ctypes.byref(frags),
           _dev(bg_img, "bg_img", (torch.float32,)), _bg(bg),
-          _dev(grad_out, "grad_out", (torch.float32,)),
+          _dev(grad_out, "grad_out", (torch.float32,)), _dev(accum, "accum", (torch.float32,)),
           _dev(grad_alpha, "grad_alpha", (torch.float32,)),
           _dev(grad_rgb, "grad_rgb", (torch.float32,)), _stream(stream))
 
@@ -594,20 +598,21 @@ class WaveletOIT(torch.autograd.Function):
     def forward(ctx, pixel, z, alpha, r, g, b, tile_offsets, desc, bg=(0.5, 0.5, 0.5)):
         frags = make_frags(pixel, z, alpha, tile_offsets, r, g, b)
         out = torch.empty(desc.P, 4, device=z.device, dtype=torch.float32)
-        wt_build_resolve(desc, frags, out, None, None, bg=bg)
-        ctx.save_for_backward(pixel, z, alpha, r, g, b, tile_offsets)
+        accum = torch.empty(desc.P, 5, device=z.device, dtype=torch.float32)  # pixel sums, 20 B each
+        wt_build_resolve(desc, frags, out, None, None, bg=bg, accum=accum)
+        ctx.save_for_backward(pixel, z, alpha, r, g, b, tile_offsets, accum)
         ctx.desc = desc
         ctx.bg = tuple(bg)
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        pixel, z, alpha, r, g, b, tile_offsets = ctx.saved_tensors
+        pixel, z, alpha, r, g, b, tile_offsets, accum = ctx.saved_tensors
         frags = make_frags(pixel, z, alpha, tile_offsets, r, g, b)
         n = z.numel()
         ga = torch.empty(n, device=z.device, dtype=torch.float32)
         gc = torch.empty(3, n, device=z.device, dtype=torch.float32)
-        wt_backward(ctx.desc, frags, grad_out.contiguous().float(), ga, gc, bg=ctx.bg)
+        wt_backward(ctx.desc, frags, grad_out.contiguous().float(), ga, gc, bg=ctx.bg, accum=accum)
         return None, None, ga, gc[0], gc[1], gc[2], None, None, None
 
 

@@ -239,13 +239,14 @@ wt_status wt_resolve_composite(const wt_desc *d, const wt_frags *f, const void *
 
 wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t first_tile, int64_t num_tiles,
                                  void *coeff, float *zmin, const float *bg_img, const float bg[3], float *out,
-                                 wt_stream stream) {
+                                 float *accum, wt_stream stream) {
     WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
     if (d->flags & WT_ACCUMULATE) return WT_ERR_UNSUPPORTED;
     if ((st = check_frags(f, true)) != WT_OK) return st;
-    if ((coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16) || (zmin && !aligned(zmin, 4)))
+    if ((coeff && !aligned(coeff, 16)) || !out || !aligned(out, 16) || (zmin && !aligned(zmin, 4)) ||
+        (accum && !aligned(accum, 4)))
         return WT_ERR_ARG;
     const int64_t nt = ntiles_of(d);
     if (first_tile < 0 || num_tiles < 0 || first_tile + num_tiles > nt) return WT_ERR_ARG;
@@ -255,6 +256,7 @@ wt_status wt_build_resolve_tiles(const wt_desc *d, const wt_frags *f, int64_t fi
     p.coeff = coeff;
     p.zmin = zmin;
     p.out = out;
+    p.accum = accum;
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     if (!(p.err = err_word())) return WT_ERR_CUDA;
     const TileLaunch *t = table(kFused0, kFused1, kFused2, kFused3, d->coeff_dtype);
@@ -314,15 +316,16 @@ wt_status wt_build_resolve_rgb(const wt_desc *d, const wt_frags *f, const float 
 }
 
 wt_status wt_build_resolve(const wt_desc *d, const wt_frags *f, void *coeff, float *zmin,
-                           const float *bg_img, const float bg[3], float *out, wt_stream stream) {
+                           const float *bg_img, const float bg[3], float *out, float *accum, wt_stream stream) {
     WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
-    return wt_build_resolve_tiles(d, f, 0, ntiles_of(d), coeff, zmin, bg_img, bg, out, stream);
+    return wt_build_resolve_tiles(d, f, 0, ntiles_of(d), coeff, zmin, bg_img, bg, out, accum, stream);
 }
 
 wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, const float bg[3],
-                      const float *grad_out, float *grad_alpha, float *grad_rgb, wt_stream stream) {
+                      const float *grad_out, const float *accum, float *grad_alpha, float *grad_rgb,
+                      wt_stream stream) {
     WT_TRACE();
     wt_status st = check_desc(d);
     if (st != WT_OK) return st;
@@ -330,7 +333,7 @@ wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, 
     if ((st = check_frags(f, true)) != WT_OK) return st;
     if (!grad_out || !aligned(grad_out, 16)) return WT_ERR_ARG;
     if (f->n > 0 && (!grad_alpha || !grad_rgb)) return WT_ERR_ARG;
-    if (!aligned(grad_alpha, 4) || !aligned(grad_rgb, 4)) return WT_ERR_ARG;
+    if (!aligned(grad_alpha, 4) || !aligned(grad_rgb, 4) || (accum && !aligned(accum, 4))) return WT_ERR_ARG;
     // grad_alpha holds intermediate values while the fragments are still
     // being read, so it must not overlap any input
     {
@@ -342,12 +345,14 @@ wt_status wt_backward(const wt_desc *d, const wt_frags *f, const float *bg_img, 
         };
         if (overlaps(f->pixel, nb) || overlaps(f->z, nb) || overlaps(f->alpha, nb) || overlaps(f->r, nb) ||
             overlaps(f->g, nb) || overlaps(f->b, nb) || overlaps(f->tile_offsets, (size_t)(ntiles_of(d) + 1) * 8) ||
-            overlaps(grad_out, pb * 16) || overlaps(bg_img, pb * 12) || overlaps(grad_rgb, 3 * nb))
+            overlaps(grad_out, pb * 16) || overlaps(bg_img, pb * 12) || overlaps(accum, pb * 20) ||
+            overlaps(grad_rgb, 3 * nb))
             return WT_ERR_ARG;
     }
     Params p = make_params(d, f);
     if ((st = set_bg(p, bg_img, bg)) != WT_OK) return st;
     p.gout = grad_out;
+    p.accum = const_cast<float *>(accum);
     p.galpha = grad_alpha;
     p.grgb = grad_rgb;
     if (!(p.err = err_word())) return WT_ERR_CUDA;

@@ -193,6 +193,14 @@ __device__ __forceinline__ void fused_tile(const Params &p, int tile, unsigned c
     if (gp >= 0) {
         const float4 a = sum_warps(accw, npx, lp);
         composite_pixel(p, gp, a.x, a.y, a.z, a.w, sS[lp]);
+        if (p.accum) {  // the pixel sums, for the adjoint
+            float *o = p.accum + 5 * gp;
+            o[0] = a.x;
+            o[1] = a.y;
+            o[2] = a.z;
+            o[3] = a.w;
+            o[4] = sS[lp];
+        }
     }
     __syncthreads();
 }
@@ -478,13 +486,21 @@ __global__ void __launch_bounds__(kThreads, MB) k_backward(Params p) {
         put_bins<J>(vals + lp * LDV, v, __uint_as_float(sZ[lp]), p.flags);
         sS[lp] = S;
     }
-    fill_zero(accw, (int)Layout<J>::accw(npx));
-    __syncthreads();
-    phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);  // forward sums, recomputed
-    __syncthreads();
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (gp >= 0) acc = sum_warps(accw, npx, lp);
-    __syncthreads();  // accumulators consumed; their space becomes Gamma
+    if (p.accum) {  // the forward call's sums
+        __syncthreads();
+        if (gp >= 0) {
+            const float *a = p.accum + 5 * gp;
+            acc = make_float4(a[0], a[1], a[2], a[3]);
+        }
+    } else {  // the forward sums, recomputed
+        fill_zero(accw, (int)Layout<J>::accw(npx));
+        __syncthreads();
+        phase_resolve<J, false>(p, T, vals, accw, nullptr, bad);
+        __syncthreads();
+        if (gp >= 0) acc = sum_warps(accw, npx, lp);
+        __syncthreads();  // accumulators consumed; their space becomes Gamma
+    }
     if (gp >= 0) {
         const float Tt = expf(-S), cover = -expm1f(-S);
         const float *go = p.gout + 4 * gp;

@@ -84,7 +84,7 @@ def test_unsupported_J_and_flags(L):
     d = wt.make_desc(64, 64, 4, flags=wt.DEFAULT_FLAGS | wt.ACCUMULATE)
     bg = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
     st = L.wt_build_resolve(ctypes.byref(d), ctypes.byref(fr), None, None, None, bg,
-                            ctypes.c_void_p(16), None)
+                            ctypes.c_void_p(16), None, None)
     assert st == 2
 
 
@@ -143,8 +143,17 @@ def test_backward_refuses_grad_alpha_overlapping_an_input(L):
                     tile_offsets=0x70000)
     gout, grgb = ctypes.c_void_p(0x80000), ctypes.c_void_p(0x90000)
     for ga in (0x30000, 0x30000 + 36, 0x10000 - 8, 0x60000, 0x70000 + 8, 0x80000 + 64, 0x90000 + 100):
-        st = L.wt_backward(ctypes.byref(d), ctypes.byref(fr), None, bg, gout, ctypes.c_void_p(ga), grgb, None)
+        st = L.wt_backward(ctypes.byref(d), ctypes.byref(fr), None, bg, gout, None, ctypes.c_void_p(ga), grgb,
+                           None)
         assert st == 1, hex(ga)
+    acc = ctypes.c_void_p(0xA0000)  # the forward's pixel sums, 64 * 64 * 20 bytes
+    for ga in (0xA0000, 0xA0000 + 64 * 64 * 20 - 4):
+        st = L.wt_backward(ctypes.byref(d), ctypes.byref(fr), None, bg, gout, acc, ctypes.c_void_p(ga), grgb,
+                           None)
+        assert st == 1, hex(ga)
+    st = L.wt_backward(ctypes.byref(d), ctypes.byref(fr), None, bg, gout, ctypes.c_void_p(0xA0002),
+                       ctypes.c_void_p(0xC0000), grgb, None)  # misaligned sums
+    assert st == 1
 
 
 def test_status_strings(L):

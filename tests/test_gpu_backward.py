@@ -96,6 +96,39 @@ def test_backward_with_colours_beyond_one(flags):
     _close(gc, rc)
 
 
+@pytest.mark.parametrize("flags,J,tile", [(7, 4, (16, 16)), (7, 5, (192, 1)), (3, 4, (7, 5)), (5, 5, (16, 16))])
+def test_backward_with_the_forward_sums_is_the_same(flags, J, tile):
+    """Given the pixel sums wt_build_resolve stored, wt_backward skips
+    recomputing them: the gradients are the same, bit for bit."""
+    fr = synth.uniform_frame(97, 41, 18.0, 120, alpha_range=(0.02, 0.6), J=J, seed=40 + flags + J,
+                             tile_w=tile[0], tile_h=tile[1])
+    dev = torch.device("cuda")
+    g = fr.to(dev)
+    d = wt.make_desc(fr.width, fr.height, J, wt.F32, flags, tile[0], tile[1])
+    f = wt.make_frags(g.pixel, g.z, g.alpha, g.tile_offsets, g.r, g.g, g.b)
+    out = torch.empty(fr.P, 4, device=dev)
+    acc = torch.full((fr.P, 5), float("nan"), device=dev)
+    wt.wt_build_resolve(d, f, out, bg=(0.2, 0.4, 0.6), accum=acc)
+    gout = torch.randn(fr.P, 4, device=dev, generator=torch.Generator(dev).manual_seed(J))
+    res = []
+    for a in (None, acc):
+        ga = torch.full((fr.n,), float("nan"), device=dev)
+        gc = torch.full((3, fr.n), float("nan"), device=dev)
+        wt.wt_backward(d, f, gout, ga, gc, bg=(0.2, 0.4, 0.6), accum=a)
+        res.append((ga, gc))
+    assert wt.wt_get_error() == 0
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    # the stored sums are the resolve's: S exact, ratios R/W as wt_resolve's
+    h = acc.double().cpu().numpy()
+    np.testing.assert_allclose(h[:, 4], _ref_S(fr), rtol=1e-5, atol=1e-6)
+
+
+def _ref_S(fr):
+    h = fr.numpy()
+    a = -np.log1p(-np.clip(h["alpha"].astype(np.float64), 0, 1 - 2 ** -20))
+    return np.bincount(h["pixel"].astype(np.int64), weights=a, minlength=fr.P)
+
+
 def test_autograd_function_matches_direct_call():
     fr = synth.uniform_frame(48, 32, 10.0, 40, alpha_range=(0.05, 0.5), J=4, seed=8)
     dev = torch.device("cuda")
