@@ -711,7 +711,8 @@ def run_backward(wt, args):
     call on the same frame is timed beside it."""
     dev = torch.device("cuda")
     tw, th = tile_of(args)
-    fr = synth.uniform_frame(512, 8192, 32.0, 256, (0.05, 0.5), 4, args.seed, dev, name="diff512",
+    bw, bh = (int(x) for x in args.backward_size.lower().split("x"))
+    fr = synth.uniform_frame(bw, bh, 32.0, 256, (0.05, 0.5), 4, args.seed, dev, name="diff512",
                              tile_w=tw, tile_h=th)
     n, P = fr.n, fr.P
     desc = wt.make_desc(fr.width, fr.height, fr.J, wt.F32, tile_w=fr.tile_w, tile_h=fr.tile_h)
@@ -745,7 +746,8 @@ def run_backward(wt, args):
     bwd_re_ms = timed(lambda: wt.wt_backward(desc, frags, grad_out, grad_alpha, grad_rgb, bg=fr.bg,
                                              stream=stream))
     assert wt.wt_get_error(stream) == 0
-    return {"workload": "16 x 512x512 stacked as 512x8192, Poisson(32) cap 256, alpha U[.05,.5], J=4, FP32",
+    stack = "16 x 512x512 stacked as 512x8192" if (bw, bh) == (512, 8192) else f"{bw}x{bh}"
+    return {"workload": f"{stack}, Poisson(32) cap 256, alpha U[.05,.5], J=4, FP32",
             "fragments": n, "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
             "backward_ms_forward_sums_recomputed": round(bwd_re_ms, 4),
             "backward_fragments_per_s": n / (bwd_ms / 1e3),
@@ -1011,6 +1013,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--backward-size", default="512x8192",
+                    help="WxH of the differentiation frame (16 frames of 512x512 stacked; smaller for profiling)")
     ap.add_argument("--no-preprocess", action="store_true")
     ap.add_argument("--no-particles", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
