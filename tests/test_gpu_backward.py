@@ -156,14 +156,20 @@ def test_diff512_batch_finite_differences():
     d = wt.make_desc(fr.width, fr.height, 4)
     f = wt.make_frags(fr.pixel, fr.z, fr.alpha, fr.tile_offsets, fr.r, fr.g, fr.b)
     out = torch.empty(fr.P, 4, device=dev)
-    wt.wt_build_resolve(d, f, out, None, None)
+    acc = torch.empty(fr.P, 5, device=dev)
+    wt.wt_build_resolve(d, f, out, None, None, accum=acc)
     target = torch.rand(fr.P, 4, device=dev, generator=torch.Generator(dev).manual_seed(5))
     target[:, 3] = out[:, 3]  # RGB loss only
     gout = (2 * (out - target)).contiguous()
     ga = torch.empty(fr.n, device=dev)
     gc = torch.empty(3, fr.n, device=dev)
     wt.wt_backward(d, f, gout, ga, gc)
+    # the autograd path (the forward's pixel sums) gives the same gradients
+    ga2, gc2 = torch.empty_like(ga), torch.empty_like(gc)
+    wt.wt_backward(d, f, gout, ga2, gc2, accum=acc)
     assert wt.wt_get_error() == 0
+    assert torch.equal(ga, ga2) and torch.equal(gc, gc2)
+    del ga2, gc2
     rng = np.random.default_rng(512)
     sample = np.sort(rng.choice(fr.n, 512, replace=False))
     st = torch.from_numpy(sample).to(dev)

@@ -186,6 +186,16 @@ def test_fused_equals_two_pass_full_frame(heavy4k):
     assert torch.equal(c1, c2)
     assert (o1 - o2).abs().max().item() <= 2e-5
     assert math.isfinite(o1.sum().item())
+    # with the build's near bounds and totals the two passes run the fused
+    # kernel's arithmetic: the same composite bit for bit, at full size
+    zmin = torch.empty(fr.P, device=dev)
+    total = torch.empty(fr.P, device=dev)
+    o3 = torch.empty(fr.P, 4, device=dev)
+    wt.wt_build(d, f, c2, zmin, total=total)
+    wt.wt_resolve_composite(d, f, c2, zmin, o3, total=total)
+    torch.cuda.synchronize()
+    assert wt.wt_get_error() == 0
+    assert torch.equal(o1, o3)
 
 
 def test_heavy4k_coloured_sampled_pixels(heavy4k):
