@@ -105,9 +105,7 @@ typedef struct wt_desc {
                                1 <= tile_w * tile_h <= 256; tiles are row-major,
                                ntiles = ceil(width/tile_w) * ceil(height/tile_h) */
     int32_t J;              /* Haar levels, 1..6; C = 2^J coefficients per pixel.
-                               J = 6 needs at most 192 pixels per tile for the
-                               single pass (wt_build_resolve_single_pass); the
-                               coloured call (wt_build_resolve_rgb) and the
+                               The coloured call (wt_build_resolve_rgb) and the
                                allocation-free batch stop at J = 5.
                                The paper's rank N is J - 1 (Wavelet3: J = 4) */
     int32_t coeff_dtype;    /* wt_dtype */

@@ -10,6 +10,8 @@ namespace wt {
 // Blocks per SM the kernels are compiled for (caps registers per thread so
 // that shared memory, not registers, sets the occupancy).
 template <int J> struct MinBlocks { static constexpr int value = J >= 6 ? 1 : (J == 5 ? 3 : 4); };
+// Tiles of at most this many pixels fit four fused blocks per SM at J = 5.
+constexpr int kFourBlockTilePx = 192;
 
 // §2.1 step 2: build the tile's coefficients and store them once.
 template <int J, typename CT, int MB = MinBlocks<J>::value>
@@ -224,26 +226,25 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused(Params p) {
 // from the previous frame).  The weight offset comes from frame t-1's near
 // bound; exponents are clamped to [0, 120] so that fragments nearer or much
 // farther than anything in frame t-1 keep finite, non-zero weights.
+// Shared memory of the single pass: that of the fused kernel.  Within a
+// tile, the resolve against frame t-1 (its bin values and the warps'
+// accumulators) comes first and the build of frame t (F and G bins) second,
+// over the tile's own fragment range both times (the second read hits L2), so
+// the two share one region.
 template <int J> struct TemporalLayout {
-    static constexpr size_t vals(int npx) { return 0; }
-    static constexpr size_t F(int npx) { return Layout<J>::vplane(npx); }
-    static constexpr size_t G(int npx) { return F(npx) + Layout<J>::plane(npx); }
-    static constexpr size_t accw(int npx) { return G(npx) + Layout<J>::plane(npx); }
-    static constexpr size_t zw(int npx) { return accw(npx) + Layout<J>::accw(npx); }
-    static constexpr size_t total(int npx) { return zw(npx) + Layout<J>::words(npx); }
+    static constexpr size_t total(int npx) { return Layout<J>::fused(npx); }
 };
 
 template <int J, typename CT, bool DEF, int MB>
 __global__ void __launch_bounds__(kThreads, MB) k_temporal(Params p, const void *coeff_prev, const float *zmin_prev) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD, LDV = Shape<J>::LDV;
-    constexpr float kFineStep = 1048576.f;  // 2^20: a step of 2^-7 under the fixed scale
     extern __shared__ __align__(16) unsigned char smem[];
     const int npx = p.g.tile_w * p.g.tile_h;
-    float *vals = reinterpret_cast<float *>(smem + TemporalLayout<J>::vals(npx));
-    unsigned *sF = reinterpret_cast<unsigned *>(smem + TemporalLayout<J>::F(npx));
-    unsigned *sG = reinterpret_cast<unsigned *>(smem + TemporalLayout<J>::G(npx));
-    float4 *accw = reinterpret_cast<float4 *>(smem + TemporalLayout<J>::accw(npx));
-    unsigned *sZ = reinterpret_cast<unsigned *>(smem + TemporalLayout<J>::zw(npx));
+    float *vals = reinterpret_cast<float *>(smem);
+    float4 *accw = reinterpret_cast<float4 *>(smem + Layout<J>::vplane(npx));
+    unsigned *sF = reinterpret_cast<unsigned *>(smem);
+    unsigned *sG = reinterpret_cast<unsigned *>(smem + Layout<J>::plane(npx));
+    unsigned *sZ = reinterpret_cast<unsigned *>(smem + Layout<J>::region(npx));
     uint4 *st = reinterpret_cast<uint4 *>(accw);  // staging of coefficient rows
     const uint32_t flags = DEF ? kDefaultFlags : p.flags;
     const Tile T = tile_of(p, p.tile0 + (int)blockIdx.x, true);
@@ -251,13 +252,13 @@ __global__ void __launch_bounds__(kThreads, MB) k_temporal(Params p, const void 
     const int lp = threadIdx.x;
     int64_t gp = -1;
     if (lp < npx) gp = global_pixel(p, T, lp);
-    // frame t-1's coefficients -> bin values (log2 units, weight offset folded in)
-    const CT *prev = static_cast<const CT *>(coeff_prev);
-    if (Staged<CT, C>::ok) load_staged<CT, C>(p, T, st, prev);
-    fill_zero(sF, (int)(2 * Layout<J>::plane(npx)));
-    for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
-    __syncthreads();
     const int64_t P = (int64_t)p.g.width * p.g.height;
+    // frame t-1's coefficients -> bin values (log2 units, its weight offset folded in)
+    const CT *prev = static_cast<const CT *>(coeff_prev);
+    if (Staged<CT, C>::ok) {
+        load_staged<CT, C>(p, T, st, prev);
+        __syncthreads();
+    }
     if (gp >= 0) {
         float v[C];
         const int e = kIsSE16<CT> ? (int)se16_expo<C>(prev, P)[gp] - kSE16Bias : 0;
@@ -269,56 +270,22 @@ __global__ void __launch_bounds__(kThreads, MB) k_temporal(Params p, const void 
     __syncthreads();  // staged rows consumed
     fill_zero(accw, (int)Layout<J>::accw(npx));
     __syncthreads();
-    // the single pass: build frame t's bins and resolve against frame t-1
-    float4 *mine = accw + (threadIdx.x >> 5) * npx;
+    // the resolve of frame t's fragments against frame t-1's visibility
     unsigned bad = 0;
-    bool retry = false;
-    for_each_group<kWithZ | kWithRGB>(T.s, T.e, p, [&](auto &G) {
-        constexpr int N = std::remove_reference_t<decltype(G)>::size;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            int lpk = -1;
-            if (G.v) {
-                if (G.z[k] == G.z[k] && G.al[k] == G.al[k]) lpk = local_pixel(G.px[k], p, T);
-                if (lpk < 0) ++bad;
-            }
-            const int l = lpk >= 0 ? lpk : 0;
-            const float ac = clamp_alpha(G.al[k]);
-            const float a = step_of(ac);
-            const float zc = clamp_depth(G.z[k]);
-            if (lpk >= 0) {
-                const float s = zc * (float)C;
-                const Floor m = floor_small(s);
-                const float f = s - m.f;
-                const float as = a * kBinScale;
-                const unsigned vF = __float2uint_rn(as * f), vG = __float2uint_rn(as * (1.f - f));
-                const unsigned oF = atomicAdd(&sF[lpk * LD + m.i], vF);
-                const unsigned oG = atomicAdd(&sG[lpk * LD + m.i], vG);
-                retry |= (oF + vF < oF) | (oG + vG < oG) | (as < kFineStep && a > 0.f);
-                if (a > 0.f) atomicMin(&sZ[lpk], __float_as_uint(zc));
-            }
-            const float Ah = fminf(absorbance_at<J>(vals + l * LDV, zc, a * kLog2e, flags), 120.f);
-            const float w = ac * ex2(-Ah);
-            warp_accumulate(mine, lpk, make_float4(G.r[k] * w, G.g[k] * w, G.b[k] * w, w));
-        }
-    });
-    flush_bad(bad, p.err);
-    const bool scaled = __syncthreads_or(retry);
-    if (scaled) {  // rebuild frame t's bins with per-pixel scales
-        fill_zero(sF, (int)(2 * Layout<J>::plane(npx)));
-        __syncthreads();
-        count_pass<J>(p, T, sF);
-        bins_pass<J, true, false>(p, T, sF, sG, sZ, bad);
-        __syncthreads();
-    }
-    // per pixel: frame t's coefficients and total absorbance, the composite
-    float c[C], S = 0.f;
+    phase_resolve<J, false, DEF, true>(p, T, vals, accw, nullptr, bad);
+    __syncthreads();
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (gp >= 0) {
-        bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
-        acc = sum_warps(accw, npx, lp);
-    }
-    __syncthreads();  // accumulators read: their space stages the new coefficients
+    if (gp >= 0) acc = sum_warps(accw, npx, lp);
+    __syncthreads();  // bin values and accumulators consumed: the region takes frame t's bins
+    fill_zero(smem, (int)(2 * Layout<J>::plane(npx)));
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) sZ[i] = 0x7f800000u;
+    __syncthreads();
+    // frame t's build (fixed-scale bins, per-pixel scales as the fallback)
+    const bool scaled = phase_bins<J>(p, T, sF, sG, sZ, bad);
+    flush_bad(bad, p.err);
+    float c[C], S = 0.f;
+    if (gp >= 0) bins_to_coeffs<J>(sF + lp * LD, sG + lp * LD, c, S, scaled);
+    __syncthreads();  // every bin row read: the region stages the new coefficients
     CT *next = static_cast<CT *>(p.coeff);
     const bool stage = Staged<CT, C>::ok && next != nullptr;
     if (gp >= 0) {
@@ -352,13 +319,15 @@ cudaError_t launch_temporal_k(const Params &p, int ntiles, const void *coeff_pre
 template <int J, typename CT>
 cudaError_t launch_temporal_t(const Params &p, int ntiles, const void *coeff_prev, const float *zmin_prev,
                               cudaStream_t s) {
-    // registers budgeted for the blocks per SM that the shared memory allows
-    // (228 KB per SM, 1 KB of it reserved per block)
-    const int npx = p.g.tile_w * p.g.tile_h;
-    const bool three = 3 * (TemporalLayout<J>::total(npx) + 1024) <= 233472;
-    if (p.flags != kDefaultFlags) return launch_temporal_k<J, CT, false, 2>(p, ntiles, coeff_prev, zmin_prev, s);
-    return three ? launch_temporal_k<J, CT, true, 3>(p, ntiles, coeff_prev, zmin_prev, s)
-                 : launch_temporal_k<J, CT, true, 2>(p, ntiles, coeff_prev, zmin_prev, s);
+    // the fused kernel's shared memory and register budgets
+    const bool def = p.flags == kDefaultFlags;
+    if constexpr (J == 5) {
+        if (p.g.tile_w * p.g.tile_h <= kFourBlockTilePx)
+            return def ? launch_temporal_k<J, CT, true, 4>(p, ntiles, coeff_prev, zmin_prev, s)
+                       : launch_temporal_k<J, CT, false, 4>(p, ntiles, coeff_prev, zmin_prev, s);
+    }
+    return def ? launch_temporal_k<J, CT, true, MinBlocks<J>::value>(p, ntiles, coeff_prev, zmin_prev, s)
+               : launch_temporal_k<J, CT, false, MinBlocks<J>::value>(p, ntiles, coeff_prev, zmin_prev, s);
 }
 
 // Serving: one persistent launch works through the tile tasks of several
@@ -799,8 +768,6 @@ cudaError_t launch_fused_k(const Params &p, int ntiles, cudaStream_t s) {
     k_fused<J, CT, DEF, MB><<<ntiles, kThreads, bytes, s>>>(p);
     return cudaGetLastError();
 }
-// Tiles of at most this many pixels fit four fused blocks per SM at J = 5.
-constexpr int kFourBlockTilePx = 192;
 template <int J, typename CT> cudaError_t launch_fused_t(const Params &p, int ntiles, cudaStream_t s) {
     const bool def = p.flags == kDefaultFlags;
     if constexpr (J == 5) {

@@ -1052,7 +1052,9 @@ __device__ __forceinline__ bool phase_bins(const Params &p, const Tile &T, unsig
 // self-exclusion is -log2(1 - alpha), taken from the hardware log2 (its
 // absolute error, ~2^-22, moves one fragment's exponent only), except when
 // S needs the accurate step.
-template <int J, bool COUNT, bool DEF = false>
+// CLAMP: exponents held to [0, 120] (the single pass, whose weight offset
+// comes from another frame).
+template <int J, bool COUNT, bool DEF = false, bool CLAMP = false>
 __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, const float *A2,
                                               float4 *accw, float *sS,
                                               unsigned &bad) {
@@ -1076,7 +1078,8 @@ __device__ __forceinline__ void phase_resolve(const Params &p, const Tile &T, co
             } else {
                 a2 = -lg2(1.f - ac);
             }
-            const float Ah = absorbance_at<J>(A2 + l * LDV, clamp_depth(G.z[k]), a2, flags);
+            float Ah = absorbance_at<J>(A2 + l * LDV, clamp_depth(G.z[k]), a2, flags);
+            if constexpr (CLAMP) Ah = fminf(fmaxf(Ah, 0.f), 120.f);
             const float w = ac * ex2(-Ah);
             if (sS && lp >= 0) atomicAdd(&sS[l], a);
             warp_accumulate(mine, lp, make_float4(G.r[k] * w, G.g[k] * w, G.b[k] * w, w));

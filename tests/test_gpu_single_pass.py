@@ -112,15 +112,22 @@ def test_single_pass_arguments():
     np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4, rtol=0)
 
 
-def test_j6_with_256_pixel_tiles_is_refused():
-    """At J = 6 the single pass keeps two bins planes, the bin values and the
-    accumulators of a tile in shared memory: 247 KB for 256 pixels, beyond one
-    CTA's 227 KB, so the call is refused as unsupported (192-pixel tiles fit)."""
+def test_j6_with_256_pixel_tiles():
+    """At J = 6 with 256-pixel tiles the single pass takes the fused kernel's
+    shared memory (the resolve against frame t-1 and frame t's bins share one
+    region): an unchanged scene gives the fused call's composite."""
     fr = _frame(51, 6, (16, 16))
     g = fr.to(DEV)
     d = desc_of(fr)
-    prev = torch.zeros(fr.P, 64, device=DEV)
+    f = frags_of(g)
+    prev = torch.empty(fr.P, 64, device=DEV)
+    zprev = torch.empty(fr.P, device=DEV)
+    wt.wt_build(d, f, prev, zprev)
+    ref = torch.empty(fr.P, 4, device=DEV)
+    wt.wt_build_resolve(d, f, ref, bg=fr.bg)
     out = torch.empty(fr.P, 4, device=DEV)
-    with pytest.raises(wt.WtError) as e:
-        wt.wt_build_resolve_single_pass(d, frags_of(g), prev, out, bg=fr.bg)
-    assert e.value.status == 2
+    nxt = torch.full((fr.P, 64), float("nan"), device=DEV)
+    wt.wt_build_resolve_single_pass(d, f, prev, out, nxt, zprev, bg=fr.bg)
+    assert wt.wt_get_error() == 0
+    torch.testing.assert_close(out, ref, atol=2e-6, rtol=0)
+    assert torch.equal(nxt, prev)
