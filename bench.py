@@ -521,7 +521,7 @@ def run_wt(args):
         serving["workload"] = (f"{args.serve_requests} requests from a pool of {SERVE_POOL} frames (sizes "
                                "{360p,720p,1080p,4K}, Poisson(lambda ~ U[2,32]) fragments/pixel per frame, "
                                "alpha U[.02,.6]), J=4, 40 GB cap, step 8192 tiles; open: Poisson arrivals "
-                               "mean 2 ms; closed: 8 requests in flight; 3 interleaved repeats, median [min, max]")
+                               "mean 2 ms; closed: 8 requests in flight; 5 interleaved repeats, median [min, max]")
         torch.cuda.empty_cache()
     kernel_name = "k_fused" if args.path == "fused" else "k_build + k_resolve"
     path_name = ("wt_build_resolve (fused kernel)" if args.path == "fused"
@@ -909,9 +909,11 @@ def run_serving(args, dtype_name, pool, mode="open", outstanding=8):
             "makespan_s": makespan_s}
 
 
-def serving_legs(args, dtypes=("bf16", "se16", "f32"), repeats=3):
+def serving_legs(args, dtypes=("bf16", "se16", "f32"), repeats=5):
     """Both serving legs for each storage type, ``repeats`` runs each,
-    interleaved across the types; per figure the median and the [min, max]."""
+    interleaved across the types; per figure the median and the [min, max], and
+    per 16-bit type the number of repeats in which it beat FP32 (the runs of one
+    repeat follow each other, so they share the box's state)."""
     pool, lams = serve_pool(args)
     runs = {(m, d): [] for m in ("open", "closed") for d in dtypes}
     for _ in range(repeats):
@@ -930,6 +932,19 @@ def serving_legs(args, dtypes=("bf16", "se16", "f32"), repeats=3):
                 else [float(v[0]), float(v[-1])]
         leg[d]["requests"] = rs[0]["requests"]
         leg[d]["makespan_s"] = round(float(np.median([r["makespan_s"] for r in rs])), 4)
+    for m in ("open", "closed"):
+        base = runs.get((m, "f32"))
+        if not base:
+            continue
+        for d in dtypes:
+            if d == "f32":
+                continue
+            rs = runs[(m, d)]
+            res[m][d]["repeats_beating_f32"] = {
+                "p50": f"{sum(a['p50_ms'] < b['p50_ms'] for a, b in zip(rs, base))}/{len(rs)}",
+                "p99": f"{sum(a['p99_ms'] < b['p99_ms'] for a, b in zip(rs, base))}/{len(rs)}",
+                "fragments_per_s": f"{sum(a['fragments_per_s'] > b['fragments_per_s'] for a, b in zip(rs, base))}"
+                                   f"/{len(rs)}"}
     del pool
     return res
 
