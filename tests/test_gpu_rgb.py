@@ -85,14 +85,15 @@ def test_grey_opacity_equals_the_mono_method():
         assert torch.equal(coeff[c], mcoeff)
 
 
-@pytest.mark.parametrize("J", [2, 4, 5])
-def test_coloured_e5b9g9r9_storage(J):
+@pytest.mark.parametrize("J,tile", [(2, (128, 1)), (4, (128, 1)), (5, (128, 1)), (5, (64, 1)), (4, (8, 8)),
+                                    (2, (16, 4))])
+def test_coloured_e5b9g9r9_storage(J, tile):
     """E5B9G9R9 storage.  The words are byte work: they equal, bit for bit, the
     oracle's encoding of the FP32 coefficients that the RGB_F32 call stores
     (the channels' coefficients come from the same integer bins).  The
     composite equals the oracle's, computed wholly on the oracle side, at
     1e-4 wherever the oracle's words are the GPU's."""
-    fr = synth.uniform_frame(96, 40, 8.0, 40, J=J, seed=90 + J, tile_w=128, tile_h=1)
+    fr = synth.uniform_frame(96, 40, 8.0, 40, J=J, seed=90 + J, tile_w=tile[0], tile_h=tile[1])
     ac = _coloured(fr, 3)
     g = fr.to(DEV)
     d = desc_of(fr, J)
@@ -115,7 +116,8 @@ def test_coloured_e5b9g9r9_storage(J):
     assert (err <= bound).all()
 
 
-@pytest.mark.parametrize("J,tile", [(1, (64, 1)), (3, (7, 3)), (4, (128, 1)), (5, (192, 1)), (5, (16, 16))])
+@pytest.mark.parametrize("J,tile", [(1, (64, 1)), (3, (7, 3)), (4, (128, 1)), (5, (192, 1)), (5, (16, 16)),
+                                    (5, (64, 1)), (4, (8, 8)), (2, (16, 4))])
 def test_coloured_e5b9g9r9_composite_does_not_depend_on_storing_the_words(J, tile):
     """With a word buffer, channels r and g wait in it (16 bits each) and in
     out until the words are formed; without one, in shared memory.  The
@@ -147,6 +149,32 @@ def test_coloured_arguments():
         wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, g.alpha, g.alpha, out, None, 7, bg=fr.bg)
     with pytest.raises(wt.WtError):
         wt.wt_build_resolve_rgb(d, frags_of(g), g.alpha, None, g.alpha, out, None, wt.RGB_F32, bg=fr.bg)
+
+
+@pytest.mark.parametrize("tile", [(64, 1), (128, 1)])
+def test_coloured_e5b9g9r9_nan_opacity(tile):
+    """NaN opacities in one channel, E5B9G9R9 storage: counted once each; the
+    composite with the word buffer is the one without it bit for bit, and the
+    words are the oracle's encoding of the FP32 call's coefficients."""
+    fr = synth.uniform_frame(96, 40, 8.0, 40, J=5, seed=96, tile_w=tile[0], tile_h=tile[1])
+    ac = _coloured(fr, 7)
+    idx = np.random.default_rng(8).choice(fr.n, 25, replace=False)
+    ac[2][idx] = np.nan
+    g = fr.to(DEV)
+    d = desc_of(fr, 5)
+    a = [torch.from_numpy(x).to(DEV) for x in ac]
+    o1 = torch.full((fr.P, 4), float("nan"), device=DEV)
+    o2 = torch.full((fr.P, 4), float("nan"), device=DEV)
+    words = torch.full((fr.P, 32), -1, device=DEV, dtype=torch.int32)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, o1, words, wt.RGB_E5B9G9R9, bg=fr.bg)
+    assert wt.wt_get_error() == 25
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, o2, None, wt.RGB_E5B9G9R9, bg=fr.bg)
+    assert wt.wt_get_error() == 25
+    assert torch.equal(o1, o2)
+    c32 = torch.empty(3, fr.P, 32, device=DEV)
+    wt.wt_build_resolve_rgb(d, frags_of(g), *a, torch.empty(fr.P, 4, device=DEV), c32, wt.RGB_F32, bg=fr.bg)
+    assert wt.wt_get_error() == 25
+    assert np.array_equal(words.cpu().numpy().view(np.uint32), e5_words_of(list(c32.cpu().numpy()), 32))
 
 
 def test_coloured_nan_opacity_leaves_the_fragment_out_of_that_channel_only():
@@ -259,11 +287,11 @@ def test_coloured_short_rows(J, fmt):
 
 @pytest.mark.parametrize("flags", [wt.SELF_EXCLUDE | wt.INTERP_LINEAR, wt.SELF_EXCLUDE | wt.RESOLVE_NORMALIZED,
                                    wt.INTERP_LINEAR | wt.RESOLVE_NORMALIZED])
-@pytest.mark.parametrize("fmt", [0, 1])
-def test_coloured_reading_flags(flags, fmt):
+@pytest.mark.parametrize("fmt,tile", [(0, (128, 1)), (1, (128, 1)), (1, (64, 1))])
+def test_coloured_reading_flags(flags, fmt, tile):
     """The literal resolve, the staircase reconstruction and the fragment's own
     step kept, in both storage formats (the kernels built for arbitrary flags)."""
-    fr = synth.uniform_frame(96, 24, 6.0, 30, J=4, seed=160 + flags + 10 * fmt, tile_w=128, tile_h=1)
+    fr = synth.uniform_frame(96, 24, 6.0, 30, J=4, seed=160 + flags + 10 * fmt, tile_w=tile[0], tile_h=tile[1])
     ac = _coloured(fr, 17)
     g = fr.to(DEV)
     d = desc_of(fr, flags=flags)
