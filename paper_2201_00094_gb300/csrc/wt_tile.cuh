@@ -948,16 +948,17 @@ __device__ __forceinline__ void put_bins(float *row, float (&v)[1 << J], float z
 // fixed 2^27 (SCALED = false) or by per-pixel scales s_p (SCALED = true, after
 // count_pass).  Each fragment adds rint(s a f) and rint(s a (1-f)) to its bin
 // with integer atomics and its depth to the pixel's nearest depth with a
-// red.min.  Under the fixed scale the pass reports whether the tile needs the
-// per-pixel scales: a bin word wrapped (seen from the atomics' return values),
-// or a fragment's step is below 2^-7, where the fixed scale would round it by
-// more than 2^-21 of itself.  Invalid fragments are counted in bad when COUNT.
+// red.min.  Under the fixed scale the pass reports what the tile may need:
+// bit 0, a bin word wrapped (seen from the atomics' return values); bit 1, a
+// fragment's step is below 2^-7, where the fixed scale rounds it by more than
+// 2^-21 of itself (phase_bins then looks at the pixels' totals).  Invalid
+// fragments are counted in bad when COUNT.
 template <int J, bool SCALED, bool COUNT>
-__device__ __forceinline__ bool bins_pass(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
-                                          unsigned *sZ, unsigned &bad) {
+__device__ __forceinline__ unsigned bins_pass(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
+                                              unsigned *sZ, unsigned &bad) {
     constexpr int C = Shape<J>::C, LD = Shape<J>::LD, AMAX = Shape<J>::AMAX;
     constexpr float kFineStep = 1048576.f;  // 2^20: a step of 2^-7 under the fixed scale
-    bool retry = false;
+    bool wrap = false, fine = false;
     for_each_group<kWithZ>(T.s, T.e, p, [&](auto &G) {
         constexpr int N = std::remove_reference_t<decltype(G)>::size;
         int lp[N];
@@ -986,11 +987,14 @@ __device__ __forceinline__ bool bins_pass(const Params &p, const Tile &T, unsign
             const unsigned vF = __float2uint_rn(as * f), vG = __float2uint_rn(as * (1.f - f));
             const unsigned oF = atomicAdd(&sF[lp[k] * LD + m.i], vF);
             const unsigned oG = atomicAdd(&sG[lp[k] * LD + m.i], vG);
-            if (!SCALED) retry |= (oF + vF < oF) | (oG + vG < oG) | (as < kFineStep && a > 0.f);
+            if (!SCALED) {
+                wrap |= (oF + vF < oF) | (oG + vG < oG);
+                fine |= as < kFineStep && a > 0.f;
+            }
             if (a > 0.f) atomicMin(&sZ[lp[k]], __float_as_uint(zc));
         }
     });
-    return retry;
+    return (wrap ? 1u : 0u) | (fine ? 2u : 0u);
 }
 
 // Counting pass of the fallback: each pixel's fragment count c_p and largest
@@ -1026,16 +1030,30 @@ __device__ __forceinline__ void count_pass(const Params &p, const Tile &T, unsig
 
 // Step 2 accumulation of one tile into its F and G bins (zeroed by the
 // caller, nearest-depth words set to +inf).  The fixed-scale pass is tried
-// first; if it reports a wrapped bin or a step too small for the fixed scale,
-// the bins are cleared and rebuilt with per-pixel scales.  Returns whether the
+// first; if it reports a wrapped bin, or a step below 2^-7 in a pixel whose
+// total step is below 2^-7 too, the bins are cleared and rebuilt with
+// per-pixel scales.  (The fixed scale rounds every step by at most 2^-28
+// absolute, so a pixel whose total is at least 2^-7 keeps its coefficients
+// within 2^-21 of that total whatever its steps.)  Returns whether the
 // per-pixel scales were used (the INV word of each pixel's F row then holds
 // 1 / s_p).  Ends with a barrier.
 template <int J>
 __device__ __forceinline__ bool phase_bins(const Params &p, const Tile &T, unsigned *sF, unsigned *sG,
                                            unsigned *sZ, unsigned &bad) {
-    const bool retry = bins_pass<J, false, true>(p, T, sF, sG, sZ, bad);
-    if (!__syncthreads_or(retry)) return false;
+    const unsigned why = bins_pass<J, false, true>(p, T, sF, sG, sZ, bad);
+    if (!__syncthreads_or(why)) return false;
     const int npx = p.g.tile_w * p.g.tile_h;
+    if (!__syncthreads_or(why & 1u)) {  // only fine steps: do the pixels' totals resolve them?
+        constexpr int C = Shape<J>::C, LD = Shape<J>::LD;
+        bool small = false;
+        for (int lp = threadIdx.x; lp < npx; lp += blockDim.x) {
+            float tot = 0.f;  // sum of the bins in fixed-point units (a relative error of 2^-18 does not matter)
+#pragma unroll 8
+            for (int m = 0; m < C; ++m) tot += (float)sF[lp * LD + m] + (float)sG[lp * LD + m];
+            small |= tot > 0.f && tot < 1048576.f;  // total step below 2^-7
+        }
+        if (!__syncthreads_or(small)) return false;
+    }
     fill_zero(sF, (int)(2 * align16((size_t)npx * Shape<J>::LD * 4)));  // F and G planes are adjacent
     __syncthreads();
     count_pass<J>(p, T, sF);

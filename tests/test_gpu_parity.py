@@ -307,6 +307,23 @@ def test_permutation_invariance_on_gpu():
     np.testing.assert_allclose(g1["out"], g2["out"], atol=2e-5)
 
 
+@pytest.mark.parametrize("J,lam,alpha_range", [(4, 2.0, (1e-4, 0.02)), (5, 40.0, (1e-3, 6e-3)),
+                                               (3, 6.0, (1e-6, 0.3))])
+def test_fine_steps_keep_their_precision(J, lam, alpha_range):
+    """Steps below 2^-7: pixels whose total step is below 2^-7 too are rebuilt
+    with per-pixel scales, the others keep the fixed scale (it rounds a step by
+    at most 2^-28); either way the coefficients stay within the derived bound
+    and the composite within 1e-4, on every path."""
+    fr = synth.uniform_frame(67, 29, lam, 200, alpha_range=alpha_range, J=J, seed=int(lam) + J,
+                             tile_w=192, tile_h=1)
+    r = oracle_run(fr)
+    for kw in (dict(), dict(fused=True), dict(totals=True)):
+        g = gpu_run(fr, **kw)
+        assert g["bad"] == 0
+        assert (np.abs(g["coeff"] - r["coeff"]) <= coeff_tol(fr)).all(), kw
+        np.testing.assert_allclose(g["out"], r["out"], atol=1e-4, rtol=0, err_msg=str(kw))
+
+
 def test_deep_pixel_underflow_safe():
     """900 fragments in one depth bin: the nearest sees A ~ 400, every FP32
     exp(-A) underflows; the offset m_p keeps the normalised colour right."""
