@@ -807,24 +807,33 @@ def measure_e2e(wt, fr, desc, coeff, out, stream, K, world, frags_all, nchunks=8
         step_e2e()
     torch.cuda.synchronize()
     assert wt.wt_get_error(stream) == 0
+    # the host link switches between a fast and a slow rate from one second to
+    # the next, so the step is timed in three rounds, each beside a round of
+    # the copies alone; the median round is reported, with the spread
     Ke = max(3, min(K, 10))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    a.record(stream)
-    for _ in range(Ke):
-        step_e2e()
-    b.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(a.elapsed_time(b) / Ke, world)
-    a.record(stream)
+    rounds = []
     for _ in range(3):
-        copies_only()
-    b.record(stream)
-    torch.cuda.synchronize()
-    link_ms = a.elapsed_time(b) / 3
+        barrier(world)
+        a.record(stream)
+        for _ in range(Ke):
+            step_e2e()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / Ke, world)
+        a.record(stream)
+        for _ in range(3):
+            copies_only()
+        b.record(stream)
+        torch.cuda.synchronize()
+        rounds.append((e2e_ms, a.elapsed_time(b) / 3))
+    rounds.sort()
+    e2e_ms, link_ms = rounds[1]
     return {"value": frags_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "chunks": len(chunks),
-            "h2d_alone_ms": round(link_ms, 3), "h2d_alone_GBps": round(h2d / (link_ms / 1e3) / 1e9, 1)}
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
+            "ms_per_step_rounds": [round(r[0], 3) for r in rounds], "chunks": len(chunks),
+            "h2d_alone_ms": round(link_ms, 3), "h2d_alone_GBps": round(h2d / (link_ms / 1e3) / 1e9, 1),
+            "h2d_alone_ms_rounds": [round(r[1], 3) for r in rounds]}
 
 
 # ---------------------------------------------------------------- serving
