@@ -9,7 +9,7 @@ the background.  Default workload: the 4K heavy-smoke frame
 J = 5), FP32 coefficient storage, fused kernel wt_build_resolve.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-(the reference arm of this build) on bounded samples of the same workload.
+(the reference arm) on bounded samples of the same workload.
 """
 from __future__ import annotations
 
