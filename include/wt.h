@@ -483,7 +483,8 @@ typedef struct wt_particles {
 } wt_particles;
 
 /* Bytes of device workspace of wt_raster_count / wt_raster_emit for n
- * particles: n + 1 int64 offsets. */
+ * particles (or triangles): n + 1 int64 offsets, then ceil(n / 4096) int64
+ * partial sums of the count pass's scan. */
 size_t wt_raster_workspace_bytes(int64_t n_particles);
 
 /*

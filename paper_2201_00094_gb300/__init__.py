@@ -502,7 +502,7 @@ def wt_raster(desc: WtDesc, cx: torch.Tensor, cy: torch.Tensor, radius: torch.Te
     pt = WtParticles(n, _dev(cx, "cx", f32), _dev(cy, "cy", f32), _dev(radius, "radius", f32),
                      _dev(z, "z", f32), _dev(alpha, "alpha", f32), _dev(r, "r", f32), _dev(g, "g", f32),
                      _dev(b, "b", f32))
-    ws = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(int(lib().wt_raster_workspace_bytes(n)) // 8, dtype=torch.int64, device=dev)
     _call("wt_raster_count", ctypes.byref(desc), ctypes.byref(pt), _dev(ws, "workspace", (torch.int64,)),
           _stream(stream))
     total = int(ws[n].item()) if capacity is None else None
@@ -533,7 +533,7 @@ def wt_raster_tri(desc: WtDesc, x: torch.Tensor, y: torch.Tensor, z: torch.Tenso
         raise ValueError("x, y and z hold three vertices per triangle")
     tr = WtTriangles(n, _dev(x, "x", f32), _dev(y, "y", f32), _dev(z, "z", f32), _dev(alpha, "alpha", f32),
                      _dev(r, "r", f32), _dev(g, "g", f32), _dev(b, "b", f32))
-    ws = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(int(lib().wt_raster_workspace_bytes(n)) // 8, dtype=torch.int64, device=dev)
     _call("wt_raster_tri_count", ctypes.byref(desc), ctypes.byref(tr), _dev(ws, "workspace", (torch.int64,)),
           _stream(stream))
     total = int(ws[n].item()) if capacity is None else None

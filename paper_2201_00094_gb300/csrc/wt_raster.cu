@@ -202,29 +202,90 @@ __global__ void __launch_bounds__(256) k_raster_count(RasterGeom g, typename Pri
     }
 }
 
-// One block: exclusive scan of n counts in place into offsets[0 .. n], each
-// thread scanning a contiguous chunk.
-__global__ void __launch_bounds__(1024) k_raster_scan(int64_t n, int64_t *__restrict__ offsets) {
-    __shared__ long long part[1024];
-    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t b = threadIdx.x * per, e = min(n, b + per);
-    long long sum = 0;
-    for (int64_t t = b; t < e; ++t) sum += offsets[t];
-    part[threadIdx.x] = sum;
+// Exclusive scan of n counts in place into offsets[0 .. n] (offsets[n] = the
+// total), in three launches: each block scans a chunk of kScanChunk counts
+// and leaves the chunk's total in part[]; one block scans the totals; every
+// chunk adds its offset.
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanChunk = kScanThreads * kScanItems;
+
+// Block-wide exclusive scan of one value per thread; *total gets the sum.
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *total) {
+    __shared__ long long warp_sum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[w] = x;
     __syncthreads();
-    for (int dd = 1; dd < (int)blockDim.x; dd <<= 1) {
-        const long long v = threadIdx.x >= (unsigned)dd ? part[threadIdx.x - dd] : 0ll;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (w == 0) {
+        long long t = lane < kScanThreads / 32 ? warp_sum[lane] : 0ll;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kScanThreads / 32) warp_sum[lane] = t;  // inclusive over warps
     }
-    long long run = part[threadIdx.x] - sum;
-    for (int64_t t = b; t < e; ++t) {
-        const long long c = offsets[t];
-        offsets[t] = run;
-        run += c;
+    __syncthreads();
+    const long long before = w > 0 ? warp_sum[w - 1] : 0ll;
+    *total = warp_sum[kScanThreads / 32 - 1];
+    __syncthreads();  // warp_sum is reused by the next call
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(int64_t n, int64_t *__restrict__ v,
+                                                              long long *__restrict__ part) {
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    long long x[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        x[k] = base + k < n ? v[base + k] : 0ll;
+        s += x[k];
     }
-    if (threadIdx.x == blockDim.x - 1) offsets[n] = part[threadIdx.x];
+    long long total;
+    long long run = block_exclusive_scan(s, &total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) v[base + k] = run;
+        run += x[k];
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the nb chunk totals in place, rounds of
+// kScanThreads; v[n] = the grand total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(int64_t nb, long long *__restrict__ part, int64_t n,
+                                                             int64_t *__restrict__ v) {
+    long long carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        const long long x = i < nb ? part[i] : 0ll;
+        long long total;
+        const long long e = block_exclusive_scan(x, &total);
+        if (i < nb) part[i] = carry + e;
+        carry += total;
+    }
+    if (threadIdx.x == 0) v[n] = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(int64_t n, int64_t *__restrict__ v,
+                                                  const long long *__restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] += part[i / kScanChunk];
+}
+
+// The scan's chunk totals behind the n + 1 offsets.
+__host__ __device__ constexpr int64_t scan_parts(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
+
+void scan_offsets(int64_t n, int64_t *offsets, cudaStream_t s) {
+    long long *part = reinterpret_cast<long long *>(offsets + n + 1);
+    const int64_t nb = scan_parts(n);
+    if (nb > 0) k_scan_chunks<<<(unsigned)nb, kScanThreads, 0, s>>>(n, offsets, part);
+    k_scan_parts<<<1, kScanThreads, 0, s>>>(nb, part, n, offsets);
+    if (nb > 1) k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, offsets, part);
 }
 
 template <class Prim>
@@ -319,7 +380,7 @@ wt_status count_t(const wt_desc *desc, const typename Prim::Input &in, void *wor
     int64_t *offsets = static_cast<int64_t *>(workspace);
     const RasterGeom g{desc->width, desc->height};
     if (in.n > 0) k_raster_count<Prim><<<warps_grid(in.n), 256, 0, s>>>(g, in, offsets);
-    k_raster_scan<<<1, 1024, 0, s>>>(in.n, offsets);
+    scan_offsets(in.n, offsets, s);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
@@ -346,7 +407,7 @@ wt_status emit_t(const wt_desc *desc, const typename Prim::Input &in, const void
 using namespace wt;
 
 extern "C" size_t wt_raster_workspace_bytes(int64_t n_particles) {
-    return n_particles < 0 ? 0 : (size_t)(n_particles + 1) * 8;
+    return n_particles < 0 ? 0 : (size_t)(n_particles + 1 + scan_parts(n_particles)) * 8;
 }
 
 extern "C" wt_status wt_raster_count(const wt_desc *desc, const wt_particles *particles, void *workspace,
