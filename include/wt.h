@@ -273,9 +273,11 @@ wt_status wt_build_resolve_tiles(const wt_desc *desc, const wt_frags *frags, int
 /*
  * wt_build_resolve_single_pass -- the single-pass variant the paper proposes
  * as future work (§4): frame t's fragments are resolved against frame t-1's
- * coefficients, which are complete before the pass starts, while the same
- * pass builds frame t's coefficients for the next frame -- one pass over the
- * fragments instead of two.  With an unchanged scene the composite equals
+ * coefficients, which are complete before the call starts, and frame t's
+ * coefficients are built for the next frame; nothing waits for this frame's
+ * build.  Per screen tile the resolve comes first and the build second, each
+ * fragment read from device memory once (the second read of a tile's range
+ * is served by L2).  With an unchanged scene the composite equals
  * wt_build_resolve's; under motion the visibility is the previous frame's
  * (the paper's approximation; nothing is reprojected).
  *   coeff_prev [P * C] frame t-1's coefficients in coeff_dtype (the coeff

@@ -217,20 +217,19 @@ __global__ void __launch_bounds__(kThreads, MB) k_fused(Params p) {
     fused_tile<J, CT, DEF>(p, p.tile0 + (int)blockIdx.x, smem);
 }
 
-// Single pass over a frame's fragments with the previous frame's
-// coefficients (the paper's proposed variant, §4): every fragment of frame t
-// is resolved against frame t-1's coefficients -- already complete, so the
-// resolve needs no second pass -- while the same pass builds frame t's
-// coefficients for the next frame.  With a static scene the result equals the
+// The single-pass variant the paper proposes (§4): every fragment of frame t
+// is resolved against frame t-1's coefficients, which are complete before the
+// frame starts, and frame t's coefficients are built for the next frame; no
+// pass waits for the build.  With a static scene the result equals the
 // two-pass method's; with motion it is the paper's approximation (visibility
 // from the previous frame).  The weight offset comes from frame t-1's near
 // bound; exponents are clamped to [0, 120] so that fragments nearer or much
 // farther than anything in frame t-1 keep finite, non-zero weights.
-// Shared memory of the single pass: that of the fused kernel.  Within a
-// tile, the resolve against frame t-1 (its bin values and the warps'
-// accumulators) comes first and the build of frame t (F and G bins) second,
-// over the tile's own fragment range both times (the second read hits L2), so
-// the two share one region.
+// Within a tile, the resolve against frame t-1 (its bin values and the
+// warps' accumulators) comes first and the build of frame t (F and G bins)
+// second, over the tile's own fragment range both times: each fragment comes
+// from HBM once (the second read hits L2), and the two phases share the fused
+// kernel's shared-memory region.
 template <int J> struct TemporalLayout {
     static constexpr size_t total(int npx) { return Layout<J>::fused(npx); }
 };
