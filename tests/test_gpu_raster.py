@@ -46,6 +46,27 @@ def test_raster_matches_the_oracle_bit_for_bit():
         np.testing.assert_array_equal(out[k].cpu().numpy(), ref[k])
 
 
+@pytest.mark.parametrize("n", [4096, 4097, 13000])
+def test_raster_scan_across_chunks_matches_the_oracle(n):
+    """The counts are scanned in chunks of 4096 particles (a scan per chunk,
+    then of the chunk totals): one chunk exactly, one particle beyond it, and
+    several chunks give the oracle's stream bit for bit."""
+    W, H = 128, 96
+    p = _particles(n, W, H, 7 + n)
+    p["radius"] = (p["radius"] * 0.3).astype(np.float32)  # small discs: a few pixels each
+    p["radius"][:3] = [0.0, -1.0, 2.0]
+    d = wt.make_desc(W, H, 4)
+    g = _dev(p)
+    out = wt.wt_raster(d, g["cx"], g["cy"], g["radius"], g["z"], g["alpha"], g["r"], g["g"], g["b"])
+    assert wt.wt_get_error() == 0
+    ref = oracle.raster_particles(W, H, p["cx"], p["cy"], p["radius"], p["z"], p["alpha"], p["r"], p["g"],
+                                  p["b"])
+    assert int(out["total"]) == len(ref["pixel"]) > 0
+    np.testing.assert_array_equal(out["pixel"].cpu().numpy().astype(np.int64), ref["pixel"])
+    for k in ("z", "alpha", "r", "g", "b"):
+        np.testing.assert_array_equal(out[k].cpu().numpy(), ref[k])
+
+
 def test_raster_capacity_drops_and_counts():
     W, H = 64, 48
     p = _particles(300, W, H, 2)
