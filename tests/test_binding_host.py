@@ -72,3 +72,23 @@ def test_static_batch_checks_every_frame_before_the_call():
     short._tile_offsets = 4
     with pytest.raises(ValueError, match="4 tiles"):
         wt.wt_build_resolve_batch_static([d, d], [f, short], [ok, ok])
+
+
+def test_totals_and_pixel_sums_are_checked_before_the_call():
+    """The optional per-pixel totals of wt_build / wt_resolve and the pixel sums
+    of wt_build_resolve / wt_backward are bare pointers too: undersized ones are
+    refused before anything reaches the library."""
+    d = wt.make_desc(7, 5, 3)  # P = 35, C = 8
+    P = 35
+    f = wt.WtFrags(0, None, None, None, None, None, None, None)
+    coeff, out = torch.empty(P, 8), torch.empty(P, 4)
+    with pytest.raises(ValueError, match="total"):
+        wt.wt_build(d, f, coeff, total=torch.empty(P - 1))
+    with pytest.raises(ValueError, match="total"):
+        wt.wt_resolve(d, f, coeff, None, torch.empty(P, 5), total=torch.empty(P - 1))
+    with pytest.raises(ValueError, match="total"):
+        wt.wt_resolve_composite(d, f, coeff, None, out, total=torch.empty(P - 1))
+    with pytest.raises(ValueError, match="accum"):
+        wt.wt_build_resolve(d, f, out, accum=torch.empty(P, 4))
+    with pytest.raises(ValueError, match="accum"):
+        wt.wt_backward(d, f, torch.empty(P, 4), torch.empty(0), torch.empty(3, 0), accum=torch.empty(P - 1, 5))
