@@ -494,9 +494,10 @@ size_t wt_raster_workspace_bytes(int64_t n_particles);
  * fragment on every pixel of the image whose centre (x + 1/2, y + 1/2) is at
  * squared distance d2 < radius^2 from (cx, cy), with opacity
  * alpha * (1 - d2 / radius^2) (every operation rounded separately in FP32, the
- * reciprocal of radius^2 taken once).  Writes into workspace (8-byte aligned)
- * the exclusive offsets of each particle's fragments and, at [n], the total:
- * read it back to size the fragment arrays of wt_raster_emit.  Particles with
+ * reciprocal of radius^2 taken once).  Writes into workspace (8-byte aligned,
+ * wt_raster_workspace_bytes(n) bytes) the exclusive offsets of each particle's
+ * fragments and, at [n], the total: read it back to size the fragment arrays
+ * of wt_raster_emit; the bytes behind [n] are the scan's scratch.  Particles with
  * a non-positive or NaN radius, or a NaN centre, give no fragments.
  */
 wt_status wt_raster_count(const wt_desc *desc, const wt_particles *particles, void *workspace,
