@@ -43,6 +43,27 @@ def test_exports_every_declared_symbol(L):
         getattr(L, name)
 
 
+def test_binding_passes_as_many_arguments_as_the_header_declares(L):
+    """Every entry point the binding calls takes, in include/wt.h, exactly the
+    number of arguments the binding passes (a call with one too few or too
+    many would hand the library a shifted pointer)."""
+    txt = ""
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt += open(os.path.join(ROOT, "include", h)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    checked = 0
+    for name, params in re.findall(r"\b(wt_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", txt):
+        params = params.strip()
+        count = 0 if params in ("", "void") else params.count(",") + 1
+        argtypes = getattr(getattr(L, name), "argtypes", None)
+        if argtypes is None:  # not called through the binding
+            continue
+        assert len(argtypes) == count, (name, count, len(argtypes))
+        checked += 1
+    assert checked >= 30
+
+
 def test_struct_layout_matches_header():
     assert ctypes.sizeof(wt.WtDesc) == 32
     assert ctypes.sizeof(wt.WtFrags) == 64
